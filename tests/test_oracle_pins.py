@@ -1,0 +1,409 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, invariants, published test vectors, library routines, exact
+statistics), never against the oracle itself.
+
+The paper prints no worked numeric example (its only numbers are dataset-level
+image quality), so the pins are:
+  * SH basis: orthonormality on the sphere by Gauss-Legendre quadrature.
+  * Philox4x32-10: the published known-answer vectors (tests/golden).
+  * Projection: hand-derived closed forms of the EWA covariance for isotropic and
+    axis-aligned Gaussians, on and off the optical axis, with a rotated camera.
+  * Compositing: closed forms for one and two Gaussians on the optical axis.
+  * Scoring: S = 1 for one Gaussian and for the per-scene resolution; 1 <= S <=
+    min(N, |Q'|) per pixel; S = N on the isolation scene of Thm. 1; the mediant
+    chain s_channel >= s_pixel >= s_tile >= s_image >= s_scene; 1x1 tiles = pixels.
+  * Sampling: inverse-CDF draws equal numpy.searchsorted; the uniform map equals
+    exact integer arithmetic; frequencies follow p (chi-square); E[w_i] = 1;
+    Thm. 2's failure rate is at most delta.
+  * Weighted render: w = 1 reproduces the full render bit for bit; the transfer
+    sandwich of Lemma "transfer" holds for every pixel.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Opts
+from paper_2607_02721_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+C0 = 1.0 / (2.0 * math.sqrt(math.pi))
+
+
+def one_scene(means, log_scales, rgb, opac_logit, quats=None):
+    """Scene of explicit Gaussians with SH degree 0 colours."""
+    means = np.asarray(means, dtype=np.float32).reshape(-1, 3).T.copy()
+    n = means.shape[1]
+    ls = np.asarray(log_scales, dtype=np.float32).reshape(n, 3).T.copy()
+    if quats is None:
+        quats = np.tile(np.array([[1.0], [0.0], [0.0], [0.0]], dtype=np.float32), (1, n))
+    else:
+        quats = np.asarray(quats, dtype=np.float32).reshape(n, 4).T.copy()
+    dc = ((np.asarray(rgb, dtype=np.float64).reshape(n, 3) - 0.5) / C0).T.reshape(1, 3, n)
+    return synth.Scene(means, ls, quats, np.asarray(opac_logit, dtype=np.float32).reshape(n), dc.astype(np.float32))
+
+
+def axis_camera(W=33, H=33, f=40.0, R=None, t=(0.0, 0.0, 0.0)):
+    R = np.eye(3) if R is None else np.asarray(R)
+    return synth.make_camera(R, np.asarray(t), W, H, fx=f)
+
+
+def sigmoid(x):
+    return 1.0 / (1.0 + math.exp(-float(np.float32(x))))
+
+
+def f32(x):
+    """The value a float32 input actually carries."""
+    return float(np.float32(x))
+
+
+def eff_scale(sig):
+    """Scale carried by the float32 log-scale input."""
+    return math.exp(f32(math.log(sig)))
+
+
+# ---------------------------------------------------------------- SH, Philox
+
+def test_sh_basis_is_orthonormal():
+    x, wx = np.polynomial.legendre.leggauss(16)  # exact for polynomials in cos(theta) up to degree 31
+    nphi = 32
+    phis = (np.arange(nphi) + 0.5) * 2 * math.pi / nphi
+    G = np.zeros((16, 16))
+    for ct, wt in zip(x, wx):
+        st = math.sqrt(1 - ct * ct)
+        for ph in phis:
+            Y = oracle.sh_basis(3, [st * math.cos(ph), st * math.sin(ph), ct])
+            G += np.outer(Y, Y) * wt * (2 * math.pi / nphi)
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-12)
+    # the lower degrees are prefixes of the degree-3 basis
+    d = np.array([0.3, -0.5, 0.81])
+    d /= np.linalg.norm(d)
+    Y3 = oracle.sh_basis(3, d)
+    for deg in range(3):
+        np.testing.assert_array_equal(oracle.sh_basis(deg, d), Y3[: (deg + 1) ** 2])
+
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+# ---------------------------------------------------------------- projection
+
+def test_projection_isotropic_on_axis_closed_form():
+    sig, z, f, dil = 0.05, 2.0, 40.0, 0.3
+    sc = one_scene([0, 0, z], [math.log(sig)] * 3, [0.2, 0.5, 0.9], 0.3)
+    P = oracle.project(sc, axis_camera(f=f))[0]
+    sig = eff_scale(sig)
+    var = (f * sig / z) ** 2 + dil
+    assert P[0] == 1
+    np.testing.assert_allclose(P[1:3], [16.0, 16.0], atol=1e-12)
+    np.testing.assert_allclose(P[6:9], [var, 0.0, var], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(P[3:6], [1 / var, 0.0, 1 / var], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(P[9], z)
+    np.testing.assert_allclose(P[10], sigmoid(0.3), rtol=1e-7)
+    np.testing.assert_allclose(P[11:14], [0.2, 0.5, 0.9], atol=1e-6)
+
+
+def test_projection_off_axis_jacobian_closed_form():
+    # Sigma = sig^2 I, J = [[f/z, 0, -f x/z^2], [0, f/z, -f y/z^2]]
+    sig, f, dil = 0.07, 50.0, 0.3
+    x0, y0, z = 0.3, -0.2, 2.5
+    sc = one_scene([x0, y0, z], [math.log(sig)] * 3, [0.5, 0.5, 0.5], 0.0)
+    P = oracle.project(sc, axis_camera(W=64, H=48, f=f))[0]
+    sig, x0, y0 = eff_scale(sig), f32(x0), f32(y0)
+    xx = sig * sig * f * f / z / z * (1 + x0 * x0 / z / z) + dil
+    yy = sig * sig * f * f / z / z * (1 + y0 * y0 / z / z) + dil
+    xy = sig * sig * f * f * x0 * y0 / z ** 4
+    np.testing.assert_allclose(P[6:9], [xx, xy, yy], rtol=1e-6)
+    np.testing.assert_allclose(P[1:3], [f * x0 / z + 31.5, f * y0 / z + 23.5], rtol=1e-7)
+
+
+def test_projection_clamps_jacobian_outside_fov():
+    # far off-axis: x/z is clamped to 1.3 * (W/2)/f inside J only
+    sig, f, dil, W = 0.05, 20.0, 0.3, 32
+    x0, z = 3.0, 2.0
+    sc = one_scene([x0, 0.0, z], [math.log(sig)] * 3, [0.5, 0.5, 0.5], 0.0)
+    P = oracle.project(sc, axis_camera(W=W, H=W, f=f))[0]
+    sig = eff_scale(sig)
+    lim = 1.3 * 0.5 * W / f
+    assert x0 / z > lim
+    xx = sig * sig * f * f / z / z * (1 + lim * lim) + dil
+    np.testing.assert_allclose(P[6], xx, rtol=1e-6)
+    np.testing.assert_allclose(P[1], f * x0 / z + (W - 1) / 2, rtol=1e-7)
+
+
+def test_projection_quaternion_and_camera_rotation():
+    # 90 degrees about z maps the local x axis to world y: Sigma = diag(sy^2, sx^2, sz^2)
+    sx, sy, sz, f, dil, z = 0.02, 0.09, 0.05, 40.0, 0.3, 3.0
+    q = [math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4)]
+    sc = one_scene([0, 0, z], [math.log(sx), math.log(sy), math.log(sz)], [0.5] * 3, 0.0, quats=q)
+    P = oracle.project(sc, axis_camera(f=f))[0]
+    sx, sy, sz = eff_scale(sx), eff_scale(sy), eff_scale(sz)
+    k = (f / z) ** 2
+    np.testing.assert_allclose(P[6:9], [k * sy * sy + dil, 0.0, k * sx * sx + dil], rtol=1e-6, atol=1e-9)
+    # a camera rotated by 90 degrees about world y, placed so the Gaussian is on its axis
+    Ry = np.array([[0.0, 0.0, -1.0], [0.0, 1.0, 0.0], [1.0, 0.0, 0.0]])  # world x -> camera z
+    mu = np.array([z, 0.0, 0.0])
+    cam = axis_camera(f=f, R=Ry, t=(0.0, 0.0, 0.0))
+    sc2 = one_scene(mu, [math.log(sx), math.log(sy), math.log(sz)], [0.5] * 3, 0.0)  # effective values
+    P2 = oracle.project(sc2, cam)[0]
+    # camera x = -world z, camera y = world y: variances (sz^2, sy^2)
+    np.testing.assert_allclose(P2[6:9], [k * sz * sz + dil, 0.0, k * sy * sy + dil], rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(P2[9], z)
+
+
+# ---------------------------------------------------------------- compositing
+
+def test_single_gaussian_closed_form_render_and_score():
+    sig, z, f, dil, lg = 0.04, 2.0, 40.0, 0.3, 1.2
+    rgb = np.array([0.8, 0.3, 0.6])
+    sc = one_scene([0, 0, z], [math.log(sig)] * 3, rgb, lg)
+    rgb = C0 * sc.sh[0, :, 0].astype(np.float64) + 0.5
+    cam = axis_camera(f=f)
+    out = oracle.render(sc, cam, Opts())
+    sig = eff_scale(sig)
+    var = (f * sig / z) ** 2 + dil
+    yy, xx = np.mgrid[0:33, 0:33]
+    d2 = ((xx - 16.0) ** 2 + (yy - 16.0) ** 2) / var
+    rho = np.minimum(0.99, sigmoid(lg) * np.exp(-0.5 * d2))
+    rho[(d2 > 9) | (rho < 1 / 255)] = 0.0
+    np.testing.assert_allclose(out["rgb"], rgb[None, None, :] * rho[..., None], atol=1e-6)
+    np.testing.assert_allclose(out["T"], 1 - rho, atol=1e-7)
+    r = oracle.score(sc, cam[None], Opts())
+    np.testing.assert_allclose(r["s"], [1.0], rtol=1e-12)
+    assert r["queries"] == int((rho > 0).sum())
+    np.testing.assert_allclose(r["S"], 1.0, rtol=1e-12)
+
+
+def test_two_gaussians_on_axis_closed_form():
+    f, dil = 40.0, 0.3
+    s1, s2, z1, z2, l1, l2 = 0.03, 0.06, 1.5, 2.5, 0.4, -0.2
+    c1, c2 = np.array([0.9, 0.1, 0.2]), np.array([0.1, 0.7, 0.6])
+    sc = one_scene([[0, 0, z2], [0, 0, z1]], [[math.log(s2)] * 3, [math.log(s1)] * 3], [c2, c1], [l2, l1])
+    c2, c1 = (C0 * sc.sh[0, :, 0].astype(np.float64) + 0.5), (C0 * sc.sh[0, :, 1].astype(np.float64) + 0.5)
+    cam = axis_camera(f=f)
+    yy, xx = np.mgrid[0:33, 0:33]
+    r2 = (xx - 16.0) ** 2 + (yy - 16.0) ** 2
+
+    def rho(s, z, lg):
+        v = (f * eff_scale(s) / z) ** 2 + dil
+        r = np.minimum(0.99, sigmoid(lg) * np.exp(-0.5 * r2 / v))
+        r[(r2 / v > 9) | (r < 1 / 255)] = 0.0
+        return r
+
+    p1, p2 = rho(s1, z1, l1), rho(s2, z2, l2)  # Gaussian index 1 is in front
+    A = c1[None, None] * p1[..., None] + c2[None, None] * (p2 * (1 - p1))[..., None]
+    out = oracle.render(sc, cam, Opts())
+    np.testing.assert_allclose(out["rgb"], A, atol=1e-12)
+    np.testing.assert_allclose(out["T"], (1 - p1) * (1 - p2), atol=1e-12)
+    a1 = c1.sum() * p1
+    a2 = c2.sum() * p2 * (1 - p1)
+    At = a1 + a2
+    m = At > 0
+    s_expect = [np.max(a2[m] / At[m]), np.max(a1[m] / At[m])]
+    r = oracle.score(sc, cam[None], Opts())
+    np.testing.assert_allclose(r["s"], s_expect, rtol=1e-12)
+    # luminance objective of the per-pixel resolution
+    wl = (0.299, 0.587, 0.114)
+    a1l, a2l = np.dot(c1, wl) * p1, np.dot(c2, wl) * p2 * (1 - p1)
+    rl = oracle.score(sc, cam[None], Opts(obj_w=wl))
+    np.testing.assert_allclose(rl["s"], [np.max(a2l[m] / (a1l + a2l)[m]), np.max(a1l[m] / (a1l + a2l)[m])], rtol=1e-12)
+
+
+def test_early_termination_and_order_invariants():
+    sc = synth.uniform_cube_scene(300, seed=3)
+    cam = synth.cube_corner_cameras(3.0, 40, 40)[0]
+    o = Opts()
+    out = oracle.render(sc, cam, o)
+    assert np.all(out["T"] >= o.t_min)
+    P = oracle.project(sc, cam, o)
+    for (px, py) in [(20, 20), (10, 25), (31, 7), (0, 0)]:
+        t = oracle.pixel_terms(sc, cam, px, py, o)
+        if len(t["gid"]) == 0:
+            continue
+        d = P[t["gid"], 9]
+        assert np.all(np.diff(d) >= 0)
+        assert np.all((t["rho"] >= o.alpha_min) & (t["rho"] <= o.rho_max))
+        np.testing.assert_allclose(t["T"], np.concatenate([[1.0], np.cumprod(1 - t["rho"])[:-1]]), rtol=1e-13)
+        np.testing.assert_allclose((t["rgb"] * (t["rho"] * t["T"])[:, None]).sum(0), out["rgb"][py, px], rtol=1e-12)
+        np.testing.assert_allclose(t["T"][-1] * (1 - t["rho"][-1]), out["T"][py, px], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- scoring
+
+def small_scene(n=400, seed=1):
+    return synth.uniform_cube_scene(n, seed=seed), synth.cube_corner_cameras(3.0, 32, 32)[:3]
+
+
+def test_sensitivity_bounds_per_pixel():
+    sc, cams = small_scene()
+    r = oracle.score(sc, cams, Opts())
+    assert r["queries"] > 0
+    assert 1.0 - 1e-12 <= r["S"] <= min(sc.n, r["queries"]) + 1e-9
+    assert np.all(r["s"] <= 1.0 + 1e-15) and np.all(r["s"] >= 0)
+
+
+def test_scene_resolution_total_sensitivity_is_one():
+    sc, cams = small_scene()
+    r = oracle.score(sc, cams, Opts(resolution=oracle.RES_SCENE))
+    np.testing.assert_allclose(r["S"], 1.0, rtol=1e-12)
+
+
+def test_resolution_mediant_chain():
+    sc, cams = small_scene(300, seed=5)
+    s = {}
+    for name, res in [("channel", oracle.RES_CHANNEL), ("pixel", oracle.RES_PIXEL), ("tile", oracle.RES_TILE),
+                      ("image", oracle.RES_IMAGE), ("scene", oracle.RES_SCENE)]:
+        s[name] = oracle.score(sc, cams, Opts(resolution=res, tile=8))["s"]
+    tol = 1e-12
+    assert np.all(s["channel"] >= s["pixel"] - tol)
+    assert np.all(s["pixel"] >= s["tile"] - tol)
+    assert np.all(s["tile"] >= s["image"] - tol)
+    assert np.all(s["image"] >= s["scene"] - tol)
+    # 1x1 tiles are pixels
+    s1 = oracle.score(sc, cams, Opts(resolution=oracle.RES_TILE, tile=1))["s"]
+    np.testing.assert_allclose(s1, s["pixel"], rtol=1e-12, atol=1e-300)
+    # one view: the image query is the scene query
+    np.testing.assert_allclose(oracle.score(sc, cams[:1], Opts(resolution=oracle.RES_IMAGE))["s"],
+                               oracle.score(sc, cams[:1], Opts(resolution=oracle.RES_SCENE))["s"], rtol=1e-10)
+
+
+def test_score_variants_definitions():
+    # no-colour: A^nc per pixel equals 1 - T_final under the pure definitions
+    sc, cams = small_scene(200, seed=9)
+    o = Opts.pure(variant=oracle.VAR_NC)
+    cam = cams[0]
+    out = oracle.render(sc, cam, o)
+    for (px, py) in [(16, 16), (5, 20)]:
+        t = oracle.pixel_terms(sc, cam, px, py, o)
+        np.testing.assert_allclose((t["rho"] * t["T"]).sum(), 1 - out["T"][py, px], rtol=1e-12)
+    # the L2 variant never exceeds the bounds either
+    r = oracle.score(sc, cams, Opts(variant=oracle.VAR_L2))
+    assert 1 - 1e-12 <= r["S"] <= min(sc.n, r["queries"]) + 1e-9
+
+
+def test_isolation_scene_theorem1():
+    # N far-apart tiny Gaussians; camera i sits right in front of Gaussian i, so at
+    # its centre pixel Gaussian i is the only contributor: s_i = 1 and S = N.
+    n = 6
+    means = [[10.0 * i, 0.0, 0.0] for i in range(n)]
+    sc = one_scene(means, [[math.log(0.01)] * 3] * n, [[0.6, 0.4, 0.3]] * n, [0.5] * n)
+    cams = []
+    for i in range(n):
+        R, t = synth.look_at([10.0 * i, -1.0, 0.0], target=[10.0 * i, 0.0, 0.0])
+        cams.append(synth.make_camera(R, t, 5, 5, fx=20.0))
+    r = oracle.score(sc, np.stack(cams), Opts())
+    np.testing.assert_allclose(r["s"], np.ones(n), rtol=1e-12)
+    np.testing.assert_allclose(r["S"], n, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- sampling
+
+def test_uniform_map_and_inverse_cdf_against_integer_math_and_searchsorted():
+    rng = np.random.default_rng(0)
+    s = rng.random(257) ** 3
+    s[rng.random(257) < 0.2] = 0.0
+    p, S = oracle.probabilities(s)
+    np.testing.assert_allclose(S, s.sum(), rtol=1e-15)
+    C = oracle.cdf(p)
+    total = int(C[-1])
+    assert abs(total - 2 ** 56) <= len(p)
+    assert np.all(np.diff(C.astype(object)) >= 0)
+    seed, m = 1234567, 500
+    r = oracle.sample(p, m, seed)
+    for t in range(m):
+        ctr = [t & 0xFFFFFFFF, t >> 32, 0, 0]
+        w = oracle.philox4x32_10(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+        x = (int(w[1]) << 32) | int(w[0])
+        u = (x * total) >> 64
+        assert u == oracle.uniform(seed, t, total)
+        j = int(np.searchsorted(C.astype(object), u, side="right"))
+        assert r["J"][t] == j
+        assert p[j] > 0
+    assert r["counts"].sum() == m
+    assert r["distinct"] == len(r["idx"]) <= m
+    np.testing.assert_allclose(r["w_sel"], r["counts"][r["idx"]] / (m * p[r["idx"]]), rtol=1e-15)
+
+
+def test_sample_frequencies_follow_p():
+    rng = np.random.default_rng(1)
+    p = rng.random(40)
+    p /= p.sum()
+    m = 200_000
+    r = oracle.sample(p, m, 99)
+    expected = m * p
+    chi2 = ((r["counts"] - expected) ** 2 / expected).sum()
+    # 39 degrees of freedom: P(chi2 > 80) < 1e-4
+    assert chi2 < 80.0
+
+
+def test_weights_are_unbiased():
+    rng = np.random.default_rng(2)
+    p = rng.random(30) + 0.05
+    p /= p.sum()
+    m, seeds = 20, 3000
+    W = np.stack([oracle.sample(p, m, 1000 + k)["w"] for k in range(seeds)])
+    mean = W.mean(0)
+    se = W.std(0) / math.sqrt(seeds)
+    assert np.all(np.abs(mean - 1.0) <= 4.5 * se + 1e-12)
+
+
+def test_theorem2_failure_rate_at_most_delta():
+    sc, cams = small_scene(150, seed=4)
+    o = Opts.pure()
+    r = oracle.score(sc, cams, o)
+    p, S = oracle.probabilities(r["s"])
+    eps, delta = 0.5, 0.25
+    m = int(math.ceil(oracle.theorem2_m(S, eps, delta, r["queries"])))
+    assert m == int(math.ceil(3 * S / eps ** 2 * math.log(2 * r["queries"] / delta)))
+    fails, trials = 0, 24
+    for k in range(trials):
+        w = oracle.sample(p, m, 77 + k)["w"]
+        worst = 0.0
+        for cam in cams:
+            t = oracle.transfer(sc, cam, w, o)
+            A = t["A"].sum(-1)
+            Ath = t["A_th"].sum(-1)
+            msk = A > 0
+            worst = max(worst, float(np.max(np.abs(Ath[msk] - A[msk]) / A[msk])))
+        fails += worst > eps
+    assert fails / trials <= delta
+
+
+# ---------------------------------------------------------------- weighted render
+
+def test_unit_weights_reproduce_full_render():
+    sc, cams = small_scene(300, seed=6)
+    a = oracle.render(sc, cams[1], Opts())
+    b = oracle.render(sc, cams[1], Opts(), w=np.ones(sc.n))
+    np.testing.assert_array_equal(a["rgb"], b["rgb"])
+    np.testing.assert_array_equal(a["T"], b["T"])
+    assert b["violations"] == 0
+
+
+def test_transfer_sandwich_and_weighted_render_agree():
+    sc, cams = small_scene(300, seed=8)
+    o = Opts.pure()
+    r = oracle.score(sc, cams, o)
+    p, S = oracle.probabilities(r["s"])
+    w = oracle.sample(p, 120, 5)["w"]
+    for cam in cams:
+        t = oracle.transfer(sc, cam, w, o)
+        valid = t["min_factor"] > 0
+        g = t["gamma"][..., None]
+        lo = np.exp(-g) * t["A_th"]
+        hi = np.exp(g) * t["A_th"]
+        ok = (t["A_w"] >= lo * (1 - 1e-12) - 1e-15) & (t["A_w"] <= hi * (1 + 1e-12) + 1e-15)
+        assert np.all(ok[valid])
+        # the same reduced render through the renderer with weights (alpha' = w alpha)
+        rw = oracle.render(sc, cam, o, w=w)
+        np.testing.assert_allclose(rw["rgb"][valid], t["A_w"][valid], rtol=1e-10, atol=1e-14)
+        rf = oracle.render(sc, cam, o)
+        np.testing.assert_allclose(rf["rgb"], t["A"], rtol=1e-12, atol=1e-15)
