@@ -1,0 +1,393 @@
+"""Benchmark of the sensitivity-scoring hot path (arXiv 2607.02721, Sec. 3, Algorithm 1).
+
+One step = one pass of the path over the whole query set: EWA projection of every
+Gaussian into every view, (tile, depth) binning, the two-pass per-pixel compositing and
+sensitivity reduction (Eq. sen), S = sum s, and the draw of a 90%-pruning coreset
+(m = 0.1 N, weights 1/(m p)).  Metric: pixel-rays scored per second.
+
+Default workload: 3,000,000 Gaussians from a 256-component mixture (SH degree 3),
+200 views of 1600x1040 on a jittered hemisphere (332.8M rays per step); synthetic,
+seeded.  The scene (708 MB) is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sensitivity rays/sec at 3M Gaussians; surrogate vs exact at ΔPSNR ≤ 0.1 dB"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "composite_score_traffic.md")
+COMPOSITE_SRC = os.path.join(ROOT, "paper_2607_02721_b300", "csrc", "k_composite.cu")
+
+# FP32-pipe operations per (ray, Gaussian) pair of the compositing kernel, counted from
+# its arithmetic: pass 1 footprint test 8 (2 FADD offsets, 5 FMUL/FFMA quadratic form,
+# 1 FSETP), contribution 10 (opacity FMUL, FMNMX clamp, FSETP alpha_min, FADD 1-rho,
+# FMUL T, FSETP t_min, FMUL rho T, 3 FFMA colour); pass 2 test 8, contribution 8
+# (FMUL, FMNMX, FSETP, FMUL rho T, 2 FMUL importance, FADD, FMUL T).  MUFU ex2 is extra.
+OPS_TEST, OPS_HIT1, OPS_HIT2 = 8, 10, 8
+SMS, FP32_LANES = 148, 128
+
+
+def workload(name: str):
+    from paper_2607_02721_b300 import synth
+
+    if name == "scene_3m":
+        scene, cams = synth.workload_scene_3m()
+    elif name == "scene_1m":
+        scene, cams = synth.workload_scene_1m()
+    elif name == "small":
+        scene, cams, _ = synth.workload_small()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return scene, cams
+
+
+def describe(name, scene, cams):
+    W, H = int(cams[0][16]), int(cams[0][17])
+    return {"workload": name, "n_gaussians": scene.n, "sh_degree": scene.sh_degree, "views": len(cams),
+            "width": W, "height": H, "rays_per_step": int(sum(int(c[16]) * int(c[17]) for c in cams)),
+            "resolution": "per-pixel (max over pixel-rays)", "objective": "R+G+B",
+            "coreset_m": int(round(0.1 * scene.n)), "scorer": "exact",
+            "l2": "inputs larger than L2 (scene %.0f MB)" % (scene_bytes(scene) / 1e6),
+            "parallelism": "replicas"}
+
+
+def scene_bytes(scene) -> int:
+    return sum(a.nbytes for a in (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh))
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self) -> dict | None:
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def traffic_per_launch():
+    """DRAM bytes per compositing launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, None
+    txt = open(TRAFFIC_FILE).read()
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m_sha or not m_b:
+        return None, None
+    sha = hashlib.sha256(open(COMPOSITE_SRC, "rb").read()).hexdigest()
+    if sha != m_sha.group(1):
+        return None, "stale"
+    return float(m_b.group(1)), None
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return {}
+
+
+def _center_pixels(cams, count):
+    """The first ``count`` pixels, row-major, of a band centred in view 0."""
+    import numpy as np
+
+    H, W = int(cams[0][17]), int(cams[0][16])
+    count = int(max(1, min(count, H * W)))
+    rows = (count + W - 1) // W
+    r0 = max(0, H // 2 - rows // 2)
+    ys, xs = np.divmod(np.arange(count) + r0 * W, W)
+    return np.stack([xs, ys], 1).astype(np.int32)
+
+
+def _oracle_step(sa, cams, pixels):
+    import oracle
+
+    if pixels is None:
+        return oracle.score(sa, cams)
+    return oracle.score_pixels(sa, cams[0], pixels)
+
+
+def _calibrate(sa, cams, budget_s):
+    """Pixel count of view 0 that the oracle scores in about ``budget_s`` seconds
+    (None: the whole workload fits)."""
+    t = time.perf_counter()
+    _oracle_step(sa, cams, _center_pixels(cams, 32))
+    t1 = time.perf_counter() - t
+    t = time.perf_counter()
+    _oracle_step(sa, cams, _center_pixels(cams, 96))
+    t2 = time.perf_counter() - t
+    per_px = max((t2 - t1) / 64, 1e-7)
+    overhead = max(t1 - 32 * per_px, 0.0)
+    rays = int(sum(int(c[16]) * int(c[17]) for c in cams))
+    if overhead * len(cams) + rays * per_px <= budget_s:
+        return None
+    return int(max(32, (budget_s - overhead) / per_px))
+
+
+def cpu_baseline(name, scene, cams, budget_s: float):
+    """The oracle, as it stands, on a bounded sample of the workload: the whole query
+    set if it fits in about ``budget_s`` seconds, else a block of pixels centred in
+    view 0."""
+    import oracle
+
+    sa = oracle.SceneArrays(scene)
+    npx = _calibrate(sa, cams, budget_s)
+    pix = None if npx is None else _center_pixels(cams, npx)
+    t = time.perf_counter()
+    _oracle_step(sa, cams, pix)
+    el = time.perf_counter() - t
+    rays = int(sum(int(c[16]) * int(c[17]) for c in cams)) if pix is None else len(pix)
+    sample = (f"the whole {name} query set ({rays} pixel-rays)" if pix is None else
+              f"{rays} pixel-rays: a block of rows centred in view 0 of the {name} workload")
+    return {"value": rays / el, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": sample + f", FP64, {el:.1f} s"}, rays, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    scene, cams = workload(args.workload)
+    cfg = describe(args.workload, scene, cams)
+    per_step = max(2.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
+    sa = oracle.SceneArrays(scene)
+    npx = _calibrate(sa, cams, per_step)
+    pix = None if npx is None else _center_pixels(cams, npx)
+    rays_step = int(sum(int(c[16]) * int(c[17]) for c in cams)) if pix is None else len(pix)
+    for _ in range(args.warmup):
+        _oracle_step(sa, cams, pix)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_step(sa, cams, pix)
+    el = time.perf_counter() - t
+    v = rays_step * args.steps / el
+    sample = ("the whole query set" if pix is None else f"{rays_step} pixel-rays centred in view 0")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"each step: {sample} of the {args.workload} workload"},
+            "e2e": {"value": v, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2607_02721_b300 as csgs
+    from paper_2607_02721_b300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    scene, cams = workload(args.workload)
+    cfg = describe(args.workload, scene, cams)
+    m = cfg["coreset_m"]
+    stream = torch.cuda.Stream(device=local)
+    ctx = csgs.Context(local, stream=stream)
+    sid = ctx.load_scene(scene)
+    ctx.set_queries(sid, cams)
+    s = torch.empty(scene.n, dtype=torch.float32, device=f"cuda:{local}")
+
+    # pair counts of one pass (untimed; counting kernels are slower)
+    ctx.score(sid, csgs.default_opts(collect_stats=1), out=s)
+    cnt = ctx.stats()
+    timing = csgs.default_opts(collect_stats=2)
+
+    def step(seed):
+        ctx.score(sid, timing, out=s)
+        st = ctx.stats()
+        ctx.sample_coreset(s, m, seed)
+        return st
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = csgs.kernel_launch_count()
+    comp_ms, comp_n, proj_ms, sort_ms = 0.0, 0, 0.0, 0.0
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.steps):
+        st = step(1000 + i)
+        comp_ms += st["composite_ms"]
+        comp_n += st["composite_launches"]
+        proj_ms += st["project_ms"]
+        sort_ms += st["sort_ms"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = csgs.kernel_launch_count() - l0
+    clk = clocks.stop()
+    el_ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([el_ms], dtype=torch.float64, device=f"cuda:{local}")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    el_ms = float(t.item())
+    rays = cfg["rays_per_step"] * args.steps * world
+    value = rays / (el_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+                for a in (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh)]
+        h2d = sum(h.numel() * 4 for h in host) + len(cams) * 80
+        s_host = torch.empty(scene.n, dtype=torch.float32).pin_memory()
+        idx_host = torch.empty(m, dtype=torch.int32).pin_memory()
+        w_host = torch.empty(m, dtype=torch.float32).pin_memory()
+
+        def e2e_step(seed):
+            sid2 = ctx.load_scene_ptrs(scene.n, scene.sh_degree, [h.data_ptr() for h in host], is_device=False)
+            ctx.set_queries(sid2, cams)
+            s2, _ = ctx.score(sid2, csgs.default_opts(), out=s)
+            idx, w = ctx.sample_coreset(s2, m, seed)
+            with torch.cuda.stream(stream):
+                s_host.copy_(s2, non_blocking=True)
+                idx_host[: idx.numel()].copy_(idx, non_blocking=True)
+                w_host[: w.numel()].copy_(w, non_blocking=True)
+            stream.synchronize()
+            ctx.free_scene(sid2)
+            return s_host.numel() * 4 + 8 * idx.numel()
+
+        e2e_step(0)
+        torch.cuda.synchronize()
+        ne = max(1, min(args.steps, 5))
+        d2h = 0
+        t0 = time.perf_counter()
+        for i in range(ne):
+            d2h = e2e_step(2000 + i)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": cfg["rays_per_step"] * ne / te, "unit": "rays/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": ne}
+
+    # ---- roofline of the dominant kernel (compositing + sensitivity reduction)
+    ops_step = (OPS_TEST * cnt["pairs_evaluated"] + OPS_HIT1 * cnt["pairs_hit"] + OPS_TEST * cnt["pairs_evaluated2"]
+                + OPS_HIT2 * cnt["pairs_hit2"])
+    launches_step = cnt["composite_launches"]
+    ops_launch = ops_step / max(launches_step, 1)
+    avg_launch_s = comp_ms / max(comp_n, 1) / 1e3
+    achieved = ops_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
+    peak = SMS * FP32_LANES * 2032e6 / 1e12
+    traffic, stale = traffic_per_launch()
+    roof = {"bound": "alu", "kernel": "k_composite<score, per-pixel>", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock); one FP32-pipe op per lane per "
+                           "clock; ops counted per pair (see DESIGN.md)",
+            "ops_per_launch": ops_launch, "avg_launch_ms": avg_launch_s * 1e3,
+            "pairs_per_ray": (cnt["pairs_evaluated"] / cfg["rays_per_step"]),
+            "contributing_pairs_per_ray": (cnt["pairs_hit"] / cfg["rays_per_step"]),
+            "share_of_step": comp_ms / max(el_ms, 1e-9)}
+    if stale:
+        roof["traffic_note"] = "ncu counters predate the current kernel source"
+
+    line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+            "gpu_launches": int(launches),
+            "phases_ms_per_step": {"project": proj_ms / args.steps, "sort_and_bin": sort_ms / args.steps,
+                                   "composite_score": comp_ms / args.steps},
+            "clocks": clk, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _, _ = cpu_baseline(args.workload, scene, cams, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="scene_3m", choices=["scene_3m", "scene_1m", "small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * csgs.h -- C ABI of the B300 (sm_103a) sensitivity-scoring library for provable
+ * 3D Gaussian Splatting coreset pruning (arXiv 2607.02721).
+ *
+ * The paper's method (Sec. 3, Algorithm 1) for a pretrained scene G and a finite
+ * query set Q (the pixel-rays of a fixed set of views):
+ *   imp(g_i, q) = a(G, g_i, q) / A(G, q)            (Algorithm 1, step 2)
+ *   s(g_i)      = max_q imp(g_i, q), S = sum_i s(g_i), p_i = s_i / S   (Eq. sen)
+ *   draw m Gaussians i.i.d. from p, w_i = n_i / (m p_i)   (Algorithm 1, steps 4-5)
+ * where a = c rho T is a Gaussian's front-to-back contribution to a pixel and A the
+ * rendered value (Sec. 3 "Scalar rendering function").
+ *
+ * Conventions shared by every entry point
+ *   - All calls are asynchronous on the context's CUDA stream unless they return a
+ *     host value that needs the GPU result (documented per call); such calls
+ *     synchronise that stream before returning.
+ *   - "device" pointers are CUDA device memory on the context's device and are
+ *     owned by the caller; the library never frees them.  "host" pointers are
+ *     ordinary host memory.
+ *   - Return value: CSGS_OK (0) or a negative csgs_status; csgs_last_error() gives a
+ *     message.  Errors of asynchronous work surface at the next synchronising call.
+ *   - Floating point: projection, compositing and transmittance are FP32; the
+ *     total sensitivity S, the probabilities p and the weights w are FP64 (w is
+ *     returned as FP32).
+ *   - No entry point allocates memory it does not own: work buffers belong to the
+ *     context (grown on demand, freed by csgs_destroy).
+ */
+#ifndef CSGS_H
+#define CSGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t csgs_status;
+
+#define CSGS_OK 0
+#define CSGS_E_INVAL (-1)        /* bad argument: null pointer, size <= 0, bad camera, non-finite input */
+#define CSGS_E_NOMEM (-2)        /* device allocation failed */
+#define CSGS_E_CUDA (-3)         /* CUDA runtime error (message has the CUDA error string) */
+#define CSGS_E_EMPTY (-4)        /* every query had A(G,q) = 0, so S = 0 (Sec. 3: such queries are discarded) */
+#define CSGS_E_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define CSGS_E_DEVICE_CHECK (-6) /* a device-side check failed (e.g. instance capacity) */
+
+typedef struct csgs_ctx csgs_ctx;
+
+/* Scene G = {g_i = (mu_i, Sigma_i, alpha_i, c_i)} (Sec. 3 "3DGS scene") in structure-
+ * of-arrays float32 layout.  Sigma_i = Rq diag(exp(log_scale))^2 Rq^T with Rq the
+ * rotation of the (normalised) quaternion; alpha_i = sigmoid(opacity_logit);
+ * c_i = max(0, SH(dir) + 0.5) with real SH of degree sh_degree evaluated along the
+ * direction from the camera centre to mu_i. */
+typedef struct {
+    int64_t n;                   /* number of Gaussians N, 1 <= N < 2^31 */
+    int32_t sh_degree;           /* 0..3 */
+    int32_t is_device;           /* 1: pointers are device memory, 0: host memory */
+    const float* means;          /* [3][N]: x[N], y[N], z[N] */
+    const float* log_scales;     /* [3][N] */
+    const float* quats;          /* [4][N]: w, x, y, z */
+    const float* opacity_logits; /* [N] */
+    const float* sh;             /* [(d+1)^2][3][N]: coefficient-major, then R, G, B */
+} csgs_scene_desc;
+
+/* A pinhole camera (query pose C = (R, t), Sec. 3 "Rendering query"): p_cam = R p + t
+ * with x right, y down, z forward; pixel (u, v) has its centre at integer
+ * coordinates, u = fx x/z + cx. */
+typedef struct {
+    float R[9];     /* row-major world-to-camera rotation */
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height; /* 1..16384 */
+    float near_z;   /* Gaussians with camera depth <= near_z are culled (> 0) */
+    float pad;
+} csgs_camera;
+
+#define CSGS_RES_PIXEL 0   /* query = pixel, objective = obj_w . RGB (Sec. 3 "Per-pixel construction") */
+#define CSGS_RES_SCENE 1   /* one aggregated query over all views and pixels (Sec. 3 "Per-scene") */
+
+#define CSGS_VAR_L1 0      /* a = c rho T (the core score) */
+
+/* Scoring / rendering conventions.  The paper fixes only the definitions; the
+ * thresholds are those of the standard 3DGS rasteriser it relies on. */
+typedef struct {
+    int32_t resolution;    /* CSGS_RES_* */
+    int32_t variant;       /* CSGS_VAR_* */
+    float obj_w[3];        /* per-pixel objective weights (1,1,1) = total colour */
+    float alpha_min;       /* pairs with rho < alpha_min are skipped (1/255) */
+    float rho_max;         /* rho = min(rho_max, alpha k) (0.99) */
+    float t_min;           /* traversal stops before T would drop below t_min (1e-4) */
+    float cut2;            /* footprint: k = 0 where d^T Sigma'^-1 d > cut2 (9 = 3 sigma) */
+    float dilation;        /* added to the diagonal of the 2-D covariance (0.3) */
+    float clamp_fov;       /* J uses x/z, y/z clamped to clamp_fov * half-FOV tangent (1.3) */
+    int32_t view_batch;    /* views projected per launch (0 = automatic) */
+    int32_t collect_stats; /* bit 0: count evaluated and contributing pairs (slower kernels);
+                              bit 1: time the phases with CUDA events on the stream */
+} csgs_score_opts;
+
+/* Counters of the last csgs_score / csgs_render call. */
+typedef struct {
+    int64_t views;
+    int64_t rays;             /* pixel-rays processed */
+    int64_t instances;        /* (Gaussian, tile) pairs summed over views */
+    int64_t pairs_evaluated;  /* compositing pass 1: (ray, Gaussian) pairs tested before the stop (bit 0) */
+    int64_t pairs_hit;        /* pass 1: pairs inside the footprint with rho >= alpha_min (bit 0) */
+    int64_t pairs_evaluated2; /* scoring pass 2: pairs tested (bit 0) */
+    int64_t pairs_hit2;       /* scoring pass 2: contributing pairs (bit 0) */
+    int64_t violations;       /* csgs_render: pairs met before the stop with w alpha k >= 1 (bit 0) */
+    int64_t capacity_retries; /* re-runs after growing the instance buffers */
+    int64_t kernel_launches;  /* kernels this library launched in the call */
+    int64_t composite_launches;
+    double score_ms;          /* the whole call on the stream (CUDA events) */
+    double project_ms;        /* phase totals (bit 1) */
+    double sort_ms;
+    double composite_ms;
+} csgs_stats;
+
+/* Fill *o with the default conventions above. */
+void csgs_default_opts(csgs_score_opts* o);
+
+/* Create a context on CUDA device `device`.  cuda_stream: an existing cudaStream_t
+ * to run on (not owned), or NULL to create one (owned).  *out receives the context. */
+csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream);
+
+/* Destroy a context: synchronises its stream, frees every scene and work buffer. */
+void csgs_destroy(csgs_ctx* ctx);
+
+/* Message of the last error on this context (owned by the context; valid until the
+ * next call). */
+const char* csgs_last_error(const csgs_ctx* ctx);
+
+/* Copy a scene into the context (host or device source per desc->is_device).
+ * Checks sizes and that every attribute is finite (non-finite -> CSGS_E_INVAL,
+ * synchronising).  *scene_id receives the handle. */
+csgs_status csgs_load_scene(csgs_ctx* ctx, const csgs_scene_desc* desc, int32_t* scene_id);
+
+/* Release a scene's device memory. */
+csgs_status csgs_free_scene(csgs_ctx* ctx, int32_t scene_id);
+
+/* Set the query views of a scene (Algorithm 1, step 1): every pixel of each camera
+ * is one query.  cams: host array of n_views cameras (copied). */
+csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera* cams, int32_t n_views);
+
+/* Sensitivity scores (Algorithm 1, steps 2-3; Eq. sen) over all query views.
+ * s_dev: device float[N], written with s_i.  S_out: host double, total
+ * sensitivity S (may be NULL).  Synchronises.  Returns CSGS_E_EMPTY when S = 0. */
+csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* s_dev, double* S_out);
+
+/* Sensitivity sampling (Algorithm 1, steps 3-5): S = sum s (FP64), p = s / S,
+ * m i.i.d. inverse-CDF draws with Philox4x32-10 uniforms (key = seed, counter =
+ * draw index), counts n_i and weights w_i = n_i / (m p_i).
+ * s_dev: device float[n] (non-negative).  idx_dev: device int32[m] receives the
+ * distinct sampled indices in ascending order; w_dev: device float[m] their
+ * weights; *n_distinct (host) their count.  Synchronises.
+ * CSGS_E_EMPTY if S = 0; CSGS_E_INVAL if m <= 0 or n <= 0. */
+csgs_status csgs_sample_coreset(csgs_ctx* ctx, const float* s_dev, int64_t n, int64_t m, uint64_t seed,
+                                int32_t* idx_dev, float* w_dev, int64_t* n_distinct);
+
+/* As csgs_sample_coreset, with the probabilities given: p_dev device double[n]
+ * (sum 1).  draws_dev: optional device int32[m] receiving every draw J_t in draw
+ * order (NULL to skip).  Used to check the sampler bit for bit. */
+csgs_status csgs_sample_coreset_p(csgs_ctx* ctx, const double* p_dev, int64_t n, int64_t m, uint64_t seed,
+                                  int32_t* idx_dev, float* w_dev, int64_t* n_distinct, int32_t* draws_dev);
+
+/* Render one query view of a scene, optionally as the weighted pruned scene A_w of
+ * Sec. 3 ("A pruned 3DGS scene"): Gaussian i gets rho' = min(rho_max, w_i alpha_i k)
+ * and Gaussians not listed are removed.  idx_dev / w_dev: device int32[n_sel] /
+ * float[n_sel] (both NULL: the full scene).  rgb_dev: device float[H][W][3].
+ * T_dev: optional device float[H][W] final transmittance.  Asynchronous; the
+ * validity-violation count appears in csgs_get_stats after csgs_sync. */
+csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev, const float* w_dev,
+                        int64_t n_sel, const csgs_score_opts* opts, float* rgb_dev, float* T_dev);
+
+/* Wait for the context's stream and report errors of asynchronous work. */
+csgs_status csgs_sync(csgs_ctx* ctx);
+
+/* Counters of the last score / render (synchronises). */
+csgs_status csgs_get_stats(csgs_ctx* ctx, csgs_stats* out);
+
+/* Total number of kernels this library has launched in the process (all contexts);
+ * the difference across a region counts that region's launches. */
+int64_t csgs_kernel_launch_count(void);
+
+/* Diagnostic: the FP32 projection of every Gaussian into one query view (the EWA
+ * step of the path, Sec. 3 "Scalar rendering function").  out_dev: device
+ * float[N][16] = valid, mean x, mean y (each as the rounded sum of a two-float
+ * value), conic a, b, c, covariance xx, xy, yy, depth, alpha, r, g, b, tile count,
+ * mean x low word. */
+csgs_status csgs_debug_project(csgs_ctx* ctx, int32_t scene_id, int32_t view, const csgs_score_opts* opts,
+                               float* out_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSGS_H */

@@ -117,6 +117,7 @@ def lib():
         _lib.or_theorem2_m.argtypes = [ctypes.c_double] * 4
         _lib.or_theorem2_m.restype = ctypes.c_double
         _lib.or_transfer.argtypes = [P, P, P, P, P]
+        _lib.or_score_pixels.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P]
         _lib.or_num_threads.restype = ctypes.c_int
     return _lib
 
@@ -293,3 +294,19 @@ def transfer(scene, cam, w, opts: Opts | None = None):
     oc = opts.c()
     lib().or_transfer(ctypes.byref(sa.c), _ptr(cam), ctypes.byref(oc), _ptr(w), _ptr(out))
     return dict(A=out[..., 0:3], A_th=out[..., 3:6], A_w=out[..., 6:9], gamma=out[..., 9], min_factor=out[..., 10])
+
+
+def score_pixels(scene, cam, pixels, opts: Opts | None = None):
+    """Per-pixel-resolution sensitivity over a list of (x, y) pixels of one camera."""
+    sa = _scene(scene)
+    opts = opts or Opts()
+    pixels = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+    s = np.zeros(sa.n)
+    touched = np.zeros(sa.n, dtype=np.uint8)
+    flags = np.zeros(pixels.shape[0], dtype=np.uint8)
+    oc = opts.c()
+    rc = lib().or_score_pixels(ctypes.byref(sa.c), _ptr(_cam(cam)), ctypes.byref(oc), pixels.shape[0], _ptr(pixels),
+                               _ptr(s), _ptr(touched), _ptr(flags))
+    if rc:
+        raise MemoryError("oracle score_pixels failed")
+    return dict(s=s, touched=touched.astype(bool), flags=flags.astype(bool))

@@ -101,6 +101,7 @@ typedef struct {
     double depth;
     int64_t gid;
     double rho;
+    int viol; /* w alpha k >= 1: the factor 1 - w rho would not be positive unclamped */
 } ocand;
 
 typedef struct {
@@ -351,7 +352,7 @@ typedef struct {
     double T;           /* transmittance after the last contributor */
     int64_t n_terms;    /* contributors */
     int64_t evaluated;  /* Gaussians inside the footprint box before the stop */
-    int64_t violations; /* pairs with w*alpha*k >= 1 inside the footprint */
+    int64_t violations; /* pairs met before the stop with w*alpha*k >= 1 */
     int flag;           /* straddle */
 } opix;
 
@@ -374,7 +375,6 @@ static void pixel_composite(const oview* v, const or_opts* o, double px, double 
         if (m > o->cut2) continue;
         double k = exp(-0.5 * m);
         double raw = g->alpha * k;
-        if (raw >= 1.0) r->violations++;
         double rho = raw < o->rho_max ? raw : o->rho_max;
         if (near_rel(rho, o->alpha_min, o->band_alpha)) r->flag = 1;
         if (rho < o->alpha_min) continue;
@@ -382,6 +382,7 @@ static void pixel_composite(const oview* v, const or_opts* o, double px, double 
         b->cand[nc].depth = g->depth;
         b->cand[nc].gid = i;
         b->cand[nc].rho = rho;
+        b->cand[nc].viol = raw >= 1.0;
         nc++;
     }
     qsort(b->cand, (size_t)nc, sizeof(ocand), cand_cmp);
@@ -393,6 +394,7 @@ static void pixel_composite(const oview* v, const or_opts* o, double px, double 
         double Tn = T * (1.0 - c->rho);
         if (near_rel(Tn, o->t_min, o->band_tmin)) r->flag = 1;
         r->evaluated++;
+        r->violations += c->viol; /* validity (Def. "valid") over the pairs the traversal meets */
         if (Tn < o->t_min) break;
         const oattr* g = &v->at[c->gid];
         oterm* t = &b->terms[nt++];
@@ -861,6 +863,41 @@ int or_transfer(const or_scene* sc, const float* cam, const or_opts* o, const do
             }
             r[9] = gam;
             r[10] = minf;
+        }
+        free(b.cand);
+        free(b.terms);
+    }
+    free_view(&v);
+    return 0;
+}
+
+/* Per-pixel-resolution sensitivity restricted to a list of pixels of one view:
+ * s[i] = max over the listed queries of a_i / A (Eq. sen over that subset); used to
+ * obtain the exact s_i of chosen Gaussians by listing every pixel of their
+ * footprints.  flags[p] marks straddling pixels; touched[i] = 1 if Gaussian i
+ * contributes to a flagged pixel. */
+int or_score_pixels(const or_scene* sc, const float* cam, const or_opts* o, int64_t npix, const int32_t* pix,
+                    double* s, uint8_t* touched, uint8_t* flags) {
+    oview v;
+    ocam cm;
+    if (build_view(sc, cam, o, NULL, &v, &cm)) return -1;
+    memset(s, 0, sizeof(double) * sc->n);
+    if (touched) memset(touched, 0, sc->n);
+#pragma omp parallel
+    {
+        obuf b = {0};
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t q = 0; q < npix; ++q) {
+            opix r;
+            pixel_composite(&v, o, pix[2 * q], pix[2 * q + 1], &b, &r);
+            if (flags) flags[q] = (uint8_t)r.flag;
+            double A = 0.0;
+            for (int64_t j = 0; j < r.n_terms; ++j) A += term_pixel(o, &b.terms[j]);
+            if (!(A > 0.0)) continue;
+            for (int64_t j = 0; j < r.n_terms; ++j) {
+                atomic_max_nonneg(&s[b.terms[j].gid], term_pixel(o, &b.terms[j]) / A);
+                if (touched && r.flag) touched[b.terms[j].gid] = 1;
+            }
         }
         free(b.cand);
         free(b.terms);

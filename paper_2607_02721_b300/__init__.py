@@ -1,0 +1,272 @@
+"""B300-native sensitivity scoring and coreset sampling for 3D Gaussian Splatting
+pruning (arXiv 2607.02721, Sec. 3 and Algorithm 1).
+
+This module is the thin Python binding of the C ABI in ``include/csgs.h``: it only
+marshals arguments (tensor data pointers, the CUDA stream handle, ctypes structs)
+into ``_lib/libcsgs.so``, where every step of the path runs in hand-written sm_103a
+kernels.  PyTorch supplies device memory and streams.  There is no CPU fallback: if
+the shared library is missing the import of the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcsgs.so")
+
+CSGS_OK = 0
+CSGS_E_INVAL = -1
+CSGS_E_NOMEM = -2
+CSGS_E_CUDA = -3
+CSGS_E_EMPTY = -4
+CSGS_E_TIMEOUT = -5
+CSGS_E_DEVICE_CHECK = -6
+RES_PIXEL = 0
+RES_SCENE = 1
+VAR_L1 = 0
+
+
+class CsgsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"csgs error {status}: {msg}")
+        self.status = status
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("is_device", ctypes.c_int32),
+                ("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("near_z", ctypes.c_float),
+                ("pad", ctypes.c_float)]
+
+
+class ScoreOpts(ctypes.Structure):
+    _fields_ = [("resolution", ctypes.c_int32), ("variant", ctypes.c_int32), ("obj_w", ctypes.c_float * 3),
+                ("alpha_min", ctypes.c_float), ("rho_max", ctypes.c_float), ("t_min", ctypes.c_float),
+                ("cut2", ctypes.c_float), ("dilation", ctypes.c_float), ("clamp_fov", ctypes.c_float),
+                ("view_batch", ctypes.c_int32), ("collect_stats", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("views", ctypes.c_int64), ("rays", ctypes.c_int64), ("instances", ctypes.c_int64),
+                ("pairs_evaluated", ctypes.c_int64), ("pairs_hit", ctypes.c_int64),
+                ("pairs_evaluated2", ctypes.c_int64), ("pairs_hit2", ctypes.c_int64), ("violations", ctypes.c_int64),
+                ("capacity_retries", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("composite_launches", ctypes.c_int64), ("score_ms", ctypes.c_double),
+                ("project_ms", ctypes.c_double), ("sort_ms", ctypes.c_double), ("composite_ms", ctypes.c_double)]
+
+
+EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",
+           "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
+           "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count")
+
+_lib = None
+
+
+def lib():
+    """Load ``libcsgs.so`` (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is missing: run paper_2607_02721_b300.build.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    V, I32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    L.csgs_default_opts.argtypes = [V]
+    L.csgs_default_opts.restype = None
+    L.csgs_create.argtypes = [V, I32, V]
+    L.csgs_destroy.argtypes = [V]
+    L.csgs_destroy.restype = None
+    L.csgs_last_error.argtypes = [V]
+    L.csgs_last_error.restype = ctypes.c_char_p
+    L.csgs_load_scene.argtypes = [V, V, V]
+    L.csgs_free_scene.argtypes = [V, I32]
+    L.csgs_set_queries.argtypes = [V, I32, V, I32]
+    L.csgs_score.argtypes = [V, I32, V, V, V]
+    L.csgs_sample_coreset.argtypes = [V, V, I64, I64, U64, V, V, V]
+    L.csgs_sample_coreset_p.argtypes = [V, V, I64, I64, U64, V, V, V, V]
+    L.csgs_render.argtypes = [V, I32, I32, V, V, I64, V, V, V]
+    L.csgs_sync.argtypes = [V]
+    L.csgs_get_stats.argtypes = [V, V]
+    L.csgs_debug_project.argtypes = [V, I32, I32, V, V]
+    L.csgs_kernel_launch_count.argtypes = []
+    L.csgs_kernel_launch_count.restype = I64
+    for name in EXPORTS:
+        f = getattr(L, name)
+        if f.restype is ctypes.c_int:  # default
+            f.restype = ctypes.c_int32
+    _lib = L
+    return L
+
+
+def default_opts(**kw) -> ScoreOpts:
+    o = ScoreOpts()
+    lib().csgs_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "obj_w":
+            o.obj_w = (ctypes.c_float * 3)(*v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def cameras(records) -> "ctypes.Array":
+    """csgs_camera array from float records [V, 20] (see synth.CAMERA_FIELDS)."""
+    rec = np.asarray(records, dtype=np.float32).reshape(-1, 20)
+    arr = (Camera * rec.shape[0])()
+    for i, r in enumerate(rec):
+        c = arr[i]
+        c.R = (ctypes.c_float * 9)(*r[0:9])
+        c.t = (ctypes.c_float * 3)(*r[9:12])
+        c.fx, c.fy, c.cx, c.cy = (float(x) for x in r[12:16])
+        c.width, c.height = int(r[16]), int(r[17])
+        c.near_z = float(r[18])
+    return arr
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_launch_count() -> int:
+    return int(lib().csgs_kernel_launch_count())
+
+
+class Context:
+    """One CUDA device + stream.  Methods mirror the csgs_* entry points."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self._stream = stream
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+        r = lib().csgs_create(ctypes.byref(h), device, st)
+        if r != CSGS_OK:
+            raise CsgsError(r, "csgs_create failed")
+        self.h = h
+        self._scenes = {}
+
+    def _check(self, r):
+        if r != CSGS_OK:
+            raise CsgsError(r, lib().csgs_last_error(self.h).decode())
+        return r
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().csgs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- scene and queries
+    def load_scene(self, scene, on_device: bool = True) -> int:
+        """Copy a scene (synth.Scene or an object with the same array attributes) into the
+        context.  on_device: stage it through device tensors first (else the library
+        copies from host memory)."""
+        torch = self.torch
+        arrs = [scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh]
+        if on_device:
+            keep = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(self.device) for a in arrs]
+            ptrs = [t.data_ptr() for t in keep]
+        else:
+            keep = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
+            ptrs = [a.ctypes.data for a in keep]
+        k = keep[4].shape[0]
+        deg = {1: 0, 4: 1, 9: 2, 16: 3}[k]
+        d = SceneDesc(int(keep[0].shape[1]), deg, 1 if on_device else 0, *ptrs)
+        sid = ctypes.c_int32()
+        self._check(lib().csgs_load_scene(self.h, ctypes.byref(d), ctypes.byref(sid)))
+        self._scenes[sid.value] = int(keep[0].shape[1])
+        return sid.value
+
+    def load_scene_ptrs(self, n: int, sh_degree: int, ptrs, is_device: bool) -> int:
+        d = SceneDesc(n, sh_degree, 1 if is_device else 0, *ptrs)
+        sid = ctypes.c_int32()
+        self._check(lib().csgs_load_scene(self.h, ctypes.byref(d), ctypes.byref(sid)))
+        self._scenes[sid.value] = n
+        return sid.value
+
+    def free_scene(self, sid: int):
+        self._check(lib().csgs_free_scene(self.h, sid))
+        self._scenes.pop(sid, None)
+
+    def set_queries(self, sid: int, cams):
+        arr = cams if isinstance(cams, ctypes.Array) else cameras(cams)
+        self._check(lib().csgs_set_queries(self.h, sid, arr, len(arr)))
+
+    # -- the hot path
+    def score(self, sid: int, opts: ScoreOpts | None = None, out=None):
+        """Sensitivities s (float32 [N] on the device) and S (host float)."""
+        torch = self.torch
+        n = self._scenes[sid]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=self.device)
+        S = ctypes.c_double()
+        opts = opts or default_opts()
+        self._check(lib().csgs_score(self.h, sid, ctypes.byref(opts), _ptr(out), ctypes.byref(S)))
+        return out, S.value
+
+    def sample_coreset(self, s, m: int, seed: int):
+        torch = self.torch
+        idx = torch.empty(m, dtype=torch.int32, device=self.device)
+        w = torch.empty(m, dtype=torch.float32, device=self.device)
+        nd = ctypes.c_int64()
+        self._check(lib().csgs_sample_coreset(self.h, _ptr(s), s.numel(), m, seed, _ptr(idx), _ptr(w),
+                                              ctypes.byref(nd)))
+        return idx[: nd.value], w[: nd.value]
+
+    def sample_coreset_p(self, p, m: int, seed: int, return_draws: bool = False):
+        torch = self.torch
+        idx = torch.empty(m, dtype=torch.int32, device=self.device)
+        w = torch.empty(m, dtype=torch.float32, device=self.device)
+        draws = torch.empty(m, dtype=torch.int32, device=self.device) if return_draws else None
+        nd = ctypes.c_int64()
+        self._check(lib().csgs_sample_coreset_p(self.h, _ptr(p), p.numel(), m, seed, _ptr(idx), _ptr(w),
+                                                ctypes.byref(nd), _ptr(draws)))
+        if return_draws:
+            return idx[: nd.value], w[: nd.value], draws
+        return idx[: nd.value], w[: nd.value]
+
+    def render(self, sid: int, view: int, idx=None, w=None, opts: ScoreOpts | None = None, H=None, W=None,
+               with_T: bool = False, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        T = torch.empty((H, W), dtype=torch.float32, device=self.device) if with_T else None
+        n_sel = 0 if idx is None else idx.numel()
+        opts = opts or default_opts()
+        self._check(lib().csgs_render(self.h, sid, view, _ptr(idx), _ptr(w), n_sel, ctypes.byref(opts), _ptr(out),
+                                      _ptr(T)))
+        return (out, T) if with_T else out
+
+    def debug_project(self, sid: int, view: int, opts: ScoreOpts | None = None):
+        torch = self.torch
+        n = self._scenes[sid]
+        out = torch.empty((n, 16), dtype=torch.float32, device=self.device)
+        opts = opts or default_opts()
+        self._check(lib().csgs_debug_project(self.h, sid, view, ctypes.byref(opts), _ptr(out)))
+        return out
+
+    def sync(self):
+        self._check(lib().csgs_sync(self.h))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(lib().csgs_get_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}

@@ -1,0 +1,762 @@
+// Host side of the C ABI declared in include/csgs.h: contexts, scenes, work buffers
+// and the stream-ordered orchestration of the scoring, sampling and rendering paths.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "csgs_internal.cuh"
+
+#include <atomic>
+
+using namespace csgs;
+
+namespace csgs {
+static std::atomic<long long> g_launches{0};
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace csgs
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct SceneRec {
+    bool alive = false;
+    int64_t n = 0;
+    int deg = 0;
+    float* means = nullptr;
+    float* log_scales = nullptr;
+    float* quats = nullptr;
+    float* opac = nullptr;
+    float* sh = nullptr;
+    std::vector<CamDev> cams;
+    CamDev* d_cams = nullptr;
+    float uploaded_clamp = -1.f;  // clamp_fov of the cameras on the device (-1: none)
+};
+
+}  // namespace
+
+struct csgs_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<SceneRec> scenes;
+    std::string err;
+    DevCounters* d_ctr = nullptr;
+    DevCounters* h_ctr = nullptr;  // pinned
+    double* h_S = nullptr;         // pinned
+    uint32_t* h_u32 = nullptr;     // pinned
+    unsigned long long* d_nconst = nullptr;
+    DevBuf splats, keys, rects, dkeys_b, dvals_a, dvals_b;
+    DevBuf ikeys_a, ikeys_b, ivals_a, ivals_b;
+    uint32_t cap = 0;
+    DevBuf ranges, hist, scan_tmp;
+    DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
+    csgs_stats stats{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> evpool;  // phase timing
+};
+
+namespace {
+
+csgs_status fail(csgs_ctx* ctx, csgs_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                          \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? CSGS_E_NOMEM : CSGS_E_CUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                              \
+    } while (0)
+
+csgs_status ensure(csgs_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (bytes <= b.bytes) return CSGS_OK;
+    if (b.p) {
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+        CUDA_TRY(ctx, cudaFree(b.p));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = bytes + bytes / 8 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, CSGS_E_NOMEM, "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    return CSGS_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+template <class T>
+T* P(DevBuf& b) {
+    return reinterpret_cast<T*>(b.p);
+}
+
+csgs_status launch_check(csgs_ctx* ctx, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, CSGS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return CSGS_OK;
+}
+
+int ceil_log2(uint32_t v) {
+    int b = 0;
+    while ((1u << b) < v) ++b;
+    return b;
+}
+
+bool finite3(const float* v, int k) {
+    for (int i = 0; i < k; ++i)
+        if (!isfinite(v[i])) return false;
+    return true;
+}
+
+csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
+    if (!o) return fail(ctx, CSGS_E_INVAL, "opts is NULL");
+    if (o->resolution != CSGS_RES_PIXEL && o->resolution != CSGS_RES_SCENE)
+        return fail(ctx, CSGS_E_INVAL, "resolution %d is not supported", o->resolution);
+    if (o->variant != CSGS_VAR_L1) return fail(ctx, CSGS_E_INVAL, "variant %d is not supported", o->variant);
+    if (!(o->alpha_min >= 0.f) || !(o->rho_max > 0.f && o->rho_max <= 1.f) || !(o->t_min >= 0.f) ||
+        !(o->cut2 > 0.f) || !(o->dilation >= 0.f) || !(o->clamp_fov > 0.f) || !finite3(o->obj_w, 3) ||
+        o->obj_w[0] < 0.f || o->obj_w[1] < 0.f || o->obj_w[2] < 0.f || o->view_batch < 0)
+        return fail(ctx, CSGS_E_INVAL, "invalid scoring options");
+    k->alpha_min = o->alpha_min;
+    k->rho_max = o->rho_max;
+    k->t_min = o->t_min;
+    k->cut2 = o->cut2;
+    k->pcut = (float)(-0.5 * 1.4426950408889634 * (double)o->cut2);
+    k->dilation = o->dilation;
+    k->clamp_fov = o->clamp_fov;
+    k->ow0 = o->obj_w[0];
+    k->ow1 = o->obj_w[1];
+    k->ow2 = o->obj_w[2];
+    k->resolution = o->resolution;
+    k->variant = o->variant;
+    return CSGS_OK;
+}
+
+SceneRec* get_scene(csgs_ctx* ctx, int32_t id) {
+    if (!ctx || id < 0 || id >= (int32_t)ctx->scenes.size() || !ctx->scenes[id].alive) return nullptr;
+    return &ctx->scenes[id];
+}
+
+SceneDev scene_dev(const SceneRec& s) {
+    SceneDev d;
+    d.n = (int)s.n;
+    d.deg = s.deg;
+    d.means = s.means;
+    d.log_scales = s.log_scales;
+    d.quats = s.quats;
+    d.opac = s.opac;
+    d.sh = s.sh;
+    return d;
+}
+
+// Per-view buffers for a batch of `vb` views and the instance buffers.
+csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles) {
+    csgs_status r;
+    if ((r = ensure(ctx, ctx->splats, sizeof(Splat) * (size_t)n * vb))) return r;
+    if ((r = ensure(ctx, ctx->keys, sizeof(uint32_t) * (size_t)n * vb))) return r;
+    if ((r = ensure(ctx, ctx->rects, sizeof(uint2) * (size_t)n * vb))) return r;
+    if ((r = ensure(ctx, ctx->dkeys_b, sizeof(uint32_t) * (size_t)n))) return r;
+    if ((r = ensure(ctx, ctx->dvals_a, sizeof(uint32_t) * (size_t)n))) return r;
+    if ((r = ensure(ctx, ctx->dvals_b, sizeof(uint32_t) * (size_t)n))) return r;
+    if ((r = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return r;
+    if ((r = ensure(ctx, ctx->hist, sizeof(uint32_t) * 256 * kSortBlocks))) return r;
+    if ((r = ensure(ctx, ctx->scan_tmp, sizeof(uint32_t) * ((size_t)(n + 2047) / 2048 + 64)))) return r;
+    if (ctx->cap == 0) {
+        uint64_t c = (uint64_t)n * 8;
+        if (c < (1u << 20)) c = 1u << 20;
+        if (c > 0xF0000000ull) c = 0xF0000000ull;
+        ctx->cap = (uint32_t)c;
+    }
+    size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
+    if ((r = ensure(ctx, ctx->ikeys_a, ib))) return r;
+    if ((r = ensure(ctx, ctx->ikeys_b, ib))) return r;
+    if ((r = ensure(ctx, ctx->ivals_a, ib))) return r;
+    if ((r = ensure(ctx, ctx->ivals_b, ib))) return r;
+    return CSGS_OK;
+}
+
+// Depth sort -> instances -> tile sort -> ranges for one projected view.
+// Returns the instance value buffer (Gaussian ids in tile, depth order).
+const uint32_t* bin_view(csgs_ctx* ctx, int64_t n, uint32_t* keys_v, const uint2* rects_v, const CamDev& cam) {
+    cudaStream_t st = ctx->st;
+    iota_u32(P<uint32_t>(ctx->dvals_a), (int)n, st);
+    int cur = radix_sort_pairs(keys_v, P<uint32_t>(ctx->dvals_a), P<uint32_t>(ctx->dkeys_b), P<uint32_t>(ctx->dvals_b),
+                               ctx->d_nconst, (uint32_t)n, 32, P<uint32_t>(ctx->hist), st);
+    const uint32_t* order = cur ? P<uint32_t>(ctx->dvals_b) : P<uint32_t>(ctx->dvals_a);
+    const uint32_t* skeys = cur ? P<uint32_t>(ctx->dkeys_b) : keys_v;
+    emit_instances(order, skeys, rects_v, (int)n, cam.tiles_x, P<uint32_t>(ctx->ikeys_a), P<uint32_t>(ctx->ivals_a),
+                   ctx->cap, P<uint32_t>(ctx->scan_tmp), ctx->d_ctr, st);
+    const int ntiles = cam.tiles_x * cam.tiles_y;
+    int cur2 = radix_sort_pairs(P<uint32_t>(ctx->ikeys_a), P<uint32_t>(ctx->ivals_a), P<uint32_t>(ctx->ikeys_b),
+                                P<uint32_t>(ctx->ivals_b), &ctx->d_ctr->n_inst, ctx->cap, ceil_log2((uint32_t)ntiles),
+                                P<uint32_t>(ctx->hist), st);
+    const uint32_t* ik = cur2 ? P<uint32_t>(ctx->ikeys_b) : P<uint32_t>(ctx->ikeys_a);
+    const uint32_t* iv = cur2 ? P<uint32_t>(ctx->ivals_b) : P<uint32_t>(ctx->ivals_a);
+    tile_ranges(ik, &ctx->d_ctr->n_inst, ctx->cap, P<uint2>(ctx->ranges), ntiles, st);
+    return iv;
+}
+
+csgs_status read_counters(csgs_ctx* ctx) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, ctx->st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    return CSGS_OK;
+}
+
+csgs_status grow_capacity(csgs_ctx* ctx) {
+    unsigned long long need = ctx->h_ctr->max_inst;
+    unsigned long long c = need + need / 4 + 4096;
+    if (c > 0xF0000000ull) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance count %llu exceeds the 32-bit index range", need);
+    ctx->cap = (uint32_t)c;
+    csgs_status r;
+    size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
+    if ((r = ensure(ctx, ctx->ikeys_a, ib))) return r;
+    if ((r = ensure(ctx, ctx->ikeys_b, ib))) return r;
+    if ((r = ensure(ctx, ctx->ivals_a, ib))) return r;
+    if ((r = ensure(ctx, ctx->ivals_b, ib))) return r;
+    return CSGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void csgs_default_opts(csgs_score_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->resolution = CSGS_RES_PIXEL;
+    o->variant = CSGS_VAR_L1;
+    o->obj_w[0] = o->obj_w[1] = o->obj_w[2] = 1.f;
+    o->alpha_min = 1.f / 255.f;
+    o->rho_max = 0.99f;
+    o->t_min = 1e-4f;
+    o->cut2 = 9.f;
+    o->dilation = 0.3f;
+    o->clamp_fov = 1.3f;
+    o->view_batch = 0;
+    o->collect_stats = 0;
+}
+
+csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
+    if (!out) return CSGS_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return CSGS_E_INVAL;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return CSGS_E_CUDA;
+    csgs_ctx* ctx = new csgs_ctx();
+    ctx->device = device;
+    if (cuda_stream) {
+        ctx->st = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return CSGS_E_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->d_ctr, sizeof(DevCounters)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_nconst, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ctr, sizeof(DevCounters)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_S, sizeof(double) * 2) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_u32, sizeof(uint32_t) * 2) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        csgs_destroy(ctx);
+        return CSGS_E_NOMEM;
+    }
+    cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->st);
+    *out = ctx;
+    return CSGS_OK;
+}
+
+void csgs_destroy(csgs_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (auto& s : ctx->scenes) {
+        if (!s.alive) continue;
+        cudaFree(s.means);
+        cudaFree(s.log_scales);
+        cudaFree(s.quats);
+        cudaFree(s.opac);
+        cudaFree(s.sh);
+        cudaFree(s.d_cams);
+    }
+    DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,   &ctx->dkeys_b, &ctx->dvals_a, &ctx->dvals_b,
+                      &ctx->ikeys_a, &ctx->ikeys_b, &ctx->ivals_a, &ctx->ivals_b, &ctx->ranges,  &ctx->hist,
+                      &ctx->scan_tmp, &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
+                      &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull};
+    for (DevBuf* b : bufs) release(*b);
+    if (ctx->d_ctr) cudaFree(ctx->d_ctr);
+    if (ctx->d_nconst) cudaFree(ctx->d_nconst);
+    if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
+    if (ctx->h_S) cudaFreeHost(ctx->h_S);
+    if (ctx->h_u32) cudaFreeHost(ctx->h_u32);
+    for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
+    delete ctx;
+}
+
+const char* csgs_last_error(const csgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+csgs_status csgs_load_scene(csgs_ctx* ctx, const csgs_scene_desc* d, int32_t* scene_id) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!d || !scene_id) return fail(ctx, CSGS_E_INVAL, "null argument");
+    if (d->n <= 0 || d->n >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "scene size %lld out of range", (long long)d->n);
+    if (d->sh_degree < 0 || d->sh_degree > 3) return fail(ctx, CSGS_E_INVAL, "sh_degree %d not in 0..3", d->sh_degree);
+    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
+        return fail(ctx, CSGS_E_INVAL, "null attribute pointer");
+    cudaSetDevice(ctx->device);
+    SceneRec s;
+    s.n = d->n;
+    s.deg = d->sh_degree;
+    const size_t n = (size_t)d->n;
+    const size_t nk = (size_t)(d->sh_degree + 1) * (d->sh_degree + 1);
+    struct {
+        float** dst;
+        const float* src;
+        size_t count;
+    } parts[] = {{&s.means, d->means, 3 * n},
+                 {&s.log_scales, d->log_scales, 3 * n},
+                 {&s.quats, d->quats, 4 * n},
+                 {&s.opac, d->opacity_logits, n},
+                 {&s.sh, d->sh, 3 * nk * n}};
+    const cudaMemcpyKind kind = d->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
+    for (auto& p : parts) {
+        if (cudaMalloc(p.dst, p.count * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& q : parts)
+                if (*q.dst) cudaFree(*q.dst);
+            return fail(ctx, CSGS_E_NOMEM, "scene allocation failed");
+        }
+        CUDA_TRY(ctx, cudaMemcpyAsync(*p.dst, p.src, p.count * sizeof(float), kind, ctx->st));
+        launch_check_finite(*p.dst, (int64_t)p.count, ctx->d_ctr, ctx->st);
+    }
+    csgs_status r = read_counters(ctx);
+    if (r) return r;
+    if (ctx->h_ctr->err & kErrNonFinite) {
+        for (auto& q : parts) cudaFree(*q.dst);
+        return fail(ctx, CSGS_E_INVAL, "scene attributes contain non-finite values");
+    }
+    s.alive = true;
+    ctx->scenes.push_back(s);
+    *scene_id = (int32_t)ctx->scenes.size() - 1;
+    return CSGS_OK;
+}
+
+csgs_status csgs_free_scene(csgs_ctx* ctx, int32_t scene_id) {
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    cudaStreamSynchronize(ctx->st);
+    cudaFree(s->means);
+    cudaFree(s->log_scales);
+    cudaFree(s->quats);
+    cudaFree(s->opac);
+    cudaFree(s->sh);
+    cudaFree(s->d_cams);
+    *s = SceneRec();
+    return CSGS_OK;
+}
+
+csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera* cams, int32_t n_views) {
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!cams || n_views <= 0) return fail(ctx, CSGS_E_INVAL, "no cameras");
+    std::vector<CamDev> v(n_views);
+    for (int i = 0; i < n_views; ++i) {
+        const csgs_camera& c = cams[i];
+        if (!finite3(c.R, 9) || !finite3(c.t, 3) || !(c.fx > 0.f) || !(c.fy > 0.f) || !isfinite(c.cx) ||
+            !isfinite(c.cy) || c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384 ||
+            !(c.near_z > 0.f) || !isfinite(c.fx) || !isfinite(c.fy))
+            return fail(ctx, CSGS_E_INVAL, "camera %d is invalid", i);
+        CamDev& d = v[i];
+        memcpy(d.R, c.R, sizeof(d.R));
+        memcpy(d.t, c.t, sizeof(d.t));
+        d.fx = c.fx;
+        d.fy = c.fy;
+        d.cx = c.cx;
+        d.cy = c.cy;
+        d.W = c.width;
+        d.H = c.height;
+        d.near_z = c.near_z;
+        for (int k = 0; k < 3; ++k)
+            d.campos[k] = (float)(-((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]));
+        d.limx = 0.f;  // set per call from clamp_fov
+        d.limy = 0.f;
+        d.tiles_x = (c.width + kTile - 1) / kTile;
+        d.tiles_y = (c.height + kTile - 1) / kTile;
+    }
+    if (s->d_cams) {
+        cudaStreamSynchronize(ctx->st);
+        cudaFree(s->d_cams);
+        s->d_cams = nullptr;
+    }
+    CUDA_TRY(ctx, cudaMalloc(&s->d_cams, sizeof(CamDev) * n_views));
+    s->cams = v;
+    s->uploaded_clamp = -1.f;
+    return CSGS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Upload the cameras with the clamp limits of this call's options.
+csgs_status upload_cams(csgs_ctx* ctx, SceneRec* s, const KOpts& k) {
+    if (s->uploaded_clamp == k.clamp_fov) return CSGS_OK;
+    s->uploaded_clamp = k.clamp_fov;
+    for (auto& c : s->cams) {
+        c.limx = (float)((double)k.clamp_fov * 0.5 * c.W / c.fx);
+        c.limy = (float)((double)k.clamp_fov * 0.5 * c.H / c.fy);
+    }
+    CUDA_TRY(ctx, cudaMemcpyAsync(s->d_cams, s->cams.data(), sizeof(CamDev) * s->cams.size(), cudaMemcpyHostToDevice,
+                                  ctx->st));
+    // the host vector must outlive the copy
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    return CSGS_OK;
+}
+
+// Phase timer: events recorded on the stream around each phase; summed after the
+// stream has been synchronised.
+struct PhaseTimer {
+    csgs_ctx* ctx;
+    bool on;
+    size_t used = 0;
+    std::vector<std::pair<int, std::pair<size_t, size_t>>> spans;  // phase, (start, end) event index
+    cudaEvent_t mark() {
+        if (used == ctx->evpool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ctx->evpool.push_back(e);
+        }
+        cudaEvent_t e = ctx->evpool[used++];
+        cudaEventRecord(e, ctx->st);
+        return e;
+    }
+    size_t begin() {
+        if (!on) return 0;
+        mark();
+        return used - 1;
+    }
+    void end(int phase, size_t b) {
+        if (!on) return;
+        mark();
+        spans.push_back({phase, {b, used - 1}});
+    }
+    void sum(double* ms3) {
+        for (auto& sp : spans) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ctx->evpool[sp.second.first], ctx->evpool[sp.second.second]);
+            ms3[sp.first] += t;
+        }
+    }
+};
+
+int auto_view_batch(int64_t n, int nv, int req) {
+    if (req > 0) return req < nv ? req : nv;
+    int64_t per = n * (int64_t)(sizeof(Splat) + 12);
+    int64_t vb = ((int64_t)2 << 30) / (per > 0 ? per : 1);
+    if (vb < 1) vb = 1;
+    if (vb > 16) vb = 16;
+    if (vb > nv) vb = nv;
+    return (int)vb;
+}
+
+}  // namespace
+
+extern "C" {
+
+csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* s_dev, double* S_out) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s_dev) return fail(ctx, CSGS_E_INVAL, "s_dev is NULL");
+    if (s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "no query views set");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    if ((r = upload_cams(ctx, s, ko))) return r;
+    const int64_t n = s->n;
+    const int nv = (int)s->cams.size();
+    const int vb = auto_view_batch(n, nv, opts->view_batch);
+    int max_tiles = 0;
+    int64_t rays = 0;
+    for (auto& c : s->cams) {
+        if (c.tiles_x * c.tiles_y > max_tiles) max_tiles = c.tiles_x * c.tiles_y;
+        rays += (int64_t)c.W * c.H;
+    }
+    if ((r = ensure_view_buffers(ctx, n, vb, max_tiles))) return r;
+    if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
+    if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * 2))) return r;
+    const SceneDev sd = scene_dev(*s);
+    cudaStream_t st = ctx->st;
+    int retries = 0;
+    const long long l0 = launches();
+    PhaseTimer pt{ctx, (opts->collect_stats & 2) != 0};
+    long long comp_launches = 0;
+    for (;;) {
+        pt.used = 0;
+        pt.spans.clear();
+        comp_launches = 0;
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
+        set_u64(ctx->d_nconst, (unsigned long long)n, st);
+        CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
+        for (int v0 = 0; v0 < nv; v0 += vb) {
+            const int nb = (nv - v0) < vb ? (nv - v0) : vb;
+            size_t e0 = pt.begin();
+            launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
+                           P<uint2>(ctx->rects), st);
+            pt.end(0, e0);
+            for (int k = 0; k < nb; ++k) {
+                const CamDev& cam = s->cams[v0 + k];
+                uint32_t* keys_v = P<uint32_t>(ctx->keys) + (size_t)k * n;
+                const uint2* rects_v = P<uint2>(ctx->rects) + (size_t)k * n;
+                size_t e1 = pt.begin();
+                const uint32_t* iv = bin_view(ctx, n, keys_v, rects_v, cam);
+                pt.end(1, e1);
+                CompositeArgs a{};
+                a.ranges = P<uint2>(ctx->ranges);
+                a.inst_gid = iv;
+                a.splats = P<Splat>(ctx->splats) + (size_t)k * n;
+                a.n_gauss = (int)n;
+                a.cam = cam;
+                a.o = ko;
+                a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
+                a.s_sum = s_dev;
+                a.ctr = ctx->d_ctr;
+                a.stats = opts->collect_stats & 1;
+                size_t e2 = pt.begin();
+                launch_composite_score(a, st);
+                pt.end(2, e2);
+                ++comp_launches;
+            }
+            if ((r = launch_check(ctx, "score kernels"))) return r;
+        }
+        if (ko.resolution == CSGS_RES_SCENE) scene_normalise(s_dev, n, &ctx->d_ctr->sumA, st);
+        sum_scores(s_dev, n, P<double>(ctx->partial), P<double>(ctx->Sdev), st);
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if ((r = read_counters(ctx))) return r;
+        if (ctx->h_ctr->err & kErrCapacity) {
+            if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+            if ((r = grow_capacity(ctx))) return r;
+            continue;
+        }
+        break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.views = nv;
+    ctx->stats.rays = rays;
+    ctx->stats.instances = (int64_t)ctx->h_ctr->inst_total;
+    ctx->stats.pairs_evaluated = (int64_t)ctx->h_ctr->pairs_eval;
+    ctx->stats.pairs_hit = (int64_t)ctx->h_ctr->pairs_hit;
+    ctx->stats.pairs_evaluated2 = (int64_t)ctx->h_ctr->pairs_eval2;
+    ctx->stats.pairs_hit2 = (int64_t)ctx->h_ctr->pairs_hit2;
+    ctx->stats.capacity_retries = retries;
+    ctx->stats.score_ms = ms;
+    ctx->stats.kernel_launches = launches() - l0;
+    ctx->stats.composite_launches = comp_launches;
+    {
+        double ph[3] = {0.0, 0.0, 0.0};
+        pt.sum(ph);
+        ctx->stats.project_ms = ph[0];
+        ctx->stats.sort_ms = ph[1];
+        ctx->stats.composite_ms = ph[2];
+    }
+    const double S = ctx->h_S[0];
+    if (S_out) *S_out = S;
+    if (!(S > 0.0)) return fail(ctx, CSGS_E_EMPTY, "every query has A = 0: total sensitivity is zero");
+    return CSGS_OK;
+}
+
+static csgs_status sample_common(csgs_ctx* ctx, const double* p, int64_t n, int64_t m, uint64_t seed, int32_t* idx,
+                                 float* w, int64_t* n_distinct, int32_t* draws) {
+    csgs_status r;
+    const size_t nb = (size_t)(n + 2047) / 2048 + 64;
+    if ((r = ensure(ctx, ctx->C, sizeof(unsigned long long) * (size_t)n))) return r;
+    if ((r = ensure(ctx, ctx->counts, sizeof(uint32_t) * (size_t)n))) return r;
+    if ((r = ensure(ctx, ctx->ctmp, sizeof(unsigned long long) * nb))) return r;
+    if ((r = ensure(ctx, ctx->stmp, sizeof(uint32_t) * nb))) return r;
+    if ((r = ensure(ctx, ctx->nout, sizeof(uint32_t) * 2))) return r;
+    SampleTemp t;
+    t.partial = nullptr;
+    t.S = nullptr;
+    t.C = P<unsigned long long>(ctx->C);
+    t.counts = P<uint32_t>(ctx->counts);
+    t.scan_tmp = P<uint32_t>(ctx->stmp);
+    t.C_tmp = P<unsigned long long>(ctx->ctmp);
+    t.n_out = P<uint32_t>(ctx->nout);
+    sample_draws(p, n, m, seed, t, draws, idx, w, ctx->st);
+    if ((r = launch_check(ctx, "sampling kernels"))) return r;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_u32, t.n_out, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    if (n_distinct) *n_distinct = (int64_t)ctx->h_u32[0];
+    return CSGS_OK;
+}
+
+csgs_status csgs_sample_coreset(csgs_ctx* ctx, const float* s_dev, int64_t n, int64_t m, uint64_t seed,
+                                int32_t* idx_dev, float* w_dev, int64_t* n_distinct) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!s_dev || !idx_dev || !w_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
+    if (n <= 0 || n >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "n = %lld out of range", (long long)n);
+    if (m <= 0 || m >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "m = %lld out of range", (long long)m);
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
+    if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * 2))) return r;
+    if ((r = ensure(ctx, ctx->p, sizeof(double) * (size_t)n))) return r;
+    sum_scores(s_dev, n, P<double>(ctx->partial), P<double>(ctx->Sdev), ctx->st);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    const double S = ctx->h_S[0];
+    if (!isfinite(S) || S < 0.0) return fail(ctx, CSGS_E_INVAL, "scores are negative or not finite");
+    if (!(S > 0.0)) return fail(ctx, CSGS_E_EMPTY, "total sensitivity is zero");
+    probabilities_from_scores(s_dev, n, P<double>(ctx->Sdev), P<double>(ctx->p), ctx->st);
+    return sample_common(ctx, P<double>(ctx->p), n, m, seed, idx_dev, w_dev, n_distinct, nullptr);
+}
+
+csgs_status csgs_sample_coreset_p(csgs_ctx* ctx, const double* p_dev, int64_t n, int64_t m, uint64_t seed,
+                                  int32_t* idx_dev, float* w_dev, int64_t* n_distinct, int32_t* draws_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!p_dev || !idx_dev || !w_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
+    if (n <= 0 || n >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "n = %lld out of range", (long long)n);
+    if (m <= 0 || m >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "m = %lld out of range", (long long)m);
+    cudaSetDevice(ctx->device);
+    return sample_common(ctx, p_dev, n, m, seed, idx_dev, w_dev, n_distinct, draws_dev);
+}
+
+csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev, const float* w_dev,
+                        int64_t n_sel, const csgs_score_opts* opts, float* rgb_dev, float* T_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
+    if (!rgb_dev) return fail(ctx, CSGS_E_INVAL, "rgb_dev is NULL");
+    if ((idx_dev == nullptr) != (w_dev == nullptr)) return fail(ctx, CSGS_E_INVAL, "idx and w must both be given");
+    if (idx_dev && (n_sel < 0 || n_sel > s->n)) return fail(ctx, CSGS_E_INVAL, "n_sel out of range");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    if ((r = upload_cams(ctx, s, ko))) return r;
+    const int64_t n = s->n;
+    const CamDev& cam = s->cams[view];
+    if ((r = ensure_view_buffers(ctx, n, 1, cam.tiles_x * cam.tiles_y))) return r;
+    cudaStream_t st = ctx->st;
+    const float* wts = nullptr;
+    if (idx_dev) {
+        if ((r = ensure(ctx, ctx->wfull, sizeof(float) * (size_t)n))) return r;
+        wts = P<float>(ctx->wfull);
+    }
+    set_u64(ctx->d_nconst, (unsigned long long)n, st);
+    const SceneDev sd = scene_dev(*s);
+    int retries = 0;
+    const long long l0 = launches();
+    for (;;) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
+        if (idx_dev) {
+            CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
+            scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
+        }
+        launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
+                       P<uint2>(ctx->rects), st);
+        const uint32_t* iv = bin_view(ctx, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam);
+        CompositeArgs a{};
+        a.ranges = P<uint2>(ctx->ranges);
+        a.inst_gid = iv;
+        a.splats = P<Splat>(ctx->splats);
+        a.n_gauss = (int)n;
+        a.cam = cam;
+        a.o = ko;
+        a.rgb = rgb_dev;
+        a.T = T_dev;
+        a.ctr = ctx->d_ctr;
+        a.stats = opts->collect_stats & 1;
+        launch_composite_render(a, st);
+        if ((r = launch_check(ctx, "render kernels"))) return r;
+        if ((r = read_counters(ctx))) return r;
+        if (ctx->h_ctr->err & kErrCapacity) {
+            if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+            if ((r = grow_capacity(ctx))) return r;
+            continue;
+        }
+        break;
+    }
+    if (ctx->h_ctr->err & kErrIndex) return fail(ctx, CSGS_E_INVAL, "coreset index out of range");
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    ctx->stats.views = 1;
+    ctx->stats.rays = (int64_t)cam.W * cam.H;
+    ctx->stats.instances = (int64_t)ctx->h_ctr->inst_total;
+    ctx->stats.pairs_evaluated = (int64_t)ctx->h_ctr->pairs_eval;
+    ctx->stats.pairs_hit = (int64_t)ctx->h_ctr->pairs_hit;
+    ctx->stats.violations = (int64_t)ctx->h_ctr->violations;
+    ctx->stats.capacity_retries = retries;
+    ctx->stats.kernel_launches = launches() - l0;
+    ctx->stats.composite_launches = 1 + retries;
+    return CSGS_OK;
+}
+
+int64_t csgs_kernel_launch_count(void) { return (int64_t)launches(); }
+
+csgs_status csgs_sync(csgs_ctx* ctx) {
+    if (!ctx) return CSGS_E_INVAL;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    return CSGS_OK;
+}
+
+csgs_status csgs_get_stats(csgs_ctx* ctx, csgs_stats* out) {
+    if (!ctx || !out) return CSGS_E_INVAL;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    *out = ctx->stats;
+    return CSGS_OK;
+}
+
+csgs_status csgs_debug_project(csgs_ctx* ctx, int32_t scene_id, int32_t view, const csgs_score_opts* opts,
+                               float* out_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
+    if (!out_dev) return fail(ctx, CSGS_E_INVAL, "out_dev is NULL");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    if ((r = upload_cams(ctx, s, ko))) return r;
+    launch_debug_project(scene_dev(*s), s->d_cams + view, ko, out_dev, ctx->st);
+    return launch_check(ctx, "debug projection");
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Internal declarations of the sm_103a sensitivity-scoring path (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "csgs.h"
+
+namespace csgs {
+
+// Number of kernels this library has launched (all contexts); every launch site adds to it.
+void count_launches(long long k);
+long long launches();
+
+constexpr int kTile = 16;          // screen tile edge (pixels); one CTA composites one tile
+constexpr int kTilePix = kTile * kTile;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-view camera, precomputed on the host from csgs_camera.
+struct CamDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int W, H;
+    float near_z;
+    float campos[3];   // -R^T t
+    float limx, limy;  // clamp_fov * tan(half FOV) per axis
+    int tiles_x, tiles_y;
+};
+
+struct SceneDev {
+    int n;
+    int deg;
+    const float* means;
+    const float* log_scales;
+    const float* quats;
+    const float* opac;
+    const float* sh;
+};
+
+// Scoring conventions in the form the kernels use.
+struct KOpts {
+    float alpha_min, rho_max, t_min;
+    float pcut;       // footprint cut in the scaled exponent domain: -0.5 log2(e) cut2
+    float cut2;
+    float dilation, clamp_fov;
+    float ow0, ow1, ow2;  // per-pixel objective weights
+    int resolution, variant;
+};
+
+// One projected Gaussian in one view (48 bytes, 16-byte aligned).
+//   m = (mean x hi, mean y hi, mean x lo, mean y lo): the pixel-space mean as an
+//       unevaluated two-float sum, so the tile-relative offset keeps FP32 accuracy
+//   q = (qa, qb, qc, opacity): exponent2 = qa dx^2 + qb dx dy + qc dy^2 is the
+//       base-2 exponent of the kernel value, i.e. the conic scaled by -0.5 log2(e)
+//   c = (r, g, b, depth)
+struct __align__(16) Splat {
+    float4 m;
+    float4 q;
+    float4 c;
+};
+
+// Device error word bits.
+enum : uint32_t { kErrCapacity = 1u, kErrNonFinite = 2u, kErrIndex = 4u };
+
+// Device counters (one block per context).
+struct DevCounters {
+    uint32_t err;
+    uint32_t pad;
+    unsigned long long n_inst;      // instances of the current view (may exceed capacity)
+    unsigned long long max_inst;    // maximum over views
+    unsigned long long inst_total;  // sum over views
+    unsigned long long pairs_eval;
+    unsigned long long pairs_hit;
+    unsigned long long pairs_eval2;
+    unsigned long long pairs_hit2;
+    unsigned long long violations;
+    double sumA;                    // scene resolution: sum of the objective over queries
+};
+
+// ---- launchers (k_project.cu)
+void launch_project(const SceneDev& sc, const CamDev* d_cams, int nv, const float* d_w, const KOpts& o,
+                    Splat* splats, uint32_t* keys, uint2* rects, cudaStream_t st);
+void launch_debug_project(const SceneDev& sc, const CamDev* d_cam, const KOpts& o, float* out, cudaStream_t st);
+void launch_check_finite(const float* p, int64_t n, DevCounters* ctr, cudaStream_t st);
+// wfull[idx[k]] = w[k] (indices outside [0, n) set kErrIndex and are skipped)
+void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* wfull, int64_t n, DevCounters* ctr,
+                     cudaStream_t st);
+
+// ---- sorting and scans (k_sort.cu)
+struct SortTemp {
+    uint32_t* hist;  // 256 * kSortBlocks
+};
+constexpr int kSortBlocks = 148 * 4;
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  n is read from
+// d_n (device) and clamped to n_max.  Returns which buffer holds the result (0: a, 1: b).
+int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,
+                     uint32_t n_max, int bits, uint32_t* hist, cudaStream_t st);
+// Gaussians in depth order -> (tile, gid) instances in depth order; writes the
+// instance count to ctr->n_inst.  scan_tmp: >= 2 * ceil(n / 2048) + 64 words.
+void emit_instances(const uint32_t* order, const uint32_t* sorted_keys, const uint2* rects, int n, int tiles_x,
+                    uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
+                    cudaStream_t st);
+void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
+                 cudaStream_t st);
+void iota_u32(uint32_t* v, int n, cudaStream_t st);
+void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
+
+// ---- compositing (k_composite.cu)
+struct CompositeArgs {
+    const uint2* ranges;
+    const uint32_t* inst_gid;
+    const Splat* splats;
+    int n_gauss;
+    CamDev cam;
+    KOpts o;
+    float* rgb;        // render: [H][W][3]
+    float* T;          // render: [H][W] (optional)
+    uint32_t* s_bits;  // pixel resolution: float bits of s, atomicMax
+    float* s_sum;      // scene resolution: sum of terms, atomicAdd
+    DevCounters* ctr;
+    int stats;
+};
+void launch_composite_render(const CompositeArgs& a, cudaStream_t st);
+void launch_composite_score(const CompositeArgs& a, cudaStream_t st);
+
+// ---- sampling (k_sample.cu)
+struct SampleTemp {
+    double* partial;      // >= 1024
+    double* S;            // 1
+    unsigned long long* C;  // n
+    uint32_t* counts;     // n
+    uint32_t* scan_tmp;   // >= 2 * ceil(n / 2048) + 64
+    unsigned long long* C_tmp;  // >= 2 * ceil(n / 2048) + 64
+    uint32_t* n_out;      // 1
+};
+void sum_scores(const float* s, int64_t n, double* partial, double* S, cudaStream_t st);
+void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st);
+void probabilities_from_scores(const float* s, int64_t n, const double* S, double* p, cudaStream_t st);
+void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const SampleTemp& t, int32_t* draws,
+                  int32_t* idx, float* w, cudaStream_t st);
+
+}  // namespace csgs

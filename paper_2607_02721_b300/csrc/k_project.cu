@@ -1,0 +1,361 @@
+// EWA projection of Gaussians into query views (the kernel k(g, q) of Sec. 3,
+// "Scalar rendering function"), batched over views: each thread loads one
+// Gaussian's attributes from the structure-of-arrays scene once (coalesced HBM
+// reads), builds its 3-D covariance once, and projects it into every view of the
+// batch.  Per (view, Gaussian) it writes a 48-byte splat record, a depth key and a
+// tile rectangle.
+#include <math.h>
+
+#include "csgs_internal.cuh"
+
+namespace csgs {
+namespace {
+
+// Error-free transformations (Dekker / Knuth) for the two-float camera transform.
+__device__ __forceinline__ float2 two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return make_float2(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fadd_rn(s, -a);
+    float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return make_float2(s, __fadd_rn(b, -__fadd_rn(s, a)));
+}
+
+// r0 x + r1 y + r2 z + t as a two-float value (compensated dot product, Ogita,
+// Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, Dot2).
+__device__ __forceinline__ float2 dot3_plus(float r0, float r1, float r2, float t, float x, float y, float z) {
+    float2 p = two_prod(r0, x);
+    float h = p.x, s = p.y;
+    float2 q = two_prod(r1, y);
+    float2 u = two_sum(h, q.x);
+    h = u.x;
+    s = __fadd_rn(s, __fadd_rn(u.y, q.y));
+    q = two_prod(r2, z);
+    u = two_sum(h, q.x);
+    h = u.x;
+    s = __fadd_rn(s, __fadd_rn(u.y, q.y));
+    u = two_sum(h, t);
+    h = u.x;
+    s = __fadd_rn(s, u.y);
+    return fast_two_sum(h, s);
+}
+
+// f * (a / b) + c for two-float a, b; result as a two-float value.
+__device__ __forceinline__ float2 persp(float f, float2 a, float2 b, float c) {
+    float q1 = __fdiv_rn(a.x, b.x);
+    float r = __fmaf_rn(-q1, b.x, a.x);
+    r = __fadd_rn(r, a.y);
+    r = __fmaf_rn(-q1, b.y, r);
+    float q2 = __fdiv_rn(r, b.x);
+    float2 p = two_prod(f, q1);
+    float e = __fmaf_rn(f, q2, p.y);
+    float2 s = two_sum(p.x, c);
+    return fast_two_sum(s.x, __fadd_rn(s.y, e));
+}
+
+struct Proj {
+    bool valid;
+    float2 mx, my;       // two-float pixel-space mean
+    float ca, cb, cc;    // 2-D covariance (dilated)
+    float ia, ib, ic;    // conic
+    float depth, op;
+    float rgb[3];
+    uint32_t tx0, ty0, tx1, ty1;
+};
+
+// Real SH basis (degree <= 3) along unit direction (x, y, z); the sign convention of
+// the 3DGS colour model.  Constants are the closed-form normalisations.
+template <int DEG>
+__device__ __forceinline__ void sh_colour(const float* shc, float x, float y, float z, float rgb[3]) {
+    float Y[16];
+    Y[0] = 0.28209479177387814f;
+    if (DEG >= 1) {
+        Y[1] = -0.48860251190291992f * y;
+        Y[2] = 0.48860251190291992f * z;
+        Y[3] = -0.48860251190291992f * x;
+    }
+    if (DEG >= 2) {
+        float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.54627421529603959f * (xx - yy);
+        if (DEG >= 3) {
+            Y[9] = -0.59004358992664352f * y * (3.f * xx - yy);
+            Y[10] = 2.8906114426405538f * x * y * z;
+            Y[11] = -0.45704579946446572f * y * (4.f * zz - xx - yy);
+            Y[12] = 0.37317633259011540f * z * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -0.45704579946446572f * x * (4.f * zz - xx - yy);
+            Y[14] = 1.4453057213202769f * z * (xx - yy);
+            Y[15] = -0.59004358992664352f * x * (xx - 3.f * yy);
+        }
+    }
+    constexpr int K = (DEG + 1) * (DEG + 1);
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc = fmaf(shc[3 * k + ch], Y[k], acc);
+        acc += 0.5f;
+        rgb[ch] = fmaxf(acc, 0.f);
+    }
+}
+
+template <int DEG>
+__device__ __forceinline__ void project_one(const float mu[3], const float cov3[6], float op, const float* shc,
+                                            const CamDev& c, const KOpts& o, Proj& r) {
+    r.valid = false;
+    float2 X = dot3_plus(c.R[0], c.R[1], c.R[2], c.t[0], mu[0], mu[1], mu[2]);
+    float2 Yc = dot3_plus(c.R[3], c.R[4], c.R[5], c.t[1], mu[0], mu[1], mu[2]);
+    float2 Z = dot3_plus(c.R[6], c.R[7], c.R[8], c.t[2], mu[0], mu[1], mu[2]);
+    float z = Z.x;
+    if (!(z > c.near_z)) return;
+    if (!(op >= o.alpha_min)) return;  // rho <= alpha < alpha_min everywhere
+
+    // camera-space covariance  Sc = R Sigma R^T   (Sigma symmetric: 00 01 02 11 12 22)
+    const float s00 = cov3[0], s01 = cov3[1], s02 = cov3[2], s11 = cov3[3], s12 = cov3[4], s22 = cov3[5];
+    float T[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float a0 = c.R[3 * i], a1 = c.R[3 * i + 1], a2 = c.R[3 * i + 2];
+        T[3 * i + 0] = a0 * s00 + a1 * s01 + a2 * s02;
+        T[3 * i + 1] = a0 * s01 + a1 * s11 + a2 * s12;
+        T[3 * i + 2] = a0 * s02 + a1 * s12 + a2 * s22;
+    }
+    float Sc[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Sc[3 * i + j] = T[3 * i] * c.R[3 * j] + T[3 * i + 1] * c.R[3 * j + 1] + T[3 * i + 2] * c.R[3 * j + 2];
+
+    // Jacobian of the perspective map linearised at the (clamped) mean
+    const float invz = 1.f / z;
+    float txz = fminf(fmaxf(X.x * invz, -c.limx), c.limx);
+    float tyz = fminf(fmaxf(Yc.x * invz, -c.limy), c.limy);
+    const float j00 = c.fx * invz, j02 = -c.fx * txz * invz;
+    const float j11 = c.fy * invz, j12 = -c.fy * tyz * invz;
+    // cov2 = J Sc J^T
+    const float u0 = j00 * Sc[0] + j02 * Sc[6], u1 = j00 * Sc[1] + j02 * Sc[7], u2 = j00 * Sc[2] + j02 * Sc[8];
+    const float v1 = j11 * Sc[4] + j12 * Sc[7], v2 = j11 * Sc[5] + j12 * Sc[8];
+    float ca = u0 * j00 + u2 * j02 + o.dilation;
+    float cb = u1 * j11 + u2 * j12;
+    float cc = v1 * j11 + v2 * j12 + o.dilation;
+    // determinant with Kahan's compensated 2x2 formula
+    float w = __fmul_rn(cb, cb);
+    float e = __fmaf_rn(-cb, cb, w);
+    float det = __fadd_rn(__fmaf_rn(ca, cc, -w), e);
+    if (!(det > 0.f)) return;
+    const float idet = 1.f / det;
+
+    float2 mx = persp(c.fx, X, Z, c.cx);
+    float2 my = persp(c.fy, Yc, Z, c.cy);
+
+    // pixel bounding box of the ellipse d^T cov^-1 d <= cut2 (|dx| <= sqrt(cut2 cov_xx)),
+    // widened slightly so FP32 rounding can never exclude a pixel that passes
+    const float rx = sqrtf(o.cut2 * ca) * 1.001f + 0.01f;
+    const float ry = sqrtf(o.cut2 * cc) * 1.001f + 0.01f;
+    float fx0 = ceilf(mx.x - rx), fx1 = floorf(mx.x + rx);
+    float fy0 = ceilf(my.x - ry), fy1 = floorf(my.x + ry);
+    fx0 = fmaxf(fx0, 0.f);
+    fy0 = fmaxf(fy0, 0.f);
+    fx1 = fminf(fx1, (float)(c.W - 1));
+    fy1 = fminf(fy1, (float)(c.H - 1));
+    if (!(fx0 <= fx1) || !(fy0 <= fy1)) return;
+    r.tx0 = (uint32_t)fx0 / kTile;
+    r.ty0 = (uint32_t)fy0 / kTile;
+    r.tx1 = (uint32_t)fx1 / kTile + 1;
+    r.ty1 = (uint32_t)fy1 / kTile + 1;
+
+    // colour along camera centre -> mean
+    float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];
+    float inv = 1.f / sqrtf(dx * dx + dy * dy + dz * dz);
+    sh_colour<DEG>(shc, dx * inv, dy * inv, dz * inv, r.rgb);
+
+    r.valid = true;
+    r.mx = mx;
+    r.my = my;
+    r.ca = ca;
+    r.cb = cb;
+    r.cc = cc;
+    r.ia = cc * idet;
+    r.ib = -cb * idet;
+    r.ic = ca * idet;
+    r.depth = z;
+    r.op = op;
+}
+
+// Loads the Gaussian's attributes and builds Sigma = Rq diag(s)^2 Rq^T.
+template <int DEG>
+__device__ __forceinline__ void load_gaussian(const SceneDev& sc, int i, const float* wts, float mu[3], float cov3[6],
+                                              float& op, float* shc) {
+    const int n = sc.n;
+    mu[0] = __ldg(sc.means + i);
+    mu[1] = __ldg(sc.means + n + i);
+    mu[2] = __ldg(sc.means + 2 * n + i);
+    const float sx = expf(__ldg(sc.log_scales + i));
+    const float sy = expf(__ldg(sc.log_scales + n + i));
+    const float sz = expf(__ldg(sc.log_scales + 2 * n + i));
+    float qw = __ldg(sc.quats + i), qx = __ldg(sc.quats + n + i), qy = __ldg(sc.quats + 2 * n + i),
+          qz = __ldg(sc.quats + 3 * n + i);
+    const float qn = 1.f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qn;
+    qx *= qn;
+    qy *= qn;
+    qz *= qn;
+    const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz), r02 = 2.f * (qx * qz + qw * qy);
+    const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz), r12 = 2.f * (qy * qz - qw * qx);
+    const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx), r22 = 1.f - 2.f * (qx * qx + qy * qy);
+    // M = Rq diag(s); Sigma = M M^T
+    const float m00 = r00 * sx, m01 = r01 * sy, m02 = r02 * sz;
+    const float m10 = r10 * sx, m11 = r11 * sy, m12 = r12 * sz;
+    const float m20 = r20 * sx, m21 = r21 * sy, m22 = r22 * sz;
+    cov3[0] = m00 * m00 + m01 * m01 + m02 * m02;
+    cov3[1] = m00 * m10 + m01 * m11 + m02 * m12;
+    cov3[2] = m00 * m20 + m01 * m21 + m02 * m22;
+    cov3[3] = m10 * m10 + m11 * m11 + m12 * m12;
+    cov3[4] = m10 * m20 + m11 * m21 + m12 * m22;
+    cov3[5] = m20 * m20 + m21 * m21 + m22 * m22;
+    op = 1.f / (1.f + expf(-__ldg(sc.opac + i)));
+    if (wts) op *= __ldg(wts + i);
+    constexpr int K = (DEG + 1) * (DEG + 1);
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) shc[3 * k + ch] = __ldg(sc.sh + (size_t)(3 * k + ch) * n + i);
+}
+
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __restrict__ cams, int nv,
+                                                 const float* __restrict__ wts, KOpts o, Splat* __restrict__ splats,
+                                                 uint32_t* __restrict__ keys, uint2* __restrict__ rects) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n) return;
+    float mu[3], cov3[6], op;
+    float shc[3 * (DEG + 1) * (DEG + 1)];
+    load_gaussian<DEG>(sc, i, wts, mu, cov3, op, shc);
+    const float K = -0.5f * kLog2e;
+    for (int v = 0; v < nv; ++v) {
+        const CamDev& c = cams[v];
+        Proj r;
+        project_one<DEG>(mu, cov3, op, shc, c, o, r);
+        const size_t off = (size_t)v * sc.n + i;
+        if (!r.valid) {
+            keys[off] = 0xFFFFFFFFu;
+            rects[off] = make_uint2(0u, 0u);
+            continue;
+        }
+        Splat s;
+        s.m = make_float4(r.mx.x, r.my.x, r.mx.y, r.my.y);
+        s.q = make_float4(K * r.ia, 2.f * K * r.ib, K * r.ic, r.op);
+        s.c = make_float4(r.rgb[0], r.rgb[1], r.rgb[2], r.depth);
+        splats[off] = s;
+        keys[off] = __float_as_uint(r.depth);
+        rects[off] = make_uint2(r.tx0 | (r.ty0 << 16), r.tx1 | (r.ty1 << 16));
+    }
+}
+
+template <int DEG>
+__global__ void k_debug_project(SceneDev sc, const CamDev* __restrict__ cam, KOpts o, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n) return;
+    float mu[3], cov3[6], op;
+    float shc[3 * (DEG + 1) * (DEG + 1)];
+    load_gaussian<DEG>(sc, i, nullptr, mu, cov3, op, shc);
+    Proj r;
+    project_one<DEG>(mu, cov3, op, shc, *cam, o, r);
+    float* d = out + (size_t)16 * i;
+    d[0] = r.valid ? 1.f : 0.f;
+    if (!r.valid) {
+        for (int k = 1; k < 16; ++k) d[k] = 0.f;
+        return;
+    }
+    d[1] = r.mx.x;
+    d[2] = r.my.x;
+    d[3] = r.ia;
+    d[4] = r.ib;
+    d[5] = r.ic;
+    d[6] = r.ca;
+    d[7] = r.cb;
+    d[8] = r.cc;
+    d[9] = r.depth;
+    d[10] = r.op;
+    d[11] = r.rgb[0];
+    d[12] = r.rgb[1];
+    d[13] = r.rgb[2];
+    d[14] = (float)((r.tx1 - r.tx0) * (r.ty1 - r.ty0));
+    d[15] = r.mx.y;
+}
+
+__global__ void k_check_finite(const float* __restrict__ p, int64_t n, DevCounters* ctr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (; i < n; i += stride) bad |= !isfinite(p[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->err, kErrNonFinite);
+}
+
+__global__ void k_scatter_weights(const int32_t* __restrict__ idx, const float* __restrict__ w, int64_t n_sel,
+                                  float* __restrict__ wfull, int64_t n, DevCounters* ctr) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_sel; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = idx[k];
+        if (i < 0 || i >= n) {
+            atomicOr(&ctr->err, kErrIndex);
+            continue;
+        }
+        wfull[i] = w[k];
+    }
+}
+
+}  // namespace
+
+void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* wfull, int64_t n, DevCounters* ctr,
+                     cudaStream_t st) {
+    if (n_sel <= 0) return;
+    int64_t blocks = (n_sel + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_scatter_weights<<<(int)blocks, 256, 0, st>>>(idx, w, n_sel, wfull, n, ctr);
+    count_launches(1);
+}
+
+void launch_project(const SceneDev& sc, const CamDev* d_cams, int nv, const float* d_w, const KOpts& o, Splat* splats,
+                    uint32_t* keys, uint2* rects, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (sc.n + threads - 1) / threads;
+    switch (sc.deg) {
+        case 0: k_project<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
+        case 1: k_project<1><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
+        case 2: k_project<2><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
+        default: k_project<3><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
+    }
+    count_launches(1);
+}
+
+void launch_debug_project(const SceneDev& sc, const CamDev* d_cam, const KOpts& o, float* out, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (sc.n + threads - 1) / threads;
+    switch (sc.deg) {
+        case 0: k_debug_project<0><<<blocks, threads, 0, st>>>(sc, d_cam, o, out); break;
+        case 1: k_debug_project<1><<<blocks, threads, 0, st>>>(sc, d_cam, o, out); break;
+        case 2: k_debug_project<2><<<blocks, threads, 0, st>>>(sc, d_cam, o, out); break;
+        default: k_debug_project<3><<<blocks, threads, 0, st>>>(sc, d_cam, o, out); break;
+    }
+    count_launches(1);
+}
+
+void launch_check_finite(const float* p, int64_t n, DevCounters* ctr, cudaStream_t st) {
+    if (n <= 0) return;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    k_check_finite<<<(int)blocks, 256, 0, st>>>(p, n, ctr);
+    count_launches(1);
+}
+
+}  // namespace csgs

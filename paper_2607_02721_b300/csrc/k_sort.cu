@@ -1,0 +1,342 @@
+// Binning of projected Gaussians into screen tiles in front-to-back order (the order
+// "induced by the view depths", Sec. 3 "Scalar rendering function"):
+//   1. stable LSD radix sort of all Gaussians of a view by depth (ties keep index order);
+//   2. one fused scan + emit pass that writes (tile, gid) instances in depth order;
+//   3. stable LSD radix sort of the instances by tile id only;
+//   4. per-tile [start, end) ranges.
+// Every tile list is therefore sorted by (depth, Gaussian index).  No CUB: the sort is
+// a reduce-then-scan radix sort with warp-level stable ranking (match.any).
+#include "csgs_internal.cuh"
+
+namespace csgs {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortGroups = 4;                               // 32-key groups per warp per sub-tile
+constexpr int kSubTile = kSortThreads * kSortGroups;          // 1024 keys
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;         // 2048
+
+__device__ __forceinline__ void sort_chunk(uint32_t n, int b, uint32_t& begin, uint32_t& end) {
+    uint32_t per = (n + kSortBlocks - 1) / kSortBlocks;
+    per = (per + kSubTile - 1) / kSubTile * kSubTile;
+    if (per < kSubTile) per = kSubTile;
+    uint64_t bg = (uint64_t)per * b;
+    begin = bg < n ? (uint32_t)bg : n;
+    uint64_t en = bg + per;
+    end = en < n ? (uint32_t)en : n;
+}
+
+__device__ __forceinline__ uint32_t read_n(const unsigned long long* d_n, uint32_t n_max) {
+    unsigned long long v = *d_n;
+    return v < n_max ? (uint32_t)v : n_max;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys,
+                                                          const unsigned long long* d_n, uint32_t n_max, int shift,
+                                                          uint32_t* __restrict__ hist) {
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t n = read_n(d_n, n_max);
+    uint32_t begin, end;
+    sort_chunk(n, blockIdx.x, begin, end);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = begin; base < end; base += kSortThreads) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t d = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[threadIdx.x * kSortBlocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of the digit-major histogram (256 x kSortBlocks) in one CTA: each
+// thread owns a contiguous run, sums it, the CTA scans the run sums, then each
+// thread rewrites its run with the running prefix.
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist) {
+    constexpr int total = 256 * kSortBlocks;
+    constexpr int per = (total + 1023) / 1024;
+    __shared__ uint32_t warp_sums[32];
+    const int tid = threadIdx.x;
+    const int b0 = tid * per;
+    uint32_t sum = 0;
+    for (int k = 0; k < per; ++k) {
+        int idx = b0 + k;
+        if (idx < total) sum += hist[idx];
+    }
+    uint32_t x = sum;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - sum + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    for (int k = 0; k < per; ++k) {
+        int idx = b0 + k;
+        if (idx < total) {
+            uint32_t c = hist[idx];
+            hist[idx] = run;
+            run += c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                             const uint32_t* __restrict__ vin,
+                                                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                             const unsigned long long* d_n, uint32_t n_max, int shift,
+                                                             const uint32_t* __restrict__ hist) {
+    __shared__ uint32_t wcnt[kSortWarps][257];
+    __shared__ uint32_t base[256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    base[tid] = hist[tid * kSortBlocks + blockIdx.x];
+    for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    const uint32_t n = read_n(d_n, n_max);
+    uint32_t begin, end;
+    sort_chunk(n, blockIdx.x, begin, end);
+    for (uint32_t sub = begin; sub < end; sub += kSubTile) {
+        uint32_t key[kSortGroups], val[kSortGroups], dig[kSortGroups], rank[kSortGroups];
+#pragma unroll
+        for (int g = 0; g < kSortGroups; ++g) {
+            uint32_t i = sub + warp * (32 * kSortGroups) + g * 32 + lane;
+            bool ok = i < end;
+            key[g] = ok ? __ldg(kin + i) : 0u;
+            val[g] = ok ? __ldg(vin + i) : 0u;
+            dig[g] = ok ? (key[g] >> shift) & 255u : 256u;
+        }
+#pragma unroll
+        for (int g = 0; g < kSortGroups; ++g) {
+            uint32_t d = dig[g];
+            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            rank[g] = wcnt[warp][d] + __popc(peers & lt);
+            __syncwarp();
+            if (lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {
+            uint32_t run = base[tid];
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = run;
+                run += c;
+            }
+            base[tid] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int g = 0; g < kSortGroups; ++g) {
+            if (dig[g] < 256u) {
+                uint32_t pos = wcnt[warp][dig[g]] + rank[g];
+                kout[pos] = key[g];
+                vout[pos] = val[g];
+            }
+        }
+        __syncthreads();
+        for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ uint32_t tile_count(uint2 r) {
+    uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu, y1 = r.y >> 16;
+    return (x1 - x0) * (y1 - y0);
+}
+
+// block-wide exclusive scan of one value per thread; returns the prefix, *total the sum
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t pre = x - v + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __restrict__ order,
+                                                              const uint2* __restrict__ rects, int n,
+                                                              uint32_t* __restrict__ partial) {
+    __shared__ uint32_t ws[32];
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int j = base + k;
+        if (j < n) sum += tile_count(__ldg(rects + __ldg(order + j)));
+    }
+    uint32_t tot;
+    block_exclusive_scan(sum, ws, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the per-block totals in one CTA (any count), plus the grand total.
+__global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ partial, int nb, DevCounters* ctr) {
+    __shared__ uint32_t ws[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        int i = b0 + threadIdx.x;
+        uint32_t v = i < nb ? partial[i] : 0u;
+        uint32_t tot;
+        uint32_t pre = block_exclusive_scan(v, ws, &tot);
+        unsigned long long c = carry;
+        if (i < nb) partial[i] = (uint32_t)(c + pre);
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && ctr) {
+        unsigned long long t = carry;
+        ctr->n_inst = t;
+        ctr->inst_total += t;
+        if (t > ctr->max_inst) ctr->max_inst = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __restrict__ order,
+                                                            const uint2* __restrict__ rects, int n, int tiles_x,
+                                                            const uint32_t* __restrict__ partial,
+                                                            uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
+                                                            uint32_t cap, DevCounters* ctr) {
+    __shared__ uint32_t ws[32];
+    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    uint32_t cnt[kScanItems], gid[kScanItems];
+    uint2 rc[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int j = base + k;
+        gid[k] = j < n ? __ldg(order + j) : 0u;
+        rc[k] = j < n ? __ldg(rects + gid[k]) : make_uint2(0u, 0u);
+        cnt[k] = tile_count(rc[k]);
+        sum += cnt[k];
+    }
+    uint32_t tot;
+    uint32_t off = block_exclusive_scan(sum, ws, &tot) + partial[blockIdx.x];
+    bool overflow = false;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (cnt[k]) {
+            if ((unsigned long long)off + cnt[k] > cap) {
+                overflow = true;
+            } else {
+                const uint32_t x0 = rc[k].x & 0xFFFFu, y0 = rc[k].x >> 16, x1 = rc[k].y & 0xFFFFu,
+                               y1 = rc[k].y >> 16;
+                uint32_t o = off;
+                for (uint32_t ty = y0; ty < y1; ++ty)
+                    for (uint32_t tx = x0; tx < x1; ++tx) {
+                        ikeys[o] = ty * (uint32_t)tiles_x + tx;
+                        ivals[o] = gid[k];
+                        ++o;
+                    }
+            }
+        }
+        off += cnt[k];
+    }
+    if (overflow) atomicOr(&ctr->err, kErrCapacity);
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_n, uint32_t n_max,
+                         uint2* __restrict__ ranges, uint32_t n_tiles) {
+    const uint32_t n = read_n(d_n, n_max);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t t = keys[i];
+        if (t >= n_tiles) continue;  // only after a capacity overflow (reported)
+        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
+        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+    }
+}
+
+__global__ void k_iota(uint32_t* v, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+}  // namespace
+
+int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, const unsigned long long* d_n,
+                     uint32_t n_max, int bits, uint32_t* hist, cudaStream_t st) {
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        uint32_t* kin = cur ? kb : ka;
+        uint32_t* vin = cur ? vb : va;
+        uint32_t* kout = cur ? ka : kb;
+        uint32_t* vout = cur ? va : vb;
+        k_rs_hist<<<kSortBlocks, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
+        count_launches(1);
+        k_rs_scan<<<1, 1024, 0, st>>>(hist);
+        count_launches(1);
+        k_rs_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist);
+        count_launches(1);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+void emit_instances(const uint32_t* order, const uint32_t* /*sorted_keys*/, const uint2* rects, int n, int tiles_x,
+                    uint32_t* ikeys, uint32_t* ivals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
+                    cudaStream_t st) {
+    const int nb = (n + kScanChunk - 1) / kScanChunk;
+    k_emit_reduce<<<nb, kScanThreads, 0, st>>>(order, rects, n, scan_tmp);
+    count_launches(1);
+    k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nb, ctr);
+    count_launches(1);
+    k_emit_down<<<nb, kScanThreads, 0, st>>>(order, rects, n, tiles_x, scan_tmp, ikeys, ivals, cap, ctr);
+    count_launches(1);
+}
+
+void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
+                 cudaStream_t st) {
+    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, st);
+    int blocks = (int)((n_max + 255) / 256);
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    if (blocks < 1) blocks = 1;
+    k_ranges<<<blocks, 256, 0, st>>>(keys, d_n, n_max, ranges, (uint32_t)n_tiles);
+    count_launches(1);
+}
+
+void iota_u32(uint32_t* v, int n, cudaStream_t st) { k_iota<<<(n + 255) / 256, 256, 0, st>>>(v, n); }
+
+void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) { k_set_u64<<<1, 1, 0, st>>>(p, v); }
+
+}  // namespace csgs

@@ -108,19 +108,20 @@ def mixture_scene(n: int, components: int = 64, sh_degree: int = 3, seed: int = 
         sig = np.exp(rng.uniform(math.log(0.1), math.log(1.0), 3))
         chol[k] = _random_rotation(rng) * sig[None, :]
     comp = rng.integers(0, components, n)
-    z = rng.standard_normal((n, 3))
-    means = cm[comp] + np.einsum("nij,nj->ni", chol[comp], z)
-    log_scales = rng.normal(-4.0, 0.5, (3, n))
+    z = rng.standard_normal((n, 3, 1))
+    means = cm[comp] + np.matmul(chol[comp], z)[:, :, 0]
+    log_scales = rng.standard_normal((3, n), dtype=np.float32)
+    log_scales *= 0.5
+    log_scales -= 4.0
     surf = rng.random(n) < surface_frac
     axis = rng.integers(0, 3, n)
     log_scales[axis[surf], np.nonzero(surf)[0]] = -7.0
     quats = _unit_quats(rng, n)
-    opac = rng.standard_normal(n)
+    opac = rng.standard_normal(n, dtype=np.float32)
     k = (sh_degree + 1) ** 2
-    sh = rng.normal(0.0, 0.2, (k, 3, n))
-    return Scene(np.ascontiguousarray(means.T, dtype=np.float32),
-                 log_scales.astype(np.float32), quats,
-                 opac.astype(np.float32), sh.astype(np.float32))
+    sh = rng.standard_normal((k, 3, n), dtype=np.float32)
+    sh *= 0.2
+    return Scene(np.ascontiguousarray(means.T, dtype=np.float32), log_scales, quats, opac, sh)
 
 
 def look_at(center, target=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0)):

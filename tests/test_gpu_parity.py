@@ -1,0 +1,318 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated for the path's results):
+  rendered colours        1e-5 absolute
+  sensitivities           1e-3 relative where the oracle's value exceeds 1e-6
+  coreset indices         bit-exact when the GPU sampler gets the oracle's p and seed
+Pixels where FP32 and FP64 can take a threshold decision differently (the oracle's
+straddle flags: footprint cut, alpha_min, t_min, near-equal depths) are excluded from
+the element-wise comparison and their share is bounded; Gaussians contributing to such
+pixels are compared through bounds instead.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Opts
+import paper_2607_02721_b300 as csgs
+from paper_2607_02721_b300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+RGB_TOL = 1e-5
+S_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    build.build()
+    c = csgs.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def small():
+    sc, cams, m = synth.workload_small()
+    return sc, cams, m, oracle.SceneArrays(sc)
+
+
+@pytest.fixture(scope="module")
+def small_sid(ctx, small):
+    sc, cams, _, _ = small
+    sid = ctx.load_scene(sc)
+    ctx.set_queries(sid, cams)
+    return sid
+
+
+def render_gpu(ctx, sid, cam, view, **kw):
+    H, W = int(cam[17]), int(cam[16])
+    out = ctx.render(sid, view, H=H, W=W, **kw)
+    return out
+
+
+# ---------------------------------------------------------------- projection
+
+def test_projection_matches_oracle(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    for v in (0, 5):
+        g = ctx.debug_project(small_sid, v).cpu().numpy().astype(np.float64)
+        o = oracle.project(sa, cams[v])
+        ov = o[:, 0] > 0
+        gv = g[:, 0] > 0
+        # the GPU additionally culls Gaussians that cannot touch the image or whose
+        # opacity is below alpha_min; every GPU-valid one is oracle-valid
+        assert np.all(ov[gv])
+        vv = gv
+        mx = g[vv, 1] + g[vv, 15]
+        np.testing.assert_allclose(mx, o[vv, 1], rtol=0, atol=2e-5)
+        np.testing.assert_allclose(g[vv, 2], o[vv, 2], rtol=0, atol=2e-4)
+        np.testing.assert_allclose(g[vv, 9], o[vv, 9], rtol=2e-7)
+        np.testing.assert_allclose(g[vv, 6:9], o[vv, 6:9], rtol=2e-5, atol=1e-6)
+        np.testing.assert_allclose(g[vv, 3:6], o[vv, 3:6], rtol=5e-5, atol=1e-5)
+        np.testing.assert_allclose(g[vv, 10], o[vv, 10], rtol=1e-6)
+        np.testing.assert_allclose(g[vv, 11:14], o[vv, 11:14], atol=2e-6)
+
+
+# ---------------------------------------------------------------- render
+
+def compare_render(rgb_gpu, ref, max_flag_frac=0.01):
+    fl = ref["flags"].astype(bool)
+    d = np.abs(rgb_gpu.astype(np.float64) - ref["rgb"])
+    assert fl.mean() <= max_flag_frac, fl.mean()
+    worst = d[~fl].max() if (~fl).any() else 0.0
+    assert worst <= RGB_TOL, (worst, np.unravel_index(np.argmax(np.where(fl[..., None], 0, d)), d.shape))
+    return worst, fl.mean()
+
+
+def test_render_matches_oracle_small(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    for v in range(len(cams)):
+        rgb = render_gpu(ctx, small_sid, cams[v], v).cpu().numpy()
+        ref = oracle.render(sa, cams[v])
+        compare_render(rgb, ref)
+
+
+def test_render_transmittance_matches_oracle(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    rgb, T = ctx.render(small_sid, 3, H=128, W=128, with_T=True)
+    ref = oracle.render(sa, cams[3])
+    fl = ref["flags"].astype(bool)
+    np.testing.assert_allclose(T.cpu().numpy()[~fl], ref["T"][~fl], atol=2e-5)
+
+
+# ---------------------------------------------------------------- score
+
+def check_scores(s_gpu, S_gpu, ref, min_val=1e-6):
+    s_gpu = s_gpu.astype(np.float64)
+    s = ref["s"]
+    clean = ~ref["touched"] & (s > min_val)
+    rel = np.abs(s_gpu[clean] - s[clean]) / s[clean]
+    assert rel.max() <= S_RTOL, (rel.max(), np.argmax(rel))
+    # touched Gaussians: the GPU max is over a superset of the clean queries
+    t = ref["touched"] & (ref["s_clean"] > min_val)
+    assert np.all(s_gpu[t] >= ref["s_clean"][t] * (1 - S_RTOL))
+    assert ref["touched"].mean() < 0.05
+    assert abs(S_gpu - ref["S"]) <= 5e-3 * ref["S"]
+
+
+def test_score_pixel_matches_oracle_small(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    s, S = ctx.score(small_sid)
+    ref = oracle.score(sa, cams)
+    check_scores(s.cpu().numpy(), S, ref)
+    assert 1.0 <= S <= min(sc.n, ref["queries"]) * (1 + 1e-6)
+
+
+def test_score_scene_matches_oracle_small(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    s, S = ctx.score(small_sid, csgs.default_opts(resolution=csgs.RES_SCENE))
+    ref = oracle.score(sa, cams, Opts(resolution=oracle.RES_SCENE))
+    s = s.cpu().numpy().astype(np.float64)
+    big = ref["s"] > 1e-6
+    rel = np.abs(s[big] - ref["s"][big]) / ref["s"][big]
+    # per-scene sums include flagged pixels on both sides; their share is tiny
+    assert np.quantile(rel, 0.999) <= S_RTOL
+    assert abs(S - 1.0) < 1e-4
+
+
+def test_score_luminance_objective(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    wl = (0.299, 0.587, 0.114)
+    s, S = ctx.score(small_sid, csgs.default_opts(obj_w=wl))
+    ref = oracle.score(sa, cams, Opts(obj_w=wl))
+    check_scores(s.cpu().numpy(), S, ref)
+
+
+def test_score_is_deterministic(ctx, small_sid):
+    a, Sa = ctx.score(small_sid)
+    b, Sb = ctx.score(small_sid)
+    assert Sa == Sb
+    assert bool((a == b).all())
+
+
+def test_view_batching_does_not_change_scores(ctx, small_sid):
+    a, Sa = ctx.score(small_sid, csgs.default_opts(view_batch=1))
+    b, Sb = ctx.score(small_sid, csgs.default_opts(view_batch=8))
+    assert bool((a == b).all()) and Sa == Sb
+
+
+# ---------------------------------------------------------------- sampling
+
+def test_sampler_bit_exact_with_oracle_probabilities(ctx, small, torch):
+    sc, cams, m, sa = small
+    ref = oracle.score(sa, cams)
+    p, S = oracle.probabilities(ref["s"])
+    for seed in (0, 1, 123456789):
+        o = oracle.sample(p, m, seed)
+        idx, w, draws = ctx.sample_coreset_p(torch.tensor(p, device="cuda"), m, seed, return_draws=True)
+        np.testing.assert_array_equal(draws.cpu().numpy(), o["J"])
+        np.testing.assert_array_equal(idx.cpu().numpy(), o["idx"])
+        np.testing.assert_array_equal(w.cpu().numpy(), o["w_sel"].astype(np.float32))
+
+
+def test_sampler_from_gpu_scores(ctx, small_sid, small, torch):
+    sc, cams, m, sa = small
+    s, S = ctx.score(small_sid)
+    idx, w = ctx.sample_coreset(s, m, 7)
+    idx_np, w_np = idx.cpu().numpy(), w.cpu().numpy()
+    assert len(idx_np) <= m and np.all(np.diff(idx_np) > 0) and np.all(w_np > 0)
+    # the same draws from the oracle given the GPU's scores
+    p, _ = oracle.probabilities(s.cpu().numpy().astype(np.float64))
+    o = oracle.sample(p, m, 7)
+    agree = np.intersect1d(idx_np, o["idx"]).size / max(len(o["idx"]), 1)
+    assert agree > 0.995
+
+
+def test_sampler_edge_cases(ctx, torch):
+    z = torch.zeros(10, device="cuda")
+    with pytest.raises(csgs.CsgsError) as e:
+        ctx.sample_coreset(z, 5, 0)
+    assert e.value.status == csgs.CSGS_E_EMPTY
+    one = torch.zeros(10, device="cuda")
+    one[3] = 2.0
+    idx, w = ctx.sample_coreset(one, 17, 0)
+    assert idx.tolist() == [3] and abs(w.item() - 1.0) < 1e-7
+    with pytest.raises(csgs.CsgsError):
+        ctx.sample_coreset(one, 0, 0)
+
+
+# ---------------------------------------------------------------- weighted render
+
+def test_weighted_render_matches_oracle(ctx, small, small_sid, torch):
+    sc, cams, m, sa = small
+    ref = oracle.score(sa, cams)
+    p, S = oracle.probabilities(ref["s"])
+    o = oracle.sample(p, m, 11)
+    w32 = o["w_sel"].astype(np.float32)
+    wfull = np.zeros(sc.n)
+    wfull[o["idx"]] = w32.astype(np.float64)
+    idx_t = torch.tensor(o["idx"], device="cuda", dtype=torch.int32)
+    w_t = torch.tensor(w32, device="cuda")
+    for v in (0, 6):
+        rgb = ctx.render(small_sid, v, idx=idx_t, w=w_t, H=128, W=128, opts=csgs.default_opts(collect_stats=1))
+        st = ctx.stats()
+        r = oracle.render(sa, cams[v], w=wfull)
+        compare_render(rgb.cpu().numpy(), r)
+        assert abs(st["violations"] - r["violations"]) <= max(2, 0.01 * r["violations"])
+
+
+def test_unit_weights_render_bit_identical(ctx, small, small_sid, torch):
+    sc, cams, _, _ = small
+    full = ctx.render(small_sid, 2, H=128, W=128)
+    idx = torch.arange(sc.n, device="cuda", dtype=torch.int32)
+    w = torch.ones(sc.n, device="cuda")
+    wr = ctx.render(small_sid, 2, idx=idx, w=w, H=128, W=128)
+    assert bool((full == wr).all())
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_ragged_image_and_tiny_scene(ctx, torch):
+    sc = synth.uniform_cube_scene(300, seed=4)
+    R, t = synth.look_at([0.0, -3.0, 0.5])
+    cams = np.stack([synth.make_camera(R, t, 37, 23), synth.make_camera(R, t, 1, 1), synth.make_camera(R, t, 70, 17)])
+    sid = ctx.load_scene(sc)
+    ctx.set_queries(sid, cams)
+    sa = oracle.SceneArrays(sc)
+    for v in range(3):
+        H, W = int(cams[v][17]), int(cams[v][16])
+        rgb = ctx.render(sid, v, H=H, W=W).cpu().numpy()
+        compare_render(rgb, oracle.render(sa, cams[v]), max_flag_frac=0.05)
+    s, S = ctx.score(sid)
+    ref = oracle.score(sa, cams)
+    check_scores(s.cpu().numpy(), S, ref)
+    ctx.free_scene(sid)
+
+
+def test_single_gaussian_has_unit_sensitivity(ctx):
+    sc = synth.uniform_cube_scene(1, seed=0)
+    sc.means[:] = 0.0
+    sc.log_scales[:] = -2.5
+    sid = ctx.load_scene(sc)
+    ctx.set_queries(sid, synth.cube_corner_cameras(3.0, 64, 48))
+    s, S = ctx.score(sid)
+    assert abs(s.item() - 1.0) < 1e-6 and abs(S - 1.0) < 1e-6
+    ctx.free_scene(sid)
+
+
+def test_empty_query_set_reports_zero_sensitivity(ctx):
+    sc = synth.uniform_cube_scene(50, seed=0)
+    sc.means[2] = -10.0  # everything behind the cameras below
+    sid = ctx.load_scene(sc)
+    R, t = synth.look_at([0.0, 0.0, -20.0], target=[0.0, 0.0, -40.0])
+    ctx.set_queries(sid, synth.make_camera(R, t, 32, 32)[None])
+    with pytest.raises(csgs.CsgsError) as e:
+        ctx.score(sid)
+    assert e.value.status == csgs.CSGS_E_EMPTY
+    ctx.free_scene(sid)
+
+
+def test_invalid_arguments(ctx, small_sid):
+    sc = synth.uniform_cube_scene(10, seed=0)
+    sc.means[0, 3] = np.nan
+    with pytest.raises(csgs.CsgsError) as e:
+        ctx.load_scene(sc)
+    assert e.value.status == csgs.CSGS_E_INVAL
+    with pytest.raises(csgs.CsgsError):
+        ctx.render(small_sid, 99, H=8, W=8)
+    bad = synth.cube_corner_cameras(3.0, 16, 16)[:1].copy()
+    bad[0, 12] = -1.0  # fx <= 0
+    with pytest.raises(csgs.CsgsError):
+        ctx.set_queries(small_sid, bad)
+    with pytest.raises(csgs.CsgsError):
+        ctx.score(small_sid, csgs.default_opts(resolution=7))
+
+
+def test_instance_capacity_growth(ctx, torch):
+    # big splats covering a 1024x1024 view: ~2000 x 4096 instances, far above the
+    # initial capacity of this context, exercise the grow-and-retry path
+    c2 = csgs.Context(0)
+    sc = synth.uniform_cube_scene(2000, seed=9)
+    sc.log_scales[:] = 0.0
+    sid = c2.load_scene(sc)
+    cams = synth.cube_corner_cameras(3.0, 1024, 1024)[:1]
+    c2.set_queries(sid, cams)
+    s, S = c2.score(sid)
+    st = c2.stats()
+    assert st["capacity_retries"] >= 1 and st["instances"] > (1 << 20)
+    sa = oracle.SceneArrays(sc)
+    rng = np.random.default_rng(0)
+    pix = rng.integers(0, 1024, (64, 2))
+    ref = oracle.render(sa, cams[0], pixels=pix)
+    rgb = c2.render(sid, 0, H=1024, W=1024).cpu().numpy()
+    got = rgb[pix[:, 1], pix[:, 0]]
+    ok = ~ref["flags"].astype(bool)
+    assert np.abs(got[ok] - ref["rgb"][ok]).max() <= RGB_TOL
+    c2.close()
