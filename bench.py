@@ -250,6 +250,8 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     scene, cams = workload(args.workload)
+    if args.max_views:
+        cams = cams[: args.max_views]
     cfg = describe(args.workload, scene, cams)
     m = cfg["coreset_m"]
     stream = torch.cuda.Stream(device=local)
@@ -259,9 +261,9 @@ def run_ours(args):
     s = torch.empty(scene.n, dtype=torch.float32, device=f"cuda:{local}")
 
     # pair counts of one pass (untimed; counting kernels are slower)
-    ctx.score(sid, csgs.default_opts(collect_stats=1), out=s)
+    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch), out=s)
     cnt = ctx.stats()
-    timing = csgs.default_opts(collect_stats=2)
+    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch)
 
     def step(seed):
         ctx.score(sid, timing, out=s)
@@ -383,6 +385,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--max-views", type=int, default=0, help="score only the first views (profiling runs)")
+    ap.add_argument("--view-batch", type=int, default=0, help="views projected per launch (0 = automatic)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -142,21 +142,35 @@ def kernel_launch_count() -> int:
 
 
 class Context:
-    """One CUDA device + stream.  Methods mirror the csgs_* entry points."""
+    """One CUDA device + stream.  Methods mirror the csgs_* entry points.
+
+    The library runs on ``self.stream`` (a torch stream, so tensors allocated for its
+    outputs belong to it).  Before a call reads caller tensors the stream waits for the
+    caller's current stream; after a call writes tensors the caller's stream waits for
+    the library's stream."""
 
     def __init__(self, device: int = 0, stream=None):
         import torch
 
         self.torch = torch
         self.device = torch.device("cuda", device)
-        self._stream = stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
         h = ctypes.c_void_p()
-        st = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
-        r = lib().csgs_create(ctypes.byref(h), device, st)
+        r = lib().csgs_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream))
         if r != CSGS_OK:
             raise CsgsError(r, "csgs_create failed")
         self.h = h
         self._scenes = {}
+
+    def _in(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream(self.device))
+
+    def _out(self):
+        self.torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    def _empty(self, shape, dtype):
+        with self.torch.cuda.stream(self.stream):
+            return self.torch.empty(shape, dtype=dtype, device=self.device)
 
     def _check(self, r):
         if r != CSGS_OK:
@@ -182,7 +196,8 @@ class Context:
         torch = self.torch
         arrs = [scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh]
         if on_device:
-            keep = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(self.device) for a in arrs]
+            with torch.cuda.stream(self.stream):
+                keep = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(self.device) for a in arrs]
             ptrs = [t.data_ptr() for t in keep]
         else:
             keep = [np.ascontiguousarray(a, dtype=np.float32) for a in arrs]
@@ -191,6 +206,7 @@ class Context:
         deg = {1: 0, 4: 1, 9: 2, 16: 3}[k]
         d = SceneDesc(int(keep[0].shape[1]), deg, 1 if on_device else 0, *ptrs)
         sid = ctypes.c_int32()
+        self._in()
         self._check(lib().csgs_load_scene(self.h, ctypes.byref(d), ctypes.byref(sid)))
         self._scenes[sid.value] = int(keep[0].shape[1])
         return sid.value
@@ -198,6 +214,7 @@ class Context:
     def load_scene_ptrs(self, n: int, sh_degree: int, ptrs, is_device: bool) -> int:
         d = SceneDesc(n, sh_degree, 1 if is_device else 0, *ptrs)
         sid = ctypes.c_int32()
+        self._in()
         self._check(lib().csgs_load_scene(self.h, ctypes.byref(d), ctypes.byref(sid)))
         self._scenes[sid.value] = n
         return sid.value
@@ -216,29 +233,35 @@ class Context:
         torch = self.torch
         n = self._scenes[sid]
         if out is None:
-            out = torch.empty(n, dtype=torch.float32, device=self.device)
+            out = self._empty(n, torch.float32)
         S = ctypes.c_double()
         opts = opts or default_opts()
+        self._in()
         self._check(lib().csgs_score(self.h, sid, ctypes.byref(opts), _ptr(out), ctypes.byref(S)))
+        self._out()
         return out, S.value
 
     def sample_coreset(self, s, m: int, seed: int):
         torch = self.torch
-        idx = torch.empty(m, dtype=torch.int32, device=self.device)
-        w = torch.empty(m, dtype=torch.float32, device=self.device)
+        idx = self._empty(m, torch.int32)
+        w = self._empty(m, torch.float32)
         nd = ctypes.c_int64()
+        self._in()
         self._check(lib().csgs_sample_coreset(self.h, _ptr(s), s.numel(), m, seed, _ptr(idx), _ptr(w),
                                               ctypes.byref(nd)))
+        self._out()
         return idx[: nd.value], w[: nd.value]
 
     def sample_coreset_p(self, p, m: int, seed: int, return_draws: bool = False):
         torch = self.torch
-        idx = torch.empty(m, dtype=torch.int32, device=self.device)
-        w = torch.empty(m, dtype=torch.float32, device=self.device)
-        draws = torch.empty(m, dtype=torch.int32, device=self.device) if return_draws else None
+        idx = self._empty(m, torch.int32)
+        w = self._empty(m, torch.float32)
+        draws = self._empty(m, torch.int32) if return_draws else None
         nd = ctypes.c_int64()
+        self._in()
         self._check(lib().csgs_sample_coreset_p(self.h, _ptr(p), p.numel(), m, seed, _ptr(idx), _ptr(w),
                                                 ctypes.byref(nd), _ptr(draws)))
+        self._out()
         if return_draws:
             return idx[: nd.value], w[: nd.value], draws
         return idx[: nd.value], w[: nd.value]
@@ -247,20 +270,24 @@ class Context:
                with_T: bool = False, out=None):
         torch = self.torch
         if out is None:
-            out = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
-        T = torch.empty((H, W), dtype=torch.float32, device=self.device) if with_T else None
+            out = self._empty((H, W, 3), torch.float32)
+        T = self._empty((H, W), torch.float32) if with_T else None
         n_sel = 0 if idx is None else idx.numel()
         opts = opts or default_opts()
+        self._in()
         self._check(lib().csgs_render(self.h, sid, view, _ptr(idx), _ptr(w), n_sel, ctypes.byref(opts), _ptr(out),
                                       _ptr(T)))
+        self._out()
         return (out, T) if with_T else out
 
     def debug_project(self, sid: int, view: int, opts: ScoreOpts | None = None):
         torch = self.torch
         n = self._scenes[sid]
-        out = torch.empty((n, 16), dtype=torch.float32, device=self.device)
+        out = self._empty((n, 16), torch.float32)
         opts = opts or default_opts()
+        self._in()
         self._check(lib().csgs_debug_project(self.h, sid, view, ctypes.byref(opts), _ptr(out)))
+        self._out()
         return out
 
     def sync(self):
