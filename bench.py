@@ -163,19 +163,24 @@ def _oracle_step(sa, cams, pixels):
 
 def _calibrate(sa, cams, budget_s):
     """Pixel count of view 0 that the oracle scores in about ``budget_s`` seconds
-    (None: the whole workload fits)."""
+    (None: the whole workload fits).  Two timed probes, each with enough pixels per
+    thread to load every core, give the per-pixel cost and the per-call overhead."""
+    import oracle
+
+    th = max(1, oracle.num_threads())
+    p0, p1 = 16 * th, 64 * th
     t = time.perf_counter()
-    _oracle_step(sa, cams, _center_pixels(cams, 32))
+    _oracle_step(sa, cams, _center_pixels(cams, p0))
+    t0 = time.perf_counter() - t
+    t = time.perf_counter()
+    _oracle_step(sa, cams, _center_pixels(cams, p1))
     t1 = time.perf_counter() - t
-    t = time.perf_counter()
-    _oracle_step(sa, cams, _center_pixels(cams, 96))
-    t2 = time.perf_counter() - t
-    per_px = max((t2 - t1) / 64, 1e-7)
-    overhead = max(t1 - 32 * per_px, 0.0)
+    per_px = max((t1 - t0) / (p1 - p0), t1 / p1 * 0.25, 1e-9)
+    overhead = max(t1 - p1 * per_px, 0.0)
     rays = int(sum(int(c[16]) * int(c[17]) for c in cams))
     if overhead * len(cams) + rays * per_px <= budget_s:
         return None
-    return int(max(32, (budget_s - overhead) / per_px))
+    return int(max(p0, min((budget_s - overhead) / per_px, p1 * budget_s / max(t1, 1e-6) * 2)))
 
 
 def cpu_baseline(name, scene, cams, budget_s: float):

@@ -88,10 +88,8 @@ void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* w
                      cudaStream_t st);
 
 // ---- sorting and scans (k_sort.cu)
-struct SortTemp {
-    uint32_t* hist;  // 256 * kSortBlocks
-};
 constexpr int kSortBlocks = 148 * 4;
+constexpr int kSortHistWords = 256 * kSortBlocks + 256;  // per-block digit counts + digit totals
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  n is read from
 // d_n (device) and clamped to n_max.  Returns which buffer holds the result (0: a, 1: b).
 int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,

@@ -7,61 +7,14 @@
 #include <math.h>
 
 #include "csgs_internal.cuh"
+#include "ffmath.cuh"
 
 namespace csgs {
 namespace {
 
-// Error-free transformations (Dekker / Knuth) for the two-float camera transform.
-__device__ __forceinline__ float2 two_prod(float a, float b) {
-    float p = __fmul_rn(a, b);
-    return make_float2(p, __fmaf_rn(a, b, -p));
-}
-__device__ __forceinline__ float2 two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fadd_rn(s, -a);
-    float e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
-    return make_float2(s, e);
-}
-__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    return make_float2(s, __fadd_rn(b, -__fadd_rn(s, a)));
-}
-
-// r0 x + r1 y + r2 z + t as a two-float value (compensated dot product, Ogita,
-// Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, Dot2).
-__device__ __forceinline__ float2 dot3_plus(float r0, float r1, float r2, float t, float x, float y, float z) {
-    float2 p = two_prod(r0, x);
-    float h = p.x, s = p.y;
-    float2 q = two_prod(r1, y);
-    float2 u = two_sum(h, q.x);
-    h = u.x;
-    s = __fadd_rn(s, __fadd_rn(u.y, q.y));
-    q = two_prod(r2, z);
-    u = two_sum(h, q.x);
-    h = u.x;
-    s = __fadd_rn(s, __fadd_rn(u.y, q.y));
-    u = two_sum(h, t);
-    h = u.x;
-    s = __fadd_rn(s, u.y);
-    return fast_two_sum(h, s);
-}
-
-// f * (a / b) + c for two-float a, b; result as a two-float value.
-__device__ __forceinline__ float2 persp(float f, float2 a, float2 b, float c) {
-    float q1 = __fdiv_rn(a.x, b.x);
-    float r = __fmaf_rn(-q1, b.x, a.x);
-    r = __fadd_rn(r, a.y);
-    r = __fmaf_rn(-q1, b.y, r);
-    float q2 = __fdiv_rn(r, b.x);
-    float2 p = two_prod(f, q1);
-    float e = __fmaf_rn(f, q2, p.y);
-    float2 s = two_sum(p.x, c);
-    return fast_two_sum(s.x, __fadd_rn(s.y, e));
-}
-
 struct Proj {
     bool valid;
-    float2 mx, my;       // two-float pixel-space mean
+    ff::F2 mx, my;       // two-float pixel-space mean
     float ca, cb, cc;    // 2-D covariance (dilated)
     float ia, ib, ic;    // conic
     float depth, op;
@@ -112,10 +65,10 @@ template <int DEG>
 __device__ __forceinline__ void project_one(const float mu[3], const float cov3[6], float op, const float* shc,
                                             const CamDev& c, const KOpts& o, Proj& r) {
     r.valid = false;
-    float2 X = dot3_plus(c.R[0], c.R[1], c.R[2], c.t[0], mu[0], mu[1], mu[2]);
-    float2 Yc = dot3_plus(c.R[3], c.R[4], c.R[5], c.t[1], mu[0], mu[1], mu[2]);
-    float2 Z = dot3_plus(c.R[6], c.R[7], c.R[8], c.t[2], mu[0], mu[1], mu[2]);
-    float z = Z.x;
+    const ff::F2 X = ff::dot3_plus(c.R[0], c.R[1], c.R[2], c.t[0], mu[0], mu[1], mu[2]);
+    const ff::F2 Yc = ff::dot3_plus(c.R[3], c.R[4], c.R[5], c.t[1], mu[0], mu[1], mu[2]);
+    const ff::F2 Z = ff::dot3_plus(c.R[6], c.R[7], c.R[8], c.t[2], mu[0], mu[1], mu[2]);
+    const float z = Z.hi;
     if (!(z > c.near_z)) return;
     if (!(op >= o.alpha_min)) return;  // rho <= alpha < alpha_min everywhere
 
@@ -138,8 +91,8 @@ __device__ __forceinline__ void project_one(const float mu[3], const float cov3[
 
     // Jacobian of the perspective map linearised at the (clamped) mean
     const float invz = 1.f / z;
-    float txz = fminf(fmaxf(X.x * invz, -c.limx), c.limx);
-    float tyz = fminf(fmaxf(Yc.x * invz, -c.limy), c.limy);
+    float txz = fminf(fmaxf(X.hi * invz, -c.limx), c.limx);
+    float tyz = fminf(fmaxf(Yc.hi * invz, -c.limy), c.limy);
     const float j00 = c.fx * invz, j02 = -c.fx * txz * invz;
     const float j11 = c.fy * invz, j12 = -c.fy * tyz * invz;
     // cov2 = J Sc J^T
@@ -155,15 +108,15 @@ __device__ __forceinline__ void project_one(const float mu[3], const float cov3[
     if (!(det > 0.f)) return;
     const float idet = 1.f / det;
 
-    float2 mx = persp(c.fx, X, Z, c.cx);
-    float2 my = persp(c.fy, Yc, Z, c.cy);
+    const ff::F2 mx = ff::persp(c.fx, X, Z, c.cx);
+    const ff::F2 my = ff::persp(c.fy, Yc, Z, c.cy);
 
     // pixel bounding box of the ellipse d^T cov^-1 d <= cut2 (|dx| <= sqrt(cut2 cov_xx)),
     // widened slightly so FP32 rounding can never exclude a pixel that passes
     const float rx = sqrtf(o.cut2 * ca) * 1.001f + 0.01f;
     const float ry = sqrtf(o.cut2 * cc) * 1.001f + 0.01f;
-    float fx0 = ceilf(mx.x - rx), fx1 = floorf(mx.x + rx);
-    float fy0 = ceilf(my.x - ry), fy1 = floorf(my.x + ry);
+    float fx0 = ceilf(mx.hi - rx), fx1 = floorf(mx.hi + rx);
+    float fy0 = ceilf(my.hi - ry), fy1 = floorf(my.hi + ry);
     fx0 = fmaxf(fx0, 0.f);
     fy0 = fmaxf(fy0, 0.f);
     fx1 = fminf(fx1, (float)(c.W - 1));
@@ -253,7 +206,7 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __re
             continue;
         }
         Splat s;
-        s.m = make_float4(r.mx.x, r.my.x, r.mx.y, r.my.y);
+        s.m = make_float4(r.mx.hi, r.my.hi, r.mx.lo, r.my.lo);
         s.q = make_float4(K * r.ia, 2.f * K * r.ib, K * r.ic, r.op);
         s.c = make_float4(r.rgb[0], r.rgb[1], r.rgb[2], r.depth);
         splats[off] = s;
@@ -277,8 +230,8 @@ __global__ void k_debug_project(SceneDev sc, const CamDev* __restrict__ cam, KOp
         for (int k = 1; k < 16; ++k) d[k] = 0.f;
         return;
     }
-    d[1] = r.mx.x;
-    d[2] = r.my.x;
+    d[1] = r.mx.hi;
+    d[2] = r.my.hi;
     d[3] = r.ia;
     d[4] = r.ib;
     d[5] = r.ic;
@@ -291,7 +244,7 @@ __global__ void k_debug_project(SceneDev sc, const CamDev* __restrict__ cam, KOp
     d[12] = r.rgb[1];
     d[13] = r.rgb[2];
     d[14] = (float)((r.tx1 - r.tx0) * (r.ty1 - r.ty0));
-    d[15] = r.mx.y;
+    d[15] = r.mx.lo;
 }
 
 __global__ void k_check_finite(const float* __restrict__ p, int64_t n, DevCounters* ctr) {

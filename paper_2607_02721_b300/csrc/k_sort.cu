@@ -54,60 +54,64 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
     hist[threadIdx.x * kSortBlocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of the digit-major histogram (256 x kSortBlocks) in one CTA: each
-// thread owns a contiguous run, sums it, the CTA scans the run sums, then each
-// thread rewrites its run with the running prefix.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist) {
-    constexpr int total = 256 * kSortBlocks;
-    constexpr int per = (total + 1023) / 1024;
-    __shared__ uint32_t warp_sums[32];
-    const int tid = threadIdx.x;
-    const int b0 = tid * per;
-    uint32_t sum = 0;
+// Exclusive scan of each digit's row of the histogram (kSortBlocks per-block counts),
+// one CTA per digit; the row totals go to row_total[256].
+__global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist, uint32_t* __restrict__ row_total) {
+    constexpr int per = (kSortBlocks + 255) / 256;
+    __shared__ uint32_t ws[8];
+    uint32_t* row = hist + (size_t)blockIdx.x * kSortBlocks;
+    const int b0 = threadIdx.x * per;
+    uint32_t v[per], sum = 0;
+#pragma unroll
     for (int k = 0; k < per; ++k) {
-        int idx = b0 + k;
-        if (idx < total) sum += hist[idx];
+        v[k] = b0 + k < kSortBlocks ? row[b0 + k] : 0u;
+        sum += v[k];
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = sum;
-    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) warp_sums[warp] = x;
+    if (lane == 31) ws[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = warp_sums[lane];
+    uint32_t pre = x - sum;
+    for (int w = 0; w < warp; ++w) pre += ws[w];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        warp_sums[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = x - sum + (warp > 0 ? warp_sums[warp - 1] : 0u);
     for (int k = 0; k < per; ++k) {
-        int idx = b0 + k;
-        if (idx < total) {
-            uint32_t c = hist[idx];
-            hist[idx] = run;
-            run += c;
-        }
+        if (b0 + k < kSortBlocks) row[b0 + k] = pre;
+        pre += v[k];
     }
+    if (threadIdx.x == 255) row_total[blockIdx.x] = pre;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                              const unsigned long long* d_n, uint32_t n_max, int shift,
-                                                             const uint32_t* __restrict__ hist) {
+                                                             const uint32_t* __restrict__ hist,
+                                                             const uint32_t* __restrict__ row_total) {
     __shared__ uint32_t wcnt[kSortWarps][257];
     __shared__ uint32_t base[256];
+    __shared__ uint32_t ws[kSortWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    base[tid] = hist[tid * kSortBlocks + blockIdx.x];
+    {
+        // offset of digit tid = sum of the totals of the smaller digits
+        const uint32_t t = row_total[tid];
+        uint32_t x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[warp] = x;
+        __syncthreads();
+        uint32_t pre = x - t;
+        for (int w = 0; w < warp; ++w) pre += ws[w];
+        base[tid] = pre + hist[tid * kSortBlocks + blockIdx.x];
+    }
     for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
     __syncthreads();
     const uint32_t n = read_n(d_n, n_max);
@@ -304,9 +308,10 @@ int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, con
         uint32_t* vout = cur ? va : vb;
         k_rs_hist<<<kSortBlocks, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
         count_launches(1);
-        k_rs_scan<<<1, 1024, 0, st>>>(hist);
+        k_rs_rowscan<<<256, 256, 0, st>>>(hist, hist + 256 * kSortBlocks);
         count_launches(1);
-        k_rs_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist);
+        k_rs_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist,
+                                                           hist + 256 * kSortBlocks);
         count_launches(1);
         cur ^= 1;
     }
