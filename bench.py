@@ -33,12 +33,13 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "composite_score_traffic.md")
 COMPOSITE_SRC = os.path.join(ROOT, "paper_2607_02721_b300", "csrc", "k_composite.cu")
 
-# FP32-pipe operations per (ray, Gaussian) pair of the compositing kernel, counted from
-# its arithmetic: pass 1 footprint test 8 (2 FADD offsets, 5 FMUL/FFMA quadratic form,
-# 1 FSETP), contribution 10 (opacity FMUL, FMNMX clamp, FSETP alpha_min, FADD 1-rho,
-# FMUL T, FSETP t_min, FMUL rho T, 3 FFMA colour); pass 2 test 8, contribution 8
-# (FMUL, FMNMX, FSETP, FMUL rho T, 2 FMUL importance, FADD, FMUL T).  MUFU ex2 is extra.
-OPS_TEST, OPS_HIT1, OPS_HIT2 = 8, 10, 8
+# FP32-pipe operations per (ray, Gaussian) pair the compositing kernel evaluates,
+# counted from its arithmetic: footprint test 6 (5 FFMA for the exponent
+# log2 alpha - e1^2 - e2^2, 1 FSETP against the combined cut/alpha_min threshold);
+# pass-1 contribution 8 (FMNMX clamp, FADD 1-rho, FMUL T, FSETP t_min, FMUL rho T,
+# 3 FFMA colour); pass-2 contribution 5 (FMNMX, FMUL rho T/A, FMUL colour weight,
+# FADD, FMUL).  The MUFU ex2 of each contribution runs on the XU pipe, outside this count.
+OPS_TEST, OPS_HIT1, OPS_HIT2 = 6, 8, 5
 SMS, FP32_LANES = 148, 128
 
 

@@ -53,22 +53,31 @@ class _Opts(ctypes.Structure):
                 ("pad", ctypes.c_int32)]
 
 
+def f32(x: float) -> float:
+    """The value of x as the float32 number the library's options carry."""
+    return float(np.float32(x))
+
+
 @dataclasses.dataclass
 class Opts:
     """Rendering/scoring conventions.  Defaults: the vanilla 3DGS rasteriser
     conventions the paper relies on (Sec. 3 and the 3-sigma footprint of the proof
-    of Thm. 1), with the straddle bands used by the parity tests."""
-    alpha_min: float = 1.0 / 255.0
-    rho_max: float = 0.99
-    t_min: float = 1e-4
+    of Thm. 1).  The thresholds are the float32 numbers the library's option struct
+    carries (e.g. 0.99f, 1e-4f), so both sides apply the same constants; this matters
+    where the conventions meet exactly, e.g. (1 - 0.99)^2 = 1e-4.  The straddle bands
+    mark queries whose decisions lie within a few times the FP32 error of the GPU
+    path; they are test parameters, not part of the method."""
+    alpha_min: float = f32(1.0 / 255.0)
+    rho_max: float = f32(0.99)
+    t_min: float = f32(1e-4)
     cut2: float = 9.0
-    dilation: float = 0.3
-    clamp_fov: float = 1.3
+    dilation: float = f32(0.3)
+    clamp_fov: float = f32(1.3)
     obj_w: tuple = (1.0, 1.0, 1.0)
-    band_cut: float = 2e-5
-    band_alpha: float = 2e-5
-    band_tmin: float = 1e-4
-    band_depth: float = 5e-7
+    band_cut: float = 5e-6     # relative band around the footprint cut
+    band_alpha: float = 2e-6   # relative error of rho: band around alpha_min, feeds the T bound
+    band_tmin: float = 4.0     # safety factor on the accumulated error bound of T near t_min
+    band_depth: float = 2.5e-7  # relative depth difference treated as a tie
     resolution: int = RES_PIXEL
     variant: int = VAR_L1
     tile: int = 16

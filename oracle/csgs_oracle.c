@@ -63,7 +63,7 @@ typedef struct {
     double obj_w[3];
     double band_cut;
     double band_alpha;
-    double band_tmin;
+    double band_tmin;  /* safety factor on the accumulated error bound of T */
     double band_depth;
     int32_t resolution; /* 0 pixel, 1 scene, 2 channel, 3 tile, 4 image */
     int32_t variant;    /* 0 L1 colour, 1 L2 colour, 2 no-colour */
@@ -101,7 +101,8 @@ typedef struct {
     double depth;
     int64_t gid;
     double rho;
-    int viol; /* w alpha k >= 1: the factor 1 - w rho would not be positive unclamped */
+    int viol;    /* w alpha k >= 1: the factor 1 - w rho would not be positive unclamped */
+    int clamped; /* rho = rho_max exactly */
 } ocand;
 
 typedef struct {
@@ -383,16 +384,21 @@ static void pixel_composite(const oview* v, const or_opts* o, double px, double 
         b->cand[nc].gid = i;
         b->cand[nc].rho = rho;
         b->cand[nc].viol = raw >= 1.0;
+        b->cand[nc].clamped = raw >= o->rho_max;
         nc++;
     }
     qsort(b->cand, (size_t)nc, sizeof(ocand), cand_cmp);
     double T = 1.0;
+    double relT = 0.0; /* error bound of an FP32 evaluation of T relative to T */
     int64_t nt = 0;
     for (int64_t j = 0; j < nc; ++j) {
         const ocand* c = &b->cand[j];
         if (j > 0 && fabs(c->depth - b->cand[j - 1].depth) <= o->band_depth * c->depth) r->flag = 1;
         double Tn = T * (1.0 - c->rho);
-        if (near_rel(Tn, o->t_min, o->band_tmin)) r->flag = 1;
+        /* each factor 1 - rho carries the relative error of rho (band_alpha, none when
+         * rho is the clamp constant) amplified by rho / (1 - rho), plus one rounding */
+        relT += (c->clamped ? 0.0 : o->band_alpha * c->rho / (1.0 - c->rho)) + 1.2e-7;
+        if (fabs(Tn - o->t_min) <= o->band_tmin * relT * o->t_min) r->flag = 1;
         r->evaluated++;
         r->violations += c->viol; /* validity (Def. "valid") over the pairs the traversal meets */
         if (Tn < o->t_min) break;

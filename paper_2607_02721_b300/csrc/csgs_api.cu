@@ -145,7 +145,8 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     k->rho_max = o->rho_max;
     k->t_min = o->t_min;
     k->cut2 = o->cut2;
-    k->pcut = (float)(-0.5 * 1.4426950408889634 * (double)o->cut2);
+    k->qcut = (float)(0.5 * 1.4426950408889634 * (double)o->cut2);
+    k->l2amin = o->alpha_min > 0.f ? (float)log2((double)o->alpha_min) : -1e30f;
     k->dilation = o->dilation;
     k->clamp_fov = o->clamp_fov;
     k->ow0 = o->obj_w[0];

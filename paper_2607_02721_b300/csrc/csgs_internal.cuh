@@ -41,7 +41,8 @@ struct SceneDev {
 // Scoring conventions in the form the kernels use.
 struct KOpts {
     float alpha_min, rho_max, t_min;
-    float pcut;       // footprint cut in the scaled exponent domain: -0.5 log2(e) cut2
+    float qcut;       // footprint cut in base-2 exponent units: 0.5 log2(e) cut2
+    float l2amin;     // log2(alpha_min)
     float cut2;
     float dilation, clamp_fov;
     float ow0, ow1, ow2;  // per-pixel objective weights
@@ -51,9 +52,12 @@ struct KOpts {
 // One projected Gaussian in one view (48 bytes, 16-byte aligned).
 //   m = (mean x hi, mean y hi, mean x lo, mean y lo): the pixel-space mean as an
 //       unevaluated two-float sum, so the tile-relative offset keeps FP32 accuracy
-//   q = (qa, qb, qc, opacity): exponent2 = qa dx^2 + qb dx dy + qc dy^2 is the
-//       base-2 exponent of the kernel value, i.e. the conic scaled by -0.5 log2(e)
-//   c = (r, g, b, depth)
+//   q = (s1, s1k, s2, thr): the base-2 exponent of rho is
+//       log2(alpha) - e1^2 - e2^2,  e1 = s1 dx + s1k dy,  e2 = s2 dy,
+//       i.e. the conic (scaled by 0.5 log2 e) in Cholesky form; thr folds the
+//       footprint cut and alpha_min into one threshold on that exponent:
+//       thr = max(log2(alpha) - qcut, log2(alpha_min))
+//   c = (r, g, b, log2(alpha))
 struct __align__(16) Splat {
     float4 m;
     float4 q;

@@ -2,17 +2,26 @@
 // function": rho = alpha k, T = prod (1 - rho), a = c rho T, A = sum a) and the
 // per-Gaussian sensitivity reduction (Eq. sen).
 //
-// Each thread owns one pixel.  The tile's depth-sorted splat list is staged through
-// shared memory 256 records at a time; a warp covers an 8x4 pixel block so its
-// lanes see similar footprints.  A thread stops at the Gaussian that would bring T
-// below t_min; the CTA leaves once every pixel has stopped.
+// Each thread owns one pixel; a warp covers an 8x4 pixel block.  The tile's
+// depth-sorted splat list is staged through shared memory 256 records at a time.
+// While staging, each splat gets a mask of the warp blocks its footprint's bounding
+// box touches, and every warp compacts the batch into its own list, so a warp only
+// evaluates splats that can reach one of its pixels.
+//
+// Per (pixel, splat) the kernel evaluates, in tile-centred pixel coordinates (X, Y),
+//   e1 = s1 X + s1k Y + c1,  e2 = s2 Y + c2,  p = log2(alpha) - e1^2 - e2^2
+// (the EWA kernel's exponent in base 2, conic in Cholesky form; five FMAs), then one
+// compare against thr = max(log2 alpha - qcut, log2 alpha_min) decides the
+// 3-sigma footprint and the alpha_min skip together, and rho = min(rho_max, 2^p).
+// A thread stops at the Gaussian that would bring T below t_min; the CTA leaves
+// once every pixel has stopped.
 //
 // Score (per-pixel resolution) runs two passes over the same list inside one CTA:
 // pass 1 yields A(q) and the index of each pixel's last contributor, pass 2 recomputes
-// rho and T bit for bit (explicitly rounded operations, the same contributor set)
-// and reduces imp = a / A per Gaussian: warp max with redux.sync on the float bits
-// (imp >= 0, so unsigned order = float order), a shared-memory max across the CTA's
-// warps, and one global atomicMax per (tile, Gaussian).
+// rho bit for bit (same operations, same contributor set) and reduces
+// imp = a / A per Gaussian: warp max with redux.sync on the float bits (imp >= 0, so
+// unsigned order = float order), a shared-memory max across the CTA's warps, and one
+// global atomicMax per (tile, Gaussian).
 // Score (per-scene resolution) is one pass: warp sums of a, one global atomicAdd per
 // (tile, Gaussian), and the CTA's sum of A added to an FP64 total.
 #include "csgs_internal.cuh"
@@ -31,51 +40,83 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Base-2 exponent of the kernel value at tile-relative offset (dx, dy).
-__device__ __forceinline__ float exponent2(float dx, float dy, float qa, float qb, float qc) {
-    const float t = __fmaf_rn(qb, dy, __fmul_rn(qa, dx));
-    const float u = __fmul_rn(__fmul_rn(qc, dy), dy);
-    return __fmaf_rn(dx, t, u);
-}
-
 struct Shared {
-    float4 m[kThreads];  // (mean x, mean y) tile-relative, qa, qb
-    float4 q[kThreads];  // qc, opacity, r, g
-    float2 c[kThreads];  // b, objective colour weight cw = obj_w . rgb
+    float4 A[kThreads];  // s1, s1k, c1, s2
+    float4 B[kThreads];  // c2, log2 alpha, thr, cw = obj_w . rgb
+    float4 C[kThreads];  // r, g, b, -
     uint32_t gid[kThreads];
+    uint32_t msk[kThreads];
+    uint8_t wl[kWarps][kThreads];  // per-warp compacted batch indices
     uint32_t red[kThreads];
     float part[kWarps][kThreads];
     int last;
     double sumA[kWarps];
 };
 
+// Stage splat i of the tile list into slot threadIdx.x (tile centre (cx, cy)).
 template <int MODE>
-__device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32_t i, uint32_t end, float ox,
-                                      float oy) {
+__device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32_t i, uint32_t end, float cx,
+                                      float cy) {
     const int tid = threadIdx.x;
     if (MODE == kScorePixel) sh.red[tid] = 0u;
     if (MODE == kScoreScene)
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) sh.part[w][tid] = 0.f;
+    sh.msk[tid] = 0u;
     if (i >= end) return;
     const uint32_t g = __ldg(a.inst_gid + i);
-    if (g >= (uint32_t)a.n_gauss) {  // only reachable after a reported capacity overflow
-        sh.m[tid] = make_float4(1e6f, 1e6f, -1.f, 0.f);
-        sh.q[tid] = make_float4(-1.f, 0.f, 0.f, 0.f);
-        sh.c[tid] = make_float2(0.f, 0.f);
-        sh.gid[tid] = 0u;
-        return;
-    }
+    if (g >= (uint32_t)a.n_gauss) return;  // only reachable after a reported capacity overflow
     const float4* sp = reinterpret_cast<const float4*>(a.splats + g);
     const float4 m = __ldg(sp), q = __ldg(sp + 1), c = __ldg(sp + 2);
-    // tile-relative mean from the two-float pixel mean
-    const float mx = __fadd_rn(__fadd_rn(m.x, -ox), m.z);
-    const float my = __fadd_rn(__fadd_rn(m.y, -oy), m.w);
-    sh.m[tid] = make_float4(mx, my, q.x, q.y);
-    sh.q[tid] = make_float4(q.z, q.w, c.x, c.y);
-    const float cw = a.o.ow0 * c.x + a.o.ow1 * c.y + a.o.ow2 * c.z;
-    sh.c[tid] = make_float2(c.z, cw);
+    // tile-centred mean from the two-float pixel mean
+    const float mx = __fadd_rn(__fadd_rn(m.x, -cx), m.z);
+    const float my = __fadd_rn(__fadd_rn(m.y, -cy), m.w);
+    const float s1 = q.x, s1k = q.y, s2 = q.z;
+    const float c1 = -__fmaf_rn(s1, mx, __fmul_rn(s1k, my));
+    const float c2 = -__fmul_rn(s2, my);
+    sh.A[tid] = make_float4(s1, s1k, c1, s2);
+    sh.B[tid] = make_float4(c2, c.w, q.w, a.o.ow0 * c.x + a.o.ow1 * c.y + a.o.ow2 * c.z);
+    sh.C[tid] = make_float4(c.x, c.y, c.z, 0.f);
     sh.gid[tid] = g;
+    // bounding box of the footprint: rx^2 = qcut (1/s1^2 + (s1k/(s1 s2))^2), ry^2 = qcut / s2^2,
+    // widened so that FP32 rounding never drops a pixel that passes the test
+    const float i1 = 1.f / s1, i2 = 1.f / s2;
+    const float kk = s1k * i1 * i2;
+    const float rx = sqrtf(a.o.qcut * (i1 * i1 + kk * kk)) * 1.001f + 0.01f;
+    const float ry = sqrtf(a.o.qcut) * i2 * 1.001f + 0.01f;
+    const float xlo = mx - rx, xhi = mx + rx, ylo = my - ry, yhi = my + ry;
+    uint32_t cols = 0u, rows = 0u;
+    cols |= (xlo <= -0.5f && xhi >= -7.5f) ? 1u : 0u;
+    cols |= (xlo <= 7.5f && xhi >= 0.5f) ? 2u : 0u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) rows |= (ylo <= -4.5f + 4.f * r && yhi >= -7.5f + 4.f * r) ? (1u << r) : 0u;
+    uint32_t mk = 0u;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (rows & (1u << r)) mk |= cols << (2 * r);
+    sh.msk[tid] = mk;
+}
+
+// Compact the staged batch into this warp's list; returns its length.
+__device__ __forceinline__ int warp_list(Shared& sh, int cnt, int warp, int lane) {
+    const uint32_t lt = (1u << lane) - 1u;
+    int nw = 0;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+        const int j = c0 + lane;
+        const bool bit = j < cnt && ((sh.msk[j] >> warp) & 1u);
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        if (bit) sh.wl[warp][nw + __popc(bal & lt)] = (uint8_t)j;
+        nw += __popc(bal);
+    }
+    __syncwarp();
+    return nw;
+}
+
+// Base-2 exponent of rho at pixel (X, Y) for staged splat j.
+__device__ __forceinline__ float exponent2(const float4& A, const float4& B, float X, float Y) {
+    const float e1 = __fmaf_rn(A.x, X, __fmaf_rn(A.y, Y, A.z));
+    const float e2 = __fmaf_rn(A.w, Y, B.x);
+    return __fmaf_rn(-e1, e1, __fmaf_rn(-e2, e2, B.y));
 }
 
 template <int MODE, bool STATS>
@@ -88,12 +129,12 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 4 + (lane >> 3);
     const int px = tx * kTile + lx, py = ty * kTile + ly;
     const bool inside = px < cam.W && py < cam.H;
-    const float fx = (float)lx, fy = (float)ly;
-    const float ox = (float)(tx * kTile), oy = (float)(ty * kTile);
+    const float X = (float)lx - 7.5f, Y = (float)ly - 7.5f;
+    const float cx = (float)(tx * kTile) + 7.5f, cy = (float)(ty * kTile) + 7.5f;
     const uint2 rg = a.ranges[tile];
     const uint32_t start = rg.x;
     const int n = (int)(rg.y - rg.x);
-    const float pcut = a.o.pcut, rho_max = a.o.rho_max, alpha_min = a.o.alpha_min, t_min = a.o.t_min;
+    const float rho_max = a.o.rho_max, t_min = a.o.t_min;
 
     float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
     int last = 0;
@@ -104,20 +145,21 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     // ---------------------------------------------------------------- pass 1
     for (int b = 0; b < n; b += kThreads) {
         if (__syncthreads_count(done) == kThreads) break;
-        stage<MODE>(a, sh, start + b + tid, rg.y, ox, oy);
+        stage<MODE>(a, sh, start + b + tid, rg.y, cx, cy);
         __syncthreads();
         const int cnt = min(kThreads, n - b);
+        const int nw = warp_list(sh, cnt, warp, lane);
         if (MODE != kScoreScene) {
             if (!done) {
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 m = sh.m[j];
-                    const float4 q = sh.q[j];
-                    const float p = exponent2(__fadd_rn(fx, -m.x), __fadd_rn(fy, -m.y), m.z, m.w, q.x);
+                for (int k = 0; k < nw; ++k) {
+                    const int j = sh.wl[warp][k];
+                    const float4 Aj = sh.A[j];
+                    const float4 Bj = sh.B[j];
+                    const float p = exponent2(Aj, Bj, X, Y);
                     if (STATS) ++n_eval;
-                    if (p < pcut) continue;
-                    const float raw = __fmul_rn(q.y, ex2_approx(p));
+                    if (p < Bj.z) continue;
+                    const float raw = ex2_approx(p);
                     const float r = fminf(rho_max, raw);
-                    if (r < alpha_min) continue;
                     if (STATS) {
                         ++n_hit;
                         n_viol += raw >= 1.f;
@@ -128,9 +170,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                         break;
                     }
                     const float w = __fmul_rn(r, T);
-                    A0 = __fmaf_rn(q.z, w, A0);
-                    A1 = __fmaf_rn(q.w, w, A1);
-                    A2 = __fmaf_rn(sh.c[j].x, w, A2);
+                    const float4 Cj = sh.C[j];
+                    A0 = __fmaf_rn(Cj.x, w, A0);
+                    A1 = __fmaf_rn(Cj.y, w, A1);
+                    A2 = __fmaf_rn(Cj.z, w, A2);
                     T = Tn;
                     last = b + j + 1;
                 }
@@ -139,31 +182,29 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             // per-scene resolution: warp-uniform loop so the warp can sum a per Gaussian
             bool act = !done;
             if (__any_sync(0xffffffffu, act)) {
-                for (int j = 0; j < cnt; ++j) {
+                for (int k = 0; k < nw; ++k) {
+                    const int j = sh.wl[warp][k];
                     float v = 0.f;
                     if (act) {
-                        const float4 m = sh.m[j];
-                        const float4 q = sh.q[j];
-                        const float p = exponent2(__fadd_rn(fx, -m.x), __fadd_rn(fy, -m.y), m.z, m.w, q.x);
+                        const float4 Aj = sh.A[j];
+                        const float4 Bj = sh.B[j];
+                        const float p = exponent2(Aj, Bj, X, Y);
                         if (STATS) ++n_eval;
-                        if (p >= pcut) {
-                            const float raw = __fmul_rn(q.y, ex2_approx(p));
-                            const float r = fminf(rho_max, raw);
-                            if (r >= alpha_min) {
-                                if (STATS) ++n_hit;
-                                const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
-                                if (Tn < t_min) {
-                                    act = false;
-                                    done = true;
-                                } else {
-                                    const float w = __fmul_rn(r, T);
-                                    const float2 c = sh.c[j];
-                                    A0 = __fmaf_rn(q.z, w, A0);
-                                    A1 = __fmaf_rn(q.w, w, A1);
-                                    A2 = __fmaf_rn(c.x, w, A2);
-                                    v = __fmul_rn(c.y, w);
-                                    T = Tn;
-                                }
+                        if (p >= Bj.z) {
+                            const float r = fminf(rho_max, ex2_approx(p));
+                            if (STATS) ++n_hit;
+                            const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
+                            if (Tn < t_min) {
+                                act = false;
+                                done = true;
+                            } else {
+                                const float w = __fmul_rn(r, T);
+                                const float4 Cj = sh.C[j];
+                                A0 = __fmaf_rn(Cj.x, w, A0);
+                                A1 = __fmaf_rn(Cj.y, w, A1);
+                                A2 = __fmaf_rn(Cj.z, w, A2);
+                                v = __fmul_rn(Bj.w, w);
+                                T = Tn;
                             }
                         }
                     }
@@ -215,35 +256,35 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     if (MODE == kScorePixel) {
         const float Aobj = a.o.ow0 * A0 + a.o.ow1 * A1 + a.o.ow2 * A2;
         const bool has = inside && Aobj > 0.f;  // queries with A = 0 are discarded
-        const float invA = has ? 1.f / Aobj : 0.f;
+        // T' = T / A: imp = cw rho T' directly
+        float Tq = has ? 1.f / Aobj : 0.f;
         if (!has) last = 0;
         __syncthreads();
         atomicMax(&sh.last, last);
         __syncthreads();
         const int n2 = sh.last;
-        T = 1.f;
         for (int b = 0; b < n2; b += kThreads) {
             __syncthreads();
-            stage<MODE>(a, sh, start + b + tid, rg.y, ox, oy);
+            stage<MODE>(a, sh, start + b + tid, rg.y, cx, cy);
             __syncthreads();
             const int cnt = min(kThreads, n2 - b);
+            const int nw = warp_list(sh, cnt, warp, lane);
             const int lim = max(0, min(cnt, last - b));
             const int jw = (int)__reduce_max_sync(0xffffffffu, (unsigned)lim);
-            for (int j = 0; j < jw; ++j) {
+            for (int k = 0; k < nw; ++k) {
+                const int j = sh.wl[warp][k];
+                if (j >= jw) break;  // the list is in increasing j; warp-uniform
                 uint32_t bits = 0u;
                 if (j < lim) {
-                    const float4 m = sh.m[j];
-                    const float4 q = sh.q[j];
-                    const float p = exponent2(__fadd_rn(fx, -m.x), __fadd_rn(fy, -m.y), m.z, m.w, q.x);
+                    const float4 Aj = sh.A[j];
+                    const float4 Bj = sh.B[j];
+                    const float p = exponent2(Aj, Bj, X, Y);
                     if (STATS) ++n_eval2;
-                    if (p >= pcut) {
-                        const float r = fminf(rho_max, __fmul_rn(q.y, ex2_approx(p)));
-                        if (r >= alpha_min) {
-                            if (STATS) ++n_hit2;
-                            const float w = __fmul_rn(r, T);
-                            bits = __float_as_uint(__fmul_rn(__fmul_rn(sh.c[j].y, w), invA));
-                            T = __fmul_rn(T, __fadd_rn(1.f, -r));
-                        }
+                    if (p >= Bj.z) {
+                        const float r = fminf(rho_max, ex2_approx(p));
+                        if (STATS) ++n_hit2;
+                        bits = __float_as_uint(__fmul_rn(Bj.w, __fmul_rn(r, Tq)));
+                        Tq = __fmul_rn(Tq, __fadd_rn(1.f, -r));
                     }
                 }
                 const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);

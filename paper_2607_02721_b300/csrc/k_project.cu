@@ -17,6 +17,7 @@ struct Proj {
     ff::F2 mx, my;       // two-float pixel-space mean
     float ca, cb, cc;    // 2-D covariance (dilated)
     float ia, ib, ic;    // conic
+    float idet;          // 1 / det(cov)
     float depth, op;
     float rgb[3];
     uint32_t tx0, ty0, tx1, ty1;
@@ -138,6 +139,7 @@ __device__ __forceinline__ void project_one(const float mu[3], const float cov3[
     r.ca = ca;
     r.cb = cb;
     r.cc = cc;
+    r.idet = idet;
     r.ia = cc * idet;
     r.ib = -cb * idet;
     r.ic = ca * idet;
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __re
     float mu[3], cov3[6], op;
     float shc[3 * (DEG + 1) * (DEG + 1)];
     load_gaussian<DEG>(sc, i, wts, mu, cov3, op, shc);
-    const float K = -0.5f * kLog2e;
+    const float K2 = 0.5f * kLog2e;
     for (int v = 0; v < nv; ++v) {
         const CamDev& c = cams[v];
         Proj r;
@@ -205,10 +207,17 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __re
             rects[off] = make_uint2(0u, 0u);
             continue;
         }
+        // Cholesky form of the base-2 exponent's quadratic form (0.5 log2 e) d^T cov^-1 d
+        // = e1^2 + e2^2: s2^2 = K2 / cov_yy, s1^2 = K2 cov_yy / det, s1k = -s1 cov_xy / cov_yy
+        const float s2 = sqrtf(K2 / r.cc);
+        const float s1 = sqrtf(K2 * r.cc * r.idet);
+        const float s1k = -s1 * r.cb / r.cc;
+        const float la = log2f(r.op);
+        const float thr = fmaxf(la - o.qcut, o.l2amin);
         Splat s;
         s.m = make_float4(r.mx.hi, r.my.hi, r.mx.lo, r.my.lo);
-        s.q = make_float4(K * r.ia, 2.f * K * r.ib, K * r.ic, r.op);
-        s.c = make_float4(r.rgb[0], r.rgb[1], r.rgb[2], r.depth);
+        s.q = make_float4(s1, s1k, s2, thr);
+        s.c = make_float4(r.rgb[0], r.rgb[1], r.rgb[2], la);
         splats[off] = s;
         keys[off] = __float_as_uint(r.depth);
         rects[off] = make_uint2(r.tx0 | (r.ty0 << 16), r.tx1 | (r.ty1 << 16));

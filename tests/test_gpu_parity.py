@@ -9,7 +9,9 @@ straddle flags: footprint cut, alpha_min, t_min, near-equal depths) are excluded
 the element-wise comparison and their share is bounded; Gaussians contributing to such
 pixels are compared through bounds instead.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -23,6 +25,22 @@ pytestmark = pytest.mark.gpu
 
 RGB_TOL = 1e-5
 S_RTOL = 1e-3
+STATS = {}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _error_stats():
+    """Collects the observed GPU-vs-oracle error magnitudes and writes them next to
+    the run's other outputs (when a gpurun_out folder exists)."""
+    yield
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "parity_stats.json"), "w") as f:
+            json.dump(STATS, f, indent=1)
+
+
+def note(key, value):
+    STATS.setdefault(key, []).append(float(value))
 
 
 @pytest.fixture(scope="module")
@@ -76,6 +94,9 @@ def test_projection_matches_oracle(ctx, small, small_sid):
         assert np.all(ov[gv])
         vv = gv
         mx = g[vv, 1] + g[vv, 15]
+        note("proj_mean_x_abs", np.abs(mx - o[vv, 1]).max())
+        note("proj_conic_rel", (np.abs(g[vv, 3:6] - o[vv, 3:6]) / (np.abs(o[vv, 3:6]) + 1e-3 * np.abs(o[vv, 3:4]))).max())
+        note("proj_rgb_abs", np.abs(g[vv, 11:14] - o[vv, 11:14]).max())
         np.testing.assert_allclose(mx, o[vv, 1], rtol=0, atol=2e-5)
         np.testing.assert_allclose(g[vv, 2], o[vv, 2], rtol=0, atol=2e-4)
         np.testing.assert_allclose(g[vv, 9], o[vv, 9], rtol=2e-7)
@@ -92,6 +113,10 @@ def compare_render(rgb_gpu, ref, max_flag_frac=0.01):
     d = np.abs(rgb_gpu.astype(np.float64) - ref["rgb"])
     assert fl.mean() <= max_flag_frac, fl.mean()
     worst = d[~fl].max() if (~fl).any() else 0.0
+    note("render_rgb_abs_unflagged", worst)
+    note("render_flagged_frac", fl.mean())
+    if fl.any():
+        note("render_rgb_abs_flagged", d[fl].max())
     assert worst <= RGB_TOL, (worst, np.unravel_index(np.argmax(np.where(fl[..., None], 0, d)), d.shape))
     return worst, fl.mean()
 
@@ -115,15 +140,22 @@ def test_render_transmittance_matches_oracle(ctx, small, small_sid):
 # ---------------------------------------------------------------- score
 
 def check_scores(s_gpu, S_gpu, ref, min_val=1e-6):
+    """Untouched Gaussians (no contribution to a straddling query): element-wise within
+    S_RTOL.  Touched ones: the GPU's max runs over a superset of the clean queries, so
+    it is at least s_clean; and only a small share may leave the tolerance."""
     s_gpu = s_gpu.astype(np.float64)
     s = ref["s"]
     clean = ~ref["touched"] & (s > min_val)
     rel = np.abs(s_gpu[clean] - s[clean]) / s[clean]
+    note("score_rel_untouched", rel.max())
+    note("touched_frac", ref["touched"].mean())
     assert rel.max() <= S_RTOL, (rel.max(), np.argmax(rel))
-    # touched Gaussians: the GPU max is over a superset of the clean queries
     t = ref["touched"] & (ref["s_clean"] > min_val)
     assert np.all(s_gpu[t] >= ref["s_clean"][t] * (1 - S_RTOL))
-    assert ref["touched"].mean() < 0.05
+    big = ref["touched"] & (s > min_val)
+    off = np.abs(s_gpu[big] - s[big]) > S_RTOL * s[big]
+    note("touched_out_of_tol_frac", off.sum() / len(s))
+    assert off.sum() <= 0.02 * len(s)
     assert abs(S_gpu - ref["S"]) <= 5e-3 * ref["S"]
 
 

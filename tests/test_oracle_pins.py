@@ -96,8 +96,11 @@ def test_philox_known_answers():
 
 # ---------------------------------------------------------------- projection
 
+DIL = Opts().dilation  # 0.3 as the float32 the options carry
+
+
 def test_projection_isotropic_on_axis_closed_form():
-    sig, z, f, dil = 0.05, 2.0, 40.0, 0.3
+    sig, z, f, dil = 0.05, 2.0, 40.0, DIL
     sc = one_scene([0, 0, z], [math.log(sig)] * 3, [0.2, 0.5, 0.9], 0.3)
     P = oracle.project(sc, axis_camera(f=f))[0]
     sig = eff_scale(sig)
@@ -113,7 +116,7 @@ def test_projection_isotropic_on_axis_closed_form():
 
 def test_projection_off_axis_jacobian_closed_form():
     # Sigma = sig^2 I, J = [[f/z, 0, -f x/z^2], [0, f/z, -f y/z^2]]
-    sig, f, dil = 0.07, 50.0, 0.3
+    sig, f, dil = 0.07, 50.0, DIL
     x0, y0, z = 0.3, -0.2, 2.5
     sc = one_scene([x0, y0, z], [math.log(sig)] * 3, [0.5, 0.5, 0.5], 0.0)
     P = oracle.project(sc, axis_camera(W=64, H=48, f=f))[0]
@@ -127,12 +130,12 @@ def test_projection_off_axis_jacobian_closed_form():
 
 def test_projection_clamps_jacobian_outside_fov():
     # far off-axis: x/z is clamped to 1.3 * (W/2)/f inside J only
-    sig, f, dil, W = 0.05, 20.0, 0.3, 32
+    sig, f, dil, W = 0.05, 20.0, DIL, 32
     x0, z = 3.0, 2.0
     sc = one_scene([x0, 0.0, z], [math.log(sig)] * 3, [0.5, 0.5, 0.5], 0.0)
     P = oracle.project(sc, axis_camera(W=W, H=W, f=f))[0]
     sig = eff_scale(sig)
-    lim = 1.3 * 0.5 * W / f
+    lim = Opts().clamp_fov * 0.5 * W / f
     assert x0 / z > lim
     xx = sig * sig * f * f / z / z * (1 + lim * lim) + dil
     np.testing.assert_allclose(P[6], xx, rtol=1e-6)
@@ -141,7 +144,7 @@ def test_projection_clamps_jacobian_outside_fov():
 
 def test_projection_quaternion_and_camera_rotation():
     # 90 degrees about z maps the local x axis to world y: Sigma = diag(sy^2, sx^2, sz^2)
-    sx, sy, sz, f, dil, z = 0.02, 0.09, 0.05, 40.0, 0.3, 3.0
+    sx, sy, sz, f, dil, z = 0.02, 0.09, 0.05, 40.0, DIL, 3.0
     q = [math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4)]
     sc = one_scene([0, 0, z], [math.log(sx), math.log(sy), math.log(sz)], [0.5] * 3, 0.0, quats=q)
     P = oracle.project(sc, axis_camera(f=f))[0]
@@ -162,7 +165,7 @@ def test_projection_quaternion_and_camera_rotation():
 # ---------------------------------------------------------------- compositing
 
 def test_single_gaussian_closed_form_render_and_score():
-    sig, z, f, dil, lg = 0.04, 2.0, 40.0, 0.3, 1.2
+    sig, z, f, dil, lg = 0.04, 2.0, 40.0, DIL, 1.2
     rgb = np.array([0.8, 0.3, 0.6])
     sc = one_scene([0, 0, z], [math.log(sig)] * 3, rgb, lg)
     rgb = C0 * sc.sh[0, :, 0].astype(np.float64) + 0.5
@@ -172,8 +175,9 @@ def test_single_gaussian_closed_form_render_and_score():
     var = (f * sig / z) ** 2 + dil
     yy, xx = np.mgrid[0:33, 0:33]
     d2 = ((xx - 16.0) ** 2 + (yy - 16.0) ** 2) / var
-    rho = np.minimum(0.99, sigmoid(lg) * np.exp(-0.5 * d2))
-    rho[(d2 > 9) | (rho < 1 / 255)] = 0.0
+    o = Opts()
+    rho = np.minimum(o.rho_max, sigmoid(lg) * np.exp(-0.5 * d2))
+    rho[(d2 > 9) | (rho < o.alpha_min)] = 0.0
     np.testing.assert_allclose(out["rgb"], rgb[None, None, :] * rho[..., None], atol=1e-6)
     np.testing.assert_allclose(out["T"], 1 - rho, atol=1e-7)
     r = oracle.score(sc, cam[None], Opts())
@@ -183,7 +187,7 @@ def test_single_gaussian_closed_form_render_and_score():
 
 
 def test_two_gaussians_on_axis_closed_form():
-    f, dil = 40.0, 0.3
+    f, dil = 40.0, DIL
     s1, s2, z1, z2, l1, l2 = 0.03, 0.06, 1.5, 2.5, 0.4, -0.2
     c1, c2 = np.array([0.9, 0.1, 0.2]), np.array([0.1, 0.7, 0.6])
     sc = one_scene([[0, 0, z2], [0, 0, z1]], [[math.log(s2)] * 3, [math.log(s1)] * 3], [c2, c1], [l2, l1])
@@ -194,8 +198,9 @@ def test_two_gaussians_on_axis_closed_form():
 
     def rho(s, z, lg):
         v = (f * eff_scale(s) / z) ** 2 + dil
-        r = np.minimum(0.99, sigmoid(lg) * np.exp(-0.5 * r2 / v))
-        r[(r2 / v > 9) | (r < 1 / 255)] = 0.0
+        o = Opts()
+        r = np.minimum(o.rho_max, sigmoid(lg) * np.exp(-0.5 * r2 / v))
+        r[(r2 / v > 9) | (r < o.alpha_min)] = 0.0
         return r
 
     p1, p2 = rho(s1, z1, l1), rho(s2, z2, l2)  # Gaussian index 1 is in front
