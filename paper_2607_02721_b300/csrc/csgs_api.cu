@@ -185,7 +185,7 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
     if ((r = ensure(ctx, ctx->dvals_b, sizeof(uint32_t) * (size_t)n))) return r;
     if ((r = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return r;
     if ((r = ensure(ctx, ctx->hist, sizeof(uint32_t) * kSortHistWords))) return r;
-    if ((r = ensure(ctx, ctx->scan_tmp, sizeof(uint32_t) * ((size_t)(n + 2047) / 2048 + 64)))) return r;
+    if ((r = ensure(ctx, ctx->scan_tmp, sizeof(uint32_t) * ((size_t)(n + 255) / 256 + 64)))) return r;
     if (ctx->cap == 0) {
         uint64_t c = (uint64_t)n * 8;
         if (c < (1u << 20)) c = 1u << 20;

@@ -99,7 +99,7 @@ constexpr int kSortHistWords = 256 * kSortBlocks + 256;  // per-block digit coun
 int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,
                      uint32_t n_max, int bits, uint32_t* hist, cudaStream_t st);
 // Gaussians in depth order -> (tile, gid) instances in depth order; writes the
-// instance count to ctr->n_inst.  scan_tmp: >= 2 * ceil(n / 2048) + 64 words.
+// instance count to ctr->n_inst.  scan_tmp: >= ceil(n / 256) + 64 words.
 void emit_instances(const uint32_t* order, const uint32_t* sorted_keys, const uint2* rects, int n, int tiles_x,
                     uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     cudaStream_t st);

@@ -13,11 +13,9 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortGroups = 4;                               // 32-key groups per warp per sub-tile
-constexpr int kSubTile = kSortThreads * kSortGroups;          // 1024 keys
+constexpr int kSortGroups = 8;                               // 32-key groups per warp per sub-tile
+constexpr int kSubTile = kSortThreads * kSortGroups;          // 2048 keys
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanChunk = kScanThreads * kScanItems;         // 2048
 
 __device__ __forceinline__ void sort_chunk(uint32_t n, int b, uint32_t& begin, uint32_t& end) {
     uint32_t per = (n + kSortBlocks - 1) / kSortBlocks;
@@ -86,6 +84,11 @@ __global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist,
     if (threadIdx.x == 255) row_total[blockIdx.x] = pre;
 }
 
+// Stable scatter of one radix pass.  Each CTA walks its chunk in sub-tiles of 2048
+// keys: warps rank their keys per digit with match.any (stable: warp, group, lane
+// order), the CTA turns the per-warp counts into positions, places the sub-tile in
+// shared memory grouped by digit, and writes each digit's run to its global slot, so
+// global stores are contiguous runs.
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -93,7 +96,10 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
                                                              const uint32_t* __restrict__ hist,
                                                              const uint32_t* __restrict__ row_total) {
     __shared__ uint32_t wcnt[kSortWarps][257];
-    __shared__ uint32_t base[256];
+    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t lstart[256];
+    __shared__ uint32_t skey[kSubTile];
+    __shared__ uint32_t sval[kSubTile];
     __shared__ uint32_t ws[kSortWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
         __syncthreads();
         uint32_t pre = x - t;
         for (int w = 0; w < warp; ++w) pre += ws[w];
-        base[tid] = pre + hist[tid * kSortBlocks + blockIdx.x];
+        gbase[tid] = pre + hist[tid * kSortBlocks + blockIdx.x];
     }
     for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
     __syncthreads();
@@ -118,45 +124,68 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
     uint32_t begin, end;
     sort_chunk(n, blockIdx.x, begin, end);
     for (uint32_t sub = begin; sub < end; sub += kSubTile) {
+        const uint32_t nvalid = min((uint32_t)kSubTile, end - sub);
         uint32_t key[kSortGroups], val[kSortGroups], dig[kSortGroups], rank[kSortGroups];
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
-            uint32_t i = sub + warp * (32 * kSortGroups) + g * 32 + lane;
-            bool ok = i < end;
+            const uint32_t i = sub + warp * (32 * kSortGroups) + g * 32 + lane;
+            const bool ok = i < end;
             key[g] = ok ? __ldg(kin + i) : 0u;
             val[g] = ok ? __ldg(vin + i) : 0u;
             dig[g] = ok ? (key[g] >> shift) & 255u : 256u;
         }
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
-            uint32_t d = dig[g];
-            uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t d = dig[g];
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
             rank[g] = wcnt[warp][d] + __popc(peers & lt);
             __syncwarp();
             if (lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        {
-            uint32_t run = base[tid];
+        // digit tid: per-warp exclusive offsets within the digit, and the digit's count
+        uint32_t cnt_d = 0;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) {
-                uint32_t c = wcnt[w][tid];
-                wcnt[w][tid] = run;
-                run += c;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = cnt_d;
+            cnt_d += c;
+        }
+        // start of digit tid's run inside the sub-tile
+        {
+            uint32_t x = cnt_d;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
             }
-            base[tid] = run;
+            __syncthreads();  // ws reuse
+            if (lane == 31) ws[warp] = x;
+            __syncthreads();
+            uint32_t pre = x - cnt_d;
+            for (int w = 0; w < warp; ++w) pre += ws[w];
+            lstart[tid] = pre;
         }
         __syncthreads();
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
             if (dig[g] < 256u) {
-                uint32_t pos = wcnt[warp][dig[g]] + rank[g];
-                kout[pos] = key[g];
-                vout[pos] = val[g];
+                const uint32_t lp = lstart[dig[g]] + wcnt[warp][dig[g]] + rank[g];
+                skey[lp] = key[g];
+                sval[lp] = val[g];
             }
         }
         __syncthreads();
+        for (uint32_t q = tid; q < nvalid; q += kSortThreads) {
+            const uint32_t k = skey[q];
+            const uint32_t d = (k >> shift) & 255u;
+            const uint32_t pos = gbase[d] + (q - lstart[d]);
+            kout[pos] = k;
+            vout[pos] = sval[q];
+        }
+        __syncthreads();
+        gbase[tid] += cnt_d;
         for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
         __syncthreads();
     }
@@ -194,19 +223,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return pre;
 }
 
+// Emit, phase 1: instance count per block of 256 depth-ordered Gaussians.
 __global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __restrict__ order,
                                                               const uint2* __restrict__ rects, int n,
                                                               uint32_t* __restrict__ partial) {
     __shared__ uint32_t ws[32];
-    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int j = base + k;
-        if (j < n) sum += tile_count(__ldg(rects + __ldg(order + j)));
-    }
+    const int j = blockIdx.x * kScanThreads + threadIdx.x;
+    const uint32_t c = j < n ? tile_count(__ldg(rects + __ldg(order + j))) : 0u;
     uint32_t tot;
-    block_exclusive_scan(sum, ws, &tot);
+    block_exclusive_scan(c, ws, &tot);
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
@@ -235,47 +260,55 @@ __global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ pa
     }
 }
 
+// Emit, phase 3: every warp expands its 32 Gaussians' tile rectangles into a
+// contiguous run of instances, lane f of each round writing instance f of the run
+// (coalesced), in depth order and row-major tile order within a Gaussian.
 __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __restrict__ order,
                                                             const uint2* __restrict__ rects, int n, int tiles_x,
                                                             const uint32_t* __restrict__ partial,
                                                             uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
                                                             uint32_t cap, DevCounters* ctr) {
     __shared__ uint32_t ws[32];
-    const int base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
-    uint32_t cnt[kScanItems], gid[kScanItems];
-    uint2 rc[kScanItems];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        int j = base + k;
-        gid[k] = j < n ? __ldg(order + j) : 0u;
-        rc[k] = j < n ? __ldg(rects + gid[k]) : make_uint2(0u, 0u);
-        cnt[k] = tile_count(rc[k]);
-        sum += cnt[k];
-    }
+    __shared__ uint32_t s_e[kScanThreads / 32][32];
+    __shared__ uint32_t s_g[kScanThreads / 32][32];
+    __shared__ uint2 s_r[kScanThreads / 32][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kScanThreads + threadIdx.x;
+    const uint32_t gid = j < n ? __ldg(order + j) : 0u;
+    const uint2 rc = j < n ? __ldg(rects + gid) : make_uint2(0u, 0u);
+    const uint32_t c = tile_count(rc);
     uint32_t tot;
-    uint32_t off = block_exclusive_scan(sum, ws, &tot) + partial[blockIdx.x];
-    bool overflow = false;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (cnt[k]) {
-            if ((unsigned long long)off + cnt[k] > cap) {
-                overflow = true;
-            } else {
-                const uint32_t x0 = rc[k].x & 0xFFFFu, y0 = rc[k].x >> 16, x1 = rc[k].y & 0xFFFFu,
-                               y1 = rc[k].y >> 16;
-                uint32_t o = off;
-                for (uint32_t ty = y0; ty < y1; ++ty)
-                    for (uint32_t tx = x0; tx < x1; ++tx) {
-                        ikeys[o] = ty * (uint32_t)tiles_x + tx;
-                        ivals[o] = gid[k];
-                        ++o;
-                    }
-            }
-        }
-        off += cnt[k];
+    const uint32_t off = block_exclusive_scan(c, ws, &tot) + partial[blockIdx.x];
+    const uint32_t wbase = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t wtot = __shfl_sync(0xffffffffu, off + c, 31) - wbase;
+    s_e[warp][lane] = off - wbase;
+    s_g[warp][lane] = gid;
+    s_r[warp][lane] = rc;
+    __syncwarp();
+    if ((unsigned long long)wbase + wtot > cap) {
+        if (lane == 0 && wtot) atomicOr(&ctr->err, kErrCapacity);
+        return;
     }
-    if (overflow) atomicOr(&ctr->err, kErrCapacity);
+    for (uint32_t f = lane; f < wtot; f += 32) {
+        // owner: the largest lane whose run starts at or before f
+        int lo = 0, hi = 31;
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_e[warp][mid] <= f)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const uint2 r = s_r[warp][lo];
+        const uint32_t local = f - s_e[warp][lo];
+        const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu;
+        const uint32_t w = x1 - x0;
+        const uint32_t dy = local / w;
+        const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
+        ikeys[wbase + f] = ty * (uint32_t)tiles_x + tx;
+        ivals[wbase + f] = s_g[warp][lo];
+    }
 }
 
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_n, uint32_t n_max,
@@ -321,7 +354,7 @@ int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, con
 void emit_instances(const uint32_t* order, const uint32_t* /*sorted_keys*/, const uint2* rects, int n, int tiles_x,
                     uint32_t* ikeys, uint32_t* ivals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     cudaStream_t st) {
-    const int nb = (n + kScanChunk - 1) / kScanChunk;
+    const int nb = (n + kScanThreads - 1) / kScanThreads;
     k_emit_reduce<<<nb, kScanThreads, 0, st>>>(order, rects, n, scan_tmp);
     count_launches(1);
     k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nb, ctr);
