@@ -177,6 +177,29 @@ csgs_status csgs_sync(csgs_ctx* ctx);
 /* Counters of the last score / render (synchronises). */
 csgs_status csgs_get_stats(csgs_ctx* ctx, csgs_stats* out);
 
+/* Largest n accepted by csgs_sample_coreset_noalloc. */
+#define CSGS_NOALLOC_MAX_N 262144
+
+/* csgs_sample_coreset_p without any memory allocation, for callers that cannot
+ * allocate device memory: code inside a host framework that owns all GPU memory
+ * through its own pool, real-time runtimes that forbid allocation after start-up,
+ * and callers without a csgs_ctx (creating one allocates work buffers).  The paper
+ * has no counterpart; this is a deployment variant of the same sampler.
+ *   The sampler's scratch (integer CDF, draw counts, scan partials; about 3 MB) is a
+ *   fixed file-scope device array that every GPU loading this library holds until
+ *   the process exits; n must not exceed CSGS_NOALLOC_MAX_N (else CSGS_E_INVAL).
+ *   It runs on the calling thread's current CUDA device, on cuda_stream (a
+ *   cudaStream_t, NULL = the legacy default stream).  The first call on a device
+ *   looks the array's device address up (cudaGetSymbolAddress); make that first
+ *   call before any stream capture.  Every call shares the one array, which keeps
+ *   the last call's contents (the counts are cleared by each call): calls that
+ *   overlap on the GPU - other streams, other host threads - race and must be
+ *   serialised by the caller.  No cudaMalloc, cudaFree or allocating library call
+ *   is made.  Arguments and outputs as csgs_sample_coreset_p (without the draw
+ *   list); *n_distinct is written on the host after the stream is synchronised. */
+csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t n, int64_t m, uint64_t seed, int32_t* idx_dev,
+                                        float* w_dev, int64_t* n_distinct, void* cuda_stream);
+
 /* Total number of kernels this library has launched in the process (all contexts);
  * the difference across a region counts that region's launches. */
 int64_t csgs_kernel_launch_count(void);

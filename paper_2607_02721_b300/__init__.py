@@ -24,6 +24,7 @@ CSGS_E_CUDA = -3
 CSGS_E_EMPTY = -4
 CSGS_E_TIMEOUT = -5
 CSGS_E_DEVICE_CHECK = -6
+CSGS_NOALLOC_MAX_N = 262144
 RES_PIXEL = 0
 RES_SCENE = 1
 VAR_L1 = 0
@@ -66,7 +67,8 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
-           "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count")
+           "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
+           "csgs_sample_coreset_noalloc")
 
 _lib = None
 
@@ -98,6 +100,7 @@ def lib():
     L.csgs_sync.argtypes = [V]
     L.csgs_get_stats.argtypes = [V, V]
     L.csgs_debug_project.argtypes = [V, I32, I32, V, V]
+    L.csgs_sample_coreset_noalloc.argtypes = [V, I64, I64, U64, V, V, V, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
