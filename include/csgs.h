@@ -74,10 +74,18 @@ typedef struct {
     float pad;
 } csgs_camera;
 
-#define CSGS_RES_PIXEL 0   /* query = pixel, objective = obj_w . RGB (Sec. 3 "Per-pixel construction") */
-#define CSGS_RES_SCENE 1   /* one aggregated query over all views and pixels (Sec. 3 "Per-scene") */
+/* Query resolutions (Sec. 3.5 "Sensitivity at Multiple Resolutions"): what one
+ * query's objective aggregates before imp = a / A and s = max over queries. */
+#define CSGS_RES_PIXEL 0   /* query = pixel, objective = obj_w . RGB ("Per-pixel construction") */
+#define CSGS_RES_SCENE 1   /* one query over all views and pixels ("Per-tile and Per-scene") */
+#define CSGS_RES_CHANNEL 2 /* query = (pixel, channel): the per-channel objective of Sec. 3 */
+#define CSGS_RES_TILE 3    /* query = one 16x16 screen tile of one view */
+#define CSGS_RES_IMAGE 4   /* query = one whole view */
 
+/* Score variants (Sec. 3.5 "Additional variants"); A is the sum of the same terms. */
 #define CSGS_VAR_L1 0      /* a = c rho T (the core score) */
+#define CSGS_VAR_L2 1      /* a = (c rho T)^2 */
+#define CSGS_VAR_NC 2      /* a = rho T (no colour) */
 
 /* Scoring / rendering conventions.  The paper fixes only the definitions; the
  * thresholds are those of the standard 3DGS rasteriser it relies on. */
@@ -109,6 +117,7 @@ typedef struct {
     int64_t capacity_retries; /* re-runs after growing the instance buffers */
     int64_t kernel_launches;  /* kernels this library launched in the call */
     int64_t composite_launches;
+    int64_t queries;          /* pixel queries with A > 0 (|Q'| of Thm. 2; pixel and channel resolutions) */
     double score_ms;          /* the whole call on the stream (CUDA events) */
     double project_ms;        /* phase totals (bit 1) */
     double sort_ms;
@@ -170,6 +179,24 @@ csgs_status csgs_sample_coreset_p(csgs_ctx* ctx, const double* p_dev, int64_t n,
  * validity-violation count appears in csgs_get_stats after csgs_sync. */
 csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev, const float* w_dev,
                         int64_t n_sel, const csgs_score_opts* opts, float* rgb_dev, float* T_dev);
+
+/* Per-pixel quantities of the transfer to true rendering (Sec. 3.3, Lemma "transfer",
+ * Thm. 3) for one view and a weighted pruned scene w (idx_dev / w_dev as in
+ * csgs_render): along the full-scene order, A = sum c rho T, the relaxed objective
+ * A_th = sum w c rho T (full-scene transmittance), the true reduced render
+ * A_w = sum w c rho T_w with T_w = prod (1 - w rho), gamma_q = max over retained
+ * Gaussians of |log T - log T_w|, and min over pairs of (1 - w rho) (validity needs
+ * it > 0).  Use the pure definitions (alpha_min = 0, rho_max = 1, t_min = 0) in opts.
+ * out_dev: device float[H][W][11] = A[3], A_th[3], A_w[3], gamma_q, min factor.
+ * Asynchronous. */
+csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev, const float* w_dev,
+                          int64_t n_sel, const csgs_score_opts* opts, float* out_dev);
+
+/* Thm. 2 sample size: ceil(3 S / eps^2 * log(2 n_queries / delta)); 0 on bad input. */
+double csgs_theorem2_sample_size(double S, double eps_c, double delta, int64_t n_queries);
+
+/* Thm. 3 rendered error: max(1 - e^-gamma (1 - eps_c), e^gamma (1 + eps_c) - 1). */
+double csgs_theorem3_eps(double gamma, double eps_c);
 
 /* Wait for the context's stream and report errors of asynchronous work. */
 csgs_status csgs_sync(csgs_ctx* ctx);

@@ -27,7 +27,12 @@ CSGS_E_DEVICE_CHECK = -6
 CSGS_NOALLOC_MAX_N = 262144
 RES_PIXEL = 0
 RES_SCENE = 1
+RES_CHANNEL = 2
+RES_TILE = 3
+RES_IMAGE = 4
 VAR_L1 = 0
+VAR_L2 = 1
+VAR_NC = 2
 
 
 class CsgsError(RuntimeError):
@@ -61,14 +66,14 @@ class Stats(ctypes.Structure):
                 ("pairs_evaluated", ctypes.c_int64), ("pairs_hit", ctypes.c_int64),
                 ("pairs_evaluated2", ctypes.c_int64), ("pairs_hit2", ctypes.c_int64), ("violations", ctypes.c_int64),
                 ("capacity_retries", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("composite_launches", ctypes.c_int64), ("score_ms", ctypes.c_double),
+                ("composite_launches", ctypes.c_int64), ("queries", ctypes.c_int64), ("score_ms", ctypes.c_double),
                 ("project_ms", ctypes.c_double), ("sort_ms", ctypes.c_double), ("composite_ms", ctypes.c_double)]
 
 
 EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
            "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
-           "csgs_sample_coreset_noalloc")
+           "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps")
 
 _lib = None
 
@@ -101,6 +106,11 @@ def lib():
     L.csgs_get_stats.argtypes = [V, V]
     L.csgs_debug_project.argtypes = [V, I32, I32, V, V]
     L.csgs_sample_coreset_noalloc.argtypes = [V, I64, I64, U64, V, V, V, V]
+    L.csgs_transfer.argtypes = [V, I32, I32, V, V, I64, V, V]
+    L.csgs_theorem2_sample_size.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, I64]
+    L.csgs_theorem2_sample_size.restype = ctypes.c_double
+    L.csgs_theorem3_eps.argtypes = [ctypes.c_double, ctypes.c_double]
+    L.csgs_theorem3_eps.restype = ctypes.c_double
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -138,6 +148,14 @@ def cameras(records) -> "ctypes.Array":
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def theorem2_sample_size(S: float, eps_c: float, delta: float, n_queries: int) -> float:
+    return float(lib().csgs_theorem2_sample_size(S, eps_c, delta, n_queries))
+
+
+def theorem3_eps(gamma: float, eps_c: float) -> float:
+    return float(lib().csgs_theorem3_eps(gamma, eps_c))
 
 
 def kernel_launch_count() -> int:
@@ -282,6 +300,17 @@ class Context:
                                       _ptr(T)))
         self._out()
         return (out, T) if with_T else out
+
+    def transfer(self, sid: int, view: int, idx, w, H: int, W: int, opts: ScoreOpts | None = None):
+        """Per-pixel A, A_th, A_w, gamma_q, min(1 - w rho) of Sec. 3.3 ([H, W, 11])."""
+        torch = self.torch
+        out = self._empty((H, W, 11), torch.float32)
+        opts = opts or default_opts(alpha_min=0.0, rho_max=1.0, t_min=0.0)
+        self._in()
+        self._check(lib().csgs_transfer(self.h, sid, view, _ptr(idx), _ptr(w), idx.numel(), ctypes.byref(opts),
+                                        _ptr(out)))
+        self._out()
+        return out
 
     def debug_project(self, sid: int, view: int, opts: ScoreOpts | None = None):
         torch = self.torch

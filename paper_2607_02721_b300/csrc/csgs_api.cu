@@ -59,6 +59,7 @@ struct csgs_ctx {
     uint32_t cap = 0;
     DevBuf ranges, hist, scan_tmp;
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
+    DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
     csgs_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evpool;  // phase timing
@@ -134,9 +135,10 @@ bool finite3(const float* v, int k) {
 
 csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     if (!o) return fail(ctx, CSGS_E_INVAL, "opts is NULL");
-    if (o->resolution != CSGS_RES_PIXEL && o->resolution != CSGS_RES_SCENE)
+    if (o->resolution < CSGS_RES_PIXEL || o->resolution > CSGS_RES_IMAGE)
         return fail(ctx, CSGS_E_INVAL, "resolution %d is not supported", o->resolution);
-    if (o->variant != CSGS_VAR_L1) return fail(ctx, CSGS_E_INVAL, "variant %d is not supported", o->variant);
+    if (o->variant < CSGS_VAR_L1 || o->variant > CSGS_VAR_NC)
+        return fail(ctx, CSGS_E_INVAL, "variant %d is not supported", o->variant);
     if (!(o->alpha_min >= 0.f) || !(o->rho_max > 0.f && o->rho_max <= 1.f) || !(o->t_min >= 0.f) ||
         !(o->cut2 > 0.f) || !(o->dilation >= 0.f) || !(o->clamp_fov > 0.f) || !finite3(o->obj_w, 3) ||
         o->obj_w[0] < 0.f || o->obj_w[1] < 0.f || o->obj_w[2] < 0.f || o->view_batch < 0)
@@ -311,7 +313,7 @@ void csgs_destroy(csgs_ctx* ctx) {
     DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,   &ctx->dkeys_b, &ctx->dvals_a, &ctx->dvals_b,
                       &ctx->ikeys_a, &ctx->ikeys_b, &ctx->ivals_a, &ctx->ivals_b, &ctx->ranges,  &ctx->hist,
                       &ctx->scan_tmp, &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
-                      &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull};
+                      &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->d_ctr) cudaFree(ctx->d_ctr);
     if (ctx->d_nconst) cudaFree(ctx->d_nconst);
@@ -518,6 +520,7 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     if ((r = ensure_view_buffers(ctx, n, vb, max_tiles))) return r;
     if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
     if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * 2))) return r;
+    if (ko.resolution == CSGS_RES_IMAGE && (r = ensure(ctx, ctx->vbuf, sizeof(float) * (size_t)n))) return r;
     const SceneDev sd = scene_dev(*s);
     cudaStream_t st = ctx->st;
     int retries = 0;
@@ -532,6 +535,8 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
         set_u64(ctx->d_nconst, (unsigned long long)n, st);
         CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
+        if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
+        if (ko.resolution == CSGS_RES_TILE && (r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap))) return r;
         for (int v0 = 0; v0 < nv; v0 += vb) {
             const int nb = (nv - v0) < vb ? (nv - v0) : vb;
             size_t e0 = pt.begin();
@@ -553,11 +558,15 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
                 a.cam = cam;
                 a.o = ko;
                 a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
-                a.s_sum = s_dev;
+                a.s_sum = ko.resolution == CSGS_RES_IMAGE ? P<float>(ctx->vbuf) : s_dev;
+                a.tile_sum = P<float>(ctx->tsum);
                 a.ctr = ctx->d_ctr;
                 a.stats = opts->collect_stats & 1;
+                if (ko.resolution == CSGS_RES_IMAGE)
+                    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
                 size_t e2 = pt.begin();
                 launch_composite_score(a, st);
+                if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
                 pt.end(2, e2);
                 ++comp_launches;
             }
@@ -589,6 +598,7 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     ctx->stats.score_ms = ms;
     ctx->stats.kernel_launches = launches() - l0;
     ctx->stats.composite_launches = comp_launches;
+    ctx->stats.queries = (int64_t)ctx->h_ctr->queries;
     {
         double ph[3] = {0.0, 0.0, 0.0};
         pt.sum(ph);
@@ -730,6 +740,69 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
 }
 
 int64_t csgs_kernel_launch_count(void) { return (int64_t)launches(); }
+
+double csgs_theorem2_sample_size(double S, double eps_c, double delta, int64_t n_queries) {
+    if (!(S > 0.0) || !(eps_c > 0.0) || !(delta > 0.0) || n_queries <= 0) return 0.0;
+    return ceil(3.0 * S / (eps_c * eps_c) * log(2.0 * (double)n_queries / delta));
+}
+
+double csgs_theorem3_eps(double gamma, double eps_c) {
+    const double a = 1.0 - exp(-gamma) * (1.0 - eps_c);
+    const double b = exp(gamma) * (1.0 + eps_c) - 1.0;
+    return a > b ? a : b;
+}
+
+csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev, const float* w_dev,
+                          int64_t n_sel, const csgs_score_opts* opts, float* out_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
+    if (!out_dev || !idx_dev || !w_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
+    if (n_sel < 0 || n_sel > s->n) return fail(ctx, CSGS_E_INVAL, "n_sel out of range");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    if ((r = upload_cams(ctx, s, ko))) return r;
+    const int64_t n = s->n;
+    const CamDev& cam = s->cams[view];
+    if ((r = ensure_view_buffers(ctx, n, 1, cam.tiles_x * cam.tiles_y))) return r;
+    if ((r = ensure(ctx, ctx->wfull, sizeof(float) * (size_t)n))) return r;
+    cudaStream_t st = ctx->st;
+    set_u64(ctx->d_nconst, (unsigned long long)n, st);
+    const SceneDev sd = scene_dev(*s);
+    int retries = 0;
+    for (;;) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
+        scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
+        launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
+                       P<uint2>(ctx->rects), st);
+        const uint32_t* iv = bin_view(ctx, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam);
+        CompositeArgs a{};
+        a.ranges = P<uint2>(ctx->ranges);
+        a.inst_gid = iv;
+        a.splats = P<Splat>(ctx->splats);
+        a.n_gauss = (int)n;
+        a.cam = cam;
+        a.o = ko;
+        a.wsel = P<float>(ctx->wfull);
+        a.aux = out_dev;
+        a.ctr = ctx->d_ctr;
+        launch_composite_transfer(a, st);
+        if ((r = launch_check(ctx, "transfer kernels"))) return r;
+        if ((r = read_counters(ctx))) return r;
+        if (ctx->h_ctr->err & kErrCapacity) {
+            if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+            if ((r = grow_capacity(ctx))) return r;
+            continue;
+        }
+        break;
+    }
+    if (ctx->h_ctr->err & kErrIndex) return fail(ctx, CSGS_E_INVAL, "coreset index out of range");
+    return CSGS_OK;
+}
 
 csgs_status csgs_sync(csgs_ctx* ctx) {
     if (!ctx) return CSGS_E_INVAL;

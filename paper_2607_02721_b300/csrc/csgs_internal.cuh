@@ -80,6 +80,8 @@ struct DevCounters {
     unsigned long long pairs_hit2;
     unsigned long long violations;
     double sumA;                    // scene resolution: sum of the objective over queries
+    double sumA_view;               // image resolution: the current view's objective
+    unsigned long long queries;     // pixel queries with A > 0 (two-pass resolutions)
 };
 
 // ---- launchers (k_project.cu)
@@ -119,12 +121,16 @@ struct CompositeArgs {
     float* rgb;        // render: [H][W][3]
     float* T;          // render: [H][W] (optional)
     uint32_t* s_bits;  // pixel resolution: float bits of s, atomicMax
-    float* s_sum;      // scene resolution: sum of terms, atomicAdd
+    float* s_sum;      // scene / image resolution: sum of terms, atomicAdd
+    float* tile_sum;   // tile resolution: per tile-list entry, the Gaussian's sum over the tile
+    const float* wsel; // transfer: coreset weight per Gaussian (0 = removed)
+    float* aux;        // transfer: [H][W][11] per-pixel outputs
     DevCounters* ctr;
     int stats;
 };
 void launch_composite_render(const CompositeArgs& a, cudaStream_t st);
 void launch_composite_score(const CompositeArgs& a, cudaStream_t st);
+void launch_composite_transfer(const CompositeArgs& a, cudaStream_t st);
 
 // ---- sampling (k_sample.cu)
 struct SampleTemp {
@@ -138,6 +144,8 @@ struct SampleTemp {
 };
 void sum_scores(const float* s, int64_t n, double* partial, double* S, cudaStream_t st);
 void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st);
+// image resolution: s = max(s, vbuf / A_view); vbuf = 0
+void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st);
 void probabilities_from_scores(const float* s, int64_t n, const double* S, double* p, cudaStream_t st);
 void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const SampleTemp& t, int32_t* draws,
                   int32_t* idx, float* w, cudaStream_t st);

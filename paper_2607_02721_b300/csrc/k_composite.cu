@@ -32,7 +32,18 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-enum { kRender = 0, kScorePixel = 1, kScoreScene = 2 };
+// Modes: the render, and the query resolutions of Sec. 3.5.  Pixel and channel
+// resolutions run two passes (A(q) first); tile, image and scene are one pass that
+// sums each Gaussian's terms over the query's pixels (warp sums).
+enum { kRender = 0, kScorePixel = 1, kScoreChannel = 2, kScoreTile = 3, kScoreImage = 4, kScoreScene = 5,
+       kTransfer = 6 };
+// Score variants (Sec. 3.5 "Additional variants"): a = c rho T, (c rho T)^2, rho T.
+enum { kL1 = 0, kL2 = 1, kNC = 2 };
+
+__host__ __device__ constexpr bool two_pass(int mode) { return mode == kScorePixel || mode == kScoreChannel; }
+__host__ __device__ constexpr bool summed(int mode) {
+    return mode == kScoreTile || mode == kScoreImage || mode == kScoreScene;
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -43,8 +54,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 struct Shared {
     float4 A[kThreads];  // s1, s1k, c1, s2
     float4 B[kThreads];  // c2, log2 alpha, thr, cw = obj_w . rgb
-    float4 C[kThreads];  // r, g, b, -
+    float4 C[kThreads];  // r, g, b, cw2 = obj_w . rgb^2
     uint32_t gid[kThreads];
+    float wsel[kThreads];  // transfer: the coreset weight w_i of the staged splat
     uint32_t msk[kThreads];
     uint8_t wl[kWarps][kThreads];  // per-warp compacted batch indices
     uint32_t red[kThreads];
@@ -58,8 +70,8 @@ template <int MODE>
 __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32_t i, uint32_t end, float cx,
                                       float cy) {
     const int tid = threadIdx.x;
-    if (MODE == kScorePixel) sh.red[tid] = 0u;
-    if (MODE == kScoreScene)
+    if (two_pass(MODE)) sh.red[tid] = 0u;
+    if (summed(MODE))
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) sh.part[w][tid] = 0.f;
     sh.msk[tid] = 0u;
@@ -76,8 +88,9 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
     const float c2 = -__fmul_rn(s2, my);
     sh.A[tid] = make_float4(s1, s1k, c1, s2);
     sh.B[tid] = make_float4(c2, c.w, q.w, a.o.ow0 * c.x + a.o.ow1 * c.y + a.o.ow2 * c.z);
-    sh.C[tid] = make_float4(c.x, c.y, c.z, 0.f);
+    sh.C[tid] = make_float4(c.x, c.y, c.z, a.o.ow0 * c.x * c.x + a.o.ow1 * c.y * c.y + a.o.ow2 * c.z * c.z);
     sh.gid[tid] = g;
+    if (MODE == kTransfer) sh.wsel[tid] = __ldg(a.wsel + g);
     // bounding box of the footprint: rx^2 = qcut (1/s1^2 + (s1k/(s1 s2))^2), ry^2 = qcut / s2^2,
     // widened so that FP32 rounding never drops a pixel that passes the test
     const float i1 = 1.f / s1, i2 = 1.f / s2;
@@ -119,7 +132,39 @@ __device__ __forceinline__ float exponent2(const float4& A, const float4& B, flo
     return __fmaf_rn(-e1, e1, __fmaf_rn(-e2, e2, B.y));
 }
 
-template <int MODE, bool STATS>
+// Per-channel accumulation of pass 1 (render: the colours; scores: the variant's
+// per-channel terms, whose sums are the per-channel objectives A_lambda).
+template <int MODE, int VAR>
+__device__ __forceinline__ void accumulate(float& A0, float& A1, float& A2, const float4& Cj, float w) {
+    if (MODE == kRender || VAR == kL1) {
+        A0 = __fmaf_rn(Cj.x, w, A0);
+        A1 = __fmaf_rn(Cj.y, w, A1);
+        A2 = __fmaf_rn(Cj.z, w, A2);
+    } else if (VAR == kL2) {
+        const float a0 = __fmul_rn(Cj.x, w), a1 = __fmul_rn(Cj.y, w), a2 = __fmul_rn(Cj.z, w);
+        A0 = __fmaf_rn(a0, a0, A0);
+        A1 = __fmaf_rn(a1, a1, A1);
+        A2 = __fmaf_rn(a2, a2, A2);
+    } else {
+        A0 = __fadd_rn(A0, w);
+    }
+}
+
+// The pixel-aggregated term a of a contributor with w = rho T.
+template <int VAR>
+__device__ __forceinline__ float pixel_term(float w, const float4& Bj, const float4& Cj) {
+    if (VAR == kL1) return __fmul_rn(Bj.w, w);
+    if (VAR == kL2) return __fmul_rn(Cj.w, __fmul_rn(w, w));
+    return w;
+}
+
+template <int VAR>
+__device__ __forceinline__ float pixel_objective(const KOpts& o, float A0, float A1, float A2) {
+    if (VAR == kNC) return A0;
+    return o.ow0 * A0 + o.ow1 * A1 + o.ow2 * A2;
+}
+
+template <int MODE, int VAR, bool STATS>
 __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     __shared__ Shared sh;
     const CamDev& cam = a.cam;
@@ -137,7 +182,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     const float rho_max = a.o.rho_max, t_min = a.o.t_min;
 
     float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
+    float tr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // transfer: A_th[3], A_w[3]
+    float Tw = 1.f, gam = 0.f, minf = 1.f;
     int last = 0;
+    int processed = 0;  // tile-list entries staged by pass 1 (CTA-uniform)
     bool done = !inside;
     unsigned long long n_eval = 0, n_hit = 0, n_viol = 0;
     if (tid == 0) sh.last = 0;
@@ -148,8 +196,42 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         stage<MODE>(a, sh, start + b + tid, rg.y, cx, cy);
         __syncthreads();
         const int cnt = min(kThreads, n - b);
+        processed = b + cnt;
         const int nw = warp_list(sh, cnt, warp, lane);
-        if (MODE != kScoreScene) {
+        if (MODE == kTransfer) {
+            // full-scene order with T and the reduced scene's T_w side by side
+            for (int k = 0; k < nw && !done; ++k) {
+                const int j = sh.wl[warp][k];
+                const float4 Aj = sh.A[j];
+                const float4 Bj = sh.B[j];
+                const float p = exponent2(Aj, Bj, X, Y);
+                if (p < Bj.z) continue;
+                const float r = fminf(rho_max, ex2_approx(p));
+                const float4 Cj = sh.C[j];
+                const float w = __fmul_rn(r, T);
+                A0 = __fmaf_rn(Cj.x, w, A0);
+                A1 = __fmaf_rn(Cj.y, w, A1);
+                A2 = __fmaf_rn(Cj.z, w, A2);
+                const float wi = sh.wsel[j];
+                if (wi > 0.f) {
+                    const float wt = __fmul_rn(wi, w);
+                    tr[0] = __fmaf_rn(Cj.x, wt, tr[0]);
+                    tr[1] = __fmaf_rn(Cj.y, wt, tr[1]);
+                    tr[2] = __fmaf_rn(Cj.z, wt, tr[2]);
+                    const float ww = __fmul_rn(__fmul_rn(wi, r), Tw);
+                    tr[3] = __fmaf_rn(Cj.x, ww, tr[3]);
+                    tr[4] = __fmaf_rn(Cj.y, ww, tr[4]);
+                    tr[5] = __fmaf_rn(Cj.z, ww, tr[5]);
+                    if (T > 0.f && Tw > 0.f) gam = fmaxf(gam, fabsf(log2f(T) - log2f(Tw)) * 0.69314718055994531f);
+                }
+                const float f = __fadd_rn(1.f, -__fmul_rn(wi, r));
+                minf = fminf(minf, f);
+                Tw = __fmul_rn(Tw, f);
+                const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
+                if (Tn < t_min) done = true;  // t_min = 0 in the pure setting: never
+                T = Tn;
+            }
+        } else if (!summed(MODE)) {
             if (!done) {
                 for (int k = 0; k < nw; ++k) {
                     const int j = sh.wl[warp][k];
@@ -170,16 +252,13 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                         break;
                     }
                     const float w = __fmul_rn(r, T);
-                    const float4 Cj = sh.C[j];
-                    A0 = __fmaf_rn(Cj.x, w, A0);
-                    A1 = __fmaf_rn(Cj.y, w, A1);
-                    A2 = __fmaf_rn(Cj.z, w, A2);
+                    accumulate<MODE, VAR>(A0, A1, A2, sh.C[j], w);
                     T = Tn;
                     last = b + j + 1;
                 }
             }
         } else {
-            // per-scene resolution: warp-uniform loop so the warp can sum a per Gaussian
+            // summed resolutions: warp-uniform loop so the warp can sum a per Gaussian
             bool act = !done;
             if (__any_sync(0xffffffffu, act)) {
                 for (int k = 0; k < nw; ++k) {
@@ -200,10 +279,8 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                             } else {
                                 const float w = __fmul_rn(r, T);
                                 const float4 Cj = sh.C[j];
-                                A0 = __fmaf_rn(Cj.x, w, A0);
-                                A1 = __fmaf_rn(Cj.y, w, A1);
-                                A2 = __fmaf_rn(Cj.z, w, A2);
-                                v = __fmul_rn(Bj.w, w);
+                                accumulate<MODE, VAR>(A0, A1, A2, Cj, w);
+                                v = pixel_term<VAR>(w, Bj, Cj);
                                 T = Tn;
                             }
                         }
@@ -221,7 +298,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                 float v = 0.f;
 #pragma unroll
                 for (int w = 0; w < kWarps; ++w) v += sh.part[w][tid];
-                if (v > 0.f) atomicAdd(a.s_sum + sh.gid[tid], v);
+                if (MODE == kScoreTile)
+                    a.tile_sum[start + b + tid] = v;
+                else if (v > 0.f)
+                    atomicAdd(a.s_sum + sh.gid[tid], v);
             }
         }
     }
@@ -236,28 +316,71 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         }
     }
 
-    if (MODE == kScoreScene) {
-        // CTA sum of the pixel objective, added to the FP64 scene total
-        double Ao = inside ? (double)(a.o.ow0 * A0 + a.o.ow1 * A1 + a.o.ow2 * A2) : 0.0;
+    if (MODE == kTransfer && inside) {
+        float* o = a.aux + ((size_t)py * cam.W + px) * 11;
+        o[0] = A0;
+        o[1] = A1;
+        o[2] = A2;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) o[3 + k] = tr[k];
+        o[9] = gam;
+        o[10] = minf;
+    }
+
+    if (two_pass(MODE)) {
+        // |Q'|: pixel queries with a non-zero objective
+        const bool nz = inside && pixel_objective<VAR>(a.o, A0, A1, A2) > 0.f;
+        const unsigned c = __popc(__ballot_sync(0xffffffffu, nz));
+        if (lane == 0 && c) atomicAdd(&a.ctr->queries, (unsigned long long)c);
+    }
+
+    if (summed(MODE)) {
+        // CTA sum of the pixel objective: the tile query's A, or a share of the
+        // image / scene query's A (FP64 totals)
+        double Ao = inside ? (double)pixel_objective<VAR>(a.o, A0, A1, A2) : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) Ao += __shfl_xor_sync(0xffffffffu, Ao, o);
         __syncthreads();
         if (lane == 0) sh.sumA[warp] = Ao;
         __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int w = 0; w < kWarps; ++w) t += sh.sumA[w];
-            if (t > 0.0) atomicAdd(&a.ctr->sumA, t);
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += sh.sumA[w];
+        if (MODE == kScoreScene && tid == 0 && t > 0.0) atomicAdd(&a.ctr->sumA, t);
+        if (MODE == kScoreImage && tid == 0 && t > 0.0) atomicAdd(&a.ctr->sumA_view, t);
+        if (MODE == kScoreTile && t > 0.0) {
+            // imp(g, tile) = (sum of g's terms over the tile) / A(tile)
+            const double inv = 1.0 / t;
+            for (int i = tid; i < processed; i += kThreads) {
+                const float v = a.tile_sum[start + i];
+                if (v > 0.f) {
+                    const uint32_t g = __ldg(a.inst_gid + start + i);
+                    if (g < (uint32_t)a.n_gauss) atomicMax(a.s_bits + g, __float_as_uint((float)((double)v * inv)));
+                }
+            }
         }
     }
 
     // ---------------------------------------------------------------- pass 2
     unsigned long long n_eval2 = 0, n_hit2 = 0;
-    if (MODE == kScorePixel) {
-        const float Aobj = a.o.ow0 * A0 + a.o.ow1 * A1 + a.o.ow2 * A2;
-        const bool has = inside && Aobj > 0.f;  // queries with A = 0 are discarded
-        // T' = T / A: imp = cw rho T' directly
-        float Tq = has ? 1.f / Aobj : 0.f;
+    if (two_pass(MODE)) {
+        // queries with A = 0 are discarded (Sec. 3.2)
+        float inv0 = 0.f, inv1 = 0.f, inv2 = 0.f;
+        bool has;
+        if (MODE == kScorePixel) {
+            const float Aobj = pixel_objective<VAR>(a.o, A0, A1, A2);
+            has = inside && Aobj > 0.f;
+            inv0 = has ? 1.f / Aobj : 0.f;
+        } else {
+            inv0 = A0 > 0.f ? 1.f / A0 : 0.f;
+            inv1 = A1 > 0.f ? 1.f / A1 : 0.f;
+            inv2 = A2 > 0.f ? 1.f / A2 : 0.f;
+            if (VAR == kNC) inv1 = inv2 = inv0;
+            has = inside && (inv0 > 0.f || inv1 > 0.f || inv2 > 0.f);
+        }
+        // pixel resolution with a term linear in T: track T / A directly
+        constexpr bool kScaled = MODE == kScorePixel && VAR != kL2;
+        T = kScaled ? inv0 : 1.f;
         if (!has) last = 0;
         __syncthreads();
         atomicMax(&sh.last, last);
@@ -283,8 +406,33 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     if (p >= Bj.z) {
                         const float r = fminf(rho_max, ex2_approx(p));
                         if (STATS) ++n_hit2;
-                        bits = __float_as_uint(__fmul_rn(Bj.w, __fmul_rn(r, Tq)));
-                        Tq = __fmul_rn(Tq, __fadd_rn(1.f, -r));
+                        const float w = __fmul_rn(r, T);
+                        float imp;
+                        if (kScaled) {
+                            imp = VAR == kL1 ? __fmul_rn(Bj.w, w) : w;
+                        } else if (MODE == kScorePixel) {
+                            imp = __fmul_rn(pixel_term<VAR>(w, Bj, sh.C[j]), inv0);
+                        } else {
+                            const float4 Cj = sh.C[j];
+                            float t0, t1, t2;
+                            if (VAR == kL1) {
+                                t0 = __fmul_rn(Cj.x, w);
+                                t1 = __fmul_rn(Cj.y, w);
+                                t2 = __fmul_rn(Cj.z, w);
+                            } else if (VAR == kL2) {
+                                t0 = __fmul_rn(Cj.x, w);
+                                t1 = __fmul_rn(Cj.y, w);
+                                t2 = __fmul_rn(Cj.z, w);
+                                t0 = __fmul_rn(t0, t0);
+                                t1 = __fmul_rn(t1, t1);
+                                t2 = __fmul_rn(t2, t2);
+                            } else {
+                                t0 = t1 = t2 = w;
+                            }
+                            imp = fmaxf(__fmul_rn(t0, inv0), fmaxf(__fmul_rn(t1, inv1), __fmul_rn(t2, inv2)));
+                        }
+                        bits = __float_as_uint(imp);
+                        T = __fmul_rn(T, __fadd_rn(1.f, -r));
                     }
                 }
                 const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
@@ -320,27 +468,46 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
 
 }  // namespace
 
+void launch_composite_transfer(const CompositeArgs& a, cudaStream_t st) {
+    const int tiles = a.cam.tiles_x * a.cam.tiles_y;
+    k_composite<kTransfer, kL1, false><<<tiles, kThreads, 0, st>>>(a);
+    count_launches(1);
+}
+
 void launch_composite_render(const CompositeArgs& a, cudaStream_t st) {
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;
     if (a.stats)
-        k_composite<kRender, true><<<tiles, kThreads, 0, st>>>(a);
+        k_composite<kRender, kL1, true><<<tiles, kThreads, 0, st>>>(a);
     else
-        k_composite<kRender, false><<<tiles, kThreads, 0, st>>>(a);
+        k_composite<kRender, kL1, false><<<tiles, kThreads, 0, st>>>(a);
     count_launches(1);
+}
+
+template <int MODE, int VAR>
+static void launch_mode(const CompositeArgs& a, int tiles, cudaStream_t st) {
+    if (a.stats)
+        k_composite<MODE, VAR, true><<<tiles, kThreads, 0, st>>>(a);
+    else
+        k_composite<MODE, VAR, false><<<tiles, kThreads, 0, st>>>(a);
+}
+
+template <int MODE>
+static void launch_var(const CompositeArgs& a, int tiles, cudaStream_t st) {
+    switch (a.o.variant) {
+        case CSGS_VAR_L2: launch_mode<MODE, kL2>(a, tiles, st); break;
+        case CSGS_VAR_NC: launch_mode<MODE, kNC>(a, tiles, st); break;
+        default: launch_mode<MODE, kL1>(a, tiles, st); break;
+    }
 }
 
 void launch_composite_score(const CompositeArgs& a, cudaStream_t st) {
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;
-    if (a.o.resolution == CSGS_RES_SCENE) {
-        if (a.stats)
-            k_composite<kScoreScene, true><<<tiles, kThreads, 0, st>>>(a);
-        else
-            k_composite<kScoreScene, false><<<tiles, kThreads, 0, st>>>(a);
-    } else {
-        if (a.stats)
-            k_composite<kScorePixel, true><<<tiles, kThreads, 0, st>>>(a);
-        else
-            k_composite<kScorePixel, false><<<tiles, kThreads, 0, st>>>(a);
+    switch (a.o.resolution) {
+        case CSGS_RES_SCENE: launch_var<kScoreScene>(a, tiles, st); break;
+        case CSGS_RES_CHANNEL: launch_var<kScoreChannel>(a, tiles, st); break;
+        case CSGS_RES_TILE: launch_var<kScoreTile>(a, tiles, st); break;
+        case CSGS_RES_IMAGE: launch_var<kScoreImage>(a, tiles, st); break;
+        default: launch_var<kScorePixel>(a, tiles, st); break;
     }
     count_launches(1);
 }

@@ -51,6 +51,18 @@ __global__ void k_scene_normalise(float* __restrict__ s, int64_t n, const double
         s[i] = A > 0.0 ? (float)((double)s[i] / A) : 0.f;
 }
 
+__global__ void k_image_fold(float* __restrict__ s, float* __restrict__ vbuf, int64_t n,
+                             const double* __restrict__ sumA_view) {
+    const double A = *sumA_view;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = vbuf[i];
+        if (v > 0.f) {
+            if (A > 0.0) s[i] = fmaxf(s[i], (float)((double)v / A));
+            vbuf[i] = 0.f;
+        }
+    }
+}
+
 __global__ void k_probs(const float* __restrict__ s, int64_t n, const double* __restrict__ S, double* __restrict__ p) {
     const double tot = *S;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -230,6 +242,11 @@ void sum_scores(const float* s, int64_t n, double* partial, double* S, cudaStrea
 
 void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st) {
     k_scene_normalise<<<148 * 8, 256, 0, st>>>(s, n, sumA);
+    count_launches(1);
+}
+
+void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st) {
+    k_image_fold<<<148 * 8, 256, 0, st>>>(s, vbuf, n, sumA_view);
     count_launches(1);
 }
 

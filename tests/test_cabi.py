@@ -45,11 +45,11 @@ def test_default_opts_are_the_rasteriser_conventions(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # csgs_camera is 80 bytes; csgs_scene_desc 56; csgs_score_opts 52; csgs_stats 120
+    # csgs_camera is 80 bytes; csgs_scene_desc 56; csgs_score_opts 52; csgs_stats 128
     assert ctypes.sizeof(csgs.Camera) == 80
     assert ctypes.sizeof(csgs.SceneDesc) == 56
     assert ctypes.sizeof(csgs.ScoreOpts) == 52
-    assert ctypes.sizeof(csgs.Stats) == 120
+    assert ctypes.sizeof(csgs.Stats) == 128
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):
@@ -57,3 +57,14 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.csgs_score(None, 0, None, None, None) == csgs.CSGS_E_INVAL
     assert lib.csgs_sync(None) == csgs.CSGS_E_INVAL
     lib.csgs_destroy(None)
+
+
+def test_theorem_helpers(lib):
+    import math
+
+    S, eps, delta, nq = 120.5, 0.2, 0.05, 131072
+    assert csgs.theorem2_sample_size(S, eps, delta, nq) == math.ceil(3 * S / eps ** 2 * math.log(2 * nq / delta))
+    assert csgs.theorem2_sample_size(0.0, eps, delta, nq) == 0.0
+    g, e = 0.1, 0.05
+    assert abs(csgs.theorem3_eps(g, e) - max(1 - math.exp(-g) * (1 - e), math.exp(g) * (1 + e) - 1)) < 1e-15
+    assert csgs.theorem3_eps(0.0, e) == pytest.approx(e)

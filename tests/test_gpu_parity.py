@@ -348,3 +348,86 @@ def test_instance_capacity_growth(ctx, torch):
     ok = ~ref["flags"].astype(bool)
     assert np.abs(got[ok] - ref["rgb"][ok]).max() <= RGB_TOL
     c2.close()
+
+
+# ---------------------------------------------------------------- resolutions and variants (Sec. 3.5)
+
+RESOLUTIONS = [("pixel", csgs.RES_PIXEL, oracle.RES_PIXEL), ("channel", csgs.RES_CHANNEL, oracle.RES_CHANNEL),
+               ("tile", csgs.RES_TILE, oracle.RES_TILE), ("image", csgs.RES_IMAGE, oracle.RES_IMAGE),
+               ("scene", csgs.RES_SCENE, oracle.RES_SCENE)]
+VARIANTS = [("L1", csgs.VAR_L1, oracle.VAR_L1), ("L2", csgs.VAR_L2, oracle.VAR_L2), ("nocolor", csgs.VAR_NC, oracle.VAR_NC)]
+
+
+@pytest.mark.parametrize("res", RESOLUTIONS, ids=[r[0] for r in RESOLUTIONS])
+@pytest.mark.parametrize("var", VARIANTS, ids=[v[0] for v in VARIANTS])
+def test_resolutions_and_variants_match_oracle(ctx, small, small_sid, res, var):
+    sc, cams, _, sa = small
+    s, S = ctx.score(small_sid, csgs.default_opts(resolution=res[1], variant=var[1]))
+    ref = oracle.score(sa, cams, Opts(resolution=res[2], variant=var[2], tile=16))
+    s = s.cpu().numpy()
+    if res[0] in ("pixel", "channel"):
+        check_scores(s, S, ref)
+    else:
+        # sums over many pixels: a straddling pixel moves a sum by its one term
+        big = ref["s"] > 1e-6
+        rel = np.abs(s[big].astype(np.float64) - ref["s"][big]) / ref["s"][big]
+        note(f"score_rel_q995_{res[0]}_{var[0]}", np.quantile(rel, 0.995))
+        assert np.quantile(rel, 0.995) <= S_RTOL
+        assert rel.mean() <= 1e-4
+        assert abs(S - ref["S"]) <= 1e-3 * ref["S"]
+    if res[0] == "scene":
+        assert abs(S - 1.0) < 1e-4
+    assert S >= 1.0 - 1e-4
+
+
+def test_resolution_mediant_chain_on_gpu(ctx, small_sid):
+    s = {}
+    for name, r, _ in RESOLUTIONS:
+        s[name] = ctx.score(small_sid, csgs.default_opts(resolution=r))[0].cpu().numpy().astype(np.float64)
+    tol = 1e-5
+    assert np.all(s["channel"] >= s["pixel"] * (1 - tol))
+    assert np.all(s["pixel"] >= s["tile"] * (1 - tol))
+    assert np.all(s["tile"] >= s["image"] * (1 - tol))
+    assert np.all(s["image"] >= s["scene"] * (1 - tol))
+
+
+# ---------------------------------------------------------------- transfer diagnostics (Sec. 3.3)
+
+def test_transfer_quantities_match_oracle(ctx, small, small_sid, torch):
+    sc, cams, m, sa = small
+    po = Opts.pure()
+    ref = oracle.score(sa, cams, po)
+    p, S = oracle.probabilities(ref["s"])
+    smp = oracle.sample(p, 4 * m, 3)
+    w32 = smp["w_sel"].astype(np.float32)
+    wfull = np.zeros(sc.n)
+    wfull[smp["idx"]] = w32.astype(np.float64)
+    idx_t = torch.tensor(smp["idx"], device="cuda", dtype=torch.int32)
+    w_t = torch.tensor(w32, device="cuda")
+    gopts = csgs.default_opts(alpha_min=0.0, rho_max=1.0, t_min=0.0)
+    for v in (1, 4):
+        got = ctx.transfer(small_sid, v, idx_t, w_t, 128, 128, gopts).cpu().numpy().astype(np.float64)
+        t = oracle.transfer(sa, cams[v], wfull, po)
+        fl = oracle.render(sa, cams[v], po)["flags"].astype(bool)
+        ok = ~fl
+        for k, key in enumerate(("A", "A_th", "A_w")):
+            err = np.abs(got[..., 3 * k:3 * k + 3] - t[key])[ok].max()
+            note(f"transfer_{key}_abs", err)
+            assert err <= RGB_TOL * 10, (key, err)
+        valid = (t["min_factor"] > 0) & ok
+        g_err = np.abs(got[..., 9] - t["gamma"])[valid]
+        note("transfer_gamma_abs", g_err.max())
+        assert g_err.max() <= 1e-3
+        # the sandwich of Lemma "transfer" on the GPU's own outputs
+        g = got[..., 9:10]
+        lo, hi = np.exp(-g) * got[..., 3:6], np.exp(g) * got[..., 3:6]
+        A_w = got[..., 6:9]
+        assert np.all((A_w >= lo * (1 - 1e-4) - 1e-6)[valid]) and np.all((A_w <= hi * (1 + 1e-4) + 1e-6)[valid])
+
+
+def test_query_count_matches_oracle(ctx, small, small_sid):
+    sc, cams, _, sa = small
+    ctx.score(small_sid)
+    q = ctx.stats()["queries"]
+    ref = oracle.score(sa, cams)
+    assert abs(q - ref["queries"]) <= ref["flagged"]
