@@ -410,14 +410,18 @@ def test_transfer_quantities_match_oracle(ctx, small, small_sid, torch):
         t = oracle.transfer(sa, cams[v], wfull, po)
         fl = oracle.render(sa, cams[v], po)["flags"].astype(bool)
         ok = ~fl
+        # FP32 log-transmittance is only accurate while every factor 1 - w rho stays away
+        # from 0 (its relative error is about 1e-6 / (1 - w rho)); compare there
+        well = ok & (t["min_factor"] > 1e-2)
+        assert well.mean() > 0.5
         for k, key in enumerate(("A", "A_th", "A_w")):
-            err = np.abs(got[..., 3 * k:3 * k + 3] - t[key])[ok].max()
+            err = np.abs(got[..., 3 * k:3 * k + 3] - t[key])[well].max()
             note(f"transfer_{key}_abs", err)
-            assert err <= RGB_TOL * 10, (key, err)
+            assert err <= RGB_TOL, (key, err)
         valid = (t["min_factor"] > 0) & ok
-        g_err = np.abs(got[..., 9] - t["gamma"])[valid]
+        g_err = np.abs(got[..., 9] - t["gamma"])[well]
         note("transfer_gamma_abs", g_err.max())
-        assert g_err.max() <= 1e-3
+        assert g_err.max() <= 1e-3 + 1e-3 * t["gamma"][well].max()
         # the sandwich of Lemma "transfer" on the GPU's own outputs
         g = got[..., 9:10]
         lo, hi = np.exp(-g) * got[..., 3:6], np.exp(g) * got[..., 3:6]
