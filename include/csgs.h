@@ -227,6 +227,13 @@ csgs_status csgs_get_stats(csgs_ctx* ctx, csgs_stats* out);
 csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t n, int64_t m, uint64_t seed, int32_t* idx_dev,
                                         float* w_dev, int64_t* n_distinct, void* cuda_stream);
 
+/* Diagnostic of the tensor-core path: C[128][N] = A[128][K] * B[N][K]^T with BF16 A, B
+ * (device, row-major) and FP32 C (device), computed by one tcgen05.mma chain with the
+ * accumulator in tensor memory.  K % 16 == 0, 16 <= K <= 128; N % 16 == 0, 16 <= N <= 256.
+ * Synchronises; CSGS_E_TIMEOUT if the MMA completion was not observed in time. */
+csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                               int32_t N);
+
 /* Total number of kernels this library has launched in the process (all contexts);
  * the difference across a region counts that region's launches. */
 int64_t csgs_kernel_launch_count(void);

@@ -73,7 +73,8 @@ class Stats(ctypes.Structure):
 EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
            "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
-           "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps")
+           "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
+           "csgs_debug_tc_gemm")
 
 _lib = None
 
@@ -111,6 +112,7 @@ def lib():
     L.csgs_theorem2_sample_size.restype = ctypes.c_double
     L.csgs_theorem3_eps.argtypes = [ctypes.c_double, ctypes.c_double]
     L.csgs_theorem3_eps.restype = ctypes.c_double
+    L.csgs_debug_tc_gemm.argtypes = [V, V, V, V, I32, I32]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -311,6 +313,15 @@ class Context:
                                         _ptr(out)))
         self._out()
         return out
+
+    def debug_tc_gemm(self, A, B):
+        """C = A @ B^T on the tensor cores (A: [128, K] bf16, B: [N, K] bf16)."""
+        torch = self.torch
+        C = self._empty((A.shape[0], B.shape[0]), torch.float32)
+        self._in()
+        self._check(lib().csgs_debug_tc_gemm(self.h, _ptr(A), _ptr(B), _ptr(C), A.shape[1], B.shape[0]))
+        self._out()
+        return C
 
     def debug_project(self, sid: int, view: int, opts: ScoreOpts | None = None):
         torch = self.torch

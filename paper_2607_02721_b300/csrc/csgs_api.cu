@@ -741,6 +741,22 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
 
 int64_t csgs_kernel_launch_count(void) { return (int64_t)launches(); }
 
+csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                               int32_t N) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!A_dev || !B_dev || !C_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
+    if (K < 16 || K > 128 || K % 16 || N < 16 || N > 256 || N % 16)
+        return fail(ctx, CSGS_E_INVAL, "unsupported GEMM shape K=%d N=%d", K, N);
+    cudaSetDevice(ctx->device);
+    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
+    gemm_check(A_dev, B_dev, C_dev, K, N, reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
+    csgs_status r;
+    if ((r = launch_check(ctx, "tensor-core GEMM"))) return r;
+    if ((r = read_counters(ctx))) return r;
+    if (ctx->h_ctr->err) return fail(ctx, CSGS_E_TIMEOUT, "MMA completion not observed");
+    return CSGS_OK;
+}
+
 double csgs_theorem2_sample_size(double S, double eps_c, double delta, int64_t n_queries) {
     if (!(S > 0.0) || !(eps_c > 0.0) || !(delta > 0.0) || n_queries <= 0) return 0.0;
     return ceil(3.0 * S / (eps_c * eps_c) * log(2.0 * (double)n_queries / delta));

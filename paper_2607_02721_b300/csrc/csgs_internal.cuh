@@ -150,4 +150,7 @@ void probabilities_from_scores(const float* s, int64_t n, const double* S, doubl
 void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const SampleTemp& t, int32_t* draws,
                   int32_t* idx, float* w, cudaStream_t st);
 
+// ---- tensor cores (k_mlp.cu)
+int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, cudaStream_t st);
+
 }  // namespace csgs
