@@ -127,6 +127,18 @@ def lib():
         _lib.or_theorem2_m.restype = ctypes.c_double
         _lib.or_transfer.argtypes = [P, P, P, P, P]
         _lib.or_score_pixels.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P]
+        _lib.or_mlp_nparam.restype = ctypes.c_int
+        _lib.or_bf16.argtypes = [ctypes.c_double]
+        _lib.or_bf16.restype = ctypes.c_double
+        _lib.or_gelu.argtypes = [ctypes.c_double]
+        _lib.or_gelu.restype = ctypes.c_double
+        _lib.or_gelu_d.argtypes = [ctypes.c_double]
+        _lib.or_gelu_d.restype = ctypes.c_double
+        _lib.or_mlp_forward.argtypes = [P, P, ctypes.c_int64, ctypes.c_int, P, P, P, P, P]
+        _lib.or_mlp_backward.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int, P]
+        _lib.or_mlp_backward.restype = ctypes.c_double
+        _lib.or_adam.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int64]
         _lib.or_num_threads.restype = ctypes.c_int
     return _lib
 
@@ -319,3 +331,56 @@ def score_pixels(scene, cam, pixels, opts: Opts | None = None):
     if rc:
         raise MemoryError("oracle score_pixels failed")
     return dict(s=s, touched=touched.astype(bool), flags=flags.astype(bool))
+
+
+# ---------------------------------------------------------------- surrogate MLP
+MLP_IN, MLP_H = 64, 256
+
+
+def mlp_nparam() -> int:
+    return lib().or_mlp_nparam()
+
+
+def mlp_split(P):
+    """Views of a parameter block: W1 [256,64], b1, W2 [256,256], b2, w3, b3."""
+    i = 0
+    out = []
+    for shape in ((MLP_H, MLP_IN), (MLP_H,), (MLP_H, MLP_H), (MLP_H,), (MLP_H,), (1,)):
+        k = int(np.prod(shape))
+        out.append(P[i:i + k].reshape(shape))
+        i += k
+    return out
+
+
+def bf16(x: float) -> float:
+    return lib().or_bf16(x)
+
+
+def gelu(z: float) -> float:
+    return lib().or_gelu(z)
+
+
+def gelu_d(z: float) -> float:
+    return lib().or_gelu_d(z)
+
+
+def mlp_forward(P, X, emulate: bool = True):
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+    y = np.zeros(X.shape[0])
+    lib().or_mlp_forward(_ptr(P), _ptr(X), X.shape[0], int(emulate), _ptr(y), None, None, None, None)
+    return y
+
+
+def mlp_backward(P, X, t, emulate: bool = True):
+    """(loss, gradient block) of the mean squared error."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float32).reshape(-1, MLP_IN)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    G = np.zeros_like(P)
+    loss = lib().or_mlp_backward(_ptr(P), _ptr(X), _ptr(t), X.shape[0], int(emulate), _ptr(G))
+    return loss, G
+
+
+def adam(p, g, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-8):
+    lib().or_adam(_ptr(p), _ptr(np.ascontiguousarray(g)), _ptr(m), _ptr(v), p.shape[0], lr, b1, b2, eps, step)

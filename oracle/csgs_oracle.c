@@ -911,3 +911,134 @@ int or_score_pixels(const or_scene* sc, const float* cam, const or_opts* o, int6
     free_view(&v);
     return 0;
 }
+
+/* ---------------------------------------------------------------- surrogate MLP */
+/* The surrogate sensitivity model (not in the paper): x (64 features, zero-padded)
+ * -> 256 (GELU) -> 256 (GELU) -> 1, predicting log-sensitivity.  FP64 arithmetic with
+ * the GPU's BF16 rounding points emulated: the inputs, W1, W2, the first hidden
+ * activation and the two back-propagated pre-activation gradients are rounded to
+ * BF16 (round to nearest even, through float32); everything else stays FP64.
+ * Parameter block (doubles): W1[256][64], b1[256], W2[256][256], b2[256], w3[256], b3. */
+#define MLP_IN 64
+#define MLP_H 256
+#define MLP_NPARAM (MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1)
+
+int or_mlp_nparam(void) { return MLP_NPARAM; }
+
+double or_bf16(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    u &= 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+static double gelu_d(double z) {
+    const double pi = 3.14159265358979323846;
+    return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * pi);
+}
+
+double or_gelu(double z) { return gelu(z); }
+double or_gelu_d(double z) { return gelu_d(z); }
+
+/* Forward of B rows.  emulate: 1 = BF16 rounding points, 0 = plain FP64 (for finite
+ * differences).  y[B]; when z1/h1/z2/h2 are non-NULL they receive [B][256]. */
+void or_mlp_forward(const double* P, const float* X, int64_t B, int emulate, double* y, double* z1o, double* h1o,
+                    double* z2o, double* h2o) {
+    const double *W1 = P, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H, *w3 = b2 + MLP_H,
+                 *b3 = w3 + MLP_H;
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < B; ++r) {
+        double x[MLP_IN], z1[MLP_H], h1[MLP_H], z2[MLP_H], h2[MLP_H];
+        for (int k = 0; k < MLP_IN; ++k) x[k] = emulate ? or_bf16(X[r * MLP_IN + k]) : X[r * MLP_IN + k];
+        for (int o = 0; o < MLP_H; ++o) {
+            double acc = 0.0;
+            for (int k = 0; k < MLP_IN; ++k) acc += (emulate ? or_bf16(W1[o * MLP_IN + k]) : W1[o * MLP_IN + k]) * x[k];
+            z1[o] = acc + b1[o];
+            h1[o] = emulate ? or_bf16(gelu(z1[o])) : gelu(z1[o]);
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            double acc = 0.0;
+            for (int k = 0; k < MLP_H; ++k) acc += (emulate ? or_bf16(W2[o * MLP_H + k]) : W2[o * MLP_H + k]) * h1[k];
+            z2[o] = acc + b2[o];
+            h2[o] = gelu(z2[o]);
+        }
+        double acc = b3[0];
+        for (int k = 0; k < MLP_H; ++k) acc += w3[k] * h2[k];
+        y[r] = acc;
+        if (z1o)
+            for (int k = 0; k < MLP_H; ++k) {
+                z1o[r * MLP_H + k] = z1[k];
+                h1o[r * MLP_H + k] = h1[k];
+                z2o[r * MLP_H + k] = z2[k];
+                h2o[r * MLP_H + k] = h2[k];
+            }
+    }
+}
+
+/* Loss mean_r (y_r - t_r)^2 and its gradient with respect to every parameter (G has the
+ * parameter block's layout).  Returns the loss. */
+double or_mlp_backward(const double* P, const float* X, const float* t, int64_t B, int emulate, double* G) {
+    const double *W1 = P, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H, *w3 = b2 + MLP_H;
+    (void)b1;
+    (void)b2;
+    double* y = (double*)malloc(sizeof(double) * B);
+    double* z1 = (double*)malloc(sizeof(double) * B * MLP_H);
+    double* h1 = (double*)malloc(sizeof(double) * B * MLP_H);
+    double* z2 = (double*)malloc(sizeof(double) * B * MLP_H);
+    double* h2 = (double*)malloc(sizeof(double) * B * MLP_H);
+    or_mlp_forward(P, X, B, emulate, y, z1, h1, z2, h2);
+    memset(G, 0, sizeof(double) * MLP_NPARAM);
+    double *gW1 = G, *gb1 = gW1 + MLP_H * MLP_IN, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H, *gw3 = gb2 + MLP_H,
+           *gb3 = gw3 + MLP_H;
+    double loss = 0.0;
+    for (int64_t r = 0; r < B; ++r) {
+        const double e = y[r] - t[r];
+        loss += e * e / (double)B;
+        const double dy = 2.0 * e / (double)B;
+        double dz2[MLP_H], dz2b[MLP_H], dz1[MLP_H];
+        gb3[0] += dy;
+        for (int o = 0; o < MLP_H; ++o) {
+            gw3[o] += dy * h2[r * MLP_H + o];
+            dz2[o] = dy * w3[o] * gelu_d(z2[r * MLP_H + o]);
+            dz2b[o] = emulate ? or_bf16(dz2[o]) : dz2[o];
+            gb2[o] += dz2[o];
+        }
+        for (int o = 0; o < MLP_H; ++o)
+            for (int k = 0; k < MLP_H; ++k) gW2[o * MLP_H + k] += dz2b[o] * h1[r * MLP_H + k];
+        for (int k = 0; k < MLP_H; ++k) {
+            double acc = 0.0;
+            for (int o = 0; o < MLP_H; ++o) acc += dz2b[o] * (emulate ? or_bf16(W2[o * MLP_H + k]) : W2[o * MLP_H + k]);
+            dz1[k] = acc * gelu_d(z1[r * MLP_H + k]);
+            gb1[k] += dz1[k];
+        }
+        for (int o = 0; o < MLP_H; ++o) {
+            const double d = emulate ? or_bf16(dz1[o]) : dz1[o];
+            for (int k = 0; k < MLP_IN; ++k)
+                gW1[o * MLP_IN + k] += d * (emulate ? or_bf16(X[r * MLP_IN + k]) : X[r * MLP_IN + k]);
+        }
+    }
+    (void)W1;
+    free(y);
+    free(z1);
+    free(h1);
+    free(z2);
+    free(h2);
+    return loss;
+}
+
+/* One Adam step (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void or_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2, double eps,
+             int64_t step) {
+    const double c1 = 1.0 - pow(b1, (double)step), c2 = 1.0 - pow(b2, (double)step);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

@@ -412,3 +412,76 @@ def test_transfer_sandwich_and_weighted_render_agree():
         np.testing.assert_allclose(rw["rgb"][valid], t["A_w"][valid], rtol=1e-10, atol=1e-14)
         rf = oracle.render(sc, cam, o)
         np.testing.assert_allclose(rf["rgb"], t["A"], rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- surrogate MLP
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    # 1 + 2^-8 is exactly halfway between bf16 neighbours 1 and 1 + 2^-7: ties go to even (1)
+    assert oracle.bf16(1.0 + 2 ** -8) == 1.0
+    assert oracle.bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6
+    assert oracle.bf16(1.0 + 2 ** -8 + 2 ** -12) == 1.0 + 2 ** -7
+    assert oracle.bf16(-3.0) == -3.0 and oracle.bf16(0.0) == 0.0
+    # against torch's bfloat16 conversion (a library routine)
+    import torch
+    x = torch.randn(2000, dtype=torch.float32) * 10
+    ref = x.to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([oracle.bf16(float(v)) for v in x])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_gelu_and_derivative():
+    from math import erf, sqrt, exp, pi
+    for z in (-3.0, -0.7, 0.0, 0.3, 2.5):
+        assert oracle.gelu(z) == pytest.approx(0.5 * z * (1 + erf(z / sqrt(2))), rel=1e-15, abs=1e-300)
+        h = 1e-6
+        fd = (oracle.gelu(z + h) - oracle.gelu(z - h)) / (2 * h)
+        assert oracle.gelu_d(z) == pytest.approx(fd, rel=1e-8, abs=1e-10)
+    assert oracle.gelu(0.0) == 0.0 and oracle.gelu_d(0.0) == 0.5
+
+
+def _mlp_params(seed=0, scale=0.15):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(oracle.mlp_nparam()) * scale
+
+
+def test_mlp_gradient_matches_central_differences():
+    rng = np.random.default_rng(1)
+    P = _mlp_params(2)
+    X = rng.standard_normal((6, oracle.MLP_IN)).astype(np.float32)
+    t = rng.standard_normal(6).astype(np.float32)
+    loss, G = oracle.mlp_backward(P, X, t, emulate=False)
+    idx = np.concatenate([rng.choice(oracle.MLP_H * oracle.MLP_IN, 12, replace=False),
+                          oracle.MLP_H * oracle.MLP_IN + rng.choice(oracle.mlp_nparam() - oracle.MLP_H * oracle.MLP_IN, 20,
+                                                                    replace=False)])
+    h = 1e-3
+    for i in idx:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        lp = np.mean((oracle.mlp_forward(Pp, X, emulate=False) - t) ** 2)
+        lm = np.mean((oracle.mlp_forward(Pm, X, emulate=False) - t) ** 2)
+        fd = (lp - lm) / (2 * h)
+        assert G[i] == pytest.approx(fd, rel=2e-4, abs=1e-8)
+    assert loss == pytest.approx(np.mean((oracle.mlp_forward(P, X, emulate=False) - t) ** 2), rel=1e-14)
+
+
+def test_mlp_forward_matches_a_dense_reference():
+    # the network written with numpy matrix products (a library routine) and erf
+    from math import erf, sqrt
+    rng = np.random.default_rng(3)
+    P = _mlp_params(4)
+    X = rng.standard_normal((5, oracle.MLP_IN)).astype(np.float32)
+    W1, b1, W2, b2, w3, b3 = oracle.mlp_split(P)
+    g = np.vectorize(lambda z: 0.5 * z * (1 + erf(z / sqrt(2))))
+    y = g(g(X.astype(np.float64) @ W1.T + b1) @ W2.T + b2) @ w3 + b3[0]
+    np.testing.assert_allclose(oracle.mlp_forward(P, X, emulate=False), y, rtol=1e-12)
+
+
+def test_adam_first_step_moves_by_lr():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -1e-4, 0.0])
+    m, v = np.zeros(3), np.zeros(3)
+    oracle.adam(p, g, m, v, 1e-2, 1)
+    # bias-corrected first step: -lr * g / (|g| + eps)
+    np.testing.assert_allclose(p, [1.0 - 1e-2 * 0.3 / (0.3 + 1e-8), -2.0 + 1e-2 * 1e-4 / (1e-4 + 1e-8), 0.5], rtol=1e-12)
