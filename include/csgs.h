@@ -198,6 +198,47 @@ double csgs_theorem2_sample_size(double S, double eps_c, double delta, int64_t n
 /* Thm. 3 rendered error: max(1 - e^-gamma (1 - eps_c), e^gamma (1 + eps_c) - 1). */
 double csgs_theorem3_eps(double gamma, double eps_c);
 
+/* ------------------------------------------------------------------ surrogate model
+ * Not in the paper: a learned stand-in for exact scoring over most query views.  A
+ * BF16 MLP x (64 features) -> 256 (GELU) -> 256 (GELU) -> 1 predicts log-sensitivity;
+ * it is trained on exact scores of a few views and applied with view statistics over
+ * all views.  Both layers run on the tensor cores (tcgen05.mma, BF16 operands, FP32
+ * accumulation in tensor memory); biases, GELU and the last layer are FP32.
+ * Parameter block (FP32, CSGS_MLP_PARAMS floats): W1[256][64], b1[256], W2[256][256],
+ * b2[256], w3[256], b3.  The context owns one model and its Adam state. */
+#define CSGS_MLP_PARAMS 82689
+
+/* Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, Adam state cleared. */
+csgs_status csgs_mlp_init(csgs_ctx* ctx, uint64_t seed);
+/* Copy a parameter block in (device float[CSGS_MLP_PARAMS]); clears the Adam state. */
+csgs_status csgs_mlp_set_params(csgs_ctx* ctx, const float* P_dev);
+/* Copy the parameter block out (device float[CSGS_MLP_PARAMS]); asynchronous. */
+csgs_status csgs_mlp_get_params(csgs_ctx* ctx, float* P_dev);
+/* y[B] = model(X); X_dev: device BF16 [B][64] row-major; y_dev: device float[B].
+ * Synchronises; CSGS_E_TIMEOUT if a tensor-core completion is not observed. */
+csgs_status csgs_mlp_forward(csgs_ctx* ctx, const void* X_dev, int64_t B, float* y_dev);
+/* Gradient block of loss = mean_r (y_r - t_r)^2 over B rows (device float[CSGS_MLP_PARAMS]);
+ * *loss_out (host, nullable) receives the loss.  Synchronises. */
+csgs_status csgs_mlp_gradient(csgs_ctx* ctx, const void* X_dev, const float* t_dev, int64_t B, float* G_dev,
+                              float* loss_out);
+/* `steps` Adam steps (beta 0.9, 0.999, eps 1e-8, learning rate lr) on minibatches of
+ * `batch` rows drawn with replacement from the n_rows rows of X / t (Philox, key = seed).
+ * *final_loss (host, nullable): the last minibatch loss.  Synchronises. */
+csgs_status csgs_mlp_train(csgs_ctx* ctx, const void* X_dev, const float* t_dev, int64_t n_rows, int32_t batch,
+                           int32_t steps, float lr, uint64_t seed, float* final_loss);
+/* Per-Gaussian statistics over the scene's query views (device float[N][3]): number of
+ * views the footprint reaches, mean and max area (px^2) of the projected 3-sigma ellipse. */
+csgs_status csgs_view_stats(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* stats_dev);
+/* Model inputs (device BF16 [N][64]): mean/4, log-scale+4, unit quaternion, opacity logit,
+ * 5 x SH coefficients (48 slots), log(1+views), log(1+mean area)/4, log(1+max area)/4, 0, 0. */
+csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, void* X_dev);
+/* t = log(s + eps) (device float[n]). */
+csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float eps, float* t_dev);
+/* s_out = max(exp(y) - eps, 0, s_exact) (s_exact nullable): the surrogate sensitivity,
+ * never below the exact score over the views that were scored. */
+csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const float* s_exact_dev, int64_t n, float eps,
+                                   float* s_out);
+
 /* Wait for the context's stream and report errors of asynchronous work. */
 csgs_status csgs_sync(csgs_ctx* ctx);
 

@@ -25,6 +25,7 @@ CSGS_E_EMPTY = -4
 CSGS_E_TIMEOUT = -5
 CSGS_E_DEVICE_CHECK = -6
 CSGS_NOALLOC_MAX_N = 262144
+CSGS_MLP_PARAMS = 82689
 RES_PIXEL = 0
 RES_SCENE = 1
 RES_CHANNEL = 2
@@ -74,7 +75,9 @@ EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error"
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
            "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
            "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
-           "csgs_debug_tc_gemm")
+           "csgs_debug_tc_gemm", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
+           "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
+           "csgs_surrogate_combine")
 
 _lib = None
 
@@ -113,6 +116,16 @@ def lib():
     L.csgs_theorem3_eps.argtypes = [ctypes.c_double, ctypes.c_double]
     L.csgs_theorem3_eps.restype = ctypes.c_double
     L.csgs_debug_tc_gemm.argtypes = [V, V, V, V, I32, I32]
+    L.csgs_mlp_init.argtypes = [V, U64]
+    L.csgs_mlp_set_params.argtypes = [V, V]
+    L.csgs_mlp_get_params.argtypes = [V, V]
+    L.csgs_mlp_forward.argtypes = [V, V, I64, V]
+    L.csgs_mlp_gradient.argtypes = [V, V, V, I64, V, V]
+    L.csgs_mlp_train.argtypes = [V, V, V, I64, I32, I32, ctypes.c_float, U64, V]
+    L.csgs_view_stats.argtypes = [V, I32, V, V]
+    L.csgs_features.argtypes = [V, I32, V, V]
+    L.csgs_log_target.argtypes = [V, V, I64, ctypes.c_float, V]
+    L.csgs_surrogate_combine.argtypes = [V, V, V, I64, ctypes.c_float, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -311,6 +324,72 @@ class Context:
         self._in()
         self._check(lib().csgs_transfer(self.h, sid, view, _ptr(idx), _ptr(w), idx.numel(), ctypes.byref(opts),
                                         _ptr(out)))
+        self._out()
+        return out
+
+    # -- surrogate model
+    def mlp_init(self, seed: int = 0):
+        self._check(lib().csgs_mlp_init(self.h, seed))
+
+    def mlp_set_params(self, P):
+        self._in()
+        self._check(lib().csgs_mlp_set_params(self.h, _ptr(P)))
+
+    def mlp_get_params(self):
+        P = self._empty(CSGS_MLP_PARAMS, self.torch.float32)
+        self._check(lib().csgs_mlp_get_params(self.h, _ptr(P)))
+        self._out()
+        return P
+
+    def mlp_forward(self, X):
+        y = self._empty(X.shape[0], self.torch.float32)
+        self._in()
+        self._check(lib().csgs_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(y)))
+        self._out()
+        return y
+
+    def mlp_gradient(self, X, t):
+        G = self._empty(CSGS_MLP_PARAMS, self.torch.float32)
+        loss = ctypes.c_float()
+        self._in()
+        self._check(lib().csgs_mlp_gradient(self.h, _ptr(X), _ptr(t), X.shape[0], _ptr(G), ctypes.byref(loss)))
+        self._out()
+        return G, loss.value
+
+    def mlp_train(self, X, t, batch: int, steps: int, lr: float, seed: int = 0) -> float:
+        loss = ctypes.c_float()
+        self._in()
+        self._check(lib().csgs_mlp_train(self.h, _ptr(X), _ptr(t), X.shape[0], batch, steps, lr, seed,
+                                         ctypes.byref(loss)))
+        self._out()
+        return loss.value
+
+    def view_stats(self, sid: int, opts: ScoreOpts | None = None):
+        st = self._empty((self._scenes[sid], 3), self.torch.float32)
+        opts = opts or default_opts()
+        self._in()
+        self._check(lib().csgs_view_stats(self.h, sid, ctypes.byref(opts), _ptr(st)))
+        self._out()
+        return st
+
+    def features(self, sid: int, stats):
+        X = self._empty((self._scenes[sid], 64), self.torch.bfloat16)
+        self._in()
+        self._check(lib().csgs_features(self.h, sid, _ptr(stats), _ptr(X)))
+        self._out()
+        return X
+
+    def log_target(self, s, eps: float):
+        t = self._empty(s.numel(), self.torch.float32)
+        self._in()
+        self._check(lib().csgs_log_target(self.h, _ptr(s), s.numel(), eps, _ptr(t)))
+        self._out()
+        return t
+
+    def surrogate_combine(self, y, s_exact, eps: float):
+        out = self._empty(y.numel(), self.torch.float32)
+        self._in()
+        self._check(lib().csgs_surrogate_combine(self.h, _ptr(y), _ptr(s_exact), y.numel(), eps, _ptr(out)))
         self._out()
         return out
 

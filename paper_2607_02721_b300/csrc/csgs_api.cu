@@ -11,6 +11,7 @@
 #include "csgs_internal.cuh"
 
 #include <atomic>
+#include <random>
 
 using namespace csgs;
 
@@ -60,6 +61,10 @@ struct csgs_ctx {
     DevBuf ranges, hist, scan_tmp;
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
     DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
+    // surrogate model
+    bool mlp_ready = false;
+    DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1;
+    int64_t mlp_rows = 0;
     csgs_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evpool;  // phase timing
@@ -313,7 +318,10 @@ void csgs_destroy(csgs_ctx* ctx) {
     DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,   &ctx->dkeys_b, &ctx->dvals_a, &ctx->dvals_b,
                       &ctx->ikeys_a, &ctx->ikeys_b, &ctx->ivals_a, &ctx->ivals_b, &ctx->ranges,  &ctx->hist,
                       &ctx->scan_tmp, &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
-                      &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf};
+                      &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
+                      &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
+                      &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
+                      &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->d_ctr) cudaFree(ctx->d_ctr);
     if (ctx->d_nconst) cudaFree(ctx->d_nconst);
@@ -847,6 +855,200 @@ csgs_status csgs_debug_project(csgs_ctx* ctx, int32_t scene_id, int32_t view, co
     if ((r = upload_cams(ctx, s, ko))) return r;
     launch_debug_project(scene_dev(*s), s->d_cams + view, ko, out_dev, ctx->st);
     return launch_check(ctx, "debug projection");
+}
+
+}  // extern "C"
+
+// ======================================================================= surrogate model
+
+namespace {
+
+csgs_status mlp_alloc(csgs_ctx* ctx) {
+    csgs_status r;
+    const size_t np = sizeof(float) * kMlpParams;
+    if ((r = ensure(ctx, ctx->mP, np)) || (r = ensure(ctx, ctx->mM, np)) || (r = ensure(ctx, ctx->mV, np)) ||
+        (r = ensure(ctx, ctx->mG, np)) || (r = ensure(ctx, ctx->mW1b, 2 * 256 * 64)) ||
+        (r = ensure(ctx, ctx->mW2b, 2 * 256 * 256)) || (r = ensure(ctx, ctx->mW2Tb, 2 * 256 * 256)) ||
+        (r = ensure(ctx, ctx->mLoss, sizeof(float) * 2)))
+        return r;
+    return CSGS_OK;
+}
+
+csgs_status mlp_rows_buffers(csgs_ctx* ctx, int64_t B) {
+    csgs_status r;
+    if ((r = ensure(ctx, ctx->mY, sizeof(float) * B)) || (r = ensure(ctx, ctx->mXb, 2 * 64 * (size_t)B)) ||
+        (r = ensure(ctx, ctx->mTb, sizeof(float) * B)) || (r = ensure(ctx, ctx->mZ1, sizeof(float) * 256 * (size_t)B)) ||
+        (r = ensure(ctx, ctx->mH1, 2 * 256 * (size_t)B)) || (r = ensure(ctx, ctx->mDz2, 2 * 256 * (size_t)B)) ||
+        (r = ensure(ctx, ctx->mDz1, 2 * 256 * (size_t)B)))
+        return r;
+    return CSGS_OK;
+}
+
+MlpBufs mlp_bufs(csgs_ctx* ctx) {
+    return mlp_layout(P<float>(ctx->mP), P<__nv_bfloat16>(ctx->mW1b), P<__nv_bfloat16>(ctx->mW2b),
+                      P<__nv_bfloat16>(ctx->mW2Tb));
+}
+
+MlpTemp mlp_temp(csgs_ctx* ctx) {
+    MlpTemp t;
+    t.z1 = P<float>(ctx->mZ1);
+    t.h1 = P<__nv_bfloat16>(ctx->mH1);
+    t.dz2 = P<__nv_bfloat16>(ctx->mDz2);
+    t.dz1 = P<__nv_bfloat16>(ctx->mDz1);
+    return t;
+}
+
+csgs_status check_err(csgs_ctx* ctx, const char* what) {
+    csgs_status r;
+    if ((r = launch_check(ctx, what))) return r;
+    if ((r = read_counters(ctx))) return r;
+    if (ctx->h_ctr->err) return fail(ctx, CSGS_E_TIMEOUT, "%s: tensor-core completion not observed", what);
+    return CSGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+csgs_status csgs_mlp_init(csgs_ctx* ctx, uint64_t seed) {
+    if (!ctx) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = mlp_alloc(ctx))) return r;
+    std::vector<float> h(kMlpParams, 0.f);
+    std::mt19937_64 gen(seed);
+    std::uniform_real_distribution<float> u1(-0.125f, 0.125f);    // 1 / sqrt(64)
+    std::uniform_real_distribution<float> u2(-0.0625f, 0.0625f);  // 1 / sqrt(256)
+    float* p = h.data();
+    for (int i = 0; i < 256 * 64; ++i) p[i] = u1(gen);
+    p += 256 * 64 + 256;
+    for (int i = 0; i < 256 * 256; ++i) p[i] = u2(gen);
+    p += 256 * 256 + 256;
+    for (int i = 0; i < 256; ++i) p[i] = u2(gen);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mP.p, h.data(), sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, ctx->st));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->mM.p, 0, sizeof(float) * kMlpParams, ctx->st));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->mV.p, 0, sizeof(float) * kMlpParams, ctx->st));
+    mlp_refresh(mlp_bufs(ctx), ctx->st);
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    ctx->mlp_ready = true;
+    return launch_check(ctx, "mlp init");
+}
+
+csgs_status csgs_mlp_set_params(csgs_ctx* ctx, const float* P_dev) {
+    if (!ctx || !P_dev) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = mlp_alloc(ctx))) return r;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->mP.p, P_dev, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, ctx->st));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->mM.p, 0, sizeof(float) * kMlpParams, ctx->st));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->mV.p, 0, sizeof(float) * kMlpParams, ctx->st));
+    mlp_refresh(mlp_bufs(ctx), ctx->st);
+    ctx->mlp_ready = true;
+    return launch_check(ctx, "mlp set params");
+}
+
+csgs_status csgs_mlp_get_params(csgs_ctx* ctx, float* P_dev) {
+    if (!ctx || !P_dev) return CSGS_E_INVAL;
+    if (!ctx->mlp_ready) return fail(ctx, CSGS_E_INVAL, "surrogate model not initialised");
+    CUDA_TRY(ctx, cudaMemcpyAsync(P_dev, ctx->mP.p, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, ctx->st));
+    return CSGS_OK;
+}
+
+csgs_status csgs_mlp_forward(csgs_ctx* ctx, const void* X_dev, int64_t B, float* y_dev) {
+    if (!ctx || !X_dev || !y_dev) return CSGS_E_INVAL;
+    if (!ctx->mlp_ready) return fail(ctx, CSGS_E_INVAL, "surrogate model not initialised");
+    if (B <= 0 || B >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "B out of range");
+    cudaSetDevice(ctx->device);
+    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
+    mlp_forward(mlp_bufs(ctx), X_dev, (int)B, y_dev, reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
+    return check_err(ctx, "mlp forward");
+}
+
+csgs_status csgs_mlp_gradient(csgs_ctx* ctx, const void* X_dev, const float* t_dev, int64_t B, float* G_dev,
+                              float* loss_out) {
+    if (!ctx || !X_dev || !t_dev || !G_dev) return CSGS_E_INVAL;
+    if (!ctx->mlp_ready) return fail(ctx, CSGS_E_INVAL, "surrogate model not initialised");
+    if (B <= 0 || B >= (1ll << 26)) return fail(ctx, CSGS_E_INVAL, "B out of range");
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = mlp_rows_buffers(ctx, B))) return r;
+    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
+    mlp_gradient(mlp_bufs(ctx), X_dev, t_dev, (int)B, P<float>(ctx->mY), G_dev, P<float>(ctx->mLoss), mlp_temp(ctx),
+                 reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
+    if ((r = check_err(ctx, "mlp gradient"))) return r;
+    if (loss_out) {
+        CUDA_TRY(ctx, cudaMemcpy(loss_out, ctx->mLoss.p, sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return CSGS_OK;
+}
+
+csgs_status csgs_mlp_train(csgs_ctx* ctx, const void* X_dev, const float* t_dev, int64_t n_rows, int32_t batch,
+                           int32_t steps, float lr, uint64_t seed, float* final_loss) {
+    if (!ctx || !X_dev || !t_dev) return CSGS_E_INVAL;
+    if (!ctx->mlp_ready) return fail(ctx, CSGS_E_INVAL, "surrogate model not initialised");
+    if (n_rows <= 0 || batch <= 0 || batch >= (1 << 26) || steps < 0 || !(lr > 0.f))
+        return fail(ctx, CSGS_E_INVAL, "bad training arguments");
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = mlp_rows_buffers(ctx, batch))) return r;
+    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
+    const MlpBufs mb = mlp_bufs(ctx);
+    const MlpTemp mt = mlp_temp(ctx);
+    for (int step = 1; step <= steps; ++step) {
+        gather_batch(X_dev, t_dev, n_rows, batch, seed, (uint32_t)step, ctx->mXb.p, P<float>(ctx->mTb), ctx->st);
+        mlp_gradient(mb, ctx->mXb.p, P<float>(ctx->mTb), batch, P<float>(ctx->mY), P<float>(ctx->mG),
+                     P<float>(ctx->mLoss), mt, reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
+        mlp_adam(mb, P<float>(ctx->mG), P<float>(ctx->mM), P<float>(ctx->mV), lr, step, ctx->st);
+        if ((step & 63) == 0 && (r = launch_check(ctx, "mlp train"))) return r;
+    }
+    if ((r = check_err(ctx, "mlp train"))) return r;
+    if (final_loss) {
+        CUDA_TRY(ctx, cudaMemcpy(final_loss, ctx->mLoss.p, sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    return CSGS_OK;
+}
+
+csgs_status csgs_view_stats(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* stats_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!stats_dev) return fail(ctx, CSGS_E_INVAL, "stats_dev is NULL");
+    if (s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "no query views set");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    if ((r = upload_cams(ctx, s, ko))) return r;
+    const int nv = (int)s->cams.size();
+    for (int v0 = 0; v0 < nv; v0 += 32)
+        launch_view_stats(scene_dev(*s), s->d_cams + v0, (nv - v0) < 32 ? (nv - v0) : 32, ko, stats_dev, v0 > 0,
+                          ctx->st);
+    return launch_check(ctx, "view statistics");
+}
+
+csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, void* X_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!stats_dev || !X_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
+    cudaSetDevice(ctx->device);
+    launch_features(scene_dev(*s), stats_dev, X_dev, ctx->st);
+    return launch_check(ctx, "features");
+}
+
+csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float eps, float* t_dev) {
+    if (!ctx || !s_dev || !t_dev || n <= 0 || !(eps > 0.f)) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    log_target(s_dev, n, eps, t_dev, ctx->st);
+    return launch_check(ctx, "log target");
+}
+
+csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const float* s_exact_dev, int64_t n, float eps,
+                                   float* s_out) {
+    if (!ctx || !y_dev || !s_out || n <= 0 || !(eps >= 0.f)) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    surrogate_combine(y_dev, s_exact_dev, n, eps, s_out, ctx->st);
+    return launch_check(ctx, "surrogate combine");
 }
 
 }  // extern "C"

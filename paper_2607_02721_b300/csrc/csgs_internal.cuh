@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a sensitivity-scoring path (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,6 +90,9 @@ void launch_project(const SceneDev& sc, const CamDev* d_cams, int nv, const floa
                     Splat* splats, uint32_t* keys, uint2* rects, cudaStream_t st);
 void launch_debug_project(const SceneDev& sc, const CamDev* d_cam, const KOpts& o, float* out, cudaStream_t st);
 void launch_check_finite(const float* p, int64_t n, DevCounters* ctr, cudaStream_t st);
+void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const KOpts& o, float* stats, int accumulate,
+                       cudaStream_t st);
+void launch_features(const SceneDev& sc, const float* stats, void* X, cudaStream_t st);
 // wfull[idx[k]] = w[k] (indices outside [0, n) set kErrIndex and are skipped)
 void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* wfull, int64_t n, DevCounters* ctr,
                      cudaStream_t st);
@@ -146,11 +150,36 @@ void sum_scores(const float* s, int64_t n, double* partial, double* S, cudaStrea
 void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st);
 // image resolution: s = max(s, vbuf / A_view); vbuf = 0
 void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st);
+void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st);
+void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, float* out, cudaStream_t st);
+void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,
+                  cudaStream_t st);
 void probabilities_from_scores(const float* s, int64_t n, const double* S, double* p, cudaStream_t st);
 void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const SampleTemp& t, int32_t* draws,
                   int32_t* idx, float* w, cudaStream_t st);
 
 // ---- tensor cores (k_mlp.cu)
 int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, cudaStream_t st);
+
+// surrogate MLP 64 -> 256 -> 256 -> 1 (parameter block: W1, b1, W2, b2, w3, b3)
+constexpr int kMlpParams = 256 * 64 + 256 + 256 * 256 + 256 + 256 + 1;
+struct MlpBufs {
+    float* P;             // FP32 master parameters
+    __nv_bfloat16* W1b;   // [256][64]
+    __nv_bfloat16* W2b;   // [256][256]
+    __nv_bfloat16* W2Tb;  // [256][256] transpose of W2
+};
+struct MlpTemp {
+    float* z1;            // [B][256]
+    __nv_bfloat16* h1;    // [B][256]
+    __nv_bfloat16* dz2;   // [B][256]
+    __nv_bfloat16* dz1;   // [B][256]
+};
+MlpBufs mlp_layout(float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b, __nv_bfloat16* W2Tb);
+void mlp_refresh(const MlpBufs& m, cudaStream_t st);
+void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cudaStream_t st);
+void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
+                  const MlpTemp& tmp, int* err, cudaStream_t st);
+void mlp_adam(const MlpBufs& m, const float* G, float* mo, float* vo, float lr, int step, cudaStream_t st);
 
 }  // namespace csgs

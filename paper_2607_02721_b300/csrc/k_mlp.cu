@@ -83,3 +83,505 @@ int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err,
 }
 
 }  // namespace csgs
+
+// ======================================================================= surrogate MLP
+// x (64 features) -> 256 (GELU) -> 256 (GELU) -> 1, BF16 operands, FP32 accumulation in
+// tensor memory.  Parameter block (FP32 master copy, same order as the host API):
+// W1[256][64], b1[256], W2[256][256], b2[256], w3[256], b3.  BF16 copies W1b, W2b and the
+// transpose W2Tb feed the tensor cores.
+namespace csgs {
+namespace {
+
+constexpr int kIn = 64, kH = 256;
+constexpr int kRows = 128;            // rows per tile (MMA M)
+constexpr uint32_t kIdesc1 = tc::idesc_bf16(128, 256);
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float z) {
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+struct MlpDev {
+    const __nv_bfloat16* W1b;
+    const __nv_bfloat16* W2b;
+    const __nv_bfloat16* W2Tb;
+    const float* b1;
+    const float* b2;
+    const float* w3;
+    const float* b3;
+};
+
+// Stage an R x K row-major BF16 matrix (rows r0.., zero beyond nrows) into the K-major
+// core-matrix layout, 16 bytes per thread step.
+__device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src, int r0, int nrows, int R,
+                                           int K, int ld) {
+    const int chunks = R * (K / 8);
+    for (int idx = threadIdx.x; idx < chunks; idx += blockDim.x) {
+        const int r = idx / (K / 8), k8 = idx % (K / 8);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r0 + r < nrows) v = *reinterpret_cast<const uint4*>(src + (size_t)(r0 + r) * ld + k8 * 8);
+        *reinterpret_cast<uint4*>(dst + tc::kmajor_off(r, k8 * 8, K)) = v;
+    }
+}
+
+// issue M=128 MMAs over K (K-major tiles a, b), commit to bar
+__device__ __forceinline__ void mma_tile(uint32_t d, const unsigned char* a, const unsigned char* b, int K,
+                                         uint32_t idesc, bool accumulate_first, uint64_t* bar) {
+    const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(b), sbo = (uint32_t)(K / 8) * 128u;
+    for (int kk = 0; kk < K / 16; ++kk)
+        tc::mma(d, tc::smem_desc(a0 + kk * 256, 128, sbo), tc::smem_desc(b0 + kk * 256, 128, sbo), idesc,
+                (kk > 0 || accumulate_first) ? 1u : 0u);
+    tc::commit(bar);
+}
+
+__device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
+    return p + ((1024u - (tc::smem_u32(p) & 1023u)) & 1023u);
+}
+
+// Forward over row tiles (persistent).  TRAIN additionally stores z1 (FP32), h1 (BF16),
+// dz2 = d loss / d z2 (BF16, loss = mean (y - t)^2 over B_total rows), and accumulates
+// d/dw3, d/db3 and the loss.
+// smem: [W region 128 KB: X 16 KB + W1 32 KB, later W2] [H1 64 KB]; TMEM 512 columns.
+template <bool TRAIN>
+__global__ void __launch_bounds__(256, 1) k_mlp_fwd(const __nv_bfloat16* __restrict__ X, int B, MlpDev p,
+                                                    float* __restrict__ y, const float* __restrict__ t,
+                                                    float* __restrict__ z1o, __nv_bfloat16* __restrict__ h1o,
+                                                    __nv_bfloat16* __restrict__ dz2o, float* __restrict__ gw3,
+                                                    float* __restrict__ gb3, float* __restrict__ loss, float inv_B,
+                                                    int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = align1k(smem_raw);
+    unsigned char* sX = sm;
+    unsigned char* sW1 = sm + kRows * kIn * 2;
+    unsigned char* sW2 = sm;
+    unsigned char* sH1 = sm + kH * kH * 2;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    __shared__ float sdot[2][kRows];
+    __shared__ float sgw3[kH];
+    __shared__ float sred[8];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, half = warp >> 2;
+    const int row = q * 32 + lane;
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (TRAIN) sgw3[tid] = 0.f;
+    if (warp == 0) tc::tmem_alloc(&slot, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = slot;
+    const uint32_t tl = taddr + ((uint32_t)(q * 32) << 16);  // this warp's TMEM lanes
+    uint32_t phase = 0;
+    float lsum = 0.f, db3 = 0.f;
+    bool failed = false;
+    const int ntiles = (B + kRows - 1) / kRows;
+    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const int r0 = tile * kRows;
+        stage_rows(sX, X, r0, B, kRows, kIn, kIn);
+        stage_rows(sW1, p.W1b, 0, kH, kH, kIn, kIn);
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) mma_tile(taddr, sX, sW1, kIn, kIdesc1, false, &bar);
+        const bool ok1 = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok1)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        // layer-1 epilogue: z1 + b1 -> GELU -> BF16 H1 (K-major for layer 2)
+        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tl + (uint32_t)c0, v);
+            uint32_t pk[8];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += p.b1[c0 + i];
+            if (TRAIN && r0 + row < B) {
+                float4* zo = reinterpret_cast<float4*>(z1o + (size_t)(r0 + row) * kH + c0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(gelu(v[2 * i]), gelu(v[2 * i + 1]));
+            *reinterpret_cast<uint4*>(sH1 + tc::kmajor_off(row, c0, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(sH1 + tc::kmajor_off(row, c0 + 8, kH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            if (TRAIN && r0 + row < B) {
+                uint4* ho = reinterpret_cast<uint4*>(h1o + (size_t)(r0 + row) * kH + c0);
+                ho[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                ho[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        // the X / W1 region is free once layer 1 has completed: stage W2 there
+        stage_rows(sW2, p.W2b, 0, kH, kH, kH, kH);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) mma_tile(taddr + 256u, sH1, sW2, kH, kIdesc1, false, &bar);
+        const bool ok2 = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok2)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        // layer-2 epilogue and layer 3: y = w3 . GELU(z2 + b2) + b3
+        float part = 0.f;
+        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) part = fmaf(p.w3[c0 + i], gelu(v[i] + p.b2[c0 + i]), part);
+        }
+        sdot[half][row] = part;
+        __syncthreads();
+        const float yr = sdot[0][row] + sdot[1][row] + p.b3[0];
+        const bool valid = r0 + row < B;
+        if (half == 0 && valid) y[r0 + row] = yr;
+        if (TRAIN) {
+            const float e = valid ? yr - t[r0 + row] : 0.f;
+            const float dy = 2.f * e * inv_B;
+            if (half == 0) {
+                lsum += e * e * inv_B;
+                db3 += dy;
+            }
+            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
+                uint32_t pk[8];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float z = v[i] + p.b2[c0 + i];
+                    float g = dy * gelu(z);  // d loss / d w3 of this row
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                    if (lane == 0) atomicAdd(&sgw3[c0 + i], g);
+                    v[i] = dy * p.w3[c0 + i] * gelu_d(z);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+                if (valid) {
+                    uint4* o = reinterpret_cast<uint4*>(dz2o + (size_t)(r0 + row) * kH + c0);
+                    o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (failed && tid == 0) atomicOr(err, 1);
+    if (failed) tc::mbar_wait(&bar, phase, kWaitBudget);  // drain before freeing TMEM
+    if (TRAIN) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            db3 += __shfl_xor_sync(0xffffffffu, db3, o);
+        }
+        __syncthreads();
+        if (lane == 0) sred[warp] = lsum;
+        __syncthreads();
+        if (tid == 0) {
+            float l = 0.f;
+            for (int w = 0; w < 8; ++w) l += sred[w];
+            atomicAdd(loss, l);
+        }
+        __syncthreads();
+        if (lane == 0) sred[warp] = db3;
+        __syncthreads();
+        if (tid == 0) {
+            float d = 0.f;
+            for (int w = 0; w < 8; ++w) d += sred[w];
+            atomicAdd(gb3, d);
+        }
+        atomicAdd(&gw3[tid], sgw3[tid]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
+// dz1 = (dz2 W2) * GELU'(z1), BF16 out; smem A = dz2 tile (64 KB), B = W2^T (128 KB).
+__global__ void __launch_bounds__(256, 1) k_mlp_dh1(const __nv_bfloat16* __restrict__ dz2, const float* __restrict__ z1,
+                                                    int B, MlpDev p, __nv_bfloat16* __restrict__ dz1, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = align1k(smem_raw);
+    unsigned char* sA = sm;
+    unsigned char* sB = sm + kRows * kH * 2;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, half = warp >> 2, row = q * 32 + lane;
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&slot, 256);
+    stage_rows(sB, p.W2Tb, 0, kH, kH, kH, kH);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = slot, tl = taddr + ((uint32_t)(q * 32) << 16);
+    uint32_t phase = 0;
+    bool failed = false;
+    const int ntiles = (B + kRows - 1) / kRows;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * kRows;
+        stage_rows(sA, dz2, r0, B, kRows, kH, kH);
+        tc::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) mma_tile(taddr, sA, sB, kH, kIdesc1, false, &bar);
+        const bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        const bool valid = r0 + row < B;
+        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tl + (uint32_t)c0, v);
+            if (valid) {
+                const float* zr = z1 + (size_t)(r0 + row) * kH + c0;
+                uint32_t pk[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i] * gelu_d(zr[2 * i]), v[2 * i + 1] * gelu_d(zr[2 * i + 1]));
+                uint4* o = reinterpret_cast<uint4*>(dz1 + (size_t)(r0 + row) * kH + c0);
+                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (failed && tid == 0) atomicOr(err, 1);
+    if (failed) tc::mbar_wait(&bar, phase, kWaitBudget);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 256);
+}
+
+// Weight gradient of one layer, split over rows: G[out][in] += sum_r dz[r][out] act[r][in]
+// for out in [128 ob, 128 ob + 128); also gb[out] += sum_r dz[r][out].  A = dz^T and
+// B = act^T are staged transposed (rows of the batch become the K dimension).
+template <int NIN>
+__global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restrict__ dz,
+                                                   const __nv_bfloat16* __restrict__ act, int B, int rows_per_cta,
+                                                   float* __restrict__ G, float* __restrict__ gb, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = align1k(smem_raw);
+    unsigned char* sA = sm;                 // [128 out][128 rows]
+    unsigned char* sB = sm + 128 * 128 * 2;  // [NIN in][128 rows]
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ob = blockIdx.y;
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&slot, NIN < 32 ? 32 : NIN);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = slot;
+    uint32_t phase = 0;
+    bool failed = false;
+    float bsum = 0.f;
+    const int rbeg = blockIdx.x * rows_per_cta;
+    const int rend = min(B, rbeg + rows_per_cta);
+    int chunk = 0;
+    for (int r0 = rbeg; r0 < rend; r0 += 128, ++chunk) {
+        // A: thread t stages rows r0 + t / 2, outs (t % 2) * 64 .. + 64 of this block
+        {
+            const int rl = tid >> 1, o0 = (tid & 1) * 64;
+            const bool ok = r0 + rl < rend;
+            const __nv_bfloat16* src = dz + (size_t)(r0 + rl) * kH + ob * 128 + o0;
+            for (int k8 = 0; k8 < 8; ++k8) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (ok) v = *reinterpret_cast<const uint4*>(src + k8 * 8);
+                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_off(o0 + k8 * 8 + i, rl, 128)) = e[i];
+            }
+        }
+        // B: thread t stages row r0 + t / 2, inputs (t % 2) * NIN/2 .. + NIN/2
+        {
+            const int rl = tid >> 1, i0 = (tid & 1) * (NIN / 2);
+            const bool ok = r0 + rl < rend;
+            const __nv_bfloat16* src = act + (size_t)(r0 + rl) * NIN + i0;
+            for (int k8 = 0; k8 < NIN / 16; ++k8) {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (ok) v = *reinterpret_cast<const uint4*>(src + k8 * 8);
+                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_off(i0 + k8 * 8 + i, rl, 128)) = e[i];
+            }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // bias gradient: thread o < 128 sums its out's row of A over the chunk
+        if (tid < 128)
+            for (int r = 0; r < 128; ++r)
+                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + tc::kmajor_off(tid, r, 128)));
+        if (tid == 0) mma_tile(taddr, sA, sB, 128, tc::idesc_bf16(128, NIN), chunk > 0, &bar);
+        const bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(err, 1);
+        tc::mbar_wait(&bar, phase, kWaitBudget);
+    } else if (chunk > 0) {
+        tc::fence_after_sync();
+        if (warp < 4) {
+            const int o = warp * 32 + lane;
+            const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
+            for (int c0 = 0; c0 < NIN; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(tl + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) atomicAdd(G + (size_t)(ob * 128 + o) * NIN + c0 + i, v[i]);
+            }
+        }
+        if (tid < 128) atomicAdd(gb + ob * 128 + tid, bsum);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, NIN < 32 ? 32 : NIN);
+}
+
+// Adam on the FP32 master block; refreshes the BF16 copies (W1b, W2b, W2Tb).
+__global__ void k_mlp_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                           float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2,
+                           __nv_bfloat16* __restrict__ W1b, __nv_bfloat16* __restrict__ W2b,
+                           __nv_bfloat16* __restrict__ W2Tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = P[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    P[i] = pi;
+    const int nW1 = kH * kIn, oW2 = nW1 + kH, nW2 = kH * kH;
+    if (i < nW1) W1b[i] = __float2bfloat16_rn(pi);
+    if (i >= oW2 && i < oW2 + nW2) {
+        const int j = i - oW2, o = j / kH, k = j % kH;
+        W2b[j] = __float2bfloat16_rn(pi);
+        W2Tb[k * kH + o] = __float2bfloat16_rn(pi);
+    }
+}
+
+__global__ void k_mlp_refresh(const float* __restrict__ P, int n, __nv_bfloat16* __restrict__ W1b,
+                              __nv_bfloat16* __restrict__ W2b, __nv_bfloat16* __restrict__ W2Tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nW1 = kH * kIn, oW2 = nW1 + kH, nW2 = kH * kH;
+    if (i < nW1) W1b[i] = __float2bfloat16_rn(P[i]);
+    if (i >= oW2 && i < oW2 + nW2) {
+        const int j = i - oW2, o = j / kH, k = j % kH;
+        W2b[j] = __float2bfloat16_rn(P[i]);
+        W2Tb[k * kH + o] = __float2bfloat16_rn(P[i]);
+    }
+}
+
+}  // namespace
+
+MlpBufs mlp_layout(float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b, __nv_bfloat16* W2Tb) {
+    MlpBufs b;
+    b.P = P;
+    b.W1b = W1b;
+    b.W2b = W2b;
+    b.W2Tb = W2Tb;
+    return b;
+}
+
+static MlpDev dev_view(const MlpBufs& m) {
+    MlpDev d;
+    d.W1b = m.W1b;
+    d.W2b = m.W2b;
+    d.W2Tb = m.W2Tb;
+    const float* P = m.P;
+    d.b1 = P + kH * kIn;
+    d.b2 = P + kH * kIn + kH + kH * kH;
+    d.w3 = d.b2 + kH;
+    d.b3 = d.w3 + kH;
+    return d;
+}
+
+static int fwd_grid(int B) {
+    const int nt = (B + kRows - 1) / kRows;
+    return nt < 148 ? nt : 148;
+}
+
+void mlp_refresh(const MlpBufs& m, cudaStream_t st) {
+    k_mlp_refresh<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m.P, kMlpParams, m.W1b, m.W2b, m.W2Tb);
+    count_launches(1);
+}
+
+void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cudaStream_t st) {
+    const size_t smem = (size_t)kH * kH * 2 + (size_t)kRows * kH * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mlp_fwd<false><<<fwd_grid(B), 256, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), B, dev_view(m), y,
+                                                     nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
+                                                     err);
+    count_launches(1);
+}
+
+void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
+                  const MlpTemp& tmp, int* err, cudaStream_t st) {
+    const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
+    const MlpDev d = dev_view(m);
+    float* gW1 = G;
+    float* gb1 = gW1 + kH * kIn;
+    float* gW2 = gb1 + kH;
+    float* gb2 = gW2 + kH * kH;
+    float* gw3 = gb2 + kH;
+    float* gb3 = gw3 + kH;
+    cudaMemsetAsync(G, 0, sizeof(float) * kMlpParams, st);
+    cudaMemsetAsync(loss, 0, sizeof(float), st);
+    const size_t smem_f = (size_t)kH * kH * 2 + (size_t)kRows * kH * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
+    k_mlp_fwd<true><<<fwd_grid(B), 256, smem_f, st>>>(Xb, B, d, y, t, tmp.z1, tmp.h1, tmp.dz2, gw3, gb3, loss,
+                                                      1.f / (float)B, err);
+    const size_t smem_d = (size_t)kRows * kH * 2 + (size_t)kH * kH * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_dh1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
+    k_mlp_dh1<<<fwd_grid(B), 256, smem_d, st>>>(tmp.dz2, tmp.z1, B, d, tmp.dz1, err);
+    const int rows_per_cta = 512;
+    const int splits = (B + rows_per_cta - 1) / rows_per_cta;
+    const size_t smem_w2 = (size_t)128 * 128 * 2 + (size_t)kH * 128 * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_wgrad<kH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w2);
+    k_mlp_wgrad<kH><<<dim3(splits, 2), 256, smem_w2, st>>>(tmp.dz2, tmp.h1, B, rows_per_cta, gW2, gb2, err);
+    const size_t smem_w1 = (size_t)128 * 128 * 2 + (size_t)kIn * 128 * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_wgrad<kIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w1);
+    k_mlp_wgrad<kIn><<<dim3(splits, 2), 256, smem_w1, st>>>(tmp.dz1, Xb, B, rows_per_cta, gW1, gb1, err);
+    count_launches(4);
+}
+
+void mlp_adam(const MlpBufs& m, const float* G, float* mo, float* vo, float lr, int step, cudaStream_t st) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = (float)(1.0 - pow(0.9, (double)step)), c2 = (float)(1.0 - pow(0.999, (double)step));
+    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m.P, G, mo, vo, kMlpParams, lr, b1, b2, eps, c1, c2, m.W1b,
+                                                         m.W2b, m.W2Tb);
+    count_launches(1);
+}
+
+}  // namespace csgs

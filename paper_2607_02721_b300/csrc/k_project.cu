@@ -264,6 +264,74 @@ __global__ void k_check_finite(const float* __restrict__ p, int64_t n, DevCounte
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->err, kErrNonFinite);
 }
 
+// Per-Gaussian statistics over query views (features of the surrogate model): number
+// of views whose image the footprint touches, and the mean and maximum area (px^2) of
+// the projected 3-sigma ellipse, pi * cut2 * sqrt(det cov2D), over those views.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_view_stats(SceneDev sc, const CamDev* __restrict__ cams, int nv, KOpts o,
+                                                    float* __restrict__ stats, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n) return;
+    float mu[3], cov3[6], op;
+    float shc[3 * (DEG + 1) * (DEG + 1)];
+    load_gaussian<DEG>(sc, i, nullptr, mu, cov3, op, shc);
+    float cnt = 0.f, sum = 0.f, mx = 0.f;
+    if (accumulate) {
+        cnt = stats[3 * i];
+        sum = stats[3 * i + 1] * cnt;
+        mx = stats[3 * i + 2];
+    }
+    for (int v = 0; v < nv; ++v) {
+        Proj r;
+        project_one<DEG>(mu, cov3, op, shc, cams[v], o, r);
+        if (!r.valid) continue;
+        const float area = 3.14159265358979f * o.cut2 * sqrtf(r.ca * r.cc - r.cb * r.cb);
+        cnt += 1.f;
+        sum += area;
+        mx = fmaxf(mx, area);
+    }
+    stats[3 * i] = cnt;
+    stats[3 * i + 1] = cnt > 0.f ? sum / cnt : 0.f;
+    stats[3 * i + 2] = mx;
+}
+
+// Surrogate features, BF16 [N][64]: mean / 4, log-scale + 4, unit quaternion, opacity
+// logit, SH coefficients x 5 (48 slots, zero beyond the degree), log(1 + view count),
+// log(1 + mean area) / 4, log(1 + max area) / 4, two zero pads.
+__global__ void k_features(SceneDev sc, const float* __restrict__ stats, __nv_bfloat16* __restrict__ X) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n) return;
+    const int n = sc.n;
+    float f[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) f[k] = 0.f;
+    for (int k = 0; k < 3; ++k) f[k] = sc.means[k * n + i] * 0.25f;
+    for (int k = 0; k < 3; ++k) f[3 + k] = sc.log_scales[k * n + i] + 4.f;
+    float q[4], qn = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        q[k] = sc.quats[k * n + i];
+        qn += q[k] * q[k];
+    }
+    qn = rsqrtf(qn);
+    for (int k = 0; k < 4; ++k) f[6 + k] = q[k] * qn;
+    f[10] = sc.opac[i];
+    const int nk = 3 * (sc.deg + 1) * (sc.deg + 1);
+    for (int k = 0; k < nk; ++k) f[11 + k] = sc.sh[(size_t)k * n + i] * 5.f;
+    f[59] = log1pf(stats[3 * i]);
+    f[60] = log1pf(stats[3 * i + 1]) * 0.25f;
+    f[61] = log1pf(stats[3 * i + 2]) * 0.25f;
+    uint4* dst = reinterpret_cast<uint4*>(X + (size_t)i * 64);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(f[8 * c], f[8 * c + 1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(f[8 * c + 2], f[8 * c + 3]);
+        __nv_bfloat162 cc = __floats2bfloat162_rn(f[8 * c + 4], f[8 * c + 5]);
+        __nv_bfloat162 d = __floats2bfloat162_rn(f[8 * c + 6], f[8 * c + 7]);
+        dst[c] = make_uint4(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b),
+                            *reinterpret_cast<uint32_t*>(&cc), *reinterpret_cast<uint32_t*>(&d));
+    }
+}
+
 __global__ void k_scatter_weights(const int32_t* __restrict__ idx, const float* __restrict__ w, int64_t n_sel,
                                   float* __restrict__ wfull, int64_t n, DevCounters* ctr) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_sel; k += (int64_t)gridDim.x * blockDim.x) {
@@ -284,6 +352,24 @@ void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* w
     int64_t blocks = (n_sel + 255) / 256;
     if (blocks > 148 * 8) blocks = 148 * 8;
     k_scatter_weights<<<(int)blocks, 256, 0, st>>>(idx, w, n_sel, wfull, n, ctr);
+    count_launches(1);
+}
+
+void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const KOpts& o, float* stats, int accumulate,
+                       cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (sc.n + threads - 1) / threads;
+    switch (sc.deg) {
+        case 0: k_view_stats<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
+        case 1: k_view_stats<1><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
+        case 2: k_view_stats<2><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
+        default: k_view_stats<3><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
+    }
+    count_launches(1);
+}
+
+void launch_features(const SceneDev& sc, const float* stats, void* X, cudaStream_t st) {
+    k_features<<<(sc.n + 255) / 256, 256, 0, st>>>(sc, stats, reinterpret_cast<__nv_bfloat16*>(X));
     count_launches(1);
 }
 

@@ -63,6 +63,50 @@ __global__ void k_image_fold(float* __restrict__ s, float* __restrict__ vbuf, in
     }
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies, round keys bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__global__ void k_log_target(const float* __restrict__ s, int64_t n, float eps, float* __restrict__ t) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = logf(s[i] + eps);
+}
+
+__global__ void k_combine(const float* __restrict__ y, const float* __restrict__ s_exact, int64_t n, float eps,
+                          float* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = expf(y[i]) - eps;
+        const float s = s_exact ? s_exact[i] : 0.f;
+        out[i] = fmaxf(fmaxf(e, 0.f), s);
+    }
+}
+
+// minibatch rows: row j of step `step` = floor(x * n / 2^32), x a Philox word (key = seed,
+// counter = (j, step)); gathers the features and targets into contiguous buffers
+__global__ void k_gather_batch(const uint4* __restrict__ X, const float* __restrict__ t, int64_t n, int B,
+                               uint64_t seed, uint32_t step, uint4* __restrict__ Xb, float* __restrict__ tb) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= B) return;
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, step, 0x5EEDu, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const int64_t row = (int64_t)(((unsigned long long)r.x * (unsigned long long)n) >> 32);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Xb[(size_t)j * 8 + c] = X[(size_t)row * 8 + c];
+    tb[j] = t[row];
+}
+
 __global__ void k_probs(const float* __restrict__ s, int64_t n, const double* __restrict__ S, double* __restrict__ p) {
     const double tot = *S;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -156,22 +200,6 @@ __global__ void __launch_bounds__(kThreads) k_cdf_down(const double* __restrict_
     }
 }
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
-// multiplies, round keys bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    return c;
-}
-
 __global__ void k_draw(const unsigned long long* __restrict__ C, int64_t n, int64_t m, uint64_t seed,
                        uint32_t* __restrict__ counts, int32_t* __restrict__ draws) {
     const unsigned long long total = C[n - 1];
@@ -247,6 +275,23 @@ void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st) {
 
 void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st) {
     k_image_fold<<<148 * 8, 256, 0, st>>>(s, vbuf, n, sumA_view);
+    count_launches(1);
+}
+
+void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st) {
+    k_log_target<<<148 * 8, 256, 0, st>>>(s, n, eps, t);
+    count_launches(1);
+}
+
+void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, float* out, cudaStream_t st) {
+    k_combine<<<148 * 8, 256, 0, st>>>(y, s_exact, n, eps, out);
+    count_launches(1);
+}
+
+void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,
+                  cudaStream_t st) {
+    k_gather_batch<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const uint4*>(X), t, n, B, seed, step,
+                                                     reinterpret_cast<uint4*>(Xb), tb);
     count_launches(1);
 }
 

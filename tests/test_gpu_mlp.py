@@ -1,0 +1,142 @@
+"""The surrogate model's tensor-core kernels against the FP64 oracle (which emulates the
+BF16 rounding points), and the feature / statistics kernels against the oracle's
+projection.
+
+Tolerances: BF16 hidden activations can round to a neighbouring BF16 value on the two
+sides (FP32 vs FP64 pre-activations), so outputs are compared at 1e-3 relative for
+99.5% of rows (1e-2 for all) and gradients by relative L2 error (1e-2) and cosine
+(>= 0.9999) per parameter group.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2607_02721_b300 as csgs
+from paper_2607_02721_b300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    build.build()
+    c = csgs.Context(0)
+    yield c
+    c.close()
+
+
+def params(seed, scale=0.2):
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal(oracle.mlp_nparam()) * scale
+    W1, b1, W2, b2, w3, b3 = oracle.mlp_split(P)
+    W1 *= 0.5
+    W2 *= 0.3
+    return P.astype(np.float32).astype(np.float64)
+
+
+def inputs(torch, B, seed):
+    g = torch.Generator().manual_seed(seed)
+    X = torch.randn(B, 64, generator=g).to(torch.bfloat16)
+    return X, X.float().numpy()
+
+
+def test_mlp_forward_matches_oracle(ctx, torch):
+    P = params(0)
+    ctx.mlp_set_params(torch.tensor(P, dtype=torch.float32, device="cuda"))
+    X, Xn = inputs(torch, 300, 1)
+    y = ctx.mlp_forward(X.cuda()).cpu().numpy().astype(np.float64)
+    ref = oracle.mlp_forward(P, Xn, emulate=True)
+    rel = np.abs(y - ref) / (1 + np.abs(ref))
+    assert np.quantile(rel, 0.995) <= 1e-3 and rel.max() <= 1e-2, (np.quantile(rel, 0.995), rel.max())
+
+
+def test_mlp_gradient_matches_oracle(ctx, torch):
+    P = params(2)
+    ctx.mlp_set_params(torch.tensor(P, dtype=torch.float32, device="cuda"))
+    X, Xn = inputs(torch, 300, 3)
+    t = np.random.default_rng(4).standard_normal(300).astype(np.float32)
+    G, loss = ctx.mlp_gradient(X.cuda(), torch.tensor(t, device="cuda"))
+    G = G.cpu().numpy().astype(np.float64)
+    loss_ref, G_ref = oracle.mlp_backward(P, Xn, t, emulate=True)
+    assert loss == pytest.approx(loss_ref, rel=2e-3)
+    for name, g, r in zip(("W1", "b1", "W2", "b2", "w3", "b3"), oracle.mlp_split(G), oracle.mlp_split(G_ref)):
+        g, r = g.ravel(), r.ravel()
+        err = np.linalg.norm(g - r) / np.linalg.norm(r)
+        cos = float(g @ r / (np.linalg.norm(g) * np.linalg.norm(r)))
+        assert err <= 1e-2 and cos >= 0.9999, (name, err, cos)
+
+
+def test_mlp_training_reduces_loss(ctx, torch):
+    ctx.mlp_init(7)
+    g = torch.Generator().manual_seed(5)
+    X = (torch.randn(8192, 64, generator=g) * 0.8).to(torch.bfloat16)
+    Xf = X.float()
+    t = (torch.sin(2 * Xf[:, 0]) + Xf[:, 1] * Xf[:, 2] - 0.5 * Xf[:, 3] ** 2).contiguous()
+    Xd, td = X.cuda(), t.cuda()
+    y0 = ctx.mlp_forward(Xd)
+    l0 = float(((y0 - td) ** 2).mean())
+    ctx.mlp_train(Xd, td, batch=1024, steps=300, lr=3e-3, seed=1)
+    y1 = ctx.mlp_forward(Xd)
+    l1 = float(((y1 - td) ** 2).mean())
+    assert l1 < 0.2 * l0, (l0, l1)
+
+
+def test_view_stats_and_features(ctx, torch):
+    sc, cams, _ = synth.workload_small()
+    sid = ctx.load_scene(sc)
+    ctx.set_queries(sid, cams)
+    st = ctx.view_stats(sid).cpu().numpy().astype(np.float64)
+    sa = oracle.SceneArrays(sc)
+    cnt = np.zeros(sc.n)
+    tot = np.zeros(sc.n)
+    mx = np.zeros(sc.n)
+    for cam in cams:
+        P = oracle.project(sa, cam)
+        W, H = int(cam[16]), int(cam[17])
+        rx, ry = np.sqrt(9 * P[:, 6]), np.sqrt(9 * P[:, 8])
+        vis = (P[:, 0] > 0) & (P[:, 1] + rx >= 0) & (P[:, 1] - rx <= W - 1) & (P[:, 2] + ry >= 0) & \
+              (P[:, 2] - ry <= H - 1) & (P[:, 10] >= 1 / 255)
+        area = math.pi * 9 * np.sqrt(np.maximum(P[:, 6] * P[:, 8] - P[:, 7] ** 2, 0))
+        cnt += vis
+        tot += np.where(vis, area, 0)
+        mx = np.maximum(mx, np.where(vis, area, 0))
+    agree = st[:, 0] == cnt
+    assert agree.mean() > 0.995
+    ok = agree & (cnt > 0)
+    np.testing.assert_allclose(st[ok, 1], tot[ok] / cnt[ok], rtol=2e-4)
+    np.testing.assert_allclose(st[ok, 2], mx[ok], rtol=2e-4)
+    X = ctx.features(sid, torch.tensor(st, dtype=torch.float32, device="cuda")).float().cpu().numpy()
+    q = sc.quats / np.linalg.norm(sc.quats, axis=0, keepdims=True)
+    exp = np.zeros((sc.n, 64))
+    exp[:, 0:3] = sc.means.T * 0.25
+    exp[:, 3:6] = sc.log_scales.T + 4
+    exp[:, 6:10] = q.T
+    exp[:, 10] = sc.opacity_logits
+    exp[:, 11:14] = sc.sh.reshape(3, sc.n).T * 5
+    exp[:, 59] = np.log1p(st[:, 0])
+    exp[:, 60] = np.log1p(st[:, 1]) * 0.25
+    exp[:, 61] = np.log1p(st[:, 2]) * 0.25
+    bf = torch.tensor(exp, dtype=torch.float32).to(torch.bfloat16).float().numpy()
+    np.testing.assert_allclose(X, bf, rtol=1e-2, atol=1e-2)
+    ctx.free_scene(sid)
+
+
+def test_log_target_and_combine(ctx, torch):
+    s = torch.tensor([0.0, 1e-9, 0.3, 1.0], device="cuda")
+    t = ctx.log_target(s, 1e-8).cpu().numpy()
+    np.testing.assert_allclose(t, np.log(np.array([0.0, 1e-9, 0.3, 1.0]) + 1e-8), rtol=1e-6)
+    y = torch.tensor([-30.0, math.log(0.5), 0.0, math.log(0.1)], device="cuda")
+    se = torch.tensor([0.2, 0.1, 0.0, 0.3], device="cuda")
+    out = ctx.surrogate_combine(y, se, 1e-8).cpu().numpy()
+    np.testing.assert_allclose(out, [0.2, 0.5 - 1e-8, 1.0 - 1e-8, 0.3], rtol=1e-6)
