@@ -381,6 +381,51 @@ def run_ours(args):
     return 0
 
 
+def run_surrogate(args):
+    """Surrogate-assisted scoring vs exact scoring on the same workload: times, and PSNR
+    of the 90%-pruned weighted coreset against the full render (views every `stride`)."""
+    import numpy as np
+    import torch
+
+    import paper_2607_02721_b300 as csgs
+    from paper_2607_02721_b300 import build, surrogate
+
+    build.build()
+    scene, cams = workload(args.workload)
+    if args.max_views:
+        cams = cams[: args.max_views]
+    cfg = describe(args.workload, scene, cams)
+    m = cfg["coreset_m"]
+    ctx = csgs.Context(0, stream=torch.cuda.Stream())
+    sid = ctx.load_scene(scene)
+    ctx.set_queries(sid, cams)
+    s_exact, _ = ctx.score(sid)  # warm-up (buffers)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(ctx.stream)
+    s_exact, S = ctx.score(sid)
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    exact_ms = ev0.elapsed_time(ev1)
+    scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps)
+    surrogate.surrogate_scores(ctx, sid, cams, scfg)  # warm-up
+    tim = {}
+    s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, scfg, timings=tim)
+    views = list(range(0, len(cams), args.psnr_stride))
+    res = {"mode": "surrogate", "config": cfg, "exact_ms": exact_ms, "surrogate": tim,
+           "speedup_total": exact_ms / tim["total_ms"],
+           "speedup_without_training": exact_ms / (tim["total_ms"] - tim["train_ms"]),
+           "psnr_views": len(views), "train_views": args.train_views, "train_steps": args.train_steps}
+    for name, sv in (("exact", s_exact), ("surrogate", s_hat), ("subset_only", s_sub)):
+        res["psnr_" + name] = surrogate.pruned_psnr(ctx, sid, cams, sv, m, 0, views)
+    res["delta_psnr_surrogate_vs_exact"] = res["psnr_surrogate"] - res["psnr_exact"]
+    res["gain_psnr_surrogate_vs_subset"] = res["psnr_surrogate"] - res["psnr_subset_only"]
+    sh, se = s_hat.double().cpu().numpy(), s_exact.double().cpu().numpy()
+    res["spearman_log"] = float(np.corrcoef(np.argsort(np.argsort(sh)), np.argsort(np.argsort(se)))[0, 1])
+    print(json.dumps(res), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,9 +438,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--max-views", type=int, default=0, help="score only the first views (profiling runs)")
     ap.add_argument("--view-batch", type=int, default=0, help="views projected per launch (0 = automatic)")
+    ap.add_argument("--surrogate", action="store_true", help="surrogate-assisted vs exact scoring report")
+    ap.add_argument("--train-views", type=int, default=20)
+    ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--psnr-stride", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate:
+        return run_surrogate(args)
     return run_ours(args)
 
 

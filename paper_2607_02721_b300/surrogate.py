@@ -1,0 +1,98 @@
+"""Surrogate-assisted sensitivity scoring (not in the paper): exact scores on a small
+subset of the query views train the library's BF16 MLP to predict log-sensitivity from
+Gaussian attributes and per-Gaussian view statistics; the model is then applied with
+statistics over all views, and its prediction is combined with the exact scores of the
+scored subset (s = max(exp(prediction) - eps, s_subset)).
+
+This module only sequences calls into the C ABI (score, view statistics, features,
+targets, training, inference, combination); every arithmetic step runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class SurrogateConfig:
+    train_views: int = 20          # exact scoring on this many views
+    aug_views: tuple = (5, 10)     # extra training sets: exact scores of smaller subsets
+    eps: float = 1e-8              # target = log(s + eps)
+    batch: int = 65536
+    steps: int = 300
+    lr: float = 1e-3
+    seed: int = 0
+
+
+def view_subset(n_views: int, k: int) -> np.ndarray:
+    """k views spread evenly over the query set (indices)."""
+    k = max(1, min(k, n_views))
+    return np.unique(np.round(np.linspace(0, n_views - 1, k)).astype(int))
+
+
+def surrogate_scores(ctx, sid: int, cams, cfg: SurrogateConfig | None = None, opts=None, timings: dict | None = None):
+    """Returns (s_hat, s_subset) on the device.  Leaves the scene's query set at `cams`."""
+    import torch
+
+    cfg = cfg or SurrogateConfig()
+    cams = np.asarray(cams, dtype=np.float32).reshape(-1, 20)
+    nv = cams.shape[0]
+    ev = {}
+
+    def mark(name):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(ctx.stream)
+        ev[name] = e
+
+    mark("start")
+    sub = view_subset(nv, cfg.train_views)
+    ctx.set_queries(sid, cams[sub])
+    s_sub, _ = ctx.score(sid, opts)
+    s_sub = s_sub.clone()
+    X_parts = [ctx.features(sid, ctx.view_stats(sid, opts))]
+    t_parts = [ctx.log_target(s_sub, cfg.eps)]
+    for k in cfg.aug_views:
+        aug = sub[view_subset(len(sub), k)]
+        ctx.set_queries(sid, cams[aug])
+        s_k, _ = ctx.score(sid, opts)
+        X_parts.append(ctx.features(sid, ctx.view_stats(sid, opts)))
+        t_parts.append(ctx.log_target(s_k, cfg.eps))
+    mark("scored")
+    with torch.cuda.stream(ctx.stream):
+        X = torch.cat(X_parts)
+        t = torch.cat(t_parts)
+    ctx.mlp_init(cfg.seed)
+    ctx.mlp_train(X, t, batch=cfg.batch, steps=cfg.steps, lr=cfg.lr, seed=cfg.seed + 1)
+    mark("trained")
+    ctx.set_queries(sid, cams)
+    Xall = ctx.features(sid, ctx.view_stats(sid, opts))
+    y = ctx.mlp_forward(Xall)
+    s_hat = ctx.surrogate_combine(y, s_sub, cfg.eps)
+    mark("inferred")
+    if timings is not None:
+        torch.cuda.synchronize()
+        timings["exact_subset_ms"] = ev["start"].elapsed_time(ev["scored"])
+        timings["train_ms"] = ev["scored"].elapsed_time(ev["trained"])
+        timings["infer_ms"] = ev["trained"].elapsed_time(ev["inferred"])
+        timings["total_ms"] = ev["start"].elapsed_time(ev["inferred"])
+    return s_hat, s_sub
+
+
+def pruned_psnr(ctx, sid: int, cams, s, m: int, seed: int, views=None, opts=None) -> float:
+    """Mean PSNR over views of the weighted coreset (m draws from s) against the full
+    render (evaluation metric; colours in [0, 1])."""
+    import torch
+
+    cams = np.asarray(cams, dtype=np.float32).reshape(-1, 20)
+    views = range(cams.shape[0]) if views is None else views
+    idx, w = ctx.sample_coreset(s, m, seed)
+    vals = []
+    for v in views:
+        H, W = int(cams[v][17]), int(cams[v][16])
+        full = ctx.render(sid, v, H=H, W=W, opts=opts)
+        pr = ctx.render(sid, v, idx=idx, w=w, H=H, W=W, opts=opts)
+        mse = float(((full - pr) ** 2).mean())
+        vals.append(10.0 * np.log10(1.0 / max(mse, 1e-20)))
+    return float(np.mean(vals))
