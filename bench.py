@@ -406,7 +406,8 @@ def run_surrogate(args):
     ev1.record(ctx.stream)
     torch.cuda.synchronize()
     exact_ms = ev0.elapsed_time(ev1)
-    scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps)
+    scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps, fill_only=args.fill_only,
+                                     aug_views=tuple(int(x) for x in args.aug_views.split(",") if x))
     surrogate.surrogate_scores(ctx, sid, cams, scfg)  # warm-up
     tim = {}
     s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, scfg, timings=tim)
@@ -414,7 +415,8 @@ def run_surrogate(args):
     res = {"mode": "surrogate", "config": cfg, "exact_ms": exact_ms, "surrogate": tim,
            "speedup_total": exact_ms / tim["total_ms"],
            "speedup_without_training": exact_ms / (tim["total_ms"] - tim["train_ms"]),
-           "psnr_views": len(views), "train_views": args.train_views, "train_steps": args.train_steps}
+           "psnr_views": len(views), "train_views": args.train_views, "train_steps": args.train_steps,
+           "fill_only": args.fill_only, "aug_views": scfg.aug_views}
     for name, sv in (("exact", s_exact), ("surrogate", s_hat), ("subset_only", s_sub)):
         res["psnr_" + name] = surrogate.pruned_psnr(ctx, sid, cams, sv, m, 0, views)
     res["delta_psnr_surrogate_vs_exact"] = res["psnr_surrogate"] - res["psnr_exact"]
@@ -442,6 +444,8 @@ def main():
     ap.add_argument("--train-views", type=int, default=20)
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--psnr-stride", type=int, default=5)
+    ap.add_argument("--fill-only", action="store_true")
+    ap.add_argument("--aug-views", default="5,10")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

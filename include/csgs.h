@@ -234,10 +234,11 @@ csgs_status csgs_view_stats(csgs_ctx* ctx, int32_t scene_id, const csgs_score_op
 csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, void* X_dev);
 /* t = log(s + eps) (device float[n]). */
 csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float eps, float* t_dev);
-/* s_out = max(exp(y) - eps, 0, s_exact) (s_exact nullable): the surrogate sensitivity,
- * never below the exact score over the views that were scored. */
+/* The surrogate sensitivity from the prediction y and the exact scores of the scored
+ * views (s_exact, nullable): fill_only = 0: s_out = max(exp(y) - eps, 0, s_exact) (never
+ * below the exact score); fill_only = 1: s_exact where it is > 0, else max(exp(y) - eps, 0). */
 csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const float* s_exact_dev, int64_t n, float eps,
-                                   float* s_out);
+                                   int32_t fill_only, float* s_out);
 
 /* Wait for the context's stream and report errors of asynchronous work. */
 csgs_status csgs_sync(csgs_ctx* ctx);

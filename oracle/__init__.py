@@ -127,6 +127,7 @@ def lib():
         _lib.or_theorem2_m.restype = ctypes.c_double
         _lib.or_transfer.argtypes = [P, P, P, P, P]
         _lib.or_score_pixels.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P]
+        _lib.or_render_backward.argtypes = [P, P, P, P, P, P, P, P]
         _lib.or_mlp_nparam.restype = ctypes.c_int
         _lib.or_bf16.argtypes = [ctypes.c_double]
         _lib.or_bf16.restype = ctypes.c_double
@@ -384,3 +385,21 @@ def mlp_backward(P, X, t, emulate: bool = True):
 
 def adam(p, g, m, v, lr, step, b1=0.9, b2=0.999, eps=1e-8):
     lib().or_adam(_ptr(p), _ptr(np.ascontiguousarray(g)), _ptr(m), _ptr(v), p.shape[0], lr, b1, b2, eps, step)
+
+
+def render_backward(scene, cam, grad_rgb, opts: Opts | None = None, w=None):
+    """Gradient of sum(grad_rgb * render) w.r.t. means [3,N], SH [(d+1)^2,3,N] and
+    opacity logits [N] (scales and rotations fixed)."""
+    sa = _scene(scene)
+    opts = opts or Opts()
+    gr = np.ascontiguousarray(grad_rgb, dtype=np.float64)
+    gm = np.zeros((3, sa.n))
+    gs = np.zeros(sa.sh.shape)
+    gl = np.zeros(sa.n)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    oc = opts.c()
+    rc = lib().or_render_backward(ctypes.byref(sa.c), _ptr(_cam(cam)), ctypes.byref(oc), _ptr(w), _ptr(gr), _ptr(gm),
+                                  _ptr(gs), _ptr(gl))
+    if rc:
+        raise MemoryError("oracle render_backward failed")
+    return gm, gs, gl

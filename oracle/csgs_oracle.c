@@ -1042,3 +1042,246 @@ void or_adam(double* p, const double* g, double* m, double* v, int64_t n, double
         p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
     }
 }
+
+/* ---------------------------------------------------------------- render gradient */
+/* Gradient of L = sum_pixels grad_rgb . C (so grad_rgb = dL/dC) of the (weighted)
+ * render of one view with respect to the means, the SH coefficients and the opacity
+ * logits (scales and rotations fixed), by the chain rule through Sec. 3's compositing
+ * (back to front: dC/drho_i = c_i T_i - (sum_{j>i} c_j rho_j T_j) / (1 - rho_i)) and the
+ * EWA projection.  Accumulates (+=) into g_means[3][N], g_sh[(d+1)^2][3][N],
+ * g_logit[N].  FP64 throughout. */
+
+static void sh_grad(int deg, const double* d, double G[16][3]) {
+    const double pi = 3.14159265358979323846;
+    double x = d[0], y = d[1], z = d[2];
+    memset(G, 0, sizeof(double) * 48);
+    if (deg < 1) return;
+    double c1 = sqrt(3.0 / (4.0 * pi));
+    G[1][1] = -c1;
+    G[2][2] = c1;
+    G[3][0] = -c1;
+    if (deg < 2) return;
+    double c2a = 0.5 * sqrt(15.0 / pi), c2b = 0.25 * sqrt(5.0 / pi), c2c = 0.25 * sqrt(15.0 / pi);
+    G[4][0] = c2a * y; G[4][1] = c2a * x;
+    G[5][1] = -c2a * z; G[5][2] = -c2a * y;
+    G[6][0] = -2.0 * c2b * x; G[6][1] = -2.0 * c2b * y; G[6][2] = 4.0 * c2b * z;
+    G[7][0] = -c2a * z; G[7][2] = -c2a * x;
+    G[8][0] = 2.0 * c2c * x; G[8][1] = -2.0 * c2c * y;
+    if (deg < 3) return;
+    double c3a = 0.25 * sqrt(35.0 / (2.0 * pi)), c3b = 0.5 * sqrt(105.0 / pi);
+    double c3c = 0.25 * sqrt(21.0 / (2.0 * pi)), c3d = 0.25 * sqrt(7.0 / pi), c3e = 0.25 * sqrt(105.0 / pi);
+    double xx = x * x, yy = y * y, zz = z * z;
+    G[9][0] = -c3a * 6.0 * x * y; G[9][1] = -c3a * (3.0 * xx - 3.0 * yy);
+    G[10][0] = c3b * y * z; G[10][1] = c3b * x * z; G[10][2] = c3b * x * y;
+    G[11][0] = c3c * 2.0 * x * y; G[11][1] = -c3c * (4.0 * zz - xx - 3.0 * yy); G[11][2] = -c3c * 8.0 * y * z;
+    G[12][0] = -c3d * 6.0 * x * z; G[12][1] = -c3d * 6.0 * y * z; G[12][2] = c3d * (6.0 * zz - 3.0 * xx - 3.0 * yy);
+    G[13][0] = -c3c * (4.0 * zz - 3.0 * xx - yy); G[13][1] = c3c * 2.0 * x * y; G[13][2] = -c3c * 8.0 * x * z;
+    G[14][0] = c3e * 2.0 * x * z; G[14][1] = -c3e * 2.0 * y * z; G[14][2] = c3e * (xx - yy);
+    G[15][0] = -c3a * (3.0 * xx - 3.0 * yy); G[15][1] = c3a * 6.0 * x * y;
+}
+
+typedef struct {
+    int64_t gid;
+    double rho, T, k, dx, dy;
+    int clamped;
+} obterm;
+
+int or_render_backward(const or_scene* sc, const float* cam, const or_opts* o, const double* w, const double* grad_rgb,
+                       double* g_means, double* g_sh, double* g_logit) {
+    oview v;
+    ocam cm;
+    if (build_view(sc, cam, o, w, &v, &cm)) return -1;
+    const int64_t n = sc->n;
+    double* g2 = (double*)calloc((size_t)n * 9, sizeof(double)); /* mean x,y; Q xx,xy,yy; alpha; r,g,b */
+    int64_t total = (int64_t)cm.W * cm.H;
+#pragma omp parallel
+    {
+        ocand* cand = NULL;
+        obterm* tl = NULL;
+        int64_t cap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < total; ++q) {
+            double px = (double)(q % cm.W), py = (double)(q / cm.W);
+            int64_t nc = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                if (!v.valid[i]) continue;
+                double dx = px - v.mx[i];
+                if (fabs(dx) > v.rx[i]) continue;
+                double dy = py - v.my[i];
+                if (fabs(dy) > v.ry[i]) continue;
+                const oattr* g = &v.at[i];
+                double m = g->a * dx * dx + 2.0 * g->b * dx * dy + g->c * dy * dy;
+                if (m > o->cut2) continue;
+                double raw = g->alpha * exp(-0.5 * m);
+                double rho = raw < o->rho_max ? raw : o->rho_max;
+                if (rho < o->alpha_min) continue;
+                if (nc == cap) {
+                    cap = cap ? 2 * cap : 256;
+                    cand = (ocand*)realloc(cand, sizeof(ocand) * cap);
+                    tl = (obterm*)realloc(tl, sizeof(obterm) * cap);
+                }
+                cand[nc].depth = g->depth;
+                cand[nc].gid = i;
+                cand[nc].rho = rho;
+                cand[nc].viol = raw >= o->rho_max; /* reused: clamped */
+                nc++;
+            }
+            qsort(cand, (size_t)nc, sizeof(ocand), cand_cmp);
+            double T = 1.0;
+            int64_t nt = 0;
+            for (int64_t j = 0; j < nc; ++j) {
+                double Tn = T * (1.0 - cand[j].rho);
+                if (Tn < o->t_min) break;
+                const oattr* g = &v.at[cand[j].gid];
+                obterm* t = &tl[nt++];
+                t->gid = cand[j].gid;
+                t->rho = cand[j].rho;
+                t->T = T;
+                t->clamped = cand[j].viol;
+                t->dx = px - v.mx[t->gid];
+                t->dy = py - v.my[t->gid];
+                t->k = exp(-0.5 * (g->a * t->dx * t->dx + 2.0 * g->b * t->dx * t->dy + g->c * t->dy * t->dy));
+                T = Tn;
+            }
+            const double* gr = grad_rgb + 3 * q;
+            double S[3] = {0.0, 0.0, 0.0};
+            for (int64_t j = nt - 1; j >= 0; --j) {
+                const obterm* t = &tl[j];
+                const oattr* g = &v.at[t->gid];
+                double* G = g2 + 9 * t->gid;
+                double drho = 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    atomic_add_double(&G[6 + ch], gr[ch] * t->rho * t->T);
+                    drho += gr[ch] * (g->rgb[ch] * t->T - S[ch] / (1.0 - t->rho));
+                }
+                for (int ch = 0; ch < 3; ++ch) S[ch] += g->rgb[ch] * t->rho * t->T;
+                if (t->clamped) continue;
+                /* rho = alpha k, k = exp(-m/2), m = d^T Q d with d = pixel - mean */
+                atomic_add_double(&G[5], drho * t->k);
+                const double dm = -0.5 * t->rho * drho;
+                atomic_add_double(&G[0], dm * -2.0 * (g->a * t->dx + g->b * t->dy));
+                atomic_add_double(&G[1], dm * -2.0 * (g->b * t->dx + g->c * t->dy));
+                atomic_add_double(&G[2], dm * t->dx * t->dx);
+                atomic_add_double(&G[3], dm * 2.0 * t->dx * t->dy);
+                atomic_add_double(&G[4], dm * t->dy * t->dy);
+            }
+        }
+        free(cand);
+        free(tl);
+    }
+    /* projection backward, per Gaussian */
+    const int deg = sc->sh_degree, nk = (deg + 1) * (deg + 1);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        if (!v.valid[i]) continue;
+        const double* G = g2 + 9 * i;
+        double mu[3] = {sc->means[i], sc->means[n + i], sc->means[2 * n + i]};
+        double pc[3];
+        for (int r = 0; r < 3; ++r)
+            pc[r] = cm.R[3 * r] * mu[0] + cm.R[3 * r + 1] * mu[1] + cm.R[3 * r + 2] * mu[2] + cm.t[r];
+        double x = pc[0], y = pc[1], z = pc[2];
+        double a = 1.0 / (1.0 + exp(-(double)sc->opacity_logits[i]));
+        double wi = w ? w[i] : 1.0;
+        g_logit[i] += G[5] * wi * a * (1.0 - a);
+        /* covariance pieces */
+        double s[3];
+        for (int k = 0; k < 3; ++k) s[k] = exp((double)sc->log_scales[k * n + i]);
+        double qw = sc->quats[i], qx = sc->quats[n + i], qy = sc->quats[2 * n + i], qz = sc->quats[3 * n + i];
+        double qn = sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw /= qn; qx /= qn; qy /= qn; qz /= qn;
+        double Rq[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                        2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                        2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+        double Sig[9], tmp[9], Sc[9];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += Rq[3 * r + k] * s[k] * s[k] * Rq[3 * c + k];
+                Sig[3 * r + c] = acc;
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += cm.R[3 * r + k] * Sig[3 * k + c];
+                tmp[3 * r + c] = acc;
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += tmp[3 * r + k] * cm.R[3 * c + k];
+                Sc[3 * r + c] = acc;
+            }
+        double limx = o->clamp_fov * 0.5 * cm.W / cm.fx, limy = o->clamp_fov * 0.5 * cm.H / cm.fy;
+        double ux = x / z, uy = y / z;
+        int fx_in = ux >= -limx && ux <= limx, fy_in = uy >= -limy && uy <= limy;
+        if (ux < -limx) ux = -limx;
+        if (ux > limx) ux = limx;
+        if (uy < -limy) uy = -limy;
+        if (uy > limy) uy = limy;
+        double J[6] = {cm.fx / z, 0.0, -cm.fx * ux / z, 0.0, cm.fy / z, -cm.fy * uy / z};
+        const oattr* ga = &v.at[i];
+        double Q[4] = {ga->a, ga->b, ga->b, ga->c};
+        double Gq[4] = {G[2], 0.5 * G[3], 0.5 * G[3], G[4]};
+        double QG[4], H[4];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) QG[2 * r + c] = Q[2 * r] * Gq[c] + Q[2 * r + 1] * Gq[2 + c];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 2; ++c) H[2 * r + c] = -(QG[2 * r] * Q[c] + QG[2 * r + 1] * Q[2 + c]);
+        /* dL/dJ = 2 H J Sc */
+        double JS[6], dJ[6];
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; ++k) acc += J[3 * r + k] * Sc[3 * k + c];
+                JS[3 * r + c] = acc;
+            }
+        for (int r = 0; r < 2; ++r)
+            for (int c = 0; c < 3; ++c) dJ[3 * r + c] = 2.0 * (H[2 * r] * JS[c] + H[2 * r + 1] * JS[3 + c]);
+        double dx = 0.0, dy = 0.0, dz = 0.0;
+        /* J00 = fx/z, J11 = fy/z, J02 = -fx u / z, J12 = -fy v / z (u, v clamped x/z, y/z) */
+        dz += dJ[0] * (-cm.fx / (z * z)) + dJ[4] * (-cm.fy / (z * z));
+        dz += dJ[2] * (cm.fx * ux / (z * z)) + dJ[5] * (cm.fy * uy / (z * z));
+        if (fx_in) {
+            dx += dJ[2] * (-cm.fx / z) / z;
+            dz += dJ[2] * (-cm.fx / z) * (-x / (z * z));
+        }
+        if (fy_in) {
+            dy += dJ[5] * (-cm.fy / z) / z;
+            dz += dJ[5] * (-cm.fy / z) * (-y / (z * z));
+        }
+        /* projected mean */
+        dx += G[0] * cm.fx / z;
+        dz += G[0] * (-cm.fx * x / (z * z));
+        dy += G[1] * cm.fy / z;
+        dz += G[1] * (-cm.fy * y / (z * z));
+        double gm[3];
+        for (int k = 0; k < 3; ++k) gm[k] = cm.R[k] * dx + cm.R[3 + k] * dy + cm.R[6 + k] * dz;
+        /* colour */
+        double cpos[3];
+        for (int k = 0; k < 3; ++k)
+            cpos[k] = -(cm.R[k] * cm.t[0] + cm.R[3 + k] * cm.t[1] + cm.R[6 + k] * cm.t[2]);
+        double dv[3] = {mu[0] - cpos[0], mu[1] - cpos[1], mu[2] - cpos[2]};
+        double len = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+        double dh[3] = {dv[0] / len, dv[1] / len, dv[2] / len};
+        double Y[16], GY[16][3];
+        or_sh_basis(deg, dh, Y);
+        sh_grad(deg, dh, GY);
+        double gdir[3] = {0.0, 0.0, 0.0};
+        for (int ch = 0; ch < 3; ++ch) {
+            double acc = 0.5;
+            for (int k = 0; k < nk; ++k) acc += (double)sc->sh[(int64_t)(3 * k + ch) * n + i] * Y[k];
+            if (!(acc > 0.0)) continue; /* clamped colour */
+            for (int k = 0; k < nk; ++k) {
+                g_sh[(int64_t)(3 * k + ch) * n + i] += G[6 + ch] * Y[k];
+                for (int c = 0; c < 3; ++c) gdir[c] += G[6 + ch] * (double)sc->sh[(int64_t)(3 * k + ch) * n + i] * GY[k][c];
+            }
+        }
+        /* d dir / d mu = (I - dir dir^T) / len */
+        double dd = gdir[0] * dh[0] + gdir[1] * dh[1] + gdir[2] * dh[2];
+        for (int k = 0; k < 3; ++k) gm[k] += (gdir[k] - dd * dh[k]) / len;
+        for (int k = 0; k < 3; ++k) g_means[k * n + i] += gm[k];
+    }
+    free(g2);
+    free_view(&v);
+    return 0;
+}

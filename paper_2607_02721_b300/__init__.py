@@ -125,7 +125,7 @@ def lib():
     L.csgs_view_stats.argtypes = [V, I32, V, V]
     L.csgs_features.argtypes = [V, I32, V, V]
     L.csgs_log_target.argtypes = [V, V, I64, ctypes.c_float, V]
-    L.csgs_surrogate_combine.argtypes = [V, V, V, I64, ctypes.c_float, V]
+    L.csgs_surrogate_combine.argtypes = [V, V, V, I64, ctypes.c_float, I32, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -386,10 +386,11 @@ class Context:
         self._out()
         return t
 
-    def surrogate_combine(self, y, s_exact, eps: float):
+    def surrogate_combine(self, y, s_exact, eps: float, fill_only: bool = False):
         out = self._empty(y.numel(), self.torch.float32)
         self._in()
-        self._check(lib().csgs_surrogate_combine(self.h, _ptr(y), _ptr(s_exact), y.numel(), eps, _ptr(out)))
+        self._check(lib().csgs_surrogate_combine(self.h, _ptr(y), _ptr(s_exact), y.numel(), eps, int(fill_only),
+                                                 _ptr(out)))
         self._out()
         return out
 

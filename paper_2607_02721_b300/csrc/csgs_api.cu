@@ -1044,10 +1044,10 @@ csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float 
 }
 
 csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const float* s_exact_dev, int64_t n, float eps,
-                                   float* s_out) {
+                                   int32_t fill_only, float* s_out) {
     if (!ctx || !y_dev || !s_out || n <= 0 || !(eps >= 0.f)) return CSGS_E_INVAL;
     cudaSetDevice(ctx->device);
-    surrogate_combine(y_dev, s_exact_dev, n, eps, s_out, ctx->st);
+    surrogate_combine(y_dev, s_exact_dev, n, eps, fill_only, s_out, ctx->st);
     return launch_check(ctx, "surrogate combine");
 }
 

@@ -151,7 +151,8 @@ void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st);
 // image resolution: s = max(s, vbuf / A_view); vbuf = 0
 void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st);
 void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st);
-void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, float* out, cudaStream_t st);
+void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, int fill_only, float* out,
+                       cudaStream_t st);
 void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,
                   cudaStream_t st);
 void probabilities_from_scores(const float* s, int64_t n, const double* S, double* p, cudaStream_t st);

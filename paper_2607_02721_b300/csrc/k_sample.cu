@@ -85,11 +85,11 @@ __global__ void k_log_target(const float* __restrict__ s, int64_t n, float eps, 
 }
 
 __global__ void k_combine(const float* __restrict__ y, const float* __restrict__ s_exact, int64_t n, float eps,
-                          float* __restrict__ out) {
+                          int fill_only, float* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float e = expf(y[i]) - eps;
+        const float e = fmaxf(expf(y[i]) - eps, 0.f);
         const float s = s_exact ? s_exact[i] : 0.f;
-        out[i] = fmaxf(fmaxf(e, 0.f), s);
+        out[i] = fill_only ? (s > 0.f ? s : e) : fmaxf(e, s);
     }
 }
 
@@ -283,8 +283,9 @@ void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st)
     count_launches(1);
 }
 
-void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, float* out, cudaStream_t st) {
-    k_combine<<<148 * 8, 256, 0, st>>>(y, s_exact, n, eps, out);
+void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, int fill_only, float* out,
+                       cudaStream_t st) {
+    k_combine<<<148 * 8, 256, 0, st>>>(y, s_exact, n, eps, fill_only, out);
     count_launches(1);
 }
 

@@ -24,6 +24,7 @@ class SurrogateConfig:
     steps: int = 300
     lr: float = 1e-3
     seed: int = 0
+    fill_only: bool = False        # use the prediction only where the scored views give s = 0
 
 
 def view_subset(n_views: int, k: int) -> np.ndarray:
@@ -69,7 +70,7 @@ def surrogate_scores(ctx, sid: int, cams, cfg: SurrogateConfig | None = None, op
     ctx.set_queries(sid, cams)
     Xall = ctx.features(sid, ctx.view_stats(sid, opts))
     y = ctx.mlp_forward(Xall)
-    s_hat = ctx.surrogate_combine(y, s_sub, cfg.eps)
+    s_hat = ctx.surrogate_combine(y, s_sub, cfg.eps, cfg.fill_only)
     mark("inferred")
     if timings is not None:
         torch.cuda.synchronize()

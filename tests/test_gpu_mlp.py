@@ -140,3 +140,5 @@ def test_log_target_and_combine(ctx, torch):
     se = torch.tensor([0.2, 0.1, 0.0, 0.3], device="cuda")
     out = ctx.surrogate_combine(y, se, 1e-8).cpu().numpy()
     np.testing.assert_allclose(out, [0.2, 0.5 - 1e-8, 1.0 - 1e-8, 0.3], rtol=1e-6)
+    out = ctx.surrogate_combine(y, se, 1e-8, fill_only=True).cpu().numpy()
+    np.testing.assert_allclose(out, [0.2, 0.1, 1.0 - 1e-8, 0.3], rtol=1e-6)

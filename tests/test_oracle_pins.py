@@ -485,3 +485,58 @@ def test_adam_first_step_moves_by_lr():
     oracle.adam(p, g, m, v, 1e-2, 1)
     # bias-corrected first step: -lr * g / (|g| + eps)
     np.testing.assert_allclose(p, [1.0 - 1e-2 * 0.3 / (0.3 + 1e-8), -2.0 + 1e-2 * 1e-4 / (1e-4 + 1e-8), 0.5], rtol=1e-12)
+
+
+# ---------------------------------------------------------------- render gradient
+
+def _grad_scene(n=10, seed=0, deg=2):
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.uniform(-0.35, 0.35, n), rng.uniform(-0.35, 0.35, n), rng.uniform(1.5, 3.0, n)]).astype(np.float32)
+    ls = rng.uniform(-3.2, -2.2, (3, n)).astype(np.float32)
+    q = rng.standard_normal((4, n))
+    q /= np.linalg.norm(q, axis=0)
+    op = rng.normal(-0.5, 0.8, n).astype(np.float32)
+    sh = (rng.standard_normal(((deg + 1) ** 2, 3, n)) * 0.3).astype(np.float32)
+    return synth.Scene(means, ls, q.astype(np.float32), op, sh)
+
+
+def test_render_gradient_matches_central_differences():
+    sc = _grad_scene()
+    cam = axis_camera(W=24, H=20, f=30.0)
+    o = Opts.pure(cut2=1e4)  # smooth: no footprint cut, no thresholds
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal((20, 24, 3))
+    w = rng.uniform(0.5, 1.5, sc.n)
+    gm, gs, gl = oracle.render_backward(sc, cam, r, o, w=w)
+
+    def L(s):
+        return float((oracle.render(s, cam, o, w=w)["rgb"] * r).sum())
+
+    h = 1e-4
+    checks = 0
+    for arr_name, grad in (("means", gm), ("sh", gs), ("opacity_logits", gl)):
+        arr = getattr(sc, arr_name)
+        flat_idx = rng.choice(arr.size, min(12, arr.size), replace=False)
+        for fi in flat_idx:
+            ix = np.unravel_index(fi, arr.shape)
+            base = arr[ix]
+            vals = []
+            for sgn in (1, -1):
+                s2 = synth.Scene(sc.means.copy(), sc.log_scales, sc.quats, sc.opacity_logits.copy(), sc.sh.copy())
+                a2 = getattr(s2, arr_name)
+                a2[ix] = np.float32(float(base) + sgn * h)
+                vals.append((L(s2), float(a2[ix]) - float(base)))
+            fd = (vals[0][0] - vals[1][0]) / (vals[0][1] - vals[1][1])
+            assert grad[ix] == pytest.approx(fd, rel=2e-3, abs=2e-4), (arr_name, ix, grad[ix], fd)
+            checks += 1
+    assert checks == 34
+
+
+def test_render_gradient_of_unit_weight_scene_matches_unweighted():
+    sc = _grad_scene(8, seed=2, deg=1)
+    cam = axis_camera(W=16, H=16, f=24.0)
+    r = np.random.default_rng(3).standard_normal((16, 16, 3))
+    a = oracle.render_backward(sc, cam, r, Opts())
+    b = oracle.render_backward(sc, cam, r, Opts(), w=np.ones(sc.n))
+    for x, y in zip(a, b):  # equal up to the order of the parallel accumulation
+        np.testing.assert_allclose(x, y, rtol=1e-12, atol=1e-15)
