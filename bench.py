@@ -399,24 +399,26 @@ def run_surrogate(args):
     ctx = csgs.Context(0, stream=torch.cuda.Stream())
     sid = ctx.load_scene(scene)
     ctx.set_queries(sid, cams)
-    s_exact, _ = ctx.score(sid)  # warm-up (buffers)
+    res_id = {"pixel": csgs.RES_PIXEL, "scene": csgs.RES_SCENE}[args.resolution]
+    sopts = csgs.default_opts(resolution=res_id)
+    s_exact, _ = ctx.score(sid, sopts)  # warm-up (buffers)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(ctx.stream)
-    s_exact, S = ctx.score(sid)
+    s_exact, S = ctx.score(sid, sopts)
     ev1.record(ctx.stream)
     torch.cuda.synchronize()
     exact_ms = ev0.elapsed_time(ev1)
     scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps, fill_only=args.fill_only,
                                      aug_views=tuple(int(x) for x in args.aug_views.split(",") if x))
-    surrogate.surrogate_scores(ctx, sid, cams, scfg)  # warm-up
+    surrogate.surrogate_scores(ctx, sid, cams, scfg, opts=sopts)  # warm-up
     tim = {}
-    s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, scfg, timings=tim)
+    s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, scfg, opts=sopts, timings=tim)
     views = list(range(0, len(cams), args.psnr_stride))
     res = {"mode": "surrogate", "config": cfg, "exact_ms": exact_ms, "surrogate": tim,
            "speedup_total": exact_ms / tim["total_ms"],
            "speedup_without_training": exact_ms / (tim["total_ms"] - tim["train_ms"]),
            "psnr_views": len(views), "train_views": args.train_views, "train_steps": args.train_steps,
-           "fill_only": args.fill_only, "aug_views": scfg.aug_views}
+           "fill_only": args.fill_only, "aug_views": scfg.aug_views, "resolution": args.resolution}
     for name, sv in (("exact", s_exact), ("surrogate", s_hat), ("subset_only", s_sub)):
         res["psnr_" + name] = surrogate.pruned_psnr(ctx, sid, cams, sv, m, 0, views)
     res["delta_psnr_surrogate_vs_exact"] = res["psnr_surrogate"] - res["psnr_exact"]
@@ -445,6 +447,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--psnr-stride", type=int, default=5)
     ap.add_argument("--fill-only", action="store_true")
+    ap.add_argument("--resolution", default="pixel", choices=["pixel", "scene"])
     ap.add_argument("--aug-views", default="5,10")
     args = ap.parse_args()
     if args.impl == "reference":

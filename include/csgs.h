@@ -240,6 +240,30 @@ csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float 
 csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const float* s_exact_dev, int64_t n, float eps,
                                    int32_t fill_only, float* s_out);
 
+/* ------------------------------------------------------------------ short recovery
+ * The paper's short post-pruning finetune (Sec. 4, "short recovery"): gradients of a
+ * loss on the weighted pruned render with respect to the means, SH coefficients and
+ * opacity logits (scales and rotations fixed). */
+
+/* Overwrite a scene's attributes in place (same N and SH degree; host or device
+ * source as desc->is_device).  Asynchronous; no finiteness check. */
+csgs_status csgs_update_scene(csgs_ctx* ctx, int32_t scene_id, const csgs_scene_desc* desc);
+
+/* Backward of csgs_render (same view, weights and options): given grad_rgb_dev =
+ * dL/dC (device float[H][W][3]), ADDS dL/d means to g_means_dev [3][N], dL/d SH to
+ * g_sh_dev [(d+1)^2][3][N] and dL/d opacity logits to g_logit_dev [N] (all device
+ * float).  Back to front through the compositing (dC/drho_i = c_i T_i - S_i / (1 -
+ * rho_i), S_i the colour behind i), no gradient through the rho_max clamp or the
+ * footprint and threshold decisions, then through the EWA projection and the SH colour
+ * (including its view direction).  Asynchronous. */
+csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev,
+                                 const float* w_dev, int64_t n_sel, const csgs_score_opts* opts, const float* grad_rgb_dev,
+                                 float* g_means_dev, float* g_sh_dev, float* g_logit_dev);
+
+/* One Adam step (Kingma & Ba) on n device floats p with gradient g and moments m, v. */
+csgs_status csgs_adam_update(csgs_ctx* ctx, float* p_dev, const float* g_dev, float* m_dev, float* v_dev, int64_t n,
+                             float lr, float beta1, float beta2, float eps, int32_t step);
+
 /* Wait for the context's stream and report errors of asynchronous work. */
 csgs_status csgs_sync(csgs_ctx* ctx);
 

@@ -77,7 +77,7 @@ EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error"
            "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
            "csgs_debug_tc_gemm", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
            "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
-           "csgs_surrogate_combine")
+           "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update")
 
 _lib = None
 
@@ -126,6 +126,10 @@ def lib():
     L.csgs_features.argtypes = [V, I32, V, V]
     L.csgs_log_target.argtypes = [V, V, I64, ctypes.c_float, V]
     L.csgs_surrogate_combine.argtypes = [V, V, V, I64, ctypes.c_float, I32, V]
+    L.csgs_update_scene.argtypes = [V, I32, V]
+    L.csgs_render_backward.argtypes = [V, I32, I32, V, V, I64, V, V, V, V, V]
+    L.csgs_adam_update.argtypes = [V, V, V, V, V, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   I32]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -393,6 +397,30 @@ class Context:
                                                  _ptr(out)))
         self._out()
         return out
+
+    # -- short recovery
+    def update_scene(self, sid: int, means, log_scales, quats, opacity_logits, sh):
+        """Overwrite a scene's attributes from device tensors (same shapes)."""
+        k = sh.shape[0]
+        deg = {1: 0, 4: 1, 9: 2, 16: 3}[k]
+        d = SceneDesc(int(means.shape[1]), deg, 1, means.data_ptr(), log_scales.data_ptr(), quats.data_ptr(),
+                      opacity_logits.data_ptr(), sh.data_ptr())
+        self._in()
+        self._check(lib().csgs_update_scene(self.h, sid, ctypes.byref(d)))
+
+    def render_backward(self, sid: int, view: int, grad_rgb, g_means, g_sh, g_logit, idx=None, w=None, opts=None):
+        n_sel = 0 if idx is None else idx.numel()
+        opts = opts or default_opts()
+        self._in()
+        self._check(lib().csgs_render_backward(self.h, sid, view, _ptr(idx), _ptr(w), n_sel, ctypes.byref(opts),
+                                               _ptr(grad_rgb), _ptr(g_means), _ptr(g_sh), _ptr(g_logit)))
+        self._out()
+
+    def adam_update(self, p, g, m, v, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-15):
+        self._in()
+        self._check(lib().csgs_adam_update(self.h, _ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), lr, beta1, beta2,
+                                           eps, step))
+        self._out()
 
     def debug_tc_gemm(self, A, B):
         """C = A @ B^T on the tensor cores (A: [128, K] bf16, B: [N, K] bf16)."""

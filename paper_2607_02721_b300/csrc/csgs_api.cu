@@ -65,6 +65,7 @@ struct csgs_ctx {
     bool mlp_ready = false;
     DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1;
     int64_t mlp_rows = 0;
+    DevBuf bRgb, bT, bLast, g2d;  // render backward
     csgs_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evpool;  // phase timing
@@ -321,7 +322,8 @@ void csgs_destroy(csgs_ctx* ctx) {
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
                       &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
-                      &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1};
+                      &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
+                      &ctx->g2d};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->d_ctr) cudaFree(ctx->d_ctr);
     if (ctx->d_nconst) cudaFree(ctx->d_nconst);
@@ -1049,6 +1051,107 @@ csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const floa
     cudaSetDevice(ctx->device);
     surrogate_combine(y_dev, s_exact_dev, n, eps, fill_only, s_out, ctx->st);
     return launch_check(ctx, "surrogate combine");
+}
+
+}  // extern "C"
+
+// ======================================================================= finetune support
+
+extern "C" {
+
+csgs_status csgs_update_scene(csgs_ctx* ctx, int32_t scene_id, const csgs_scene_desc* d) {
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!d || d->n != s->n || d->sh_degree != s->deg) return fail(ctx, CSGS_E_INVAL, "scene shape mismatch");
+    if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
+        return fail(ctx, CSGS_E_INVAL, "null attribute pointer");
+    cudaSetDevice(ctx->device);
+    const size_t n = (size_t)s->n, nk = (size_t)(s->deg + 1) * (s->deg + 1);
+    const cudaMemcpyKind kind = d->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(ctx, cudaMemcpyAsync(s->means, d->means, 3 * n * sizeof(float), kind, ctx->st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s->log_scales, d->log_scales, 3 * n * sizeof(float), kind, ctx->st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s->quats, d->quats, 4 * n * sizeof(float), kind, ctx->st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s->opac, d->opacity_logits, n * sizeof(float), kind, ctx->st));
+    CUDA_TRY(ctx, cudaMemcpyAsync(s->sh, d->sh, 3 * nk * n * sizeof(float), kind, ctx->st));
+    return CSGS_OK;
+}
+
+csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev,
+                                 const float* w_dev, int64_t n_sel, const csgs_score_opts* opts, const float* grad_rgb_dev,
+                                 float* g_means_dev, float* g_sh_dev, float* g_logit_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
+    if (!grad_rgb_dev || !g_means_dev || !g_sh_dev || !g_logit_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
+    if ((idx_dev == nullptr) != (w_dev == nullptr)) return fail(ctx, CSGS_E_INVAL, "idx and w must both be given");
+    if (idx_dev && (n_sel < 0 || n_sel > s->n)) return fail(ctx, CSGS_E_INVAL, "n_sel out of range");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    if ((r = upload_cams(ctx, s, ko))) return r;
+    const int64_t n = s->n;
+    const CamDev& cam = s->cams[view];
+    const size_t npx = (size_t)cam.W * cam.H;
+    if ((r = ensure_view_buffers(ctx, n, 1, cam.tiles_x * cam.tiles_y))) return r;
+    if ((r = ensure(ctx, ctx->bRgb, sizeof(float) * 3 * npx)) || (r = ensure(ctx, ctx->bT, sizeof(float) * npx)) ||
+        (r = ensure(ctx, ctx->bLast, sizeof(int) * npx)) || (r = ensure(ctx, ctx->g2d, sizeof(float) * 9 * (size_t)n)))
+        return r;
+    const float* wts = nullptr;
+    if (idx_dev) {
+        if ((r = ensure(ctx, ctx->wfull, sizeof(float) * (size_t)n))) return r;
+        wts = P<float>(ctx->wfull);
+    }
+    cudaStream_t st = ctx->st;
+    set_u64(ctx->d_nconst, (unsigned long long)n, st);
+    const SceneDev sd = scene_dev(*s);
+    int retries = 0;
+    for (;;) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
+        if (idx_dev) {
+            CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
+            scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
+        }
+        launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
+                       P<uint2>(ctx->rects), st);
+        const uint32_t* iv = bin_view(ctx, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam);
+        CompositeArgs a{};
+        a.ranges = P<uint2>(ctx->ranges);
+        a.inst_gid = iv;
+        a.splats = P<Splat>(ctx->splats);
+        a.n_gauss = (int)n;
+        a.cam = cam;
+        a.o = ko;
+        a.rgb = P<float>(ctx->bRgb);
+        a.T = P<float>(ctx->bT);
+        a.last = P<int>(ctx->bLast);
+        a.ctr = ctx->d_ctr;
+        launch_composite_render(a, st);
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->g2d.p, 0, sizeof(float) * 9 * (size_t)n, st));
+        a.grad_rgb = grad_rgb_dev;
+        a.g2d = P<float>(ctx->g2d);
+        launch_composite_backward(a, st);
+        if ((r = launch_check(ctx, "render backward kernels"))) return r;
+        if ((r = read_counters(ctx))) return r;
+        if (ctx->h_ctr->err & kErrCapacity) {
+            if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+            if ((r = grow_capacity(ctx))) return r;
+            continue;
+        }
+        break;
+    }
+    if (ctx->h_ctr->err & kErrIndex) return fail(ctx, CSGS_E_INVAL, "coreset index out of range");
+    launch_project_backward(sd, s->d_cams + view, wts, ko, P<float>(ctx->g2d), g_means_dev, g_sh_dev, g_logit_dev, st);
+    return launch_check(ctx, "projection backward");
+}
+
+csgs_status csgs_adam_update(csgs_ctx* ctx, float* p_dev, const float* g_dev, float* m_dev, float* v_dev, int64_t n,
+                             float lr, float beta1, float beta2, float eps, int32_t step) {
+    if (!ctx || !p_dev || !g_dev || !m_dev || !v_dev || n <= 0 || step < 1) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    adam_update(p_dev, g_dev, m_dev, v_dev, n, lr, beta1, beta2, eps, step, ctx->st);
+    return launch_check(ctx, "adam");
 }
 
 }  // extern "C"

@@ -93,6 +93,10 @@ void launch_check_finite(const float* p, int64_t n, DevCounters* ctr, cudaStream
 void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const KOpts& o, float* stats, int accumulate,
                        cudaStream_t st);
 void launch_features(const SceneDev& sc, const float* stats, void* X, cudaStream_t st);
+// chain the per-Gaussian 2-D gradients of one view to means [3][N], SH [(d+1)^2][3][N]
+// and opacity logits [N] (accumulated)
+void launch_project_backward(const SceneDev& sc, const CamDev* d_cam, const float* d_w, const KOpts& o,
+                             const float* g2d, float* g_means, float* g_sh, float* g_logit, cudaStream_t st);
 // wfull[idx[k]] = w[k] (indices outside [0, n) set kErrIndex and are skipped)
 void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* wfull, int64_t n, DevCounters* ctr,
                      cudaStream_t st);
@@ -129,12 +133,16 @@ struct CompositeArgs {
     float* tile_sum;   // tile resolution: per tile-list entry, the Gaussian's sum over the tile
     const float* wsel; // transfer: coreset weight per Gaussian (0 = removed)
     float* aux;        // transfer: [H][W][11] per-pixel outputs
+    int* last;         // render: [H][W] index + 1 of each pixel's last contributor (optional)
+    const float* grad_rgb;  // backward: dL/dC [H][W][3]
+    float* g2d;        // backward: per Gaussian dL/d(mean x, mean y, Q xx, Q xy, Q yy, alpha, r, g, b)
     DevCounters* ctr;
     int stats;
 };
 void launch_composite_render(const CompositeArgs& a, cudaStream_t st);
 void launch_composite_score(const CompositeArgs& a, cudaStream_t st);
 void launch_composite_transfer(const CompositeArgs& a, cudaStream_t st);
+void launch_composite_backward(const CompositeArgs& a, cudaStream_t st);
 
 // ---- sampling (k_sample.cu)
 struct SampleTemp {
@@ -151,6 +159,8 @@ void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st);
 // image resolution: s = max(s, vbuf / A_view); vbuf = 0
 void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st);
 void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st);
+void adam_update(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
+                 int step, cudaStream_t st);
 void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, int fill_only, float* out,
                        cudaStream_t st);
 void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,

@@ -313,6 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             a.rgb[3 * pix + 1] = A1;
             a.rgb[3 * pix + 2] = A2;
             if (a.T) a.T[pix] = T;
+            if (a.last) a.last[pix] = last;
         }
     }
 
@@ -466,7 +467,131 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     }
 }
 
+// Backward of the render (Sec. 3's compositing, back to front): for contributor i of a
+// pixel, with S the colour composited behind it,
+//   dC/dc_i = rho_i T_i,  dC/drho_i = c_i T_i - S / (1 - rho_i),  T_i = T_{i+1} / (1 - rho_i),
+// rho_i = min(rho_max, alpha k) (no gradient through the clamp), k = exp(-m / 2),
+// m = d^T Q d, d = pixel - mean.  rho is recomputed exactly as in the forward pass and
+// the contributor set is the forward's (the pixel's last contributor).  Per-Gaussian
+// sums over the tile's pixels: warp sums, shared-memory sums, one global add per
+// (tile, Gaussian) and component.
+__global__ void __launch_bounds__(kThreads) k_composite_bwd(const CompositeArgs a) {
+    __shared__ Shared sh;
+    __shared__ float4 sD[kThreads];      // mean x, mean y (tile-centred), Q xx, Q xy
+    __shared__ float2 sE[kThreads];      // Q yy, alpha
+    __shared__ float acc[kThreads][9];
+    const CamDev& cam = a.cam;
+    const int tile = blockIdx.x;
+    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 4 + (lane >> 3);
+    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const bool inside = px < cam.W && py < cam.H;
+    const float X = (float)lx - 7.5f, Y = (float)ly - 7.5f;
+    const float cx = (float)(tx * kTile) + 7.5f, cy = (float)(ty * kTile) + 7.5f;
+    const uint2 rg = a.ranges[tile];
+    const uint32_t start = rg.x;
+    const float rho_max = a.o.rho_max;
+    const float K2inv = 1.f / (0.5f * kLog2e);
+    const size_t pix = (size_t)py * cam.W + px;
+    float T = inside ? a.T[pix] : 1.f;
+    int last = inside ? a.last[pix] : 0;
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (inside) {
+        g0 = a.grad_rgb[3 * pix];
+        g1 = a.grad_rgb[3 * pix + 1];
+        g2 = a.grad_rgb[3 * pix + 2];
+    }
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+    if (tid == 0) sh.last = 0;
+    __syncthreads();
+    atomicMax(&sh.last, last);
+    __syncthreads();
+    const int n2 = sh.last;
+    for (int b = ((n2 - 1) / kThreads) * kThreads; n2 > 0 && b >= 0; b -= kThreads) {
+        __syncthreads();
+        stage<kRender>(a, sh, start + b + tid, rg.y, cx, cy);
+        {
+            const float4 Aj = sh.A[tid];
+            // tile-centred mean and natural-unit conic back from the Cholesky form
+            const float s1 = Aj.x, s1k = Aj.y, s2 = Aj.w;
+            const float my = -sh.B[tid].x / s2;
+            const float mx = -(Aj.z + s1k * my) / s1;
+            sD[tid] = make_float4(mx, my, s1 * s1 * K2inv, s1 * s1k * K2inv);
+            sE[tid] = make_float2((s1k * s1k + s2 * s2) * K2inv, exp2f(sh.B[tid].y));
+#pragma unroll
+            for (int c = 0; c < 9; ++c) acc[tid][c] = 0.f;
+        }
+        __syncthreads();
+        const int cnt = min(kThreads, n2 - b);
+        const int nw = warp_list(sh, cnt, warp, lane);
+        const int lim = max(0, min(cnt, last - b));
+        for (int k = nw - 1; k >= 0; --k) {
+            const int j = sh.wl[warp][k];
+            float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            bool any = false;
+            if (j < lim) {
+                const float4 Aj = sh.A[j];
+                const float4 Bj = sh.B[j];
+                const float p = exponent2(Aj, Bj, X, Y);
+                if (p >= Bj.z) {
+                    any = true;
+                    const float raw = ex2_approx(p);
+                    const float r = fminf(rho_max, raw);
+                    const float Ti = T / (1.f - r);
+                    const float4 Cj = sh.C[j];
+                    const float rT = r * Ti;
+                    v[6] = g0 * rT;
+                    v[7] = g1 * rT;
+                    v[8] = g2 * rT;
+                    const float inv1 = 1.f / (1.f - r);
+                    const float drho = g0 * (Cj.x * Ti - S0 * inv1) + g1 * (Cj.y * Ti - S1 * inv1) +
+                                       g2 * (Cj.z * Ti - S2 * inv1);
+                    S0 = fmaf(Cj.x, rT, S0);
+                    S1 = fmaf(Cj.y, rT, S1);
+                    S2 = fmaf(Cj.z, rT, S2);
+                    T = Ti;
+                    if (raw < rho_max) {
+                        const float4 D = sD[j];
+                        const float2 E = sE[j];
+                        v[5] = drho * raw / E.y;
+                        const float dm = -0.5f * raw * drho;
+                        const float dx = X - D.x, dy = Y - D.y;
+                        v[0] = -2.f * dm * (D.z * dx + D.w * dy);
+                        v[1] = -2.f * dm * (D.w * dx + E.x * dy);
+                        v[2] = dm * dx * dx;
+                        v[3] = 2.f * dm * dx * dy;
+                        v[4] = dm * dy * dy;
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    float x = v[c];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                    if (lane == 0 && x != 0.f) atomicAdd(&acc[j][c], x);
+                }
+            }
+        }
+        __syncthreads();
+        if (tid < cnt && sh.msk[tid]) {
+            const uint32_t g = sh.gid[tid];
+#pragma unroll
+            for (int c = 0; c < 9; ++c)
+                if (acc[tid][c] != 0.f) atomicAdd(a.g2d + (size_t)g * 9 + c, acc[tid][c]);
+        }
+    }
+}
+
 }  // namespace
+
+void launch_composite_backward(const CompositeArgs& a, cudaStream_t st) {
+    const int tiles = a.cam.tiles_x * a.cam.tiles_y;
+    k_composite_bwd<<<tiles, kThreads, 0, st>>>(a);
+    count_launches(1);
+}
 
 void launch_composite_transfer(const CompositeArgs& a, cudaStream_t st) {
     const int tiles = a.cam.tiles_x * a.cam.tiles_y;

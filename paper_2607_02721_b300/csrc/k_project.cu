@@ -332,6 +332,151 @@ __global__ void k_features(SceneDev sc, const float* __restrict__ stats, __nv_bf
     }
 }
 
+// Gradients of the real SH basis (degree <= 3) with respect to the direction (x, y, z).
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float* Y, float (*G)[3]) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        Y[k] = 0.f;
+        G[k][0] = G[k][1] = G[k][2] = 0.f;
+    }
+    Y[0] = 0.28209479177387814f;
+    if (DEG >= 1) {
+        const float c1 = 0.48860251190291992f;
+        Y[1] = -c1 * y; Y[2] = c1 * z; Y[3] = -c1 * x;
+        G[1][1] = -c1; G[2][2] = c1; G[3][0] = -c1;
+    }
+    if (DEG >= 2) {
+        const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.54627421529603959f;
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = a * x * y; Y[5] = -a * y * z; Y[6] = b * (2.f * zz - xx - yy); Y[7] = -a * x * z; Y[8] = c * (xx - yy);
+        G[4][0] = a * y; G[4][1] = a * x;
+        G[5][1] = -a * z; G[5][2] = -a * y;
+        G[6][0] = -2.f * b * x; G[6][1] = -2.f * b * y; G[6][2] = 4.f * b * z;
+        G[7][0] = -a * z; G[7][2] = -a * x;
+        G[8][0] = 2.f * c * x; G[8][1] = -2.f * c * y;
+        if (DEG >= 3) {
+            const float e0 = 0.59004358992664352f, e1 = 2.8906114426405538f, e2 = 0.45704579946446572f,
+                        e3 = 0.37317633259011540f, e4 = 1.4453057213202769f;
+            Y[9] = -e0 * y * (3.f * xx - yy); Y[10] = e1 * x * y * z; Y[11] = -e2 * y * (4.f * zz - xx - yy);
+            Y[12] = e3 * z * (2.f * zz - 3.f * xx - 3.f * yy); Y[13] = -e2 * x * (4.f * zz - xx - yy);
+            Y[14] = e4 * z * (xx - yy); Y[15] = -e0 * x * (xx - 3.f * yy);
+            G[9][0] = -6.f * e0 * x * y; G[9][1] = -e0 * (3.f * xx - 3.f * yy);
+            G[10][0] = e1 * y * z; G[10][1] = e1 * x * z; G[10][2] = e1 * x * y;
+            G[11][0] = 2.f * e2 * x * y; G[11][1] = -e2 * (4.f * zz - xx - 3.f * yy); G[11][2] = -8.f * e2 * y * z;
+            G[12][0] = -6.f * e3 * x * z; G[12][1] = -6.f * e3 * y * z; G[12][2] = e3 * (6.f * zz - 3.f * xx - 3.f * yy);
+            G[13][0] = -e2 * (4.f * zz - 3.f * xx - yy); G[13][1] = 2.f * e2 * x * y; G[13][2] = -8.f * e2 * x * z;
+            G[14][0] = 2.f * e4 * x * z; G[14][1] = -2.f * e4 * y * z; G[14][2] = e4 * (xx - yy);
+            G[15][0] = -e0 * (3.f * xx - 3.f * yy); G[15][1] = 6.f * e0 * x * y;
+        }
+    }
+}
+
+// Projection backward of one view, per Gaussian: the 2-D gradients g2d[i] = dL/d(mean x,
+// mean y, Q xx, Q xy, Q yy, alpha', r, g, b) chained to the mean (through the projected
+// mean, the Jacobian J of the EWA covariance and the SH view direction), the SH
+// coefficients (unclamped colours) and the opacity logit (alpha' = w sigmoid(logit)).
+// With Q = cov'^-1: dL/dcov' = -Q G Q, dL/dJ = 2 (dL/dcov') J Sigma_cam.
+template <int DEG>
+__global__ void __launch_bounds__(256) k_project_bwd(SceneDev sc, const CamDev* __restrict__ camp,
+                                                     const float* __restrict__ wts, KOpts o,
+                                                     const float* __restrict__ g2d, float* __restrict__ g_means,
+                                                     float* __restrict__ g_sh, float* __restrict__ g_logit) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n) return;
+    const float* G = g2d + (size_t)9 * i;
+    float gsum = 0.f;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) gsum += fabsf(G[c]);
+    if (gsum == 0.f) return;
+    const CamDev& c = *camp;
+    const int n = sc.n;
+    float mu[3], cov3[6], op;
+    float shc[3 * (DEG + 1) * (DEG + 1)];
+    load_gaussian<DEG>(sc, i, nullptr, mu, cov3, op, shc);
+    const float w = wts ? wts[i] : 1.f;
+    g_logit[i] += G[5] * w * op * (1.f - op);
+    const float x = c.R[0] * mu[0] + c.R[1] * mu[1] + c.R[2] * mu[2] + c.t[0];
+    const float y = c.R[3] * mu[0] + c.R[4] * mu[1] + c.R[5] * mu[2] + c.t[1];
+    const float z = c.R[6] * mu[0] + c.R[7] * mu[1] + c.R[8] * mu[2] + c.t[2];
+    const float s00 = cov3[0], s01 = cov3[1], s02 = cov3[2], s11 = cov3[3], s12 = cov3[4], s22 = cov3[5];
+    float T[9], Sc[9];
+    for (int r = 0; r < 3; ++r) {
+        const float a0 = c.R[3 * r], a1 = c.R[3 * r + 1], a2 = c.R[3 * r + 2];
+        T[3 * r + 0] = a0 * s00 + a1 * s01 + a2 * s02;
+        T[3 * r + 1] = a0 * s01 + a1 * s11 + a2 * s12;
+        T[3 * r + 2] = a0 * s02 + a1 * s12 + a2 * s22;
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q)
+            Sc[3 * r + q] = T[3 * r] * c.R[3 * q] + T[3 * r + 1] * c.R[3 * q + 1] + T[3 * r + 2] * c.R[3 * q + 2];
+    float ux = x / z, uy = y / z;
+    const bool inx = ux >= -c.limx && ux <= c.limx, iny = uy >= -c.limy && uy <= c.limy;
+    ux = fminf(fmaxf(ux, -c.limx), c.limx);
+    uy = fminf(fmaxf(uy, -c.limy), c.limy);
+    const float J[6] = {c.fx / z, 0.f, -c.fx * ux / z, 0.f, c.fy / z, -c.fy * uy / z};
+    float JS[6];
+    for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 3; ++q) JS[3 * r + q] = J[3 * r] * Sc[q] + J[3 * r + 1] * Sc[3 + q] + J[3 * r + 2] * Sc[6 + q];
+    const float ca = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2] + o.dilation;
+    const float cb = JS[0] * J[3] + JS[1] * J[4] + JS[2] * J[5];
+    const float cc = JS[3] * J[3] + JS[4] * J[4] + JS[5] * J[5] + o.dilation;
+    const float idet = 1.f / (ca * cc - cb * cb);
+    const float Q[4] = {cc * idet, -cb * idet, -cb * idet, ca * idet};
+    const float Gq[4] = {G[2], 0.5f * G[3], 0.5f * G[3], G[4]};
+    float QG[4], H[4];
+    for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 2; ++q) QG[2 * r + q] = Q[2 * r] * Gq[q] + Q[2 * r + 1] * Gq[2 + q];
+    for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 2; ++q) H[2 * r + q] = -(QG[2 * r] * Q[q] + QG[2 * r + 1] * Q[2 + q]);
+    float dJ[6];
+    for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 3; ++q) dJ[3 * r + q] = 2.f * (H[2 * r] * JS[q] + H[2 * r + 1] * JS[3 + q]);
+    float dx = 0.f, dy = 0.f, dz = 0.f;
+    const float iz = 1.f / z, iz2 = iz * iz;
+    dz += dJ[0] * (-c.fx * iz2) + dJ[4] * (-c.fy * iz2);
+    dz += dJ[2] * (c.fx * ux * iz2) + dJ[5] * (c.fy * uy * iz2);
+    if (inx) {
+        dx += dJ[2] * (-c.fx * iz) * iz;
+        dz += dJ[2] * (-c.fx * iz) * (-x * iz2);
+    }
+    if (iny) {
+        dy += dJ[5] * (-c.fy * iz) * iz;
+        dz += dJ[5] * (-c.fy * iz) * (-y * iz2);
+    }
+    dx += G[0] * c.fx * iz;
+    dz += G[0] * (-c.fx * x * iz2);
+    dy += G[1] * c.fy * iz;
+    dz += G[1] * (-c.fy * y * iz2);
+    float gm[3];
+    for (int k = 0; k < 3; ++k) gm[k] = c.R[k] * dx + c.R[3 + k] * dy + c.R[6 + k] * dz;
+    // colour through the SH basis and the view direction
+    const float vx = mu[0] - c.campos[0], vy = mu[1] - c.campos[1], vz = mu[2] - c.campos[2];
+    const float len = sqrtf(vx * vx + vy * vy + vz * vz), il = 1.f / len;
+    const float hx = vx * il, hy = vy * il, hz = vz * il;
+    float Y[16], GY[16][3];
+    sh_basis_grad<DEG>(hx, hy, hz, Y, GY);
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    float gd[3] = {0.f, 0.f, 0.f};
+    for (int ch = 0; ch < 3; ++ch) {
+        float acc = 0.5f;
+        for (int k = 0; k < K; ++k) acc = fmaf(shc[3 * k + ch], Y[k], acc);
+        if (!(acc > 0.f)) continue;
+        const float gc = G[6 + ch];
+        for (int k = 0; k < K; ++k) {
+            g_sh[(size_t)(3 * k + ch) * n + i] += gc * Y[k];
+            gd[0] += gc * shc[3 * k + ch] * GY[k][0];
+            gd[1] += gc * shc[3 * k + ch] * GY[k][1];
+            gd[2] += gc * shc[3 * k + ch] * GY[k][2];
+        }
+    }
+    const float dd = gd[0] * hx + gd[1] * hy + gd[2] * hz;
+    gm[0] += (gd[0] - dd * hx) * il;
+    gm[1] += (gd[1] - dd * hy) * il;
+    gm[2] += (gd[2] - dd * hz) * il;
+    for (int k = 0; k < 3; ++k) g_means[(size_t)k * n + i] += gm[k];
+}
+
 __global__ void k_scatter_weights(const int32_t* __restrict__ idx, const float* __restrict__ w, int64_t n_sel,
                                   float* __restrict__ wfull, int64_t n, DevCounters* ctr) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_sel; k += (int64_t)gridDim.x * blockDim.x) {
@@ -364,6 +509,19 @@ void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const K
         case 1: k_view_stats<1><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
         case 2: k_view_stats<2><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
         default: k_view_stats<3><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
+    }
+    count_launches(1);
+}
+
+void launch_project_backward(const SceneDev& sc, const CamDev* d_cam, const float* d_w, const KOpts& o,
+                             const float* g2d, float* g_means, float* g_sh, float* g_logit, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (sc.n + threads - 1) / threads;
+    switch (sc.deg) {
+        case 0: k_project_bwd<0><<<blocks, threads, 0, st>>>(sc, d_cam, d_w, o, g2d, g_means, g_sh, g_logit); break;
+        case 1: k_project_bwd<1><<<blocks, threads, 0, st>>>(sc, d_cam, d_w, o, g2d, g_means, g_sh, g_logit); break;
+        case 2: k_project_bwd<2><<<blocks, threads, 0, st>>>(sc, d_cam, d_w, o, g2d, g_means, g_sh, g_logit); break;
+        default: k_project_bwd<3><<<blocks, threads, 0, st>>>(sc, d_cam, d_w, o, g2d, g_means, g_sh, g_logit); break;
     }
     count_launches(1);
 }

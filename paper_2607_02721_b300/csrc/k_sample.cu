@@ -107,6 +107,18 @@ __global__ void k_gather_batch(const uint4* __restrict__ X, const float* __restr
     tb[j] = t[row];
 }
 
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
 __global__ void k_probs(const float* __restrict__ s, int64_t n, const double* __restrict__ S, double* __restrict__ p) {
     const double tot = *S;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -293,6 +305,15 @@ void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed
                   cudaStream_t st) {
     k_gather_batch<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const uint4*>(X), t, n, B, seed, step,
                                                      reinterpret_cast<uint4*>(Xb), tb);
+    count_launches(1);
+}
+
+void adam_update(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
+                 int step, cudaStream_t st) {
+    const float c1 = (float)(1.0 - pow((double)b1, (double)step)), c2 = (float)(1.0 - pow((double)b2, (double)step));
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 148 * 8) blocks = 148 * 8;
+    k_adam<<<(int)blocks, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
     count_launches(1);
 }
 
