@@ -155,6 +155,30 @@ csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera*
  * sensitivity S (may be NULL).  Synchronises.  Returns CSGS_E_EMPTY when S = 0. */
 csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* s_dev, double* S_out);
 
+/* Sensitivity scores of several scenes in one submission (Algorithm 1, steps 2-3, per
+ * scene; each scene keeps its own query views).  scene_ids: host int32[n_scenes]
+ * (1 <= n_scenes <= 64); s_devs: host array of n_scenes device float pointers, scene
+ * k's scores (float[N_k]); S_out: host double[n_scenes], S per scene (required).
+ * use_graph != 0: the first call runs every launch eagerly (this settles the
+ * instance capacity), then captures the whole batch - every projection, sort,
+ * composite and reduction launch of every scene - into one CUDA graph, which later
+ * calls with the same scenes, views, options and output pointers replay with a
+ * single launch.  A graph holds the context's work buffers, so the context must
+ * not be used from another thread during the call.  Only statistics views, rays,
+ * instances, queries, score_ms and kernel_launches are filled.  Synchronises.
+ * Does not return CSGS_E_EMPTY: check S_out. */
+csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* scene_ids, const csgs_score_opts* opts,
+                             float* const* s_devs, double* S_out, int32_t use_graph);
+
+/* Choose the view batch (views projected per launch) of one scene and the
+ * radix-sort grid of the context by timing csgs_score's work on the first
+ * probe_views query views (0: min(16, views)) for view batches {1,2,4,8,16} and sort
+ * grids {296,592,1184,1776} blocks.  The result applies to later csgs_score /
+ * csgs_score_batch calls whose opts->view_batch is 0; scores do not depend on it
+ * (the footprint test is per pixel).  Outputs may be NULL.  Synchronises. */
+csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,
+                          int32_t* view_batch_out, int32_t* sort_blocks_out);
+
 /* Sensitivity sampling (Algorithm 1, steps 3-5): S = sum s (FP64), p = s / S,
  * m i.i.d. inverse-CDF draws with Philox4x32-10 uniforms (key = seed, counter =
  * draw index), counts n_i and weights w_i = n_i / (m p_i).

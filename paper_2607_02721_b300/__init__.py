@@ -77,7 +77,8 @@ EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error"
            "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
            "csgs_debug_tc_gemm", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
            "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
-           "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update")
+           "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update",
+           "csgs_score_batch", "csgs_autotune")
 
 _lib = None
 
@@ -130,6 +131,8 @@ def lib():
     L.csgs_render_backward.argtypes = [V, I32, I32, V, V, I64, V, V, V, V, V]
     L.csgs_adam_update.argtypes = [V, V, V, V, V, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    I32]
+    L.csgs_score_batch.argtypes = [V, I32, V, V, V, V, I32]
+    L.csgs_autotune.argtypes = [V, I32, V, I32, V, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -280,6 +283,35 @@ class Context:
         self._check(lib().csgs_score(self.h, sid, ctypes.byref(opts), _ptr(out), ctypes.byref(S)))
         self._out()
         return out, S.value
+
+    def score_batch(self, sids, opts: ScoreOpts | None = None, outs=None, use_graph: bool = True):
+        """Scores of several scenes in one submission (replayed as one CUDA graph after
+        the first call).  Returns ([s_k], [S_k]).  Reuse `outs` to replay the graph."""
+        torch = self.torch
+        sids = [int(k) for k in sids]
+        for k in sids:
+            if k not in self._scenes:
+                raise CsgsError(CSGS_E_INVAL, f"unknown scene id {k}")
+        if outs is None:
+            outs = [self._empty(self._scenes[k], torch.float32) for k in sids]
+        ids = (ctypes.c_int32 * len(sids))(*sids)
+        ptrs = (ctypes.c_void_p * len(sids))(*[o.data_ptr() for o in outs])
+        S = (ctypes.c_double * len(sids))()
+        opts = opts or default_opts()
+        self._in()
+        self._check(lib().csgs_score_batch(self.h, len(sids), ids, ctypes.byref(opts), ptrs, S, int(use_graph)))
+        self._out()
+        return outs, list(S)
+
+    def autotune(self, sid: int, opts: ScoreOpts | None = None, probe_views: int = 0):
+        """Tune the view batch of a scene and the sort grid; returns (view_batch, sort_blocks)."""
+        vb, g = ctypes.c_int32(), ctypes.c_int32()
+        opts = opts or default_opts()
+        self._in()
+        self._check(lib().csgs_autotune(self.h, sid, ctypes.byref(opts), probe_views, ctypes.byref(vb),
+                                        ctypes.byref(g)))
+        self._out()
+        return vb.value, g.value
 
     def sample_coreset(self, s, m: int, seed: int):
         torch = self.torch

@@ -5,13 +5,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <memory>
+#include <random>
 #include <string>
 #include <vector>
 
 #include "csgs_internal.cuh"
-
-#include <atomic>
-#include <random>
 
 using namespace csgs;
 
@@ -28,6 +28,16 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Buffers of one view's binning (depth sort, instances, tile sort, ranges).  Scoring
+// alternates two slots so that the binning of the next view, on the slot's own
+// high-priority stream, overlaps the compositing of the current one.
+struct BinSlot {
+    DevBuf dkeys_b, dvals_a, dvals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, ranges, hist, scan_tmp;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ready = nullptr;  // binning done
+    cudaEvent_t freed = nullptr;  // the compositing that read the slot is done
+};
+
 struct SceneRec {
     bool alive = false;
     int64_t n = 0;
@@ -40,6 +50,7 @@ struct SceneRec {
     std::vector<CamDev> cams;
     CamDev* d_cams = nullptr;
     float uploaded_clamp = -1.f;  // clamp_fov of the cameras on the device (-1: none)
+    int tuned_vb = 0;             // view batch chosen by csgs_autotune (0: automatic)
 };
 
 }  // namespace
@@ -55,10 +66,11 @@ struct csgs_ctx {
     double* h_S = nullptr;         // pinned
     uint32_t* h_u32 = nullptr;     // pinned
     unsigned long long* d_nconst = nullptr;
-    DevBuf splats, keys, rects, dkeys_b, dvals_a, dvals_b;
-    DevBuf ikeys_a, ikeys_b, ivals_a, ivals_b;
+    DevBuf splats, keys, rects;
+    BinSlot slot[2];
+    cudaEvent_t ev_proj = nullptr;  // projection of the current view batch done
     uint32_t cap = 0;
-    DevBuf ranges, hist, scan_tmp;
+    int sort_blocks = kSortBlocks;  // radix-sort grid (autotuned)
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
     DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
     // surrogate model
@@ -69,6 +81,10 @@ struct csgs_ctx {
     csgs_stats stats{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evpool;  // phase timing
+    cudaGraphExec_t graph_exec = nullptr;  // captured multi-scene scoring
+    std::string graph_key;
+    long long graph_nodes_launches = 0;
+    unsigned long long buf_gen = 0;  // bumped whenever a work buffer is reallocated
 };
 
 namespace {
@@ -107,6 +123,7 @@ csgs_status ensure(csgs_ctx* ctx, DevBuf& b, size_t bytes) {
         return fail(ctx, CSGS_E_NOMEM, "device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
     }
     b.bytes = want;
+    ++ctx->buf_gen;
     return CSGS_OK;
 }
 
@@ -188,44 +205,48 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
     if ((r = ensure(ctx, ctx->splats, sizeof(Splat) * (size_t)n * vb))) return r;
     if ((r = ensure(ctx, ctx->keys, sizeof(uint32_t) * (size_t)n * vb))) return r;
     if ((r = ensure(ctx, ctx->rects, sizeof(uint2) * (size_t)n * vb))) return r;
-    if ((r = ensure(ctx, ctx->dkeys_b, sizeof(uint32_t) * (size_t)n))) return r;
-    if ((r = ensure(ctx, ctx->dvals_a, sizeof(uint32_t) * (size_t)n))) return r;
-    if ((r = ensure(ctx, ctx->dvals_b, sizeof(uint32_t) * (size_t)n))) return r;
-    if ((r = ensure(ctx, ctx->ranges, sizeof(uint2) * (size_t)max_tiles))) return r;
-    if ((r = ensure(ctx, ctx->hist, sizeof(uint32_t) * kSortHistWords))) return r;
-    if ((r = ensure(ctx, ctx->scan_tmp, sizeof(uint32_t) * ((size_t)(n + 255) / 256 + 64)))) return r;
     if (ctx->cap == 0) {
         uint64_t c = (uint64_t)n * 8;
         if (c < (1u << 20)) c = 1u << 20;
         if (c > 0xF0000000ull) c = 0xF0000000ull;
         ctx->cap = (uint32_t)c;
     }
-    size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
-    if ((r = ensure(ctx, ctx->ikeys_a, ib))) return r;
-    if ((r = ensure(ctx, ctx->ikeys_b, ib))) return r;
-    if ((r = ensure(ctx, ctx->ivals_a, ib))) return r;
-    if ((r = ensure(ctx, ctx->ivals_b, ib))) return r;
+    const size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
+    for (BinSlot& b : ctx->slot) {
+        if ((r = ensure(ctx, b.dkeys_b, sizeof(uint32_t) * (size_t)n))) return r;
+        if ((r = ensure(ctx, b.dvals_a, sizeof(uint32_t) * (size_t)n))) return r;
+        if ((r = ensure(ctx, b.dvals_b, sizeof(uint32_t) * (size_t)n))) return r;
+        if ((r = ensure(ctx, b.ranges, sizeof(uint2) * (size_t)max_tiles))) return r;
+        if ((r = ensure(ctx, b.hist, sizeof(uint32_t) * kSortHistWords))) return r;
+        if ((r = ensure(ctx, b.scan_tmp, sizeof(uint32_t) * ((size_t)(n + 255) / 256 + 64)))) return r;
+        if ((r = ensure(ctx, b.ikeys_a, ib))) return r;
+        if ((r = ensure(ctx, b.ikeys_b, ib))) return r;
+        if ((r = ensure(ctx, b.ivals_a, ib))) return r;
+        if ((r = ensure(ctx, b.ivals_b, ib))) return r;
+    }
     return CSGS_OK;
 }
 
-// Depth sort -> instances -> tile sort -> ranges for one projected view.
-// Returns the instance value buffer (Gaussian ids in tile, depth order).
-const uint32_t* bin_view(csgs_ctx* ctx, int64_t n, uint32_t* keys_v, const uint2* rects_v, const CamDev& cam) {
-    cudaStream_t st = ctx->st;
-    iota_u32(P<uint32_t>(ctx->dvals_a), (int)n, st);
-    int cur = radix_sort_pairs(keys_v, P<uint32_t>(ctx->dvals_a), P<uint32_t>(ctx->dkeys_b), P<uint32_t>(ctx->dvals_b),
-                               ctx->d_nconst, (uint32_t)n, 32, P<uint32_t>(ctx->hist), st);
-    const uint32_t* order = cur ? P<uint32_t>(ctx->dvals_b) : P<uint32_t>(ctx->dvals_a);
-    const uint32_t* skeys = cur ? P<uint32_t>(ctx->dkeys_b) : keys_v;
-    emit_instances(order, skeys, rects_v, (int)n, cam.tiles_x, P<uint32_t>(ctx->ikeys_a), P<uint32_t>(ctx->ivals_a),
-                   ctx->cap, P<uint32_t>(ctx->scan_tmp), ctx->d_ctr, st);
+// Depth sort -> instances -> tile sort -> ranges for one projected view, in binning
+// slot `k` on stream `st`.  Returns the instance value buffer (Gaussian ids in tile,
+// depth order); the ranges are in slot k's `ranges`.
+const uint32_t* bin_view(csgs_ctx* ctx, int k, int64_t n, uint32_t* keys_v, const uint2* rects_v, const CamDev& cam,
+                         cudaStream_t st) {
+    BinSlot& b = ctx->slot[k];
+    unsigned long long* n_inst = &ctx->d_ctr->n_inst[k];
+    iota_u32(P<uint32_t>(b.dvals_a), (int)n, st);
+    int cur = radix_sort_pairs(keys_v, P<uint32_t>(b.dvals_a), P<uint32_t>(b.dkeys_b), P<uint32_t>(b.dvals_b),
+                               ctx->d_nconst, (uint32_t)n, 32, P<uint32_t>(b.hist), ctx->sort_blocks, st);
+    const uint32_t* order = cur ? P<uint32_t>(b.dvals_b) : P<uint32_t>(b.dvals_a);
+    emit_instances(order, rects_v, (int)n, cam.tiles_x, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
+                   P<uint32_t>(b.scan_tmp), ctx->d_ctr, n_inst, st);
     const int ntiles = cam.tiles_x * cam.tiles_y;
-    int cur2 = radix_sort_pairs(P<uint32_t>(ctx->ikeys_a), P<uint32_t>(ctx->ivals_a), P<uint32_t>(ctx->ikeys_b),
-                                P<uint32_t>(ctx->ivals_b), &ctx->d_ctr->n_inst, ctx->cap, ceil_log2((uint32_t)ntiles),
-                                P<uint32_t>(ctx->hist), st);
-    const uint32_t* ik = cur2 ? P<uint32_t>(ctx->ikeys_b) : P<uint32_t>(ctx->ikeys_a);
-    const uint32_t* iv = cur2 ? P<uint32_t>(ctx->ivals_b) : P<uint32_t>(ctx->ivals_a);
-    tile_ranges(ik, &ctx->d_ctr->n_inst, ctx->cap, P<uint2>(ctx->ranges), ntiles, st);
+    int cur2 = radix_sort_pairs(P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), P<uint32_t>(b.ikeys_b),
+                                P<uint32_t>(b.ivals_b), n_inst, ctx->cap, ceil_log2((uint32_t)ntiles),
+                                P<uint32_t>(b.hist), ctx->sort_blocks, st);
+    const uint32_t* ik = cur2 ? P<uint32_t>(b.ikeys_b) : P<uint32_t>(b.ikeys_a);
+    const uint32_t* iv = cur2 ? P<uint32_t>(b.ivals_b) : P<uint32_t>(b.ivals_a);
+    tile_ranges(ik, n_inst, ctx->cap, P<uint2>(b.ranges), ntiles, st);
     return iv;
 }
 
@@ -241,11 +262,13 @@ csgs_status grow_capacity(csgs_ctx* ctx) {
     if (c > 0xF0000000ull) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance count %llu exceeds the 32-bit index range", need);
     ctx->cap = (uint32_t)c;
     csgs_status r;
-    size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
-    if ((r = ensure(ctx, ctx->ikeys_a, ib))) return r;
-    if ((r = ensure(ctx, ctx->ikeys_b, ib))) return r;
-    if ((r = ensure(ctx, ctx->ivals_a, ib))) return r;
-    if ((r = ensure(ctx, ctx->ivals_b, ib))) return r;
+    const size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
+    for (BinSlot& b : ctx->slot) {
+        if ((r = ensure(ctx, b.ikeys_a, ib))) return r;
+        if ((r = ensure(ctx, b.ikeys_b, ib))) return r;
+        if ((r = ensure(ctx, b.ivals_a, ib))) return r;
+        if ((r = ensure(ctx, b.ivals_b, ib))) return r;
+    }
     return CSGS_OK;
 }
 
@@ -298,6 +321,20 @@ csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
         csgs_destroy(ctx);
         return CSGS_E_NOMEM;
     }
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    for (BinSlot& b : ctx->slot) {
+        if (cudaStreamCreateWithPriority(&b.st, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.freed, cudaEventDisableTiming) != cudaSuccess) {
+            csgs_destroy(ctx);
+            return CSGS_E_CUDA;
+        }
+    }
+    if (cudaEventCreateWithFlags(&ctx->ev_proj, cudaEventDisableTiming) != cudaSuccess) {
+        csgs_destroy(ctx);
+        return CSGS_E_CUDA;
+    }
     cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->st);
     *out = ctx;
     return CSGS_OK;
@@ -316,9 +353,17 @@ void csgs_destroy(csgs_ctx* ctx) {
         cudaFree(s.sh);
         cudaFree(s.d_cams);
     }
-    DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,   &ctx->dkeys_b, &ctx->dvals_a, &ctx->dvals_b,
-                      &ctx->ikeys_a, &ctx->ikeys_b, &ctx->ivals_a, &ctx->ivals_b, &ctx->ranges,  &ctx->hist,
-                      &ctx->scan_tmp, &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
+    for (BinSlot& b : ctx->slot) {
+        DevBuf* sb[] = {&b.dkeys_b, &b.dvals_a, &b.dvals_b, &b.ikeys_a, &b.ikeys_b,
+                        &b.ivals_a, &b.ivals_b, &b.ranges,  &b.hist,    &b.scan_tmp};
+        for (DevBuf* x : sb) release(*x);
+        if (b.st) cudaStreamDestroy(b.st);
+        if (b.ready) cudaEventDestroy(b.ready);
+        if (b.freed) cudaEventDestroy(b.freed);
+    }
+    if (ctx->ev_proj) cudaEventDestroy(ctx->ev_proj);
+    DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,
+                      &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
                       &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
@@ -331,6 +376,7 @@ void csgs_destroy(csgs_ctx* ctx) {
     if (ctx->h_S) cudaFreeHost(ctx->h_S);
     if (ctx->h_u32) cudaFreeHost(ctx->h_u32);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->own_stream && ctx->st) cudaStreamDestroy(ctx->st);
@@ -464,24 +510,24 @@ struct PhaseTimer {
     bool on;
     size_t used = 0;
     std::vector<std::pair<int, std::pair<size_t, size_t>>> spans;  // phase, (start, end) event index
-    cudaEvent_t mark() {
+    cudaEvent_t mark(cudaStream_t st) {
         if (used == ctx->evpool.size()) {
             cudaEvent_t e;
             cudaEventCreate(&e);
             ctx->evpool.push_back(e);
         }
         cudaEvent_t e = ctx->evpool[used++];
-        cudaEventRecord(e, ctx->st);
+        cudaEventRecord(e, st);
         return e;
     }
-    size_t begin() {
+    size_t begin(cudaStream_t st) {
         if (!on) return 0;
-        mark();
+        mark(st);
         return used - 1;
     }
-    void end(int phase, size_t b) {
+    void end(int phase, size_t b, cudaStream_t st) {
         if (!on) return;
-        mark();
+        mark(st);
         spans.push_back({phase, {b, used - 1}});
     }
     void sum(double* ms3) {
@@ -507,6 +553,107 @@ int auto_view_batch(int64_t n, int nv, int req) {
 
 extern "C" {
 
+}  // extern "C"
+
+namespace {
+
+// Enqueue the scoring of views [v0, v1) of one scene: no host synchronisation and no
+// allocation (buffers must be sized), so it can be captured.  Projection and
+// compositing run on the context's stream; the binning of view k runs on the stream of
+// slot k % 2, after the projection of its batch and after the compositing that last
+// read the slot, so that it overlaps the compositing of view k - 1.  Every slot stream
+// ends in an event the context's stream waits on (the capture joins them).
+csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int vb, int v0_all, int v1_all,
+                                int stats, float* s_dev, double* S_dev, PhaseTimer& pt, long long& comp_launches) {
+    const int64_t n = s->n;
+    cudaStream_t st = ctx->st;
+    csgs_status r;
+    const SceneDev sd = scene_dev(*s);
+    set_u64(ctx->d_nconst, (unsigned long long)n, st);
+    CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
+    if (ko.resolution == CSGS_RES_SCENE) CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA, 0, sizeof(double), st));
+    if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
+    bool freed_recorded[2] = {false, false};
+    int view = 0;
+    for (int v0 = v0_all; v0 < v1_all; v0 += vb) {
+        const int nb = (v1_all - v0) < vb ? (v1_all - v0) : vb;
+        size_t e0 = pt.begin(st);
+        launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
+                       P<uint2>(ctx->rects), st);
+        pt.end(0, e0, st);
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_proj, st));
+        for (int k = 0; k < nb; ++k, ++view) {
+            const CamDev& cam = s->cams[v0 + k];
+            const int sl = view & 1;
+            BinSlot& slot = ctx->slot[sl];
+            uint32_t* keys_v = P<uint32_t>(ctx->keys) + (size_t)k * n;
+            const uint2* rects_v = P<uint2>(ctx->rects) + (size_t)k * n;
+            CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, ctx->ev_proj, 0));
+            if (freed_recorded[sl]) CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, slot.freed, 0));
+            size_t e1 = pt.begin(slot.st);
+            const uint32_t* iv = bin_view(ctx, sl, n, keys_v, rects_v, cam, slot.st);
+            pt.end(1, e1, slot.st);
+            CUDA_TRY(ctx, cudaEventRecord(slot.ready, slot.st));
+            CUDA_TRY(ctx, cudaStreamWaitEvent(st, slot.ready, 0));
+            CompositeArgs a{};
+            a.ranges = P<uint2>(slot.ranges);
+            a.inst_gid = iv;
+            a.splats = P<Splat>(ctx->splats) + (size_t)k * n;
+            a.n_gauss = (int)n;
+            a.cam = cam;
+            a.o = ko;
+            a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
+            a.s_sum = ko.resolution == CSGS_RES_IMAGE ? P<float>(ctx->vbuf) : s_dev;
+            a.tile_sum = P<float>(ctx->tsum);
+            a.ctr = ctx->d_ctr;
+            a.stats = stats & 1;
+            if (ko.resolution == CSGS_RES_IMAGE)
+                CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
+            size_t e2 = pt.begin(st);
+            launch_composite_score(a, st);
+            if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
+            pt.end(2, e2, st);
+            CUDA_TRY(ctx, cudaEventRecord(slot.freed, st));
+            freed_recorded[sl] = true;
+            ++comp_launches;
+        }
+        if ((r = launch_check(ctx, "score kernels"))) return r;
+    }
+    if (ko.resolution == CSGS_RES_SCENE) scene_normalise(s_dev, n, &ctx->d_ctr->sumA, st);
+    sum_scores(s_dev, n, P<double>(ctx->partial), S_dev, st);
+    return launch_check(ctx, "score reduction");
+}
+
+// Size every buffer the scoring of these scenes needs.
+csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns, const KOpts& ko) {
+    csgs_status r;
+    int64_t nmax = 0;
+    int vbmax = 1, tiles = 0;
+    for (int k = 0; k < ns; ++k) {
+        if ((r = upload_cams(ctx, sc[k], ko))) return r;
+        if (sc[k]->n > nmax) nmax = sc[k]->n;
+        if (vb[k] > vbmax) vbmax = vb[k];
+        for (auto& c : sc[k]->cams)
+            if (c.tiles_x * c.tiles_y > tiles) tiles = c.tiles_x * c.tiles_y;
+    }
+    if ((r = ensure_view_buffers(ctx, nmax, vbmax, tiles))) return r;
+    if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
+    if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * (ns + 1)))) return r;
+    if (ko.resolution == CSGS_RES_IMAGE && (r = ensure(ctx, ctx->vbuf, sizeof(float) * (size_t)nmax))) return r;
+    if (ko.resolution == CSGS_RES_TILE && (r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap))) return r;
+    return CSGS_OK;
+}
+
+int scene_view_batch(const SceneRec* s, const csgs_score_opts* opts) {
+    if (opts->view_batch > 0) return opts->view_batch < (int)s->cams.size() ? opts->view_batch : (int)s->cams.size();
+    if (s->tuned_vb > 0) return s->tuned_vb < (int)s->cams.size() ? s->tuned_vb : (int)s->cams.size();
+    return auto_view_batch(s->n, (int)s->cams.size(), 0);
+}
+
+}  // namespace
+
+extern "C" {
+
 csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* s_dev, double* S_out) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
@@ -517,21 +664,11 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     csgs_status r;
     if ((r = make_kopts(ctx, opts, &ko))) return r;
     cudaSetDevice(ctx->device);
-    if ((r = upload_cams(ctx, s, ko))) return r;
-    const int64_t n = s->n;
     const int nv = (int)s->cams.size();
-    const int vb = auto_view_batch(n, nv, opts->view_batch);
-    int max_tiles = 0;
+    const int vb = scene_view_batch(s, opts);
+    if ((r = prepare_scoring(ctx, &s, &vb, 1, ko))) return r;
     int64_t rays = 0;
-    for (auto& c : s->cams) {
-        if (c.tiles_x * c.tiles_y > max_tiles) max_tiles = c.tiles_x * c.tiles_y;
-        rays += (int64_t)c.W * c.H;
-    }
-    if ((r = ensure_view_buffers(ctx, n, vb, max_tiles))) return r;
-    if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
-    if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * 2))) return r;
-    if (ko.resolution == CSGS_RES_IMAGE && (r = ensure(ctx, ctx->vbuf, sizeof(float) * (size_t)n))) return r;
-    const SceneDev sd = scene_dev(*s);
+    for (auto& c : s->cams) rays += (int64_t)c.W * c.H;
     cudaStream_t st = ctx->st;
     int retries = 0;
     const long long l0 = launches();
@@ -543,53 +680,16 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
         comp_launches = 0;
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
-        set_u64(ctx->d_nconst, (unsigned long long)n, st);
-        CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
-        if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
-        if (ko.resolution == CSGS_RES_TILE && (r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap))) return r;
-        for (int v0 = 0; v0 < nv; v0 += vb) {
-            const int nb = (nv - v0) < vb ? (nv - v0) : vb;
-            size_t e0 = pt.begin();
-            launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
-                           P<uint2>(ctx->rects), st);
-            pt.end(0, e0);
-            for (int k = 0; k < nb; ++k) {
-                const CamDev& cam = s->cams[v0 + k];
-                uint32_t* keys_v = P<uint32_t>(ctx->keys) + (size_t)k * n;
-                const uint2* rects_v = P<uint2>(ctx->rects) + (size_t)k * n;
-                size_t e1 = pt.begin();
-                const uint32_t* iv = bin_view(ctx, n, keys_v, rects_v, cam);
-                pt.end(1, e1);
-                CompositeArgs a{};
-                a.ranges = P<uint2>(ctx->ranges);
-                a.inst_gid = iv;
-                a.splats = P<Splat>(ctx->splats) + (size_t)k * n;
-                a.n_gauss = (int)n;
-                a.cam = cam;
-                a.o = ko;
-                a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
-                a.s_sum = ko.resolution == CSGS_RES_IMAGE ? P<float>(ctx->vbuf) : s_dev;
-                a.tile_sum = P<float>(ctx->tsum);
-                a.ctr = ctx->d_ctr;
-                a.stats = opts->collect_stats & 1;
-                if (ko.resolution == CSGS_RES_IMAGE)
-                    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
-                size_t e2 = pt.begin();
-                launch_composite_score(a, st);
-                if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
-                pt.end(2, e2);
-                ++comp_launches;
-            }
-            if ((r = launch_check(ctx, "score kernels"))) return r;
-        }
-        if (ko.resolution == CSGS_RES_SCENE) scene_normalise(s_dev, n, &ctx->d_ctr->sumA, st);
-        sum_scores(s_dev, n, P<double>(ctx->partial), P<double>(ctx->Sdev), st);
+        if ((r = enqueue_scene_score(ctx, s, ko, vb, 0, nv, opts->collect_stats, s_dev, P<double>(ctx->Sdev), pt,
+                                     comp_launches)))
+            return r;
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         if ((r = read_counters(ctx))) return r;
         if (ctx->h_ctr->err & kErrCapacity) {
             if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
             if ((r = grow_capacity(ctx))) return r;
+            if ((r = prepare_scoring(ctx, &s, &vb, 1, ko))) return r;
             continue;
         }
         break;
@@ -619,6 +719,176 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     const double S = ctx->h_S[0];
     if (S_out) *S_out = S;
     if (!(S > 0.0)) return fail(ctx, CSGS_E_EMPTY, "every query has A = 0: total sensitivity is zero");
+    return CSGS_OK;
+}
+
+csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* scene_ids, const csgs_score_opts* opts,
+                             float* const* s_devs, double* S_out, int32_t use_graph) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (n_scenes <= 0 || n_scenes > 64 || !scene_ids || !s_devs || !S_out)
+        return fail(ctx, CSGS_E_INVAL, "bad batch arguments");
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    std::vector<SceneRec*> sc(n_scenes);
+    std::vector<int> vb(n_scenes);
+    int64_t rays = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        sc[k] = get_scene(ctx, scene_ids[k]);
+        if (!sc[k] || sc[k]->cams.empty() || !s_devs[k]) return fail(ctx, CSGS_E_INVAL, "bad scene %d in batch", k);
+        vb[k] = scene_view_batch(sc[k], opts);
+        for (auto& c : sc[k]->cams) rays += (int64_t)c.W * c.H;
+    }
+    if ((r = prepare_scoring(ctx, sc.data(), vb.data(), n_scenes, ko))) return r;
+    cudaStream_t st = ctx->st;
+    // identity of the captured work: scenes, their sizes and views, outputs, options, buffers
+    std::string key((const char*)opts, sizeof(*opts));
+    key.append((const char*)scene_ids, sizeof(int32_t) * n_scenes);
+    key.append((const char*)s_devs, sizeof(float*) * n_scenes);
+    // (the launches bake in the scene pointers, the host copies of the cameras and every
+    // work-buffer address, so all of them are part of the key)
+    for (int k = 0; k < n_scenes; ++k) {
+        const int64_t meta[3] = {(int64_t)sc[k]->cams.size(), vb[k], (int64_t)(uintptr_t)sc[k]->d_cams};
+        key.append((const char*)meta, sizeof(meta));
+        const SceneDev sd = scene_dev(*sc[k]);
+        key.append((const char*)&sd, sizeof(sd));
+        key.append((const char*)sc[k]->cams.data(), sizeof(CamDev) * sc[k]->cams.size());
+    }
+    PhaseTimer off{ctx, false};
+    long long cl = 0;
+    const long long l0 = launches();
+    float ms = 0.f;
+    long long replayed = 0;
+    for (int attempt = 0;; ++attempt) {
+        const int64_t bmeta[3] = {(int64_t)ctx->cap, ctx->sort_blocks, (int64_t)ctx->buf_gen};
+        const std::string full_key = key + std::string((const char*)bmeta, sizeof(bmeta));
+        const bool replay = use_graph && ctx->graph_exec && ctx->graph_key == full_key;
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
+        if (replay) {
+            CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph_exec, st));
+            replayed += ctx->graph_nodes_launches;
+        } else if (use_graph && attempt > 0) {
+            // capture the whole batch (every launch and memset of every scene) once
+            if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+            cudaGraph_t g = nullptr;
+            const long long lc0 = launches();
+            CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            csgs_status er = CSGS_OK;
+            cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st);
+            for (int k = 0; k < n_scenes && !er; ++k)
+                er = enqueue_scene_score(ctx, sc[k], ko, vb[k], 0, (int)sc[k]->cams.size(), 0, s_devs[k],
+                                         P<double>(ctx->Sdev) + k, off, cl);
+            cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (er) {
+                if (g) cudaGraphDestroy(g);
+                return er;
+            }
+            if (ce != cudaSuccess) return fail(ctx, CSGS_E_CUDA, "stream capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return fail(ctx, CSGS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            ctx->graph_key = full_key;
+            ctx->graph_nodes_launches = launches() - lc0;
+            CUDA_TRY(ctx, cudaGraphLaunch(ctx->graph_exec, st));
+        } else {
+            // eager pass: settles the instance capacity before a capture
+            CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
+            for (int k = 0; k < n_scenes; ++k)
+                if ((r = enqueue_scene_score(ctx, sc[k], ko, vb[k], 0, (int)sc[k]->cams.size(), 0, s_devs[k],
+                                             P<double>(ctx->Sdev) + k, off, cl)))
+                    return r;
+        }
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if ((r = read_counters(ctx))) return r;
+        if (ctx->h_ctr->err & kErrCapacity) {
+            if (attempt > 4) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+            if ((r = grow_capacity(ctx))) return r;
+            if ((r = prepare_scoring(ctx, sc.data(), vb.data(), n_scenes, ko))) return r;
+            ctx->graph_key.clear();
+            continue;
+        }
+        if (use_graph && !replay && attempt == 0) continue;  // now capture
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        break;
+    }
+    CUDA_TRY(ctx, cudaMemcpy(S_out, ctx->Sdev.p, sizeof(double) * n_scenes, cudaMemcpyDeviceToHost));
+    memset(&ctx->stats, 0, sizeof(ctx->stats));
+    int64_t views = 0;
+    for (int k = 0; k < n_scenes; ++k) views += (int64_t)sc[k]->cams.size();
+    ctx->stats.views = views;
+    ctx->stats.rays = rays;
+    ctx->stats.instances = (int64_t)ctx->h_ctr->inst_total;
+    ctx->stats.score_ms = ms;
+    ctx->stats.kernel_launches = launches() - l0 + replayed;
+    ctx->stats.queries = (int64_t)ctx->h_ctr->queries;
+    return CSGS_OK;
+}
+
+csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,
+                          int32_t* view_batch_out, int32_t* sort_blocks_out) {
+    if (!ctx) return CSGS_E_INVAL;
+    SceneRec* s = get_scene(ctx, scene_id);
+    if (!s || s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    KOpts ko;
+    csgs_status r;
+    if ((r = make_kopts(ctx, opts, &ko))) return r;
+    cudaSetDevice(ctx->device);
+    const int nv = (int)s->cams.size();
+    const int pv = probe_views > 0 && probe_views < nv ? probe_views : (nv < 16 ? nv : 16);
+    const int vbs[5] = {1, 2, 4, 8, 16};
+    const int gs[4] = {148 * 2, 148 * 4, 148 * 8, 148 * 12};
+    float* s_tmp = nullptr;
+    CUDA_TRY(ctx, cudaMalloc(&s_tmp, sizeof(float) * (size_t)s->n));
+    std::unique_ptr<float, cudaError_t (*)(void*)> s_tmp_owner(s_tmp, cudaFree);
+    float best = 1e30f;
+    int best_vb = auto_view_batch(s->n, nv, 0), best_g = ctx->sort_blocks;
+    PhaseTimer off{ctx, false};
+    long long cl = 0;
+    int grows = 0;
+    for (int vb : vbs) {
+        if (vb > pv) continue;
+        if ((int64_t)vb * s->n * (int64_t)(sizeof(Splat) + 12) > ((int64_t)4 << 30)) continue;
+        for (int g : gs) {
+            ctx->sort_blocks = g;
+            if ((r = prepare_scoring(ctx, &s, &vb, 1, ko))) break;
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up (and settles capacity)
+                CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->st));
+                CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->st));
+                if ((r = enqueue_scene_score(ctx, s, ko, vb, 0, pv, 0, s_tmp, P<double>(ctx->Sdev), off, cl))) break;
+                CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->st));
+                if ((r = read_counters(ctx))) break;
+                if (ctx->h_ctr->err & kErrCapacity) {
+                    if (++grows > 4) {
+                        r = fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+                        break;
+                    }
+                    if ((r = grow_capacity(ctx)) || (r = prepare_scoring(ctx, &s, &vb, 1, ko))) break;
+                    --rep;
+                    continue;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                if (rep > 0 && ms < t) t = ms;
+            }
+            if (r) break;
+            if (t < best) {
+                best = t;
+                best_vb = vb;
+                best_g = g;
+            }
+        }
+        if (r) break;
+    }
+    if (r) return r;
+    ctx->sort_blocks = best_g;
+    s->tuned_vb = best_vb;
+    ctx->graph_key.clear();
+    if (view_batch_out) *view_batch_out = best_vb;
+    if (sort_blocks_out) *sort_blocks_out = best_g;
     return CSGS_OK;
 }
 
@@ -713,9 +983,9 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
         }
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
                        P<uint2>(ctx->rects), st);
-        const uint32_t* iv = bin_view(ctx, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam, st);
         CompositeArgs a{};
-        a.ranges = P<uint2>(ctx->ranges);
+        a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
         a.splats = P<Splat>(ctx->splats);
         a.n_gauss = (int)n;
@@ -805,9 +1075,9 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
                        P<uint2>(ctx->rects), st);
-        const uint32_t* iv = bin_view(ctx, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam, st);
         CompositeArgs a{};
-        a.ranges = P<uint2>(ctx->ranges);
+        a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
         a.splats = P<Splat>(ctx->splats);
         a.n_gauss = (int)n;
@@ -1115,9 +1385,9 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
         }
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
                        P<uint2>(ctx->rects), st);
-        const uint32_t* iv = bin_view(ctx, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam, st);
         CompositeArgs a{};
-        a.ranges = P<uint2>(ctx->ranges);
+        a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
         a.splats = P<Splat>(ctx->splats);
         a.n_gauss = (int)n;

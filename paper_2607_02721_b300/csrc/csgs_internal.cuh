@@ -72,7 +72,7 @@ enum : uint32_t { kErrCapacity = 1u, kErrNonFinite = 2u, kErrIndex = 4u };
 struct DevCounters {
     uint32_t err;
     uint32_t pad;
-    unsigned long long n_inst;      // instances of the current view (may exceed capacity)
+    unsigned long long n_inst[2];   // instances of the view in each binning slot (may exceed capacity)
     unsigned long long max_inst;    // maximum over views
     unsigned long long inst_total;  // sum over views
     unsigned long long pairs_eval;
@@ -102,17 +102,18 @@ void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* w
                      cudaStream_t st);
 
 // ---- sorting and scans (k_sort.cu)
-constexpr int kSortBlocks = 148 * 4;
-constexpr int kSortHistWords = 256 * kSortBlocks + 256;  // per-block digit counts + digit totals
+constexpr int kSortBlocks = 148 * 4;       // default radix-sort grid (the autotuner may pick another)
+constexpr int kSortMaxBlocks = 2048;
+constexpr int kSortHistWords = 256 * kSortMaxBlocks + 256;  // per-block digit counts + digit totals
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  n is read from
 // d_n (device) and clamped to n_max.  Returns which buffer holds the result (0: a, 1: b).
 int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, uint32_t* hist, cudaStream_t st);
+                     uint32_t n_max, int bits, uint32_t* hist, int G, cudaStream_t st);
 // Gaussians in depth order -> (tile, gid) instances in depth order; writes the
 // instance count to ctr->n_inst.  scan_tmp: >= ceil(n / 256) + 64 words.
-void emit_instances(const uint32_t* order, const uint32_t* sorted_keys, const uint2* rects, int n, int tiles_x,
+void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x,
                     uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
-                    cudaStream_t st);
+                    unsigned long long* n_inst, cudaStream_t st);
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
                  cudaStream_t st);
 void iota_u32(uint32_t* v, int n, cudaStream_t st);

@@ -91,22 +91,38 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
     sh.C[tid] = make_float4(c.x, c.y, c.z, a.o.ow0 * c.x * c.x + a.o.ow1 * c.y * c.y + a.o.ow2 * c.z * c.z);
     sh.gid[tid] = g;
     if (MODE == kTransfer) sh.wsel[tid] = __ldg(a.wsel + g);
-    // bounding box of the footprint: rx^2 = qcut (1/s1^2 + (s1k/(s1 s2))^2), ry^2 = qcut / s2^2,
-    // widened so that FP32 rounding never drops a pixel that passes the test
+    // Warp-block mask.  The test p >= thr is the ellipse e1^2 + e2^2 <= R with R =
+    // log2 alpha - thr (the 3-sigma cut and the alpha_min skip in one), e1 = s1 u + s1k v,
+    // e2 = s2 v, (u, v) = pixel - mean.  For each 4-row band of warp blocks, take the
+    // exact x-extent of the ellipse over the band's v-interval: the right end
+    // (sqrt(R - (s2 v)^2) - s1k v) / s1 is concave in v with its maximum at
+    // v* = -s1k sqrt(R) / (s2 sqrt(s1k^2 + s2^2)) (the left end mirrors it at -v*), so
+    // clamping v* to the interval gives the band's extreme.  R and every bound are
+    // padded so that FP32 rounding never drops a pixel that passes the test.
+    const float R = fmaf(fmaxf(c.w - q.w, 0.f), 1.002f, 1e-5f);
+    const float sR = sqrtf(R);
     const float i1 = 1.f / s1, i2 = 1.f / s2;
-    const float kk = s1k * i1 * i2;
-    const float rx = sqrtf(a.o.qcut * (i1 * i1 + kk * kk)) * 1.001f + 0.01f;
-    const float ry = sqrtf(a.o.qcut) * i2 * 1.001f + 0.01f;
-    const float xlo = mx - rx, xhi = mx + rx, ylo = my - ry, yhi = my + ry;
-    uint32_t cols = 0u, rows = 0u;
-    cols |= (xlo <= -0.5f && xhi >= -7.5f) ? 1u : 0u;
-    cols |= (xlo <= 7.5f && xhi >= 0.5f) ? 2u : 0u;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) rows |= (ylo <= -4.5f + 4.f * r && yhi >= -7.5f + 4.f * r) ? (1u << r) : 0u;
+    const float vmax = sR * i2 * 1.001f + 0.01f;
+    const float vstar = -s1k * sR * i2 / sqrtf(fmaf(s1k, s1k, s2 * s2));
     uint32_t mk = 0u;
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-        if (rows & (1u << r)) mk |= cols << (2 * r);
+    for (int r = 0; r < 4; ++r) {
+        const float va = fmaxf(-7.52f + 4.f * r - my, -vmax);
+        const float vb = fminf(-4.48f + 4.f * r - my, vmax);
+        if (!(va <= vb)) continue;
+        const float vr = fminf(fmaxf(vstar, va), vb);
+        const float vl = fminf(fmaxf(-vstar, va), vb);
+        const float er = s2 * vr, el = s2 * vl;
+        const float wr = sqrtf(fmaxf(fmaf(-er, er, R), 0.f));
+        const float wl = sqrtf(fmaxf(fmaf(-el, el, R), 0.f));
+        const float xr = mx + (wr - s1k * vr) * i1;
+        const float xl = mx - (wl + s1k * vl) * i1;
+        const float pad = 0.02f + 1e-3f * (wr + wl) * i1;
+        uint32_t cols = 0u;
+        cols |= (xl - pad <= -0.5f && xr + pad >= -7.5f) ? 1u : 0u;
+        cols |= (xl - pad <= 7.5f && xr + pad >= 0.5f) ? 2u : 0u;
+        mk |= cols << (2 * r);
+    }
     sh.msk[tid] = mk;
 }
 

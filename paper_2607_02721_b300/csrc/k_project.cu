@@ -112,10 +112,12 @@ __device__ __forceinline__ void project_one(const float mu[3], const float cov3[
     const ff::F2 mx = ff::persp(c.fx, X, Z, c.cx);
     const ff::F2 my = ff::persp(c.fy, Yc, Z, c.cy);
 
-    // pixel bounding box of the ellipse d^T cov^-1 d <= cut2 (|dx| <= sqrt(cut2 cov_xx)),
-    // widened slightly so FP32 rounding can never exclude a pixel that passes
-    const float rx = sqrtf(o.cut2 * ca) * 1.001f + 0.01f;
-    const float ry = sqrtf(o.cut2 * cc) * 1.001f + 0.01f;
+    // pixel bounding box of the ellipse d^T cov^-1 d <= m (|dx| <= sqrt(m cov_xx)), where
+    // m = min(cut2, 2 ln(alpha / alpha_min)) also applies the alpha_min skip (alpha k <
+    // alpha_min outside it); widened so FP32 rounding can never exclude a pixel that passes
+    const float m_eff = fminf(o.cut2, fmaf(2.f / kLog2e, log2f(op) - o.l2amin, 1e-4f));
+    const float rx = sqrtf(m_eff * ca) * 1.001f + 0.01f;
+    const float ry = sqrtf(m_eff * cc) * 1.001f + 0.01f;
     float fx0 = ceilf(mx.hi - rx), fx1 = floorf(mx.hi + rx);
     float fy0 = ceilf(my.hi - ry), fy1 = floorf(my.hi + ry);
     fx0 = fmaxf(fx0, 0.f);

@@ -17,8 +17,10 @@ constexpr int kSortGroups = 8;                               // 32-key groups pe
 constexpr int kSubTile = kSortThreads * kSortGroups;          // 2048 keys
 constexpr int kScanThreads = 256;
 
+// chunk of the key array handled by block b of a grid of G blocks (multiples of sub-tiles)
 __device__ __forceinline__ void sort_chunk(uint32_t n, int b, uint32_t& begin, uint32_t& end) {
-    uint32_t per = (n + kSortBlocks - 1) / kSortBlocks;
+    const uint32_t G = gridDim.x;
+    uint32_t per = (n + G - 1) / G;
     per = (per + kSubTile - 1) / kSubTile * kSubTile;
     if (per < kSubTile) per = kSubTile;
     uint64_t bg = (uint64_t)per * b;
@@ -42,27 +44,37 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
     uint32_t begin, end;
     sort_chunk(n, blockIdx.x, begin, end);
     const int lane = threadIdx.x & 31;
-    for (uint32_t base = begin; base < end; base += kSortThreads) {
-        uint32_t i = base + threadIdx.x;
-        uint32_t d = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+    // a chunk is a whole number of 2048-key sub-tiles: 8 coalesced loads in flight per thread
+    for (uint32_t base = begin; base < end; base += kSubTile) {
+        uint32_t d[kSortGroups];
+#pragma unroll
+        for (int g = 0; g < kSortGroups; ++g) {
+            const uint32_t i = base + g * kSortThreads + threadIdx.x;
+            d[g] = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
+        }
+#pragma unroll
+        for (int g = 0; g < kSortGroups; ++g) {
+            const uint32_t peers = __match_any_sync(0xffffffffu, d[g]);
+            if (d[g] < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d[g]], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
-    hist[threadIdx.x * kSortBlocks + blockIdx.x] = cnt[threadIdx.x];
+    hist[threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of each digit's row of the histogram (kSortBlocks per-block counts),
-// one CTA per digit; the row totals go to row_total[256].
-__global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist, uint32_t* __restrict__ row_total) {
-    constexpr int per = (kSortBlocks + 255) / 256;
+// Exclusive scan of each digit's row of the histogram (G per-block counts, G <=
+// kSortMaxBlocks), one CTA per digit; the row totals go to row_total[256].
+__global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist, uint32_t* __restrict__ row_total,
+                                                    int G) {
+    constexpr int kPer = (kSortMaxBlocks + 255) / 256;
     __shared__ uint32_t ws[8];
-    uint32_t* row = hist + (size_t)blockIdx.x * kSortBlocks;
+    const int per = (G + 255) / 256;
+    uint32_t* row = hist + (size_t)blockIdx.x * G;
     const int b0 = threadIdx.x * per;
-    uint32_t v[per], sum = 0;
+    uint32_t v[kPer], sum = 0;
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-        v[k] = b0 + k < kSortBlocks ? row[b0 + k] : 0u;
+    for (int k = 0; k < kPer; ++k) {
+        v[k] = (k < per && b0 + k < G) ? row[b0 + k] : 0u;
         sum += v[k];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -77,8 +89,8 @@ __global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist,
     uint32_t pre = x - sum;
     for (int w = 0; w < warp; ++w) pre += ws[w];
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-        if (b0 + k < kSortBlocks) row[b0 + k] = pre;
+    for (int k = 0; k < kPer; ++k) {
+        if (k < per && b0 + k < G) row[b0 + k] = pre;
         pre += v[k];
     }
     if (threadIdx.x == 255) row_total[blockIdx.x] = pre;
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
         __syncthreads();
         uint32_t pre = x - t;
         for (int w = 0; w < warp; ++w) pre += ws[w];
-        gbase[tid] = pre + hist[tid * kSortBlocks + blockIdx.x];
+        gbase[tid] = pre + hist[tid * gridDim.x + blockIdx.x];
     }
     for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
     __syncthreads();
@@ -236,7 +248,8 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __
 }
 
 // Exclusive scan of the per-block totals in one CTA (any count), plus the grand total.
-__global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ partial, int nb, DevCounters* ctr) {
+__global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ partial, int nb, DevCounters* ctr,
+                                                       unsigned long long* n_inst) {
     __shared__ uint32_t ws[32];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
@@ -253,10 +266,11 @@ __global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ pa
         __syncthreads();
     }
     if (threadIdx.x == 0 && ctr) {
+        // the other binning slot may update the totals concurrently
         unsigned long long t = carry;
-        ctr->n_inst = t;
-        ctr->inst_total += t;
-        if (t > ctr->max_inst) ctr->max_inst = t;
+        *n_inst = t;
+        atomicAdd(&ctr->inst_total, t);
+        atomicMax(&ctr->max_inst, t);
     }
 }
 
@@ -332,32 +346,32 @@ __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v;
 }  // namespace
 
 int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, uint32_t* hist, cudaStream_t st) {
+                     uint32_t n_max, int bits, uint32_t* hist, int G, cudaStream_t st) {
+    if (G < 1) G = 1;
+    if (G > kSortMaxBlocks) G = kSortMaxBlocks;
     int cur = 0;
     for (int shift = 0; shift < bits; shift += 8) {
         uint32_t* kin = cur ? kb : ka;
         uint32_t* vin = cur ? vb : va;
         uint32_t* kout = cur ? ka : kb;
         uint32_t* vout = cur ? va : vb;
-        k_rs_hist<<<kSortBlocks, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
+        k_rs_hist<<<G, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
         count_launches(1);
-        k_rs_rowscan<<<256, 256, 0, st>>>(hist, hist + 256 * kSortBlocks);
+        k_rs_rowscan<<<256, 256, 0, st>>>(hist, hist + 256 * G, G);
         count_launches(1);
-        k_rs_scatter<<<kSortBlocks, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist,
-                                                           hist + 256 * kSortBlocks);
+        k_rs_scatter<<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, hist + 256 * G);
         count_launches(1);
         cur ^= 1;
     }
     return cur;
 }
 
-void emit_instances(const uint32_t* order, const uint32_t* /*sorted_keys*/, const uint2* rects, int n, int tiles_x,
-                    uint32_t* ikeys, uint32_t* ivals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
-                    cudaStream_t st) {
+void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x, uint32_t* ikeys, uint32_t* ivals,
+                    uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr, unsigned long long* n_inst, cudaStream_t st) {
     const int nb = (n + kScanThreads - 1) / kScanThreads;
     k_emit_reduce<<<nb, kScanThreads, 0, st>>>(order, rects, n, scan_tmp);
     count_launches(1);
-    k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nb, ctr);
+    k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nb, ctr, n_inst);
     count_launches(1);
     k_emit_down<<<nb, kScanThreads, 0, st>>>(order, rects, n, tiles_x, scan_tmp, ikeys, ivals, cap, ctr);
     count_launches(1);
@@ -373,8 +387,14 @@ void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n
     count_launches(1);
 }
 
-void iota_u32(uint32_t* v, int n, cudaStream_t st) { k_iota<<<(n + 255) / 256, 256, 0, st>>>(v, n); }
+void iota_u32(uint32_t* v, int n, cudaStream_t st) {
+    k_iota<<<(n + 255) / 256, 256, 0, st>>>(v, n);
+    count_launches(1);
+}
 
-void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) { k_set_u64<<<1, 1, 0, st>>>(p, v); }
+void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st) {
+    k_set_u64<<<1, 1, 0, st>>>(p, v);
+    count_launches(1);
+}
 
 }  // namespace csgs

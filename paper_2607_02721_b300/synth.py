@@ -215,3 +215,16 @@ def workload_scene_3m(seed: int = 0, n_views: int = 200, width: int = 1600, heig
                       n: int = 3_000_000):
     """3M Gaussians from a 256-component mixture (SH degree 3), 200 views 1600x1040."""
     return mixture_scene(n, 256, 3, seed), hemisphere_cameras(n_views, width, height, seed=seed)
+
+
+# (Gaussians, views, width, height) of the six scenes of the batched workload
+BATCH6 = ((50_000, 32, 512, 512), (200_000, 64, 800, 600), (500_000, 100, 800, 800),
+          (1_000_000, 100, 1024, 768), (2_000_000, 150, 1280, 960), (3_000_000, 200, 1600, 1040))
+
+
+def workload_batch6(seed: int = 0):
+    """Six scenes of uneven size (50k to 3M Gaussians, 64-component mixtures with SH
+    degree 3), each with its own hemisphere of 32-200 views at 512x512 to 1600x1040
+    (about 7.0e8 pixel-rays in all).  Returns [(scene, cams)]."""
+    return [(mixture_scene(n, 64, 3, seed + k), hemisphere_cameras(v, W, H, seed=seed + k))
+            for k, (n, v, W, H) in enumerate(BATCH6)]

@@ -1,0 +1,118 @@
+"""Multi-scene scoring in one submission (eager, captured as a CUDA graph, replayed)
+and the view-batch / sort-grid autotuner: every path returns the scores csgs_score
+returns scene by scene."""
+import numpy as np
+import pytest
+
+import paper_2607_02721_b300 as csgs
+from paper_2607_02721_b300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx(torch):
+    build.build()
+    c = csgs.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def scenes(ctx):
+    """Three scenes of uneven size, each with its own views (count and resolution)."""
+    spec = [(3000, 5, 96, 80, 1), (12000, 9, 128, 128, 2), (6000, 3, 200, 120, 3)]
+    sids = []
+    for n, v, W, H, seed in spec:
+        sc = synth.mixture_scene(n, 16, 3, seed, half_extent=2.0)
+        cams = synth.hemisphere_cameras(v, W, H, radius=7.0, seed=seed)
+        sid = ctx.load_scene(sc)
+        ctx.set_queries(sid, cams)
+        sids.append(sid)
+    return sids
+
+
+def one_by_one(ctx, sids, opts):
+    out = [ctx.score(k, opts) for k in sids]
+    return [o[0].cpu().numpy() for o in out], [o[1] for o in out]
+
+
+def test_batch_matches_single_scene_scoring(ctx, scenes):
+    opts = csgs.default_opts()
+    ref_s, ref_S = one_by_one(ctx, scenes, opts)
+    for use_graph in (False, True):
+        s, S = ctx.score_batch(scenes, opts, use_graph=use_graph)
+        for k in range(len(scenes)):
+            # pixel resolution: a max of per-pixel values, so any schedule gives the same bits
+            np.testing.assert_array_equal(s[k].cpu().numpy(), ref_s[k])
+            assert S[k] == ref_S[k]
+
+
+def test_graph_replay_is_one_launch_and_repeats_results(ctx, scenes):
+    opts = csgs.default_opts()
+    outs, S0 = ctx.score_batch(scenes, opts, use_graph=True)  # eager pass + capture
+    first = [o.cpu().numpy().copy() for o in outs]
+    for o in outs:
+        o.zero_()
+    n0 = csgs.kernel_launch_count()
+    outs2, S1 = ctx.score_batch(scenes, opts, outs=outs, use_graph=True)  # replay
+    assert csgs.kernel_launch_count() == n0  # nothing launched one by one
+    st = ctx.stats()
+    assert st["kernel_launches"] > 3 * len(scenes)  # the graph's kernels
+    assert st["views"] == 5 + 9 + 3
+    for k in range(len(scenes)):
+        np.testing.assert_array_equal(outs2[k].cpu().numpy(), first[k])
+        assert S1[k] == S0[k]
+
+
+def test_graph_follows_scene_and_view_changes(ctx, scenes, torch):
+    """A replay reads the scene from device memory (in-place updates are seen); new
+    query views change the captured launches, so they force a new capture."""
+    opts = csgs.default_opts()
+    outs, _ = ctx.score_batch(scenes, opts, use_graph=True)
+    outs, _ = ctx.score_batch(scenes, opts, outs=outs, use_graph=True)
+    cams = synth.hemisphere_cameras(4, 112, 96, radius=6.5, seed=11)
+    ctx.set_queries(scenes[1], cams)
+    ref_s, ref_S = one_by_one(ctx, scenes, opts)
+    outs, S = ctx.score_batch(scenes, opts, outs=outs, use_graph=True)
+    for k in range(len(scenes)):
+        np.testing.assert_array_equal(outs[k].cpu().numpy(), ref_s[k])
+        assert S[k] == ref_S[k]
+
+
+def test_batch_scene_resolution(ctx, scenes):
+    """Per-scene resolution sums in FP32 atomics: same values up to summation order."""
+    opts = csgs.default_opts(resolution=csgs.RES_SCENE)
+    ref_s, ref_S = one_by_one(ctx, scenes, opts)
+    s, S = ctx.score_batch(scenes, opts, use_graph=True)
+    s, S = ctx.score_batch(scenes, opts, outs=s, use_graph=True)
+    for k in range(len(scenes)):
+        np.testing.assert_allclose(s[k].cpu().numpy(), ref_s[k], rtol=1e-4, atol=1e-9)
+        assert abs(S[k] - 1.0) < 1e-4
+
+
+def test_autotune_keeps_scores(ctx, scenes):
+    opts = csgs.default_opts()
+    ref, Sref = ctx.score(scenes[1], opts)
+    ref = ref.cpu().numpy()
+    vb, g = ctx.autotune(scenes[1], opts, probe_views=4)
+    assert vb in (1, 2, 4) and g in (296, 592, 1184, 1776)
+    s, S = ctx.score(scenes[1], opts)
+    np.testing.assert_array_equal(s.cpu().numpy(), ref)
+    assert S == Sref
+
+
+def test_batch_rejects_bad_arguments(ctx, scenes):
+    with pytest.raises(csgs.CsgsError):
+        ctx.score_batch([scenes[0], 12345])
+    with pytest.raises(csgs.CsgsError):
+        ctx.score_batch([])
