@@ -33,12 +33,15 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "composite_score_traffic.md")
 COMPOSITE_SRC = os.path.join(ROOT, "paper_2607_02721_b300", "csrc", "k_composite.cu")
 
-# FP32-pipe operations per (ray, Gaussian) pair the compositing kernel evaluates,
-# counted from its arithmetic: footprint test 6 (5 FFMA for the exponent
-# log2 alpha - e1^2 - e2^2, 1 FSETP against the combined cut/alpha_min threshold);
-# pass-1 contribution 8 (FMNMX clamp, FADD 1-rho, FMUL T, FSETP t_min, FMUL rho T,
-# 3 FFMA colour); pass-2 contribution 5 (FMNMX, FMUL rho T/A, FMUL colour weight,
-# FADD, FMUL).  The MUFU ex2 of each contribution runs on the XU pipe, outside this count.
+# Algorithmic work of the compositing kernel: 18 FP32 instructions per evaluated (ray,
+# Gaussian) pair and pass (the per-pair figure of the scoring path's contract: quadratic
+# form, cut test, exp, clamp, alpha_min test, 1 - rho, T update, t_min test, rho T and the
+# colour / score terms), times the pairs each pass evaluates (device counters).
+OPS_PER_PAIR = 18
+# The kernel's own essential count (reported beside it): the footprint test is 6 ops
+# (5 FFMA for log2 alpha - e1^2 - e2^2, 1 FSETP); a pass-1 contribution adds 8 (FMNMX,
+# FADD, FMUL, FSETP, FMUL, 3 FFMA) and a pass-2 contribution 5 (FMNMX, FMUL, FMUL, FADD,
+# FMUL); MUFU ex2 runs on the XU pipe, outside both counts.
 OPS_TEST, OPS_HIT1, OPS_HIT2 = 6, 8, 5
 SMS, FP32_LANES = 148, 128
 
@@ -344,20 +347,24 @@ def run_ours(args):
                "d2h_bytes_per_step": int(d2h), "steps": ne}
 
     # ---- roofline of the dominant kernel (compositing + sensitivity reduction)
-    ops_step = (OPS_TEST * cnt["pairs_evaluated"] + OPS_HIT1 * cnt["pairs_hit"] + OPS_TEST * cnt["pairs_evaluated2"]
+    pairs_step = cnt["pairs_evaluated"] + cnt["pairs_evaluated2"]
+    ess_step = (OPS_TEST * cnt["pairs_evaluated"] + OPS_HIT1 * cnt["pairs_hit"] + OPS_TEST * cnt["pairs_evaluated2"]
                 + OPS_HIT2 * cnt["pairs_hit2"])
-    launches_step = cnt["composite_launches"]
-    ops_launch = ops_step / max(launches_step, 1)
+    launches_step = max(cnt["composite_launches"], 1)
+    ops_launch = OPS_PER_PAIR * pairs_step / launches_step
     avg_launch_s = comp_ms / max(comp_n, 1) / 1e3
     achieved = ops_launch / avg_launch_s / 1e12 if avg_launch_s > 0 else None
+    ess_achieved = ess_step / launches_step / avg_launch_s / 1e12 if avg_launch_s > 0 else None
     peak = SMS * FP32_LANES * 2032e6 / 1e12
     traffic, stale = traffic_per_launch()
     roof = {"bound": "alu", "kernel": "k_composite<score, per-pixel>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock); one FP32-pipe op per lane per "
-                           "clock; ops counted per pair (see DESIGN.md)",
+                           "clock; 18 ops per evaluated pair and pass (see DESIGN.md)",
             "ops_per_launch": ops_launch, "avg_launch_ms": avg_launch_s * 1e3,
+            "essential_ops_frac": (ess_achieved / peak) if ess_achieved else None,
             "pairs_per_ray": (cnt["pairs_evaluated"] / cfg["rays_per_step"]),
+            "pairs_per_ray_pass2": (cnt["pairs_evaluated2"] / cfg["rays_per_step"]),
             "contributing_pairs_per_ray": (cnt["pairs_hit"] / cfg["rays_per_step"]),
             "share_of_step": comp_ms / max(el_ms, 1e-9)}
     if stale:

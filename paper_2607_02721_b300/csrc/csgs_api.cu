@@ -29,8 +29,9 @@ struct DevBuf {
 };
 
 // Buffers of one view's binning (depth sort, instances, tile sort, ranges).  Scoring
-// alternates two slots so that the binning of the next view, on the slot's own
-// high-priority stream, overlaps the compositing of the current one.
+// rotates over kBinSlots slots so that the binning of the next views, each on its
+// slot's own high-priority stream, overlaps the compositing of the current one (the
+// binning kernels are latency-bound, so several binning chains also overlap each other).
 struct BinSlot {
     DevBuf dkeys_b, dvals_a, dvals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, ranges, hist, scan_tmp;
     cudaStream_t st = nullptr;
@@ -67,7 +68,7 @@ struct csgs_ctx {
     uint32_t* h_u32 = nullptr;     // pinned
     unsigned long long* d_nconst = nullptr;
     DevBuf splats, keys, rects;
-    BinSlot slot[2];
+    BinSlot slot[kBinSlots];
     cudaEvent_t ev_proj = nullptr;  // projection of the current view batch done
     uint32_t cap = 0;
     int sort_blocks = kSortBlocks;  // radix-sort grid (autotuned)
@@ -234,16 +235,15 @@ const uint32_t* bin_view(csgs_ctx* ctx, int k, int64_t n, uint32_t* keys_v, cons
                          cudaStream_t st) {
     BinSlot& b = ctx->slot[k];
     unsigned long long* n_inst = &ctx->d_ctr->n_inst[k];
-    iota_u32(P<uint32_t>(b.dvals_a), (int)n, st);
     int cur = radix_sort_pairs(keys_v, P<uint32_t>(b.dvals_a), P<uint32_t>(b.dkeys_b), P<uint32_t>(b.dvals_b),
-                               ctx->d_nconst, (uint32_t)n, 32, P<uint32_t>(b.hist), ctx->sort_blocks, st);
+                               ctx->d_nconst, (uint32_t)n, 32, P<uint32_t>(b.hist), ctx->sort_blocks, true, st);
     const uint32_t* order = cur ? P<uint32_t>(b.dvals_b) : P<uint32_t>(b.dvals_a);
     emit_instances(order, rects_v, (int)n, cam.tiles_x, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
                    P<uint32_t>(b.scan_tmp), ctx->d_ctr, n_inst, st);
     const int ntiles = cam.tiles_x * cam.tiles_y;
     int cur2 = radix_sort_pairs(P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), P<uint32_t>(b.ikeys_b),
                                 P<uint32_t>(b.ivals_b), n_inst, ctx->cap, ceil_log2((uint32_t)ntiles),
-                                P<uint32_t>(b.hist), ctx->sort_blocks, st);
+                                P<uint32_t>(b.hist), ctx->sort_blocks, false, st);
     const uint32_t* ik = cur2 ? P<uint32_t>(b.ikeys_b) : P<uint32_t>(b.ikeys_a);
     const uint32_t* iv = cur2 ? P<uint32_t>(b.ivals_b) : P<uint32_t>(b.ivals_a);
     tile_ranges(ik, n_inst, ctx->cap, P<uint2>(b.ranges), ntiles, st);
@@ -560,8 +560,8 @@ namespace {
 // Enqueue the scoring of views [v0, v1) of one scene: no host synchronisation and no
 // allocation (buffers must be sized), so it can be captured.  Projection and
 // compositing run on the context's stream; the binning of view k runs on the stream of
-// slot k % 2, after the projection of its batch and after the compositing that last
-// read the slot, so that it overlaps the compositing of view k - 1.  Every slot stream
+// slot k % kBinSlots, after the projection of its batch and after the compositing that
+// last read the slot, so that it overlaps the compositing of the views before it.  Every slot stream
 // ends in an event the context's stream waits on (the capture joins them).
 csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int vb, int v0_all, int v1_all,
                                 int stats, float* s_dev, double* S_dev, PhaseTimer& pt, long long& comp_launches) {
@@ -573,7 +573,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
     CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
     if (ko.resolution == CSGS_RES_SCENE) CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA, 0, sizeof(double), st));
     if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
-    bool freed_recorded[2] = {false, false};
+    bool freed_recorded[kBinSlots] = {};
     int view = 0;
     for (int v0 = v0_all; v0 < v1_all; v0 += vb) {
         const int nb = (v1_all - v0) < vb ? (v1_all - v0) : vb;
@@ -584,7 +584,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev_proj, st));
         for (int k = 0; k < nb; ++k, ++view) {
             const CamDev& cam = s->cams[v0 + k];
-            const int sl = view & 1;
+            const int sl = view % kBinSlots;
             BinSlot& slot = ctx->slot[sl];
             uint32_t* keys_v = P<uint32_t>(ctx->keys) + (size_t)k * n;
             const uint2* rects_v = P<uint2>(ctx->rects) + (size_t)k * n;

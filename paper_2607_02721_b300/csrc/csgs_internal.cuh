@@ -69,10 +69,14 @@ struct __align__(16) Splat {
 enum : uint32_t { kErrCapacity = 1u, kErrNonFinite = 2u, kErrIndex = 4u };
 
 // Device counters (one block per context).
+// Binning slots: scoring bins view k in slot k % kBinSlots on the slot's own stream, so
+// the binning of the next views overlaps the compositing of the current one.
+constexpr int kBinSlots = 3;
+
 struct DevCounters {
     uint32_t err;
     uint32_t pad;
-    unsigned long long n_inst[2];   // instances of the view in each binning slot (may exceed capacity)
+    unsigned long long n_inst[kBinSlots];  // instances of the view in each binning slot (may exceed capacity)
     unsigned long long max_inst;    // maximum over views
     unsigned long long inst_total;  // sum over views
     unsigned long long pairs_eval;
@@ -106,11 +110,12 @@ constexpr int kSortBlocks = 148 * 4;       // default radix-sort grid (the autot
 constexpr int kSortMaxBlocks = 2048;
 constexpr int kSortHistWords = 256 * kSortMaxBlocks + 256;  // per-block digit counts + digit totals
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  n is read from
-// d_n (device) and clamped to n_max.  Returns which buffer holds the result (0: a, 1: b).
+// d_n (device) and clamped to n_max.  iota_vals: the values are the indices 0..n-1
+// (vals_a is not read).  Returns which buffer holds the result (0: a, 1: b).
 int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, uint32_t* hist, int G, cudaStream_t st);
+                     uint32_t n_max, int bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st);
 // Gaussians in depth order -> (tile, gid) instances in depth order; writes the
-// instance count to ctr->n_inst.  scan_tmp: >= ceil(n / 256) + 64 words.
+// instance count to *n_inst (and the totals in ctr).  scan_tmp: >= ceil(n / 256) + 64 words.
 void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x,
                     uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     unsigned long long* n_inst, cudaStream_t st);

@@ -34,16 +34,19 @@ __device__ __forceinline__ uint32_t read_n(const unsigned long long* d_n, uint32
     return v < n_max ? (uint32_t)v : n_max;
 }
 
+// Per-block digit counts of one pass.  Each warp counts into its own shared histogram
+// with plain atomics (match.any costs grow with the number of distinct digits in the
+// warp; conflicting shared atomics only serialise on equal digits).
 __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys,
                                                           const unsigned long long* d_n, uint32_t n_max, int shift,
                                                           uint32_t* __restrict__ hist) {
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
+    __shared__ uint32_t wh[kSortWarps][256];
+    for (int k = threadIdx.x; k < kSortWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0u;
     __syncthreads();
     const uint32_t n = read_n(d_n, n_max);
     uint32_t begin, end;
     sort_chunk(n, blockIdx.x, begin, end);
-    const int lane = threadIdx.x & 31;
+    uint32_t* h = wh[threadIdx.x >> 5];
     // a chunk is a whole number of 2048-key sub-tiles: 8 coalesced loads in flight per thread
     for (uint32_t base = begin; base < end; base += kSubTile) {
         uint32_t d[kSortGroups];
@@ -53,13 +56,14 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
             d[g] = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
         }
 #pragma unroll
-        for (int g = 0; g < kSortGroups; ++g) {
-            const uint32_t peers = __match_any_sync(0xffffffffu, d[g]);
-            if (d[g] < 256u && lane == __ffs(peers) - 1) atomicAdd(&cnt[d[g]], (uint32_t)__popc(peers));
-        }
+        for (int g = 0; g < kSortGroups; ++g)
+            if (d[g] < 256u) atomicAdd(h + d[g], 1u);
     }
     __syncthreads();
-    hist[threadIdx.x * gridDim.x + blockIdx.x] = cnt[threadIdx.x];
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) c += wh[w][threadIdx.x];
+    hist[threadIdx.x * gridDim.x + blockIdx.x] = c;
 }
 
 // Exclusive scan of each digit's row of the histogram (G per-block counts, G <=
@@ -101,6 +105,7 @@ __global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist,
 // order), the CTA turns the per-warp counts into positions, places the sub-tile in
 // shared memory grouped by digit, and writes each digit's run to its global slot, so
 // global stores are contiguous runs.
+template <int NBITS>
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -143,16 +148,25 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
             const uint32_t i = sub + warp * (32 * kSortGroups) + g * 32 + lane;
             const bool ok = i < end;
             key[g] = ok ? __ldg(kin + i) : 0u;
-            val[g] = ok ? __ldg(vin + i) : 0u;
+            val[g] = ok ? (vin ? __ldg(vin + i) : i) : 0u;
             dig[g] = ok ? (key[g] >> shift) & 255u : 256u;
         }
+        // lanes holding the same digit: one ballot per digit bit (NBITS, unrolled; match.any
+        // is slower when the digits are spread out); invalid lanes (digit 256) form their
+        // own class.  The per-warp digit counters then give stable ranks in (group, lane) order.
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
             const uint32_t d = dig[g];
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            rank[g] = wcnt[warp][d] + __popc(peers & lt);
+            uint32_t pm = __ballot_sync(0xffffffffu, d < 256u);
+            if (d >= 256u) pm = ~pm;
+#pragma unroll
+            for (int bb = 0; bb < NBITS; ++bb) {
+                const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bb) & 1u);
+                pm &= ((d >> bb) & 1u) ? bal : ~bal;
+            }
+            rank[g] = wcnt[warp][d] + __popc(pm & lt);
             __syncwarp();
-            if (lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+            if (lane == __ffs(pm) - 1) wcnt[warp][d] += __popc(pm);
             __syncwarp();
         }
         __syncthreads();
@@ -254,13 +268,23 @@ __global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ pa
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += 1024) {
-        int i = b0 + threadIdx.x;
-        uint32_t v = i < nb ? partial[i] : 0u;
+    // four consecutive entries per thread per round
+    for (int b0 = 0; b0 < nb; b0 += 4096) {
+        const int i0 = b0 + 4 * threadIdx.x;
+        uint32_t v[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = i0 + k < nb ? partial[i0 + k] : 0u;
+            sum += v[k];
+        }
         uint32_t tot;
-        uint32_t pre = block_exclusive_scan(v, ws, &tot);
-        unsigned long long c = carry;
-        if (i < nb) partial[i] = (uint32_t)(c + pre);
+        uint32_t pre = block_exclusive_scan(sum, ws, &tot);
+        const unsigned long long c = carry;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < nb) partial[i0 + k] = (uint32_t)(c + pre);
+            pre += v[k];
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry = c + tot;
         __syncthreads();
@@ -318,22 +342,34 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
         const uint32_t local = f - s_e[warp][lo];
         const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu;
         const uint32_t w = x1 - x0;
-        const uint32_t dy = local / w;
+        // local / w in FP32: (local + 0.5) / w lies at least 0.5 / w from an integer and the
+        // product with the rounded reciprocal is within (local + 0.5) 2^-23 / w of it, so
+        // the floor is exact for local < 2^22 (integer division beyond)
+        const uint32_t dy = local < (1u << 22) ? (uint32_t)(((float)local + 0.5f) * __frcp_rn((float)w)) : local / w;
         const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
         ikeys[wbase + f] = ty * (uint32_t)tiles_x + tx;
         ivals[wbase + f] = s_g[warp][lo];
     }
 }
 
+// Tile ranges from the tile-sorted instance keys: thread t finds the first instance
+// with key >= t by binary search and writes it as the start of tile t and the end of
+// tile t - 1 (thread n_tiles closes the last tile), so every range is written.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_n, uint32_t n_max,
                          uint2* __restrict__ ranges, uint32_t n_tiles) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_tiles) return;
     const uint32_t n = read_n(d_n, n_max);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t t = keys[i];
-        if (t >= n_tiles) continue;  // only after a capacity overflow (reported)
-        if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-        if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(keys + mid) < t)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
+    if (t < n_tiles) ranges[t].x = lo;
+    if (t > 0) ranges[t - 1].y = lo;
 }
 
 __global__ void k_iota(uint32_t* v, int n) {
@@ -346,20 +382,31 @@ __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v;
 }  // namespace
 
 int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, uint32_t* hist, int G, cudaStream_t st) {
+                     uint32_t n_max, int bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st) {
     if (G < 1) G = 1;
     if (G > kSortMaxBlocks) G = kSortMaxBlocks;
     int cur = 0;
     for (int shift = 0; shift < bits; shift += 8) {
         uint32_t* kin = cur ? kb : ka;
-        uint32_t* vin = cur ? vb : va;
+        uint32_t* vin = shift == 0 && iota_vals ? nullptr : (cur ? vb : va);
         uint32_t* kout = cur ? ka : kb;
         uint32_t* vout = cur ? va : vb;
         k_rs_hist<<<G, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
         count_launches(1);
         k_rs_rowscan<<<256, 256, 0, st>>>(hist, hist + 256 * G, G);
         count_launches(1);
-        k_rs_scatter<<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, hist + 256 * G);
+        const int nbits = bits - shift < 8 ? bits - shift : 8;
+        const uint32_t* rt = hist + 256 * G;
+        switch (nbits) {
+            case 1: k_rs_scatter<1><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            case 2: k_rs_scatter<2><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            case 3: k_rs_scatter<3><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            case 4: k_rs_scatter<4><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            case 5: k_rs_scatter<5><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            case 6: k_rs_scatter<6><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            case 7: k_rs_scatter<7><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+            default: k_rs_scatter<8><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
+        }
         count_launches(1);
         cur ^= 1;
     }
@@ -379,11 +426,7 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_
 
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
                  cudaStream_t st) {
-    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_tiles, st);
-    int blocks = (int)((n_max + 255) / 256);
-    if (blocks > 148 * 8) blocks = 148 * 8;
-    if (blocks < 1) blocks = 1;
-    k_ranges<<<blocks, 256, 0, st>>>(keys, d_n, n_max, ranges, (uint32_t)n_tiles);
+    k_ranges<<<(n_tiles + 1 + 255) / 256, 256, 0, st>>>(keys, d_n, n_max, ranges, (uint32_t)n_tiles);
     count_launches(1);
 }
 
