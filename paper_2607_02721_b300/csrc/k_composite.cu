@@ -411,47 +411,49 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             const int nw = warp_list(sh, cnt, warp, lane);
             const int lim = max(0, min(cnt, last - b));
             const int jw = (int)__reduce_max_sync(0xffffffffu, (unsigned)lim);
+#pragma unroll 4
             for (int k = 0; k < nw; ++k) {
                 const int j = sh.wl[warp][k];
                 if (j >= jw) break;  // the list is in increasing j; warp-uniform
-                uint32_t bits = 0u;
-                if (j < lim) {
-                    const float4 Aj = sh.A[j];
-                    const float4 Bj = sh.B[j];
-                    const float p = exponent2(Aj, Bj, X, Y);
-                    if (STATS) ++n_eval2;
-                    if (p >= Bj.z) {
-                        const float r = fminf(rho_max, ex2_approx(p));
-                        if (STATS) ++n_hit2;
-                        const float w = __fmul_rn(r, T);
-                        float imp;
-                        if (kScaled) {
-                            imp = VAR == kL1 ? __fmul_rn(Bj.w, w) : w;
-                        } else if (MODE == kScorePixel) {
-                            imp = __fmul_rn(pixel_term<VAR>(w, Bj, sh.C[j]), inv0);
-                        } else {
-                            const float4 Cj = sh.C[j];
-                            float t0, t1, t2;
-                            if (VAR == kL1) {
-                                t0 = __fmul_rn(Cj.x, w);
-                                t1 = __fmul_rn(Cj.y, w);
-                                t2 = __fmul_rn(Cj.z, w);
-                            } else if (VAR == kL2) {
-                                t0 = __fmul_rn(Cj.x, w);
-                                t1 = __fmul_rn(Cj.y, w);
-                                t2 = __fmul_rn(Cj.z, w);
-                                t0 = __fmul_rn(t0, t0);
-                                t1 = __fmul_rn(t1, t1);
-                                t2 = __fmul_rn(t2, t2);
-                            } else {
-                                t0 = t1 = t2 = w;
-                            }
-                            imp = fmaxf(__fmul_rn(t0, inv0), fmaxf(__fmul_rn(t1, inv1), __fmul_rn(t2, inv2)));
-                        }
-                        bits = __float_as_uint(imp);
-                        T = __fmul_rn(T, __fadd_rn(1.f, -r));
-                    }
+                // branch-free: every lane evaluates the entry and keeps the result only where
+                // it is one of its pass-1 contributors (the warp takes this path anyway as
+                // soon as one lane contributes)
+                const float4 Aj = sh.A[j];
+                const float4 Bj = sh.B[j];
+                const float p = exponent2(Aj, Bj, X, Y);
+                const bool hit = j < lim && p >= Bj.z;
+                if (STATS) {
+                    n_eval2 += j < lim;
+                    n_hit2 += hit;
                 }
+                const float r = fminf(rho_max, ex2_approx(p));
+                const float w = __fmul_rn(r, T);
+                float imp;
+                if (kScaled) {
+                    imp = VAR == kL1 ? __fmul_rn(Bj.w, w) : w;
+                } else if (MODE == kScorePixel) {
+                    imp = __fmul_rn(pixel_term<VAR>(w, Bj, sh.C[j]), inv0);
+                } else {
+                    const float4 Cj = sh.C[j];
+                    float t0, t1, t2;
+                    if (VAR == kL1) {
+                        t0 = __fmul_rn(Cj.x, w);
+                        t1 = __fmul_rn(Cj.y, w);
+                        t2 = __fmul_rn(Cj.z, w);
+                    } else if (VAR == kL2) {
+                        t0 = __fmul_rn(Cj.x, w);
+                        t1 = __fmul_rn(Cj.y, w);
+                        t2 = __fmul_rn(Cj.z, w);
+                        t0 = __fmul_rn(t0, t0);
+                        t1 = __fmul_rn(t1, t1);
+                        t2 = __fmul_rn(t2, t2);
+                    } else {
+                        t0 = t1 = t2 = w;
+                    }
+                    imp = fmaxf(__fmul_rn(t0, inv0), fmaxf(__fmul_rn(t1, inv1), __fmul_rn(t2, inv2)));
+                }
+                const uint32_t bits = hit ? __float_as_uint(imp) : 0u;
+                T = hit ? __fmul_rn(T, __fadd_rn(1.f, -r)) : T;
                 const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
                 if (lane == 0 && mx) atomicMax(&sh.red[j], mx);
             }
