@@ -432,6 +432,24 @@ def run_surrogate(args):
     res["gain_psnr_surrogate_vs_subset"] = res["psnr_surrogate"] - res["psnr_subset_only"]
     sh, se = s_hat.double().cpu().numpy(), s_exact.double().cpu().numpy()
     res["spearman_log"] = float(np.corrcoef(np.argsort(np.argsort(sh)), np.argsort(np.argsort(se)))[0, 1])
+    # tensor-core roofline of the network's forward over every Gaussian (inference GEMMs)
+    X = ctx.features(sid, ctx.view_stats(sid, sopts))
+    for _ in range(3):
+        ctx.mlp_forward(X)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    reps = 10
+    for _ in range(reps):
+        ctx.mlp_forward(X)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * (64 * 256 + 256 * 256 + 256) * X.shape[0]
+    pk = peaks()
+    bf16 = pk.get("bf16_tflops") if pk else None
+    res["mlp_forward"] = {"rows": int(X.shape[0]), "ms": fwd_ms, "tflops": flops / fwd_ms / 1e9,
+                          "peak_tflops": bf16, "frac": (flops / fwd_ms / 1e9 / bf16) if bf16 else None,
+                          "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if bf16 else None}
     print(json.dumps(res), flush=True)
     ctx.close()
     return 0
@@ -504,6 +522,127 @@ def run_batch(args):
     return 0
 
 
+def _psnr_views(ctx, sid, cams, targets, idx, w, views):
+    vals = []
+    for v in views:
+        H, W = int(cams[v][17]), int(cams[v][16])
+        img = ctx.render(sid, v, idx=idx, w=w, H=H, W=W)
+        mse = float(((img - targets[v]) ** 2).mean())
+        vals.append(10.0 * math.log10(1.0 / max(mse, 1e-20)))
+    return sum(vals) / len(vals)
+
+
+def run_finetune(args):
+    """Short post-prune recovery on the 3M-Gaussian scene: a 10% weighted coreset drawn by
+    sensitivity (and, as the baseline, uniformly) is fitted for `--ft-steps` Adam steps to
+    the full scene's renders of the first `--ft-views` views; PSNR before/after, ms/step."""
+    import numpy as np
+    import torch
+
+    import paper_2607_02721_b300 as csgs
+    from paper_2607_02721_b300 import build, finetune
+
+    build.build()
+    scene, cams = workload(args.workload)
+    cams = cams[: args.ft_views]
+    n = scene.n
+    m = int(round(0.1 * n))
+    ctx = csgs.Context(0, stream=torch.cuda.Stream())
+    sid = ctx.load_scene(scene)
+    ctx.set_queries(sid, cams)
+    res_id = {"pixel": csgs.RES_PIXEL, "scene": csgs.RES_SCENE}[args.resolution]
+    s, S = ctx.score(sid, csgs.default_opts(resolution=res_id))
+    targets = []
+    for v in range(len(cams)):
+        H, W = int(cams[v][17]), int(cams[v][16])
+        targets.append(ctx.render(sid, v, H=H, W=W).clone())
+    ctx.free_scene(sid)
+    out = {"mode": "finetune", "config": {"workload": args.workload, "views": len(cams), "coreset_m": m,
+                                          "steps": args.ft_steps, "resolution": args.resolution,
+                                          "lr": {"means": 1e-3, "sh": 1e-3, "opacity_logits": 5e-3}}}
+    eval_views = list(range(0, len(cams), max(1, len(cams) // 20)))
+    for method in ("sensitivity", "uniform"):
+        if method == "sensitivity":
+            idx, w = ctx.sample_coreset(s, m, 0)
+        else:
+            pu = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+            idx, w = ctx.sample_coreset_p(pu, m, 0)
+        sub = scene.subset(idx.cpu().numpy())
+        sid2 = ctx.load_scene(sub)
+        ctx.set_queries(sid2, cams)
+        params = {k: torch.tensor(getattr(sub, k), device="cuda").contiguous()
+                  for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+        ar = torch.arange(sub.n, dtype=torch.int32, device="cuda")
+        before = _psnr_views(ctx, sid2, cams, targets, ar, w, eval_views)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = finetune.finetune(ctx, sid2, cams, params, ar, w, targets, steps=args.ft_steps, seed=1)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / max(args.ft_steps, 1)
+        after = _psnr_views(ctx, sid2, cams, targets, ar, w, eval_views)
+        out[method] = {"distinct": int(sub.n), "psnr_before": before, "psnr_after": after, "ms_per_step": ms,
+                       "loss_first": losses[0] if losses else None, "loss_last": losses[-1] if losses else None}
+        ctx.free_scene(sid2)
+    out["psnr_views"] = len(eval_views)
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_diagnostics(args):
+    """Theory diagnostics of one coreset (Sec. 3.3): S and |Q'|, Theorem 2's m for
+    (eps_c, delta), the measured relative error of the relaxed objective A_th, the
+    transmittance gap gamma, Theorem 3's eps_r at that gamma, and the validity violations
+    (pairs with w alpha k >= 1), for prune ratios 0.8 / 0.9 / 0.95."""
+    import numpy as np
+    import torch
+
+    import paper_2607_02721_b300 as csgs
+    from paper_2607_02721_b300 import build
+
+    build.build()
+    scene, cams = workload(args.workload)
+    if args.max_views:
+        cams = cams[: args.max_views]
+    ctx = csgs.Context(0, stream=torch.cuda.Stream())
+    sid = ctx.load_scene(scene)
+    ctx.set_queries(sid, cams)
+    s, S = ctx.score(sid)
+    q = ctx.stats()["queries"]
+    out = {"mode": "diagnostics", "config": {"workload": args.workload, "views": len(cams), "n": scene.n},
+           "S": S, "queries": q, "eps_c": 0.1, "delta": 0.1,
+           "theorem2_m": csgs.theorem2_sample_size(S, 0.1, 0.1, q), "ratios": []}
+    views = list(range(0, len(cams), max(1, len(cams) // 4)))
+    for r in (0.8, 0.9, 0.95):
+        m = int(round((1 - r) * scene.n))
+        idx, w = ctx.sample_coreset(s, m, 0)
+        rel, gam = [], []
+        for v in views:
+            H, W = int(cams[v][17]), int(cams[v][16])
+            t = ctx.transfer(sid, v, idx, w, H, W)
+            A = t[..., 0:3].sum(-1).double()
+            Ath = t[..., 3:6].sum(-1).double()
+            g = t[..., 9].double()
+            ok = A > 1e-6
+            rel.append(((Ath[ok] - A[ok]).abs() / A[ok]).cpu().numpy())
+            gam.append(g[ok].cpu().numpy())
+        rel, gam = np.concatenate(rel), np.concatenate(gam)
+        qs = (50, 90, 99)
+        rq = {f"p{q}": float(np.percentile(rel, q)) for q in qs}
+        gq = {f"p{q}": float(np.percentile(gam, q)) for q in qs}
+        rq["max"], gq["max"] = float(rel.max()), float(gam.max())
+        ctx.render(sid, views[0], idx=idx, w=w, H=int(cams[views[0]][17]), W=int(cams[views[0]][16]),
+                   opts=csgs.default_opts(collect_stats=1))
+        st = ctx.stats()
+        out["ratios"].append({"prune": r, "m": m, "distinct": int(idx.numel()),
+                              "rel_err_A_th": rq, "gamma": gq,
+                              "theorem3_eps_r_at": {k: csgs.theorem3_eps(gq[k], rq[k]) for k in ("p50", "p90")},
+                              "violations_view0": st["violations"], "pairs_view0": st["pairs_evaluated"]})
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -524,6 +663,10 @@ def main():
     ap.add_argument("--resolution", default="pixel", choices=["pixel", "scene"])
     ap.add_argument("--aug-views", default="5,10")
     ap.add_argument("--batch", action="store_true", help="six-scene graph-captured batch report")
+    ap.add_argument("--finetune", action="store_true", help="post-prune recovery report (sensitivity vs uniform)")
+    ap.add_argument("--ft-steps", type=int, default=500)
+    ap.add_argument("--ft-views", type=int, default=100)
+    ap.add_argument("--diagnostics", action="store_true", help="theory diagnostics report")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -532,6 +675,10 @@ def main():
         return run_surrogate(args)
     if args.batch:
         return run_batch(args)
+    if args.finetune:
+        return run_finetune(args)
+    if args.diagnostics:
+        return run_diagnostics(args)
     return run_ours(args)
 
 
