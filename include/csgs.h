@@ -324,6 +324,12 @@ csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t n, int64_t 
 csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
                                int32_t N);
 
+/* Diagnostic: the surrogate network's activation as its kernels evaluate it:
+ * out_dev[2i] = GELU(z_i) = z_i Phi(z_i), out_dev[2i+1] = GELU'(z_i) (erf by Abramowitz &
+ * Stegun 7.1.26, |error| <= 1.5e-7, with the hardware reciprocal and exponential).
+ * z_dev: device float[n]; out_dev: device float[2n].  Asynchronous. */
+csgs_status csgs_debug_gelu(csgs_ctx* ctx, const float* z_dev, int64_t n, float* out_dev);
+
 /* Total number of kernels this library has launched in the process (all contexts);
  * the difference across a region counts that region's launches. */
 int64_t csgs_kernel_launch_count(void);

@@ -78,7 +78,7 @@ EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error"
            "csgs_debug_tc_gemm", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
            "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
            "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update",
-           "csgs_score_batch", "csgs_autotune")
+           "csgs_score_batch", "csgs_autotune", "csgs_debug_gelu")
 
 _lib = None
 
@@ -133,6 +133,7 @@ def lib():
                                    I32]
     L.csgs_score_batch.argtypes = [V, I32, V, V, V, V, I32]
     L.csgs_autotune.argtypes = [V, I32, V, I32, V, V]
+    L.csgs_debug_gelu.argtypes = [V, V, I64, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
     for name in EXPORTS:
@@ -364,6 +365,14 @@ class Context:
         return out
 
     # -- surrogate model
+    def debug_gelu(self, z):
+        """[n, 2]: GELU and its derivative as the surrogate kernels evaluate them."""
+        out = self._empty((z.numel(), 2), self.torch.float32)
+        self._in()
+        self._check(lib().csgs_debug_gelu(self.h, _ptr(z), z.numel(), _ptr(out)))
+        self._out()
+        return out
+
     def mlp_init(self, seed: int = 0):
         self._check(lib().csgs_mlp_init(self.h, seed))
 

@@ -1037,6 +1037,14 @@ csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_d
     return CSGS_OK;
 }
 
+csgs_status csgs_debug_gelu(csgs_ctx* ctx, const float* z_dev, int64_t n, float* out_dev) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!z_dev || !out_dev || n <= 0 || n > (1ll << 30)) return fail(ctx, CSGS_E_INVAL, "bad arguments");
+    cudaSetDevice(ctx->device);
+    debug_gelu(z_dev, (int)n, out_dev, ctx->st);
+    return launch_check(ctx, "GELU check");
+}
+
 double csgs_theorem2_sample_size(double S, double eps_c, double delta, int64_t n_queries) {
     if (!(S > 0.0) || !(eps_c > 0.0) || !(delta > 0.0) || n_queries <= 0) return 0.0;
     return ceil(3.0 * S / (eps_c * eps_c) * log(2.0 * (double)n_queries / delta));

@@ -177,6 +177,8 @@ void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const Sa
 
 // ---- tensor cores (k_mlp.cu)
 int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, cudaStream_t st);
+// out[2i] = GELU(z[i]), out[2i+1] = GELU'(z[i]) with the surrogate kernels' device functions
+void debug_gelu(const float* z, int n, float* out, cudaStream_t st);
 
 // surrogate MLP 64 -> 256 -> 256 -> 1 (parameter block: W1, b1, W2, b2, w3, b3)
 constexpr int kMlpParams = 256 * 64 + 256 + 256 * 256 + 256 + 256 + 1;

@@ -96,9 +96,36 @@ constexpr int kIn = 64, kH = 256;
 constexpr int kRows = 128;            // rows per tile (MMA M)
 constexpr uint32_t kIdesc1 = tc::idesc_bf16(128, 256);
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26:
+// erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2), t = 1 / (1 + p x),
+// x >= 0, |error| <= 1.5e-7 (odd extension for x < 0); the reciprocal and the
+// exponential use the hardware approximations (relative error ~2^-22).
+__device__ __forceinline__ float ex2_fast(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float erf_as(float x) {
+    const float ax = fabsf(x);
+    const float t = rcp_fast(fmaf(0.3275911f, ax, 1.f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    poly *= t;
+    const float e = ex2_fast(-ax * ax * 1.4426950408889634f);
+    return copysignf(fmaf(-poly, e, 1.f), x);
+}
+// GELU(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)); GELU'(z) = Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erf_as(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float z) {
-    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    return fmaf(0.5f, erf_as(z * 0.70710678118654752f), 0.5f) +
+           z * ex2_fast(-0.5f * 1.4426950408889634f * z * z) * 0.39894228040143268f;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -304,6 +331,141 @@ __global__ void __launch_bounds__(256, 1) k_mlp_fwd(const __nv_bfloat16* __restr
         }
         atomicAdd(&gw3[tid], sgw3[tid]);
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, 512);
+}
+
+// Inference forward, persistent over 128-row tiles with the weights resident in shared
+// memory (W1 32 KB + W2 128 KB, staged once per CTA), an X tile (16 KB) and one
+// 128-column K-chunk of the first hidden layer (32 KB).  Per tile:
+//   layer 1: X W1^T -> TMEM columns [0, 256)
+//   epilogue 1, columns [0, 128) -> H chunk; layer 2, K = 0..127 -> TMEM [256, 512)
+//   epilogue 1, columns [128, 256) -> H chunk (after the first half has been read);
+//   layer 2, K = 128..255 (accumulate); the next tile's X is staged meanwhile
+//   layer 1 of the next tile is issued before epilogue 2 (it writes columns [0, 256),
+//   which epilogue 1 has finished reading), so it runs under epilogue 2
+//   epilogue 2: y = w3 . GELU(z2 + b2) + b3.
+constexpr int kHc = 128;  // K-chunk of the hidden layer held in shared memory
+
+__device__ __forceinline__ void mma_tile_k(uint32_t d, const unsigned char* a, int Ka, const unsigned char* b, int Kb,
+                                           int k0, int nk, uint32_t idesc, bool accumulate_first, uint64_t* bar) {
+    // A: K-major tile with Ka columns (starting at its column 0); B: K-major with Kb columns, from column k0
+    const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(b) + (uint32_t)(k0 / 8) * 128u;
+    const uint32_t sboa = (uint32_t)(Ka / 8) * 128u, sbob = (uint32_t)(Kb / 8) * 128u;
+    for (int kk = 0; kk < nk / 16; ++kk)
+        tc::mma(d, tc::smem_desc(a0 + kk * 256, 128, sboa), tc::smem_desc(b0 + kk * 256, 128, sbob), idesc,
+                (kk > 0 || accumulate_first) ? 1u : 0u);
+    tc::commit(bar);
+}
+
+// layer-1 epilogue for hidden columns [c_base, c_base + 128): this thread's row, the
+// quarter `qt` of the chunk (32 columns)
+__device__ __forceinline__ void epi1_chunk(uint32_t tl, int c_base, int qt, int row, const MlpDev& p,
+                                           unsigned char* sH) {
+#pragma unroll
+    for (int c = qt * 32; c < qt * 32 + 32; c += 16) {
+        float v[16];
+        tc::tmem_ld16(tl + (uint32_t)(c_base + c), v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            pk[i] = pack_bf16(gelu(v[2 * i] + p.b1[c_base + c + 2 * i]), gelu(v[2 * i + 1] + p.b1[c_base + c + 2 * i + 1]));
+        *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c, kHc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c + 8, kHc)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+}
+
+// 512 threads: warp w reads TMEM lanes 32 (w % 4).. and handles column quarter w / 4.
+__global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __restrict__ X, int B, MlpDev p,
+                                                      float* __restrict__ y, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = align1k(smem_raw);
+    unsigned char* sW1 = sm;                         // 256 x 64
+    unsigned char* sW2 = sW1 + kH * kIn * 2;         // 256 x 256
+    unsigned char* sX = sW2 + kH * kH * 2;           // 128 x 64
+    unsigned char* sH = sX + kRows * kIn * 2;        // 128 x 128
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    __shared__ float sdot[4][kRows];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, qt = warp >> 2, row = q * 32 + lane;
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&slot, 512);
+    stage_rows(sW1, p.W1b, 0, kH, kH, kIn, kIn);
+    stage_rows(sW2, p.W2b, 0, kH, kH, kH, kH);
+    const int ntiles = (B + kRows - 1) / kRows;
+    int tile = blockIdx.x;
+    if (tile < ntiles) stage_rows(sX, X, tile * kRows, B, kRows, kIn, kIn);
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = slot;
+    const uint32_t tl = taddr + ((uint32_t)(q * 32) << 16);
+    uint32_t phase = 0;
+    bool failed = false;
+    if (tile < ntiles && tid == 0) mma_tile_k(taddr, sX, kIn, sW1, kIn, 0, kIn, kIdesc1, false, &bar);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * kRows;
+        // layer 1 done
+        bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        epi1_chunk(tl, 0, qt, row, p, sH);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) mma_tile_k(taddr + 256u, sH, kHc, sW2, kH, 0, kHc, kIdesc1, false, &bar);
+        ok = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        epi1_chunk(tl, kHc, qt, row, p, sH);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) mma_tile_k(taddr + 256u, sH, kHc, sW2, kH, kHc, kHc, kIdesc1, true, &bar);
+        // the X tile is free (layer 1 has completed): stage the next one meanwhile
+        const int next = tile + gridDim.x;
+        if (next < ntiles) stage_rows(sX, X, next * kRows, B, kRows, kIn, kIn);
+        tc::fence_smem_to_async();
+        ok = tc::mbar_wait(&bar, phase, kWaitBudget);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        // columns [0, 256) were read by epilogue 1: the next tile's layer 1 runs under epilogue 2
+        if (next < ntiles && tid == 0) mma_tile_k(taddr, sX, kIn, sW1, kIn, 0, kIn, kIdesc1, false, &bar);
+        float part = 0.f;
+#pragma unroll
+        for (int c0 = qt * 64; c0 < qt * 64 + 64; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) part = fmaf(p.w3[c0 + i], gelu(v[i] + p.b2[c0 + i]), part);
+        }
+        sdot[qt][row] = part;
+        tc::fence_before_sync();
+        __syncthreads();
+        if (qt == 0 && r0 + row < B) y[r0 + row] = (sdot[0][row] + sdot[1][row]) + (sdot[2][row] + sdot[3][row]) + p.b3[0];
+    }
+    if (failed && tid == 0) atomicOr(err, 1);
+    if (failed) tc::mbar_wait(&bar, phase, kWaitBudget);  // drain before freeing TMEM
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, 512);
@@ -532,17 +694,30 @@ static int fwd_grid(int B) {
     return nt < 148 ? nt : 148;
 }
 
+namespace {
+__global__ void k_debug_gelu(const float* __restrict__ z, int n, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[2 * i] = gelu(z[i]);
+    out[2 * i + 1] = gelu_d(z[i]);
+}
+}  // namespace
+
+void debug_gelu(const float* z, int n, float* out, cudaStream_t st) {
+    k_debug_gelu<<<(n + 255) / 256, 256, 0, st>>>(z, n, out);
+    count_launches(1);
+}
+
 void mlp_refresh(const MlpBufs& m, cudaStream_t st) {
     k_mlp_refresh<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m.P, kMlpParams, m.W1b, m.W2b, m.W2Tb);
     count_launches(1);
 }
 
 void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cudaStream_t st) {
-    const size_t smem = (size_t)kH * kH * 2 + (size_t)kRows * kH * 2 + 1024;
-    cudaFuncSetAttribute(k_mlp_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mlp_fwd<false><<<fwd_grid(B), 256, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), B, dev_view(m), y,
-                                                     nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0.f,
-                                                     err);
+    const size_t smem = (size_t)kH * kIn * 2 + (size_t)kH * kH * 2 + (size_t)kRows * kIn * 2 +
+                        (size_t)kRows * kHc * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mlp_infer<<<fwd_grid(B), 512, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), B, dev_view(m), y, err);
     count_launches(1);
 }
 

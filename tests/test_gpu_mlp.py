@@ -142,3 +142,16 @@ def test_log_target_and_combine(ctx, torch):
     np.testing.assert_allclose(out, [0.2, 0.5 - 1e-8, 1.0 - 1e-8, 0.3], rtol=1e-6)
     out = ctx.surrogate_combine(y, se, 1e-8, fill_only=True).cpu().numpy()
     np.testing.assert_allclose(out, [0.2, 0.1, 1.0 - 1e-8, 0.3], rtol=1e-6)
+
+
+def test_gelu_device_function_matches_oracle(ctx, torch):
+    """The kernels' GELU (erf by Abramowitz & Stegun 7.1.26, error <= 1.5e-7) and its
+    derivative against the FP64 definitions, over the range the network sees."""
+    z = torch.linspace(-12.0, 12.0, 20001, dtype=torch.float32, device="cuda")
+    out = ctx.debug_gelu(z).cpu().numpy().astype(np.float64)
+    zz = z.cpu().numpy().astype(np.float64)
+    ref = np.array([[oracle.gelu(v), oracle.gelu_d(v)] for v in zz])
+    err = np.abs(out - ref)
+    # absolute error of erf (1.5e-7 + hardware rcp/exp) scaled by |z|/2, plus FP32 rounding
+    bound = 4e-7 * (1.0 + np.abs(zz))[:, None] + 2e-7 * np.abs(ref)
+    assert np.all(err <= bound), float((err / bound).max())
