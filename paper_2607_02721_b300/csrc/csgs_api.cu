@@ -76,7 +76,7 @@ struct csgs_ctx {
     DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
     // surrogate model
     bool mlp_ready = false;
-    DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1;
+    DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1, mPart;
     int64_t mlp_rows = 0;
     DevBuf bRgb, bT, bLast, g2d;  // render backward
     csgs_stats stats{};
@@ -367,7 +367,7 @@ void csgs_destroy(csgs_ctx* ctx) {
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
                       &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
-                      &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
+                      &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->mPart,   &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
                       &ctx->g2d};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->d_ctr) cudaFree(ctx->d_ctr);
@@ -1159,7 +1159,8 @@ csgs_status mlp_rows_buffers(csgs_ctx* ctx, int64_t B) {
     if ((r = ensure(ctx, ctx->mY, sizeof(float) * B)) || (r = ensure(ctx, ctx->mXb, 2 * 64 * (size_t)B)) ||
         (r = ensure(ctx, ctx->mTb, sizeof(float) * B)) || (r = ensure(ctx, ctx->mZ1, sizeof(float) * 256 * (size_t)B)) ||
         (r = ensure(ctx, ctx->mH1, 2 * 256 * (size_t)B)) || (r = ensure(ctx, ctx->mDz2, 2 * 256 * (size_t)B)) ||
-        (r = ensure(ctx, ctx->mDz1, 2 * 256 * (size_t)B)))
+        (r = ensure(ctx, ctx->mDz1, 2 * 256 * (size_t)B)) ||
+        (r = ensure(ctx, ctx->mPart, sizeof(float) * (size_t)mlp_wgrad_splits(B) * (256 * 256 + 256 * 64))))
         return r;
     return CSGS_OK;
 }
@@ -1175,6 +1176,7 @@ MlpTemp mlp_temp(csgs_ctx* ctx) {
     t.h1 = P<__nv_bfloat16>(ctx->mH1);
     t.dz2 = P<__nv_bfloat16>(ctx->mDz2);
     t.dz1 = P<__nv_bfloat16>(ctx->mDz1);
+    t.wpart = P<float>(ctx->mPart);
     return t;
 }
 

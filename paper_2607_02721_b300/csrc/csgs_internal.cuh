@@ -193,7 +193,9 @@ struct MlpTemp {
     __nv_bfloat16* h1;    // [B][256]
     __nv_bfloat16* dz2;   // [B][256]
     __nv_bfloat16* dz1;   // [B][256]
+    float* wpart;         // split-K partials: mlp_wgrad_splits(B) x (256 x 256 + 256 x 64)
 };
+int mlp_wgrad_splits(int64_t B);
 MlpBufs mlp_layout(float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b, __nv_bfloat16* W2Tb);
 void mlp_refresh(const MlpBufs& m, cudaStream_t st);
 void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cudaStream_t st);

@@ -170,175 +170,9 @@ __device__ __forceinline__ unsigned char* align1k(unsigned char* p) {
     return p + ((1024u - (tc::smem_u32(p) & 1023u)) & 1023u);
 }
 
-// Forward over row tiles (persistent).  TRAIN additionally stores z1 (FP32), h1 (BF16),
-// dz2 = d loss / d z2 (BF16, loss = mean (y - t)^2 over B_total rows), and accumulates
-// d/dw3, d/db3 and the loss.
-// smem: [W region 128 KB: X 16 KB + W1 32 KB, later W2] [H1 64 KB]; TMEM 512 columns.
-template <bool TRAIN>
-__global__ void __launch_bounds__(256, 1) k_mlp_fwd(const __nv_bfloat16* __restrict__ X, int B, MlpDev p,
-                                                    float* __restrict__ y, const float* __restrict__ t,
-                                                    float* __restrict__ z1o, __nv_bfloat16* __restrict__ h1o,
-                                                    __nv_bfloat16* __restrict__ dz2o, float* __restrict__ gw3,
-                                                    float* __restrict__ gb3, float* __restrict__ loss, float inv_B,
-                                                    int* err) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* sm = align1k(smem_raw);
-    unsigned char* sX = sm;
-    unsigned char* sW1 = sm + kRows * kIn * 2;
-    unsigned char* sW2 = sm;
-    unsigned char* sH1 = sm + kH * kH * 2;
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t slot;
-    __shared__ float sdot[2][kRows];
-    __shared__ float sgw3[kH];
-    __shared__ float sred[8];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, half = warp >> 2;
-    const int row = q * 32 + lane;
-    if (tid == 0) {
-        tc::mbar_init(&bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (TRAIN) sgw3[tid] = 0.f;
-    if (warp == 0) tc::tmem_alloc(&slot, 512);
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t taddr = slot;
-    const uint32_t tl = taddr + ((uint32_t)(q * 32) << 16);  // this warp's TMEM lanes
-    uint32_t phase = 0;
-    float lsum = 0.f, db3 = 0.f;
-    bool failed = false;
-    const int ntiles = (B + kRows - 1) / kRows;
-    for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        const int r0 = tile * kRows;
-        stage_rows(sX, X, r0, B, kRows, kIn, kIn);
-        stage_rows(sW1, p.W1b, 0, kH, kH, kIn, kIn);
-        tc::fence_smem_to_async();
-        __syncthreads();
-        if (tid == 0) mma_tile(taddr, sX, sW1, kIn, kIdesc1, false, &bar);
-        const bool ok1 = tc::mbar_wait(&bar, phase, kWaitBudget);
-        phase ^= 1u;
-        if (!__syncthreads_and(ok1)) {
-            failed = true;
-            break;
-        }
-        tc::fence_after_sync();
-        // layer-1 epilogue: z1 + b1 -> GELU -> BF16 H1 (K-major for layer 2)
-        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tl + (uint32_t)c0, v);
-            uint32_t pk[8];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += p.b1[c0 + i];
-            if (TRAIN && r0 + row < B) {
-                float4* zo = reinterpret_cast<float4*>(z1o + (size_t)(r0 + row) * kH + c0);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(gelu(v[2 * i]), gelu(v[2 * i + 1]));
-            *reinterpret_cast<uint4*>(sH1 + tc::kmajor_off(row, c0, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *reinterpret_cast<uint4*>(sH1 + tc::kmajor_off(row, c0 + 8, kH)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            if (TRAIN && r0 + row < B) {
-                uint4* ho = reinterpret_cast<uint4*>(h1o + (size_t)(r0 + row) * kH + c0);
-                ho[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                ho[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-        }
-        // the X / W1 region is free once layer 1 has completed: stage W2 there
-        stage_rows(sW2, p.W2b, 0, kH, kH, kH, kH);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) mma_tile(taddr + 256u, sH1, sW2, kH, kIdesc1, false, &bar);
-        const bool ok2 = tc::mbar_wait(&bar, phase, kWaitBudget);
-        phase ^= 1u;
-        if (!__syncthreads_and(ok2)) {
-            failed = true;
-            break;
-        }
-        tc::fence_after_sync();
-        // layer-2 epilogue and layer 3: y = w3 . GELU(z2 + b2) + b3
-        float part = 0.f;
-        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) part = fmaf(p.w3[c0 + i], gelu(v[i] + p.b2[c0 + i]), part);
-        }
-        sdot[half][row] = part;
-        __syncthreads();
-        const float yr = sdot[0][row] + sdot[1][row] + p.b3[0];
-        const bool valid = r0 + row < B;
-        if (half == 0 && valid) y[r0 + row] = yr;
-        if (TRAIN) {
-            const float e = valid ? yr - t[r0 + row] : 0.f;
-            const float dy = 2.f * e * inv_B;
-            if (half == 0) {
-                lsum += e * e * inv_B;
-                db3 += dy;
-            }
-            for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-                float v[16];
-                tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
-                uint32_t pk[8];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float z = v[i] + p.b2[c0 + i];
-                    float g = dy * gelu(z);  // d loss / d w3 of this row
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-                    if (lane == 0) atomicAdd(&sgw3[c0 + i], g);
-                    v[i] = dy * p.w3[c0 + i] * gelu_d(z);
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
-                if (valid) {
-                    uint4* o = reinterpret_cast<uint4*>(dz2o + (size_t)(r0 + row) * kH + c0);
-                    o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-    }
-    if (failed && tid == 0) atomicOr(err, 1);
-    if (failed) tc::mbar_wait(&bar, phase, kWaitBudget);  // drain before freeing TMEM
-    if (TRAIN) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-            db3 += __shfl_xor_sync(0xffffffffu, db3, o);
-        }
-        __syncthreads();
-        if (lane == 0) sred[warp] = lsum;
-        __syncthreads();
-        if (tid == 0) {
-            float l = 0.f;
-            for (int w = 0; w < 8; ++w) l += sred[w];
-            atomicAdd(loss, l);
-        }
-        __syncthreads();
-        if (lane == 0) sred[warp] = db3;
-        __syncthreads();
-        if (tid == 0) {
-            float d = 0.f;
-            for (int w = 0; w < 8; ++w) d += sred[w];
-            atomicAdd(gb3, d);
-        }
-        atomicAdd(&gw3[tid], sgw3[tid]);
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(taddr, 512);
-}
-
-// Inference forward, persistent over 128-row tiles with the weights resident in shared
-// memory (W1 32 KB + W2 128 KB, staged once per CTA), an X tile (16 KB) and one
-// 128-column K-chunk of the first hidden layer (32 KB).  Per tile:
+// Forward, persistent over 128-row tiles with the weights resident in shared memory
+// (W1 32 KB + W2 128 KB, staged once per CTA), an X tile (16 KB) and one 128-column
+// K-chunk of the first hidden layer (32 KB).  Per tile:
 //   layer 1: X W1^T -> TMEM columns [0, 256)
 //   epilogue 1, columns [0, 128) -> H chunk; layer 2, K = 0..127 -> TMEM [256, 512)
 //   epilogue 1, columns [128, 256) -> H chunk (after the first half has been read);
@@ -359,26 +193,42 @@ __device__ __forceinline__ void mma_tile_k(uint32_t d, const unsigned char* a, i
     tc::commit(bar);
 }
 
-// layer-1 epilogue for hidden columns [c_base, c_base + 128): this thread's row, the
-// quarter `qt` of the chunk (32 columns)
-__device__ __forceinline__ void epi1_chunk(uint32_t tl, int c_base, int qt, int row, const MlpDev& p,
-                                           unsigned char* sH) {
+// Sum of 16 per-lane values over the warp's 32 lanes, one column per lane pair:
+// vector-halving butterfly (8 + 4 + 2 + 1 + 1 shuffles).  Returns the sum of column
+// 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of the lane index), held by lanes 2c and 2c + 1.
+__device__ __forceinline__ float warp_colsum16(const float (&v)[16], int lane) {
+    float a[8], b[4], c[2];
+    const bool h1 = lane & 16, h2 = lane & 8, h3 = lane & 4, h4 = lane & 2;
 #pragma unroll
-    for (int c = qt * 32; c < qt * 32 + 32; c += 16) {
-        float v[16];
-        tc::tmem_ld16(tl + (uint32_t)(c_base + c), v);
-        uint32_t pk[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            pk[i] = pack_bf16(gelu(v[2 * i] + p.b1[c_base + c + 2 * i]), gelu(v[2 * i + 1] + p.b1[c_base + c + 2 * i + 1]));
-        *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c, kHc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c + 8, kHc)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    for (int i = 0; i < 8; ++i) {
+        const float send = h1 ? v[i] : v[i + 8];
+        a[i] = (h1 ? v[i + 8] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = h2 ? a[i] : a[i + 4];
+        b[i] = (h2 ? a[i + 4] : a[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = h3 ? b[i] : b[i + 2];
+        c[i] = (h3 ? b[i + 2] : b[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const float send = h4 ? c[0] : c[1];
+    float d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
+    return d + __shfl_xor_sync(0xffffffffu, d, 1);
 }
 
 // 512 threads: warp w reads TMEM lanes 32 (w % 4).. and handles column quarter w / 4.
-__global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __restrict__ X, int B, MlpDev p,
-                                                      float* __restrict__ y, int* err) {
+// TRAIN additionally stores z1 (FP32), h1 (BF16) and dz2 = d loss / d z2 (BF16) per row
+// (loss = mean (y - t)^2 over the B rows) and accumulates d/dw3, d/db3 and the loss.
+template <bool TRAIN>
+__global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __restrict__ X, int B, MlpDev p,
+                                                     float* __restrict__ y, const float* __restrict__ t,
+                                                     float* __restrict__ z1o, __nv_bfloat16* __restrict__ h1o,
+                                                     __nv_bfloat16* __restrict__ dz2o, float* __restrict__ gw3,
+                                                     float* __restrict__ gb3, float* __restrict__ loss, float inv_B,
+                                                     int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = align1k(smem_raw);
     unsigned char* sW1 = sm;                         // 256 x 64
@@ -388,12 +238,15 @@ __global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __res
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t slot;
     __shared__ float sdot[4][kRows];
+    __shared__ float sgw3[kH];
+    __shared__ float sred[2][16];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, qt = warp >> 2, row = q * 32 + lane;
     if (tid == 0) {
         tc::mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (TRAIN && tid < kH) sgw3[tid] = 0.f;
     if (warp == 0) tc::tmem_alloc(&slot, 512);
     stage_rows(sW1, p.W1b, 0, kH, kH, kIn, kIn);
     stage_rows(sW2, p.W2b, 0, kH, kH, kH, kH);
@@ -408,10 +261,11 @@ __global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __res
     const uint32_t tl = taddr + ((uint32_t)(q * 32) << 16);
     uint32_t phase = 0;
     bool failed = false;
+    float lsum = 0.f, db3 = 0.f;
     if (tile < ntiles && tid == 0) mma_tile_k(taddr, sX, kIn, sW1, kIn, 0, kIn, kIdesc1, false, &bar);
     for (; tile < ntiles; tile += gridDim.x) {
         const int r0 = tile * kRows;
-        // layer 1 done
+        const bool valid = r0 + row < B;
         bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -419,26 +273,47 @@ __global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __res
             break;
         }
         tc::fence_after_sync();
-        epi1_chunk(tl, 0, qt, row, p, sH);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) mma_tile_k(taddr + 256u, sH, kHc, sW2, kH, 0, kHc, kIdesc1, false, &bar);
-        ok = tc::mbar_wait(&bar, phase, kWaitBudget);
-        phase ^= 1u;
-        if (!__syncthreads_and(ok)) {
-            failed = true;
-            break;
+        for (int h = 0; h < 2; ++h) {
+            const int c_base = h * kHc;
+            if (h == 1) {
+                // the first K-chunk must have been consumed before the H buffer is rewritten
+                ok = tc::mbar_wait(&bar, phase, kWaitBudget);
+                phase ^= 1u;
+                if (!__syncthreads_and(ok)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+            }
+#pragma unroll
+            for (int c = qt * 32; c < qt * 32 + 32; c += 16) {
+                float v[16];
+                tc::tmem_ld16(tl + (uint32_t)(c_base + c), v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] += p.b1[c_base + c + i];
+                if (TRAIN && valid) {
+                    float4* zo = reinterpret_cast<float4*>(z1o + (size_t)(r0 + row) * kH + c_base + c);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+                uint32_t pk[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(gelu(v[2 * i]), gelu(v[2 * i + 1]));
+                *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c, kHc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c + 8, kHc)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                if (TRAIN && valid) {
+                    uint4* ho = reinterpret_cast<uint4*>(h1o + (size_t)(r0 + row) * kH + c_base + c);
+                    ho[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    ho[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+            tc::fence_smem_to_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            if (tid == 0) mma_tile_k(taddr + 256u, sH, kHc, sW2, kH, c_base, kHc, kIdesc1, h == 1, &bar);
         }
-        tc::fence_after_sync();
-        epi1_chunk(tl, kHc, qt, row, p, sH);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) mma_tile_k(taddr + 256u, sH, kHc, sW2, kH, kHc, kHc, kIdesc1, true, &bar);
-        // the X tile is free (layer 1 has completed): stage the next one meanwhile
+        if (failed) break;
         const int next = tile + gridDim.x;
         if (next < ntiles) stage_rows(sX, X, next * kRows, B, kRows, kIn, kIn);
         tc::fence_smem_to_async();
@@ -449,7 +324,6 @@ __global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __res
             break;
         }
         tc::fence_after_sync();
-        // columns [0, 256) were read by epilogue 1: the next tile's layer 1 runs under epilogue 2
         if (next < ntiles && tid == 0) mma_tile_k(taddr, sX, kIn, sW1, kIn, 0, kIn, kIdesc1, false, &bar);
         float part = 0.f;
 #pragma unroll
@@ -460,19 +334,79 @@ __global__ void __launch_bounds__(512, 1) k_mlp_infer(const __nv_bfloat16* __res
             for (int i = 0; i < 16; ++i) part = fmaf(p.w3[c0 + i], gelu(v[i] + p.b2[c0 + i]), part);
         }
         sdot[qt][row] = part;
+        __syncthreads();
+        const float yr = (sdot[0][row] + sdot[1][row]) + (sdot[2][row] + sdot[3][row]) + p.b3[0];
+        if (qt == 0 && valid) y[r0 + row] = yr;
+        if (TRAIN) {
+            const float e = valid ? yr - t[r0 + row] : 0.f;
+            const float dy = 2.f * e * inv_B;
+            if (qt == 0) {
+                lsum += e * e * inv_B;
+                db3 += dy;
+            }
+#pragma unroll
+            for (int c0 = qt * 64; c0 < qt * 64 + 64; c0 += 16) {
+                float v[16], g[16];
+                tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float z = v[i] + p.b2[c0 + i];
+                    g[i] = dy * gelu(z);  // this row's d loss / d w3
+                    v[i] = dy * p.w3[c0 + i] * gelu_d(z);
+                }
+                const float cs = warp_colsum16(g, lane);
+                if ((lane & 1) == 0) {
+                    const int col = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+                    atomicAdd(&sgw3[c0 + col], cs);
+                }
+                if (valid) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+                    uint4* o = reinterpret_cast<uint4*>(dz2o + (size_t)(r0 + row) * kH + c0);
+                    o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+            }
+        }
         tc::fence_before_sync();
         __syncthreads();
-        if (qt == 0 && r0 + row < B) y[r0 + row] = (sdot[0][row] + sdot[1][row]) + (sdot[2][row] + sdot[3][row]) + p.b3[0];
     }
     if (failed && tid == 0) atomicOr(err, 1);
     if (failed) tc::mbar_wait(&bar, phase, kWaitBudget);  // drain before freeing TMEM
+    if (TRAIN) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            db3 += __shfl_xor_sync(0xffffffffu, db3, o);
+        }
+        __syncthreads();
+        if (lane == 0) {
+            sred[0][warp] = lsum;
+            sred[1][warp] = db3;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float l = 0.f, d = 0.f;
+            for (int w = 0; w < 16; ++w) {
+                l += sred[0][w];
+                d += sred[1][w];
+            }
+            atomicAdd(loss, l);
+            atomicAdd(gb3, d);
+        }
+        if (tid < kH) atomicAdd(&gw3[tid], sgw3[tid]);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
-// dz1 = (dz2 W2) * GELU'(z1), BF16 out; smem A = dz2 tile (64 KB), B = W2^T (128 KB).
-__global__ void __launch_bounds__(256, 1) k_mlp_dh1(const __nv_bfloat16* __restrict__ dz2, const float* __restrict__ z1,
+// dz1 = (dz2 W2) * GELU'(z1), BF16 out; smem A = dz2 tile (64 KB), B = W2^T (128 KB,
+// resident).  512 threads: warp w reads TMEM lanes 32 (w % 4).. and handles column
+// quarter w / 4; the next tile's dz2 rows are loaded into registers while the tensor
+// core works on the current one.
+__global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restrict__ dz2, const float* __restrict__ z1,
                                                     int B, MlpDev p, __nv_bfloat16* __restrict__ dz1, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = align1k(smem_raw);
@@ -481,7 +415,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_dh1(const __nv_bfloat16* __restr
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, half = warp >> 2, row = q * 32 + lane;
+    const int q = warp & 3, qt = warp >> 2, row = q * 32 + lane;
     if (tid == 0) {
         tc::mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -495,12 +429,31 @@ __global__ void __launch_bounds__(256, 1) k_mlp_dh1(const __nv_bfloat16* __restr
     uint32_t phase = 0;
     bool failed = false;
     const int ntiles = (B + kRows - 1) / kRows;
+    // thread t holds 16-byte chunks t, t + 512, ... of a tile (128 rows x 32 chunks)
+    constexpr int kChunks = kRows * (kH / 8) / 512;
+    uint4 pre[kChunks];
+    auto load_tile = [&](int r0) {
+#pragma unroll
+        for (int k = 0; k < kChunks; ++k) {
+            const int idx = tid + k * 512, r = idx / (kH / 8), k8 = idx % (kH / 8);
+            pre[k] = r0 + r < B ? *reinterpret_cast<const uint4*>(dz2 + (size_t)(r0 + r) * kH + k8 * 8)
+                                : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    if (blockIdx.x < ntiles) load_tile(blockIdx.x * kRows);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int r0 = tile * kRows;
-        stage_rows(sA, dz2, r0, B, kRows, kH, kH);
+#pragma unroll
+        for (int k = 0; k < kChunks; ++k) {
+            const int idx = tid + k * 512, r = idx / (kH / 8), k8 = idx % (kH / 8);
+            *reinterpret_cast<uint4*>(sA + tc::kmajor_off(r, k8 * 8, kH)) = pre[k];
+        }
         tc::fence_smem_to_async();
         __syncthreads();
+        tc::fence_after_sync();
         if (tid == 0) mma_tile(taddr, sA, sB, kH, kIdesc1, false, &bar);
+        const int next = tile + gridDim.x;
+        if (next < ntiles) load_tile(next * kRows);
         const bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -509,14 +462,24 @@ __global__ void __launch_bounds__(256, 1) k_mlp_dh1(const __nv_bfloat16* __restr
         }
         tc::fence_after_sync();
         const bool valid = r0 + row < B;
-        for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+#pragma unroll
+        for (int c0 = qt * 64; c0 < qt * 64 + 64; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tl + (uint32_t)c0, v);
             if (valid) {
-                const float* zr = z1 + (size_t)(r0 + row) * kH + c0;
+                const float4* zr = reinterpret_cast<const float4*>(z1 + (size_t)(r0 + row) * kH + c0);
+                float zz[16];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 f = zr[i];
+                    zz[4 * i] = f.x;
+                    zz[4 * i + 1] = f.y;
+                    zz[4 * i + 2] = f.z;
+                    zz[4 * i + 3] = f.w;
+                }
                 uint32_t pk[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i] * gelu_d(zr[2 * i]), v[2 * i + 1] * gelu_d(zr[2 * i + 1]));
+                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i] * gelu_d(zz[2 * i]), v[2 * i + 1] * gelu_d(zz[2 * i + 1]));
                 uint4* o = reinterpret_cast<uint4*>(dz1 + (size_t)(r0 + row) * kH + c0);
                 o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -532,13 +495,10 @@ __global__ void __launch_bounds__(256, 1) k_mlp_dh1(const __nv_bfloat16* __restr
     if (warp == 0) tc::tmem_dealloc(taddr, 256);
 }
 
-// Weight gradient of one layer, split over rows: G[out][in] += sum_r dz[r][out] act[r][in]
-// for out in [128 ob, 128 ob + 128); also gb[out] += sum_r dz[r][out].  A = dz^T and
-// B = act^T are staged transposed (rows of the batch become the K dimension).
 template <int NIN>
 __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restrict__ dz,
                                                    const __nv_bfloat16* __restrict__ act, int B, int rows_per_cta,
-                                                   float* __restrict__ G, float* __restrict__ gb, int* err) {
+                                                   float* __restrict__ part, float* __restrict__ gb, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = align1k(smem_raw);
     unsigned char* sA = sm;                 // [128 out][128 rows]
@@ -610,16 +570,21 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restri
     if (failed) {
         if (tid == 0) atomicOr(err, 1);
         tc::mbar_wait(&bar, phase, kWaitBudget);
-    } else if (chunk > 0) {
+    } else if (chunk == 0) {
+        float* dst = part + (size_t)blockIdx.x * kH * NIN + (size_t)ob * 128 * NIN;
+        for (int i = tid; i < 128 * NIN; i += 256) dst[i] = 0.f;
+    } else {
         tc::fence_after_sync();
         if (warp < 4) {
             const int o = warp * 32 + lane;
             const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
+            float* dst = part + (size_t)blockIdx.x * kH * NIN + (size_t)(ob * 128 + o) * NIN;
             for (int c0 = 0; c0 < NIN; c0 += 16) {
                 float v[16];
                 tc::tmem_ld16(tl + (uint32_t)c0, v);
+                float4* d4 = reinterpret_cast<float4*>(dst + c0);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) atomicAdd(G + (size_t)(ob * 128 + o) * NIN + c0 + i, v[i]);
+                for (int i = 0; i < 4; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
         }
         if (tid < 128) atomicAdd(gb + ob * 128 + tid, bsum);
@@ -667,6 +632,13 @@ __global__ void k_mlp_refresh(const float* __restrict__ P, int n, __nv_bfloat16*
 
 }  // namespace
 
+int mlp_wgrad_splits(int64_t B) {
+    // about 512 rows per CTA, at most 148 x 2 CTAs per weight-gradient launch
+    int64_t s = (B + 511) / 512;
+    if (s > 148) s = 148;
+    return s < 1 ? 1 : (int)s;
+}
+
 MlpBufs mlp_layout(float* P, __nv_bfloat16* W1b, __nv_bfloat16* W2b, __nv_bfloat16* W2Tb) {
     MlpBufs b;
     b.P = P;
@@ -695,6 +667,14 @@ static int fwd_grid(int B) {
 }
 
 namespace {
+__global__ void k_sum_partials(const float* __restrict__ part, int splits, int n, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float acc = 0.f;
+    for (int k = 0; k < splits; ++k) acc += part[(size_t)k * n + i];
+    out[i] = acc;
+}
+
 __global__ void k_debug_gelu(const float* __restrict__ z, int n, float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -716,8 +696,10 @@ void mlp_refresh(const MlpBufs& m, cudaStream_t st) {
 void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cudaStream_t st) {
     const size_t smem = (size_t)kH * kIn * 2 + (size_t)kH * kH * 2 + (size_t)kRows * kIn * 2 +
                         (size_t)kRows * kHc * 2 + 1024;
-    cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mlp_infer<<<fwd_grid(B), 512, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), B, dev_view(m), y, err);
+    cudaFuncSetAttribute(k_mlp_fwd2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_mlp_fwd2<false><<<fwd_grid(B), 512, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(X), B, dev_view(m), y,
+                                                      nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                      0.f, err);
     count_launches(1);
 }
 
@@ -733,22 +715,27 @@ void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float*
     float* gb3 = gw3 + kH;
     cudaMemsetAsync(G, 0, sizeof(float) * kMlpParams, st);
     cudaMemsetAsync(loss, 0, sizeof(float), st);
-    const size_t smem_f = (size_t)kH * kH * 2 + (size_t)kRows * kH * 2 + 1024;
-    cudaFuncSetAttribute(k_mlp_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
-    k_mlp_fwd<true><<<fwd_grid(B), 256, smem_f, st>>>(Xb, B, d, y, t, tmp.z1, tmp.h1, tmp.dz2, gw3, gb3, loss,
-                                                      1.f / (float)B, err);
+    const size_t smem_f = (size_t)kH * kIn * 2 + (size_t)kH * kH * 2 + (size_t)kRows * kIn * 2 +
+                          (size_t)kRows * kHc * 2 + 1024;
+    cudaFuncSetAttribute(k_mlp_fwd2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
+    k_mlp_fwd2<true><<<fwd_grid(B), 512, smem_f, st>>>(Xb, B, d, y, t, tmp.z1, tmp.h1, tmp.dz2, gw3, gb3, loss,
+                                                       1.f / (float)B, err);
     const size_t smem_d = (size_t)kRows * kH * 2 + (size_t)kH * kH * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_dh1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
-    k_mlp_dh1<<<fwd_grid(B), 256, smem_d, st>>>(tmp.dz2, tmp.z1, B, d, tmp.dz1, err);
-    const int rows_per_cta = 512;
-    const int splits = (B + rows_per_cta - 1) / rows_per_cta;
+    k_mlp_dh1<<<fwd_grid(B), 512, smem_d, st>>>(tmp.dz2, tmp.z1, B, d, tmp.dz1, err);
+    const int splits = mlp_wgrad_splits(B);
+    const int rows_per_cta = (B + splits - 1) / splits;
+    float* part2 = tmp.wpart;
+    float* part1 = tmp.wpart + (size_t)splits * kH * kH;
     const size_t smem_w2 = (size_t)128 * 128 * 2 + (size_t)kH * 128 * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_wgrad<kH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w2);
-    k_mlp_wgrad<kH><<<dim3(splits, 2), 256, smem_w2, st>>>(tmp.dz2, tmp.h1, B, rows_per_cta, gW2, gb2, err);
+    k_mlp_wgrad<kH><<<dim3(splits, 2), 256, smem_w2, st>>>(tmp.dz2, tmp.h1, B, rows_per_cta, part2, gb2, err);
     const size_t smem_w1 = (size_t)128 * 128 * 2 + (size_t)kIn * 128 * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_wgrad<kIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w1);
-    k_mlp_wgrad<kIn><<<dim3(splits, 2), 256, smem_w1, st>>>(tmp.dz1, Xb, B, rows_per_cta, gW1, gb1, err);
-    count_launches(4);
+    k_mlp_wgrad<kIn><<<dim3(splits, 2), 256, smem_w1, st>>>(tmp.dz1, Xb, B, rows_per_cta, part1, gb1, err);
+    k_sum_partials<<<(kH * kH + 255) / 256, 256, 0, st>>>(part2, splits, kH * kH, gW2);
+    k_sum_partials<<<(kH * kIn + 255) / 256, 256, 0, st>>>(part1, splits, kH * kIn, gW1);
+    count_launches(6);
 }
 
 void mlp_adam(const MlpBufs& m, const float* G, float* mo, float* vo, float lr, int step, cudaStream_t st) {
