@@ -522,20 +522,42 @@ def run_batch(args):
     return 0
 
 
-def _psnr_views(ctx, sid, cams, targets, idx, w, views):
-    vals = []
+def _ssim(img, ref):
+    """SSIM (Wang et al. 2004): 11x11 Gaussian window, sigma 1.5, C1 = 0.01^2, C2 = 0.03^2
+    for values in [0, 1], mean over pixels and channels.  img, ref: [H, W, 3] device."""
+    import torch
+
+    x = img.permute(2, 0, 1).unsqueeze(0).clamp(0, 1)
+    y = ref.permute(2, 0, 1).unsqueeze(0).clamp(0, 1)
+    g = torch.arange(11, dtype=torch.float32, device=img.device) - 5.0
+    g = torch.exp(-(g * g) / (2 * 1.5 ** 2))
+    g = g / g.sum()
+    k = (g[:, None] * g[None, :]).expand(3, 1, 11, 11).contiguous()
+    conv = lambda t: torch.nn.functional.conv2d(t, k, groups=3)
+    mx, my = conv(x), conv(y)
+    sxx, syy, sxy = conv(x * x) - mx * mx, conv(y * y) - my * my, conv(x * y) - mx * my
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    s = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return float(s.mean())
+
+
+def _quality(ctx, sid, cams, targets, idx, w, views):
+    """Mean PSNR and SSIM over `views` of the weighted render against the targets."""
+    ps, ss = [], []
     for v in views:
         H, W = int(cams[v][17]), int(cams[v][16])
         img = ctx.render(sid, v, idx=idx, w=w, H=H, W=W)
         mse = float(((img - targets[v]) ** 2).mean())
-        vals.append(10.0 * math.log10(1.0 / max(mse, 1e-20)))
-    return sum(vals) / len(vals)
+        ps.append(10.0 * math.log10(1.0 / max(mse, 1e-20)))
+        ss.append(_ssim(img, targets[v]))
+    return sum(ps) / len(ps), sum(ss) / len(ss)
 
 
 def run_finetune(args):
-    """Short post-prune recovery on the 3M-Gaussian scene: a 10% weighted coreset drawn by
-    sensitivity (and, as the baseline, uniformly) is fitted for `--ft-steps` Adam steps to
-    the full scene's renders of the first `--ft-views` views; PSNR before/after, ms/step."""
+    """Short post-prune recovery (Sec. 4): for each prune ratio r, a weighted coreset of
+    m = (1 - r) N draws by sensitivity and, as the baseline, uniformly is fitted by Adam
+    to the full scene's renders of the first `--ft-views` views; PSNR and SSIM (20 of the
+    views) before recovery and at each checkpoint, ms per step."""
     import numpy as np
     import torch
 
@@ -546,7 +568,9 @@ def run_finetune(args):
     scene, cams = workload(args.workload)
     cams = cams[: args.ft_views]
     n = scene.n
-    m = int(round(0.1 * n))
+    ratios = [float(x) for x in args.ratios.split(",") if x]
+    checkpoints = sorted({int(x) for x in args.ft_checkpoints.split(",") if x} | {args.ft_steps})
+    checkpoints = [c for c in checkpoints if c <= args.ft_steps]
     ctx = csgs.Context(0, stream=torch.cuda.Stream())
     sid = ctx.load_scene(scene)
     ctx.set_queries(sid, cams)
@@ -557,33 +581,50 @@ def run_finetune(args):
         H, W = int(cams[v][17]), int(cams[v][16])
         targets.append(ctx.render(sid, v, H=H, W=W).clone())
     ctx.free_scene(sid)
-    out = {"mode": "finetune", "config": {"workload": args.workload, "views": len(cams), "coreset_m": m,
-                                          "steps": args.ft_steps, "resolution": args.resolution,
-                                          "lr": {"means": 1e-3, "sh": 1e-3, "opacity_logits": 5e-3}}}
+    out = {"mode": "finetune", "config": {"workload": args.workload, "views": len(cams), "steps": args.ft_steps,
+                                          "checkpoints": checkpoints, "resolution": args.resolution,
+                                          "lr": {"means": 1e-3, "sh": 1e-3, "opacity_logits": 5e-3}},
+           "ratios": []}
     eval_views = list(range(0, len(cams), max(1, len(cams) // 20)))
-    for method in ("sensitivity", "uniform"):
-        if method == "sensitivity":
-            idx, w = ctx.sample_coreset(s, m, 0)
-        else:
-            pu = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
-            idx, w = ctx.sample_coreset_p(pu, m, 0)
-        sub = scene.subset(idx.cpu().numpy())
-        sid2 = ctx.load_scene(sub)
-        ctx.set_queries(sid2, cams)
-        params = {k: torch.tensor(getattr(sub, k), device="cuda").contiguous()
-                  for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
-        ar = torch.arange(sub.n, dtype=torch.int32, device="cuda")
-        before = _psnr_views(ctx, sid2, cams, targets, ar, w, eval_views)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        losses = finetune.finetune(ctx, sid2, cams, params, ar, w, targets, steps=args.ft_steps, seed=1)
-        torch.cuda.synchronize()
-        ms = (time.perf_counter() - t0) * 1e3 / max(args.ft_steps, 1)
-        after = _psnr_views(ctx, sid2, cams, targets, ar, w, eval_views)
-        out[method] = {"distinct": int(sub.n), "psnr_before": before, "psnr_after": after, "ms_per_step": ms,
-                       "loss_first": losses[0] if losses else None, "loss_last": losses[-1] if losses else None}
-        ctx.free_scene(sid2)
-    out["psnr_views"] = len(eval_views)
+    for r in ratios:
+        m = max(1, int(round((1.0 - r) * n)))
+        entry = {"prune": r, "coreset_m": m}
+        for method in ("sensitivity", "uniform"):
+            if method == "sensitivity":
+                idx, w = ctx.sample_coreset(s, m, 0)
+            else:
+                pu = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+                idx, w = ctx.sample_coreset_p(pu, m, 0)
+            sub = scene.subset(idx.cpu().numpy())
+            sid2 = ctx.load_scene(sub)
+            ctx.set_queries(sid2, cams)
+            params = {k: torch.tensor(getattr(sub, k), device="cuda").contiguous()
+                      for k in ("means", "log_scales", "quats", "opacity_logits", "sh")}
+            ar = torch.arange(sub.n, dtype=torch.int32, device="cuda")
+            p0, s0 = _quality(ctx, sid2, cams, targets, ar, w, eval_views)
+            curve = {"0": {"psnr": p0, "ssim": s0}}
+            t_train = [0.0]
+            t_mark = [time.perf_counter()]
+
+            def cb(step):
+                if step in checkpoints:
+                    torch.cuda.synchronize()
+                    t_train[0] += time.perf_counter() - t_mark[0]
+                    ctx.update_scene(sid2, params["means"], params["log_scales"], params["quats"],
+                                     params["opacity_logits"], params["sh"])
+                    p, q = _quality(ctx, sid2, cams, targets, ar, w, eval_views)
+                    curve[str(step)] = {"psnr": p, "ssim": q}
+                    torch.cuda.synchronize()
+                    t_mark[0] = time.perf_counter()
+
+            torch.cuda.synchronize()
+            t_mark[0] = time.perf_counter()
+            finetune.finetune(ctx, sid2, cams, params, ar, w, targets, steps=args.ft_steps, seed=1, callback=cb)
+            entry[method] = {"distinct": int(sub.n), "curve": curve,
+                             "ms_per_step": t_train[0] * 1e3 / max(args.ft_steps, 1)}
+            ctx.free_scene(sid2)
+        out["ratios"].append(entry)
+    out["eval_views"] = len(eval_views)
     print(json.dumps(out), flush=True)
     ctx.close()
     return 0
@@ -666,6 +707,8 @@ def main():
     ap.add_argument("--finetune", action="store_true", help="post-prune recovery report (sensitivity vs uniform)")
     ap.add_argument("--ft-steps", type=int, default=500)
     ap.add_argument("--ft-views", type=int, default=100)
+    ap.add_argument("--ratios", default="0.9", help="prune ratios of the recovery report")
+    ap.add_argument("--ft-checkpoints", default="10,50,100,200", help="recovery steps at which to evaluate")
     ap.add_argument("--diagnostics", action="store_true", help="theory diagnostics report")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()

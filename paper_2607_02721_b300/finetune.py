@@ -48,11 +48,13 @@ def coreset_render(ctx, sid, view, means, sh, logits, log_scales, quats, idx, w,
 
 
 def finetune(ctx, sid, cams, params: dict, idx, w, targets, steps: int, lr_means=1e-3, lr_colour=1e-3,
-             lr_opacity=5e-3, seed: int = 0, opts=None, log_every: int = 0):
+             lr_opacity=5e-3, seed: int = 0, opts=None, log_every: int = 0, callback=None):
     """Adam on means, SH and opacity logits, one seeded-random view per step, loss = mean
     absolute error against the target render of that view.  params: device tensors
     means [3,N], log_scales [3,N], quats [4,N], opacity_logits [N], sh [K,3,N] of the
-    scene `sid` (updated in place).  Returns the per-step losses."""
+    scene `sid` (updated in place).  callback(step) runs after each step's update (the
+    library's copy of the scene is refreshed only by the next step's forward, so a callback
+    that renders calls ctx.update_scene first).  Returns the per-step losses."""
     import torch
 
     cams = np.asarray(cams, dtype=np.float32).reshape(-1, 20)
@@ -71,9 +73,11 @@ def finetune(ctx, sid, cams, params: dict, idx, w, targets, steps: int, lr_means
         for k, lr in trainable.items():
             m, vv = state[k]
             ctx.adam_update(params[k], leaves[k].grad.contiguous(), m, vv, lr, step)
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
         if log_every and step % log_every == 0:
             print(f"step {step} loss {losses[-1]:.5f}")
+        if callback is not None:
+            callback(step)
     ctx.update_scene(sid, params["means"], params["log_scales"], params["quats"], params["opacity_logits"],
                      params["sh"])
     return losses
