@@ -630,6 +630,53 @@ def run_finetune(args):
     return 0
 
 
+def run_mlp(args):
+    """Tensor-core roofline of the surrogate network alone: forward over `--mlp-rows` random
+    BF16 feature rows and the training step (64k-row batch: forward, backward, Adam)."""
+    import torch
+
+    import paper_2607_02721_b300 as csgs
+    from paper_2607_02721_b300 import build
+
+    build.build()
+    ctx = csgs.Context(0, stream=torch.cuda.Stream())
+    n = args.mlp_rows
+    g = torch.Generator(device="cuda").manual_seed(0)
+    with torch.cuda.stream(ctx.stream):
+        X = (0.5 * torch.randn(n, 64, device="cuda", generator=g)).to(torch.bfloat16)
+        t = torch.randn(n, device="cuda", generator=g)
+    ctx.mlp_init(0)
+    flops_row = 2.0 * (64 * 256 + 256 * 256 + 256)
+    for _ in range(args.warmup):
+        ctx.mlp_forward(X)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        ctx.mlp_forward(X)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / args.steps
+    batch, steps = 65536, 50
+    ctx.mlp_train(X, t, batch=batch, steps=3, lr=1e-3, seed=1)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    ctx.mlp_train(X, t, batch=batch, steps=steps, lr=1e-3, seed=2)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / steps
+    pk = peaks()
+    bf16 = pk.get("bf16_tflops")
+    fwd_tf = flops_row * n / fwd_ms / 1e9
+    train_tf = 3.0 * flops_row * batch / step_ms / 1e9  # forward + two backward GEMM sets
+    print(json.dumps({"mode": "mlp", "rows": n, "forward_ms": fwd_ms, "forward_tflops": fwd_tf,
+                      "train_batch": batch, "train_step_ms": step_ms, "train_tflops": train_tf,
+                      "peak_tflops": bf16, "forward_frac": fwd_tf / bf16 if bf16 else None,
+                      "train_frac": train_tf / bf16 if bf16 else None,
+                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}), flush=True)
+    ctx.close()
+    return 0
+
+
 def run_diagnostics(args):
     """Theory diagnostics of one coreset (Sec. 3.3): S and |Q'|, Theorem 2's m for
     (eps_c, delta), the measured relative error of the relaxed objective A_th, the
@@ -710,6 +757,8 @@ def main():
     ap.add_argument("--ratios", default="0.9", help="prune ratios of the recovery report")
     ap.add_argument("--ft-checkpoints", default="10,50,100,200", help="recovery steps at which to evaluate")
     ap.add_argument("--diagnostics", action="store_true", help="theory diagnostics report")
+    ap.add_argument("--mlp", action="store_true", help="surrogate network tensor-core report")
+    ap.add_argument("--mlp-rows", type=int, default=3_000_000)
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -722,6 +771,8 @@ def main():
         return run_finetune(args)
     if args.diagnostics:
         return run_diagnostics(args)
+    if args.mlp:
+        return run_mlp(args)
     return run_ours(args)
 
 
