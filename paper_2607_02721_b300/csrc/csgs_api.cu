@@ -74,6 +74,7 @@ struct csgs_ctx {
     int sort_blocks = kSortBlocks;  // radix-sort grid (autotuned)
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
     DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
+    DevBuf mskb;        // pixel / channel resolution: warp mask per instance (pass 1 -> pass 2)
     // surrogate model
     bool mlp_ready = false;
     DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1, mPart;
@@ -365,6 +366,7 @@ void csgs_destroy(csgs_ctx* ctx) {
     DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,
                       &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
+                      &ctx->mskb,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
                       &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
                       &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->mPart,   &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
@@ -605,6 +607,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
             a.s_sum = ko.resolution == CSGS_RES_IMAGE ? P<float>(ctx->vbuf) : s_dev;
             a.tile_sum = P<float>(ctx->tsum);
+            a.mskbuf = P<uint8_t>(ctx->mskb);
             a.ctr = ctx->d_ctr;
             a.stats = stats & 1;
             if (ko.resolution == CSGS_RES_IMAGE)
@@ -641,6 +644,9 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
     if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * (ns + 1)))) return r;
     if (ko.resolution == CSGS_RES_IMAGE && (r = ensure(ctx, ctx->vbuf, sizeof(float) * (size_t)nmax))) return r;
     if (ko.resolution == CSGS_RES_TILE && (r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap))) return r;
+    if ((ko.resolution == CSGS_RES_PIXEL || ko.resolution == CSGS_RES_CHANNEL) &&
+        (r = ensure(ctx, ctx->mskb, (size_t)ctx->cap)))
+        return r;
     return CSGS_OK;
 }
 

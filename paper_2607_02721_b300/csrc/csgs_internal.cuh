@@ -137,6 +137,7 @@ struct CompositeArgs {
     uint32_t* s_bits;  // pixel resolution: float bits of s, atomicMax
     float* s_sum;      // scene / image resolution: sum of terms, atomicAdd
     float* tile_sum;   // tile resolution: per tile-list entry, the Gaussian's sum over the tile
+    uint8_t* mskbuf;   // pixel / channel resolution: pass 1's warp mask per tile-list entry
     const float* wsel; // transfer: coreset weight per Gaussian (0 = removed)
     float* aux;        // transfer: [H][W][11] per-pixel outputs
     int* last;         // render: [H][W] index + 1 of each pixel's last contributor (optional)

@@ -65,8 +65,10 @@ struct Shared {
     double sumA[kWarps];
 };
 
-// Stage splat i of the tile list into slot threadIdx.x (tile centre (cx, cy)).
-template <int MODE>
+// Stage splat i of the tile list into slot threadIdx.x (tile centre (cx, cy)).  MSK = 1:
+// also store the warp mask per tile-list entry (pass 1 of the two-pass modes); MSK = 2:
+// load it instead of recomputing it (pass 2).
+template <int MODE, int MSK = 0>
 __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32_t i, uint32_t end, float cx,
                                       float cy) {
     const int tid = threadIdx.x;
@@ -91,6 +93,10 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
     sh.C[tid] = make_float4(c.x, c.y, c.z, a.o.ow0 * c.x * c.x + a.o.ow1 * c.y * c.y + a.o.ow2 * c.z * c.z);
     sh.gid[tid] = g;
     if (MODE == kTransfer) sh.wsel[tid] = __ldg(a.wsel + g);
+    if (MSK == 2) {
+        sh.msk[tid] = a.mskbuf[i];
+        return;
+    }
     // Warp-block mask.  The test p >= thr is the ellipse e1^2 + e2^2 <= R with R =
     // log2 alpha - thr (the 3-sigma cut and the alpha_min skip in one), e1 = s1 u + s1k v,
     // e2 = s2 v, (u, v) = pixel - mean.  For each 4-row band of warp blocks, take the
@@ -124,6 +130,7 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
         mk |= cols << (2 * r);
     }
     sh.msk[tid] = mk;
+    if (MSK == 1) a.mskbuf[i] = (uint8_t)mk;
 }
 
 // Compact the staged batch into this warp's list; returns its length.
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     // ---------------------------------------------------------------- pass 1
     for (int b = 0; b < n; b += kThreads) {
         if (__syncthreads_count(done) == kThreads) break;
-        stage<MODE>(a, sh, start + b + tid, rg.y, cx, cy);
+        stage<MODE, two_pass(MODE) ? 1 : 0>(a, sh, start + b + tid, rg.y, cx, cy);
         __syncthreads();
         const int cnt = min(kThreads, n - b);
         processed = b + cnt;
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         const int n2 = sh.last;
         for (int b = 0; b < n2; b += kThreads) {
             __syncthreads();
-            stage<MODE>(a, sh, start + b + tid, rg.y, cx, cy);
+            stage<MODE, 2>(a, sh, start + b + tid, rg.y, cx, cy);
             __syncthreads();
             const int cnt = min(kThreads, n2 - b);
             const int nw = warp_list(sh, cnt, warp, lane);
