@@ -238,6 +238,24 @@ def run_reference(args):
     return 0
 
 
+def job_time_ms(local_ms: float, dist=None, device=None) -> float:
+    """The job's time: the maximum of the ranks' timed regions (replicas run the same
+    work on their own GPU; the slowest one ends the job)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, job_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job's time."""
+    return units_per_rank * world / (job_ms / 1e3)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -268,6 +286,11 @@ def run_ours(args):
     sid = ctx.load_scene(scene)
     ctx.set_queries(sid, cams)
     s = torch.empty(scene.n, dtype=torch.float32, device=f"cuda:{local}")
+    tuned = None
+    if not args.no_autotune and not args.view_batch:
+        # view batch and radix-sort grid picked by the library's autotuner (untimed)
+        tuned = ctx.autotune(sid, csgs.default_opts(), probe_views=8)
+        cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1]}
 
     # pair counts of one pass (untimed; counting kernels are slower)
     ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch), out=s)
@@ -302,14 +325,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = csgs.kernel_launch_count() - l0
     clk = clocks.stop()
-    el_ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([el_ms], dtype=torch.float64, device=f"cuda:{local}")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    el_ms = float(t.item())
-    rays = cfg["rays_per_step"] * args.steps * world
-    value = rays / (el_ms / 1e3)
+    el_ms = job_time_ms(ev0.elapsed_time(ev1), dist, torch.device("cuda", local))
+    value = job_rate(cfg["rays_per_step"] * args.steps, world, el_ms)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
