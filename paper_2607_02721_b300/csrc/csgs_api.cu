@@ -67,9 +67,12 @@ struct csgs_ctx {
     double* h_S = nullptr;         // pinned
     uint32_t* h_u32 = nullptr;     // pinned
     unsigned long long* d_nconst = nullptr;
-    DevBuf splats, keys, rects;
+    DevBuf splats[2], keys[2], rects[2];  // projected view batches, double-buffered
     BinSlot slot[kBinSlots];
-    cudaEvent_t ev_proj = nullptr;  // projection of the current view batch done
+    cudaStream_t pst = nullptr;           // projection stream (scoring)
+    cudaEvent_t ev_start = nullptr;       // enqueue start on the context's stream
+    cudaEvent_t ev_proj[2] = {};          // projection of the batch in buffer set k done
+    cudaEvent_t ev_setfree[2] = {};       // last compositing that read buffer set k done
     uint32_t cap = 0;
     int sort_blocks = kSortBlocks;  // radix-sort grid (autotuned)
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
@@ -204,9 +207,11 @@ SceneDev scene_dev(const SceneRec& s) {
 // Per-view buffers for a batch of `vb` views and the instance buffers.
 csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles) {
     csgs_status r;
-    if ((r = ensure(ctx, ctx->splats, sizeof(Splat) * (size_t)n * vb))) return r;
-    if ((r = ensure(ctx, ctx->keys, sizeof(uint32_t) * (size_t)n * vb))) return r;
-    if ((r = ensure(ctx, ctx->rects, sizeof(uint2) * (size_t)n * vb))) return r;
+    for (int k = 0; k < 2; ++k) {
+        if ((r = ensure(ctx, ctx->splats[k], sizeof(Splat) * (size_t)n * vb))) return r;
+        if ((r = ensure(ctx, ctx->keys[k], sizeof(uint32_t) * (size_t)n * vb))) return r;
+        if ((r = ensure(ctx, ctx->rects[k], sizeof(uint2) * (size_t)n * vb))) return r;
+    }
     if (ctx->cap == 0) {
         uint64_t c = (uint64_t)n * 8;
         if (c < (1u << 20)) c = 1u << 20;
@@ -332,7 +337,12 @@ csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
             return CSGS_E_CUDA;
         }
     }
-    if (cudaEventCreateWithFlags(&ctx->ev_proj, cudaEventDisableTiming) != cudaSuccess) {
+    bool ev_ok = cudaStreamCreateWithFlags(&ctx->pst, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < 2 && ev_ok; ++k)
+        ev_ok = cudaEventCreateWithFlags(&ctx->ev_proj[k], cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_setfree[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ev_ok) {
         csgs_destroy(ctx);
         return CSGS_E_CUDA;
     }
@@ -362,8 +372,16 @@ void csgs_destroy(csgs_ctx* ctx) {
         if (b.ready) cudaEventDestroy(b.ready);
         if (b.freed) cudaEventDestroy(b.freed);
     }
-    if (ctx->ev_proj) cudaEventDestroy(ctx->ev_proj);
-    DevBuf* bufs[] = {&ctx->splats, &ctx->keys,    &ctx->rects,
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->ev_proj[k]) cudaEventDestroy(ctx->ev_proj[k]);
+        if (ctx->ev_setfree[k]) cudaEventDestroy(ctx->ev_setfree[k]);
+        release(ctx->splats[k]);
+        release(ctx->keys[k]);
+        release(ctx->rects[k]);
+    }
+    if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    if (ctx->pst) cudaStreamDestroy(ctx->pst);
+    DevBuf* bufs[] = {
                       &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
                       &ctx->mskb,
@@ -560,37 +578,46 @@ extern "C" {
 namespace {
 
 // Enqueue the scoring of views [v0, v1) of one scene: no host synchronisation and no
-// allocation (buffers must be sized), so it can be captured.  Projection and
-// compositing run on the context's stream; the binning of view k runs on the stream of
-// slot k % kBinSlots, after the projection of its batch and after the compositing that
-// last read the slot, so that it overlaps the compositing of the views before it.  Every slot stream
-// ends in an event the context's stream waits on (the capture joins them).
+// allocation (buffers must be sized), so it can be captured.  Three kinds of streams:
+//   - projection (ctx->pst): view batch b into buffer set b % 2, once the compositing
+//     that last read that set (batch b - 2) is done, so it runs ahead of the compositing;
+//   - binning: view k in slot k % kBinSlots on the slot's high-priority stream, after the
+//     projection of its batch and the compositing that last read the slot;
+//   - compositing and the reductions on the context's stream, each view after its
+//     binning.
+// Every side stream's last operation is waited on by the context's stream (the capture
+// joins them).
 csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int vb, int v0_all, int v1_all,
                                 int stats, float* s_dev, double* S_dev, PhaseTimer& pt, long long& comp_launches) {
     const int64_t n = s->n;
-    cudaStream_t st = ctx->st;
+    cudaStream_t st = ctx->st, ps = ctx->pst;
     csgs_status r;
     const SceneDev sd = scene_dev(*s);
     set_u64(ctx->d_nconst, (unsigned long long)n, st);
     CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
     if (ko.resolution == CSGS_RES_SCENE) CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA, 0, sizeof(double), st));
     if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev_start, st));
+    CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_start, 0));
     bool freed_recorded[kBinSlots] = {};
-    int view = 0;
-    for (int v0 = v0_all; v0 < v1_all; v0 += vb) {
+    bool set_used[2] = {false, false};
+    int view = 0, batch = 0;
+    for (int v0 = v0_all; v0 < v1_all; v0 += vb, ++batch) {
         const int nb = (v1_all - v0) < vb ? (v1_all - v0) : vb;
-        size_t e0 = pt.begin(st);
-        launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
-                       P<uint2>(ctx->rects), st);
-        pt.end(0, e0, st);
-        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_proj, st));
+        const int set = batch & 1;
+        if (set_used[set]) CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_setfree[set], 0));
+        size_t e0 = pt.begin(ps);
+        launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats[set]), P<uint32_t>(ctx->keys[set]),
+                       P<uint2>(ctx->rects[set]), ps);
+        pt.end(0, e0, ps);
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_proj[set], ps));
         for (int k = 0; k < nb; ++k, ++view) {
             const CamDev& cam = s->cams[v0 + k];
             const int sl = view % kBinSlots;
             BinSlot& slot = ctx->slot[sl];
-            uint32_t* keys_v = P<uint32_t>(ctx->keys) + (size_t)k * n;
-            const uint2* rects_v = P<uint2>(ctx->rects) + (size_t)k * n;
-            CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, ctx->ev_proj, 0));
+            uint32_t* keys_v = P<uint32_t>(ctx->keys[set]) + (size_t)k * n;
+            const uint2* rects_v = P<uint2>(ctx->rects[set]) + (size_t)k * n;
+            CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, ctx->ev_proj[set], 0));
             if (freed_recorded[sl]) CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, slot.freed, 0));
             size_t e1 = pt.begin(slot.st);
             const uint32_t* iv = bin_view(ctx, sl, n, keys_v, rects_v, cam, slot.st);
@@ -600,7 +627,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             CompositeArgs a{};
             a.ranges = P<uint2>(slot.ranges);
             a.inst_gid = iv;
-            a.splats = P<Splat>(ctx->splats) + (size_t)k * n;
+            a.splats = P<Splat>(ctx->splats[set]) + (size_t)k * n;
             a.n_gauss = (int)n;
             a.cam = cam;
             a.o = ko;
@@ -620,6 +647,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             freed_recorded[sl] = true;
             ++comp_launches;
         }
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_setfree[set], st));
+        set_used[set] = true;
         if ((r = launch_check(ctx, "score kernels"))) return r;
     }
     if (ko.resolution == CSGS_RES_SCENE) scene_normalise(s_dev, n, &ctx->d_ctr->sumA, st);
@@ -987,13 +1016,13 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
             CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
             scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         }
-        launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
-                       P<uint2>(ctx->rects), st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam, st);
+        launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
+                       P<uint2>(ctx->rects[0]), st);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
-        a.splats = P<Splat>(ctx->splats);
+        a.splats = P<Splat>(ctx->splats[0]);
         a.n_gauss = (int)n;
         a.cam = cam;
         a.o = ko;
@@ -1087,13 +1116,13 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
         scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
-        launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
-                       P<uint2>(ctx->rects), st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam, st);
+        launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
+                       P<uint2>(ctx->rects[0]), st);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
-        a.splats = P<Splat>(ctx->splats);
+        a.splats = P<Splat>(ctx->splats[0]);
         a.n_gauss = (int)n;
         a.cam = cam;
         a.o = ko;
@@ -1399,13 +1428,13 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
             CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
             scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         }
-        launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats), P<uint32_t>(ctx->keys),
-                       P<uint2>(ctx->rects), st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys), P<uint2>(ctx->rects), cam, st);
+        launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
+                       P<uint2>(ctx->rects[0]), st);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
-        a.splats = P<Splat>(ctx->splats);
+        a.splats = P<Splat>(ctx->splats[0]);
         a.n_gauss = (int)n;
         a.cam = cam;
         a.o = ko;

@@ -51,6 +51,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Single-instruction approximations (relative error ~2^-22) for the conservative culling
+// bounds, which carry margins far larger than that.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 struct Shared {
     float4 A[kThreads];  // s1, s1k, c1, s2
     float4 B[kThreads];  // c2, log2 alpha, thr, cw = obj_w . rgb
@@ -104,12 +122,13 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
     // (sqrt(R - (s2 v)^2) - s1k v) / s1 is concave in v with its maximum at
     // v* = -s1k sqrt(R) / (s2 sqrt(s1k^2 + s2^2)) (the left end mirrors it at -v*), so
     // clamping v* to the interval gives the band's extreme.  R and every bound are
-    // padded so that FP32 rounding never drops a pixel that passes the test.
+    // padded so that FP32 rounding (and the approximate square roots and reciprocals)
+    // never drops a pixel that passes the test.
     const float R = fmaf(fmaxf(c.w - q.w, 0.f), 1.002f, 1e-5f);
-    const float sR = sqrtf(R);
-    const float i1 = 1.f / s1, i2 = 1.f / s2;
+    const float sR = sqrt_approx(R);
+    const float i1 = rcp_approx(s1), i2 = rcp_approx(s2);
     const float vmax = sR * i2 * 1.001f + 0.01f;
-    const float vstar = -s1k * sR * i2 / sqrtf(fmaf(s1k, s1k, s2 * s2));
+    const float vstar = -s1k * sR * i2 * rsqrt_approx(fmaf(s1k, s1k, s2 * s2));
     uint32_t mk = 0u;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -119,8 +138,8 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
         const float vr = fminf(fmaxf(vstar, va), vb);
         const float vl = fminf(fmaxf(-vstar, va), vb);
         const float er = s2 * vr, el = s2 * vl;
-        const float wr = sqrtf(fmaxf(fmaf(-er, er, R), 0.f));
-        const float wl = sqrtf(fmaxf(fmaf(-el, el, R), 0.f));
+        const float wr = sqrt_approx(fmaxf(fmaf(-er, er, R), 0.f));
+        const float wl = sqrt_approx(fmaxf(fmaf(-el, el, R), 0.f));
         const float xr = mx + (wr - s1k * vr) * i1;
         const float xl = mx - (wl + s1k * vl) * i1;
         const float pad = 0.02f + 1e-3f * (wr + wl) * i1;
