@@ -60,6 +60,12 @@ def workload(name: str):
     return scene, cams
 
 
+# --score-resolution: (library code, description) of the query resolutions of Sec. 3.5
+SCORE_RESOLUTIONS = {"pixel": (0, "per-pixel (max over pixel-rays)"), "scene": (1, "per-scene (one query)"),
+                     "channel": (2, "per-channel (max over pixel-ray channels)"),
+                     "tile": (3, "per-tile (max over 16x16 tiles)"), "image": (4, "per-image (max over views)")}
+
+
 def describe(name, scene, cams):
     W, H = int(cams[0][16]), int(cams[0][17])
     return {"workload": name, "n_gaussians": scene.n, "sh_degree": scene.sh_degree, "views": len(cams),
@@ -280,6 +286,9 @@ def run_ours(args):
     if args.max_views:
         cams = cams[: args.max_views]
     cfg = describe(args.workload, scene, cams)
+    res_id, res_name = SCORE_RESOLUTIONS[args.score_resolution]
+    if args.score_resolution != "pixel":
+        cfg["resolution"] = res_name
     m = cfg["coreset_m"]
     stream = torch.cuda.Stream(device=local)
     ctx = csgs.Context(local, stream=stream)
@@ -293,9 +302,9 @@ def run_ours(args):
         cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1]}
 
     # pair counts of one pass (untimed; counting kernels are slower)
-    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch), out=s)
+    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch, resolution=res_id), out=s)
     cnt = ctx.stats()
-    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch)
+    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch, resolution=res_id)
 
     def step(seed):
         ctx.score(sid, timing, out=s)
@@ -341,7 +350,7 @@ def run_ours(args):
         def e2e_step(seed):
             sid2 = ctx.load_scene_ptrs(scene.n, scene.sh_degree, [h.data_ptr() for h in host], is_device=False)
             ctx.set_queries(sid2, cams)
-            s2, _ = ctx.score(sid2, csgs.default_opts(), out=s)
+            s2, _ = ctx.score(sid2, csgs.default_opts(resolution=res_id), out=s)
             idx, w = ctx.sample_coreset(s2, m, seed)
             with torch.cuda.stream(stream):
                 s_host.copy_(s2, non_blocking=True)
@@ -374,7 +383,7 @@ def run_ours(args):
     ess_achieved = ess_step / launches_step / avg_launch_s / 1e12 if avg_launch_s > 0 else None
     peak = SMS * FP32_LANES * 2032e6 / 1e12
     traffic, stale = traffic_per_launch()
-    roof = {"bound": "alu", "kernel": "k_composite<score, per-pixel>", "achieved": achieved, "peak": peak,
+    roof = {"bound": "alu", "kernel": f"k_composite<score, {args.score_resolution}>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock); one FP32-pipe op per lane per "
                            "clock; 18 ops per evaluated pair and pass (see DESIGN.md)",
@@ -777,6 +786,8 @@ def main():
     ap.add_argument("--mlp", action="store_true", help="surrogate network tensor-core report")
     ap.add_argument("--mlp-rows", type=int, default=3_000_000)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--score-resolution", default="pixel", choices=list(SCORE_RESOLUTIONS),
+                    help="query resolution of the timed scoring (Sec. 3.5); the headline is per-pixel")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

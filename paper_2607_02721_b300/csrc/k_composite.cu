@@ -300,38 +300,42 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                 }
             }
         } else {
-            // summed resolutions: warp-uniform loop so the warp can sum a per Gaussian
+            // summed resolutions: warp-uniform loop over chunks of 16 entries; the warp's sum
+            // of each entry's terms comes from one vector-halving butterfly per chunk
             bool act = !done;
             if (__any_sync(0xffffffffu, act)) {
-                for (int k = 0; k < nw; ++k) {
-                    const int j = sh.wl[warp][k];
-                    float v = 0.f;
-                    if (act) {
-                        const float4 Aj = sh.A[j];
-                        const float4 Bj = sh.B[j];
-                        const float p = exponent2(Aj, Bj, X, Y);
-                        if (STATS) ++n_eval;
-                        if (p >= Bj.z) {
-                            const float r = fminf(rho_max, ex2_approx(p));
-                            if (STATS) ++n_hit;
-                            const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
-                            if (Tn < t_min) {
-                                act = false;
-                                done = true;
-                            } else {
-                                const float w = __fmul_rn(r, T);
-                                const float4 Cj = sh.C[j];
-                                accumulate<MODE, VAR>(A0, A1, A2, Cj, w);
-                                v = pixel_term<VAR>(w, Bj, Cj);
-                                T = Tn;
+                for (int k0 = 0; k0 < nw; k0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        v[u] = 0.f;
+                        if (k0 + u < nw && act) {
+                            const int j = sh.wl[warp][k0 + u];
+                            const float4 Aj = sh.A[j];
+                            const float4 Bj = sh.B[j];
+                            const float p = exponent2(Aj, Bj, X, Y);
+                            if (STATS) ++n_eval;
+                            if (p >= Bj.z) {
+                                const float r = fminf(rho_max, ex2_approx(p));
+                                if (STATS) ++n_hit;
+                                const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
+                                if (Tn < t_min) {
+                                    act = false;
+                                    done = true;
+                                } else {
+                                    const float w = __fmul_rn(r, T);
+                                    const float4 Cj = sh.C[j];
+                                    accumulate<MODE, VAR>(A0, A1, A2, Cj, w);
+                                    v[u] = pixel_term<VAR>(w, Bj, Cj);
+                                    T = Tn;
+                                }
                             }
                         }
                     }
-                    if (__any_sync(0xffffffffu, v > 0.f)) {
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (lane == 0) sh.part[warp][j] = v;
-                    }
+                    const float cs = warp_colsum16(v, lane);
+                    const int c = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                                  ((lane >> 1) & 1);
+                    if ((lane & 1) == 0 && k0 + c < nw) sh.part[warp][sh.wl[warp][k0 + c]] = cs;
                     if (!__any_sync(0xffffffffu, act)) break;
                 }
             }

@@ -193,32 +193,6 @@ __device__ __forceinline__ void mma_tile_k(uint32_t d, const unsigned char* a, i
     tc::commit(bar);
 }
 
-// Sum of 16 per-lane values over the warp's 32 lanes, one column per lane pair:
-// vector-halving butterfly (8 + 4 + 2 + 1 + 1 shuffles).  Returns the sum of column
-// 8 b4 + 4 b3 + 2 b2 + b1 (b_k = bit k of the lane index), held by lanes 2c and 2c + 1.
-__device__ __forceinline__ float warp_colsum16(const float (&v)[16], int lane) {
-    float a[8], b[4], c[2];
-    const bool h1 = lane & 16, h2 = lane & 8, h3 = lane & 4, h4 = lane & 2;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float send = h1 ? v[i] : v[i + 8];
-        a[i] = (h1 ? v[i + 8] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float send = h2 ? a[i] : a[i + 4];
-        b[i] = (h2 ? a[i + 4] : a[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float send = h3 ? b[i] : b[i + 2];
-        c[i] = (h3 ? b[i + 2] : b[i]) + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    const float send = h4 ? c[0] : c[1];
-    float d = (h4 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, send, 2);
-    return d + __shfl_xor_sync(0xffffffffu, d, 1);
-}
-
 // 512 threads: warp w reads TMEM lanes 32 (w % 4).. and handles column quarter w / 4.
 // TRAIN additionally stores z1 (FP32), h1 (BF16) and dz2 = d loss / d z2 (BF16) per row
 // (loss = mean (y - t)^2 over the B rows) and accumulates d/dw3, d/db3 and the loss.
