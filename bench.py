@@ -298,7 +298,7 @@ def run_ours(args):
     tuned = None
     if not args.no_autotune and not args.view_batch:
         # view batch and radix-sort grid picked by the library's autotuner (untimed)
-        tuned = ctx.autotune(sid, csgs.default_opts(), probe_views=8)
+        tuned = ctx.autotune(sid, csgs.default_opts(), probe_views=16)
         cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1]}
 
     # pair counts of one pass (untimed; counting kernels are slower)

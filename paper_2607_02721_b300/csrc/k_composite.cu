@@ -4,9 +4,11 @@
 //
 // Each thread owns one pixel; a warp covers an 8x4 pixel block.  The tile's
 // depth-sorted splat list is staged through shared memory 256 records at a time.
-// While staging, each splat gets a mask of the warp blocks its footprint's bounding
-// box touches, and every warp compacts the batch into its own list, so a warp only
-// evaluates splats that can reach one of its pixels.
+// While staging, each splat gets a mask of the warp blocks its footprint reaches (the
+// ellipse's exact extent over each 4-row band), and every warp compacts the batch into
+// its own list, so a warp only evaluates splats that can reach one of its pixels.
+// Pass 2 of the two-pass modes reuses pass 1's masks (one 8-bit mask per tile-list entry
+// kept in global memory).
 //
 // Per (pixel, splat) the kernel evaluates, in tile-centred pixel coordinates (X, Y),
 //   e1 = s1 X + s1k Y + c1,  e2 = s2 Y + c2,  p = log2(alpha) - e1^2 - e2^2
@@ -22,8 +24,9 @@
 // imp = a / A per Gaussian: warp max with redux.sync on the float bits (imp >= 0, so
 // unsigned order = float order), a shared-memory max across the CTA's warps, and one
 // global atomicMax per (tile, Gaussian).
-// Score (per-scene resolution) is one pass: warp sums of a, one global atomicAdd per
-// (tile, Gaussian), and the CTA's sum of A added to an FP64 total.
+// Score (per-scene, per-image and per-tile resolutions) is one pass: warp sums of a (16
+// entries per vector-halving butterfly), one global atomicAdd per (tile, Gaussian), and the
+// CTA's sum of A added to an FP64 total.
 #include "csgs_internal.cuh"
 
 namespace csgs {
