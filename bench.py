@@ -392,6 +392,8 @@ def run_ours(args):
             "pairs_per_ray": (cnt["pairs_evaluated"] / cfg["rays_per_step"]),
             "pairs_per_ray_pass2": (cnt["pairs_evaluated2"] / cfg["rays_per_step"]),
             "contributing_pairs_per_ray": (cnt["pairs_hit"] / cfg["rays_per_step"]),
+            "staged_fraction": [cnt["entries_staged"] / max(cnt["instances"], 1),
+                                cnt["entries_staged2"] / max(cnt["instances"], 1)],
             "share_of_step": comp_ms / max(el_ms, 1e-9)}
     if stale:
         roof["traffic_note"] = "ncu counters predate the current kernel source"

@@ -122,6 +122,8 @@ typedef struct {
     double project_ms;        /* phase totals (bit 1) */
     double sort_ms;
     double composite_ms;
+    int64_t entries_staged;   /* tile-list entries staged by compositing pass 1 (bit 0) */
+    int64_t entries_staged2;  /* tile-list entries staged by pass 2 (bit 0) */
 } csgs_stats;
 
 /* Fill *o with the default conventions above. */

@@ -744,6 +744,8 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     ctx->stats.kernel_launches = launches() - l0;
     ctx->stats.composite_launches = comp_launches;
     ctx->stats.queries = (int64_t)ctx->h_ctr->queries;
+    ctx->stats.entries_staged = (int64_t)ctx->h_ctr->staged1;
+    ctx->stats.entries_staged2 = (int64_t)ctx->h_ctr->staged2;
     {
         double ph[3] = {0.0, 0.0, 0.0};
         pt.sum(ph);

@@ -113,6 +113,8 @@ struct DevCounters {
     double sumA;                    // scene resolution: sum of the objective over queries
     double sumA_view;               // image resolution: the current view's objective
     unsigned long long queries;     // pixel queries with A > 0 (two-pass resolutions)
+    unsigned long long staged1;     // tile-list entries staged by compositing pass 1 (counting runs)
+    unsigned long long staged2;     // ... and by pass 2
 };
 
 // ---- launchers (k_project.cu)

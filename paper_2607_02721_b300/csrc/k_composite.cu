@@ -508,6 +508,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             h2 += __shfl_xor_sync(0xffffffffu, h2, o);
             vv += __shfl_xor_sync(0xffffffffu, vv, o);
         }
+        if (tid == 0) {
+            atomicAdd(&a.ctr->staged1, (unsigned long long)processed);
+            if (two_pass(MODE)) atomicAdd(&a.ctr->staged2, (unsigned long long)sh.last);
+        }
         if (lane == 0) {
             if (e) atomicAdd(&a.ctr->pairs_eval, e);
             if (h) atomicAdd(&a.ctr->pairs_hit, h);
