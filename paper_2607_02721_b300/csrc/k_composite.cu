@@ -441,13 +441,13 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             stage<MODE, 2>(a, sh, start + b + tid, rg.y, cx, cy);
             __syncthreads();
             const int cnt = min(kThreads, n2 - b);
-            const int nw = warp_list(sh, cnt, warp, lane);
             const int lim = max(0, min(cnt, last - b));
+            // the warp's list holds only entries below its lanes' largest contributor bound
             const int jw = (int)__reduce_max_sync(0xffffffffu, (unsigned)lim);
+            const int nw = warp_list(sh, jw, warp, lane);
 #pragma unroll 4
             for (int k = 0; k < nw; ++k) {
                 const int j = sh.wl[warp][k];
-                if (j >= jw) break;  // the list is in increasing j; warp-uniform
                 // branch-free: every lane evaluates the entry and keeps the result only where
                 // it is one of its pass-1 contributors (the warp takes this path anyway as
                 // soon as one lane contributes)
