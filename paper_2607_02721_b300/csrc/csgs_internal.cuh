@@ -149,7 +149,6 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_
                     unsigned long long* n_inst, cudaStream_t st);
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
                  cudaStream_t st);
-void iota_u32(uint32_t* v, int n, cudaStream_t st);
 void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 
 // ---- compositing (k_composite.cu)

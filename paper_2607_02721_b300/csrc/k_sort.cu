@@ -372,11 +372,6 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long 
     if (t > 0) ranges[t - 1].y = lo;
 }
 
-__global__ void k_iota(uint32_t* v, int n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = (uint32_t)i;
-}
-
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
 
 }  // namespace
@@ -427,11 +422,6 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
                  cudaStream_t st) {
     k_ranges<<<(n_tiles + 1 + 255) / 256, 256, 0, st>>>(keys, d_n, n_max, ranges, (uint32_t)n_tiles);
-    count_launches(1);
-}
-
-void iota_u32(uint32_t* v, int n, cudaStream_t st) {
-    k_iota<<<(n + 255) / 256, 256, 0, st>>>(v, n);
     count_launches(1);
 }
 

@@ -99,3 +99,19 @@ def test_fullsize_exact_sensitivity_two_views(setup):
         else:
             assert abs(s[g] - s_exact[g]) <= S_RTOL * s_exact[g], (g, s[g], s_exact[g])
     ctx.free_scene(sid2)
+
+
+def test_fullsize_resolution_chain_and_scene_total(setup):
+    """At full size: the per-scene scores sum to 1 (one query, Sec. 3.5), and every
+    Gaussian's score can only grow from per-scene to per-image to per-pixel (a max of
+    ratios dominates the ratio of sums: the mediant inequality)."""
+    scene, cams, sa, ctx, sid = setup
+    s_scene, S_scene = ctx.score(sid, csgs.default_opts(resolution=csgs.RES_SCENE))
+    assert abs(S_scene - 1.0) < 1e-4
+    s_scene = s_scene.cpu().numpy().astype(np.float64)
+    s_image = ctx.score(sid, csgs.default_opts(resolution=csgs.RES_IMAGE))[0].cpu().numpy().astype(np.float64)
+    s_pixel = ctx.score(sid)[0].cpu().numpy().astype(np.float64)
+    tol = 1e-4
+    assert np.all(s_image >= s_scene * (1 - tol) - 1e-12)
+    assert np.all(s_pixel >= s_image * (1 - tol) - 1e-12)
+    assert np.all(s_pixel[s_scene > 0] > 0)  # a Gaussian that contributes anywhere has s > 0
