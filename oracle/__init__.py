@@ -110,6 +110,7 @@ def lib():
         P = ctypes.c_void_p
         _lib.or_project.argtypes = [P, P, P, P, P]
         _lib.or_render.argtypes = [P, P, P, P, ctypes.c_int64, P, P, P, P, P, P]
+        _lib.or_render_tiled.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, P, P, P]
         _lib.or_pixel_terms.argtypes = [P, P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                         P, P, P, P, P]
         _lib.or_pixel_terms.restype = ctypes.c_int64
@@ -214,6 +215,25 @@ def render(scene, cam, opts: Opts | None = None, w=None, pixels=None):
     if rc:
         raise MemoryError("oracle render failed")
     return dict(rgb=rgb, T=T, n_terms=nt, flags=fl, violations=int(cnt[0]), flagged=int(cnt[1]))
+
+
+def render_tiled(scene, cam, tile_w: int, tile_h: int, opts: Opts | None = None, w=None):
+    """The whole camera rendered by tiles of tile_w x tile_h pixels (each pixel composites
+    only its tile's list).  Returns dict with rgb [H,W,3], T, n_terms."""
+    sa = _scene(scene)
+    opts = opts or Opts()
+    cam = _cam(cam)
+    W, H = int(cam[16]), int(cam[17])
+    rgb = np.zeros((H, W, 3), dtype=np.float64)
+    T = np.zeros((H, W), dtype=np.float64)
+    nt = np.zeros((H, W), dtype=np.int32)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    oc = opts.c()
+    rc = lib().or_render_tiled(ctypes.byref(sa.c), _ptr(cam), ctypes.byref(oc), _ptr(w), tile_w, tile_h, _ptr(rgb),
+                               _ptr(T), _ptr(nt))
+    if rc:
+        raise MemoryError("oracle tiled render failed")
+    return dict(rgb=rgb, T=T, n_terms=nt)
 
 
 def pixel_terms(scene, cam, px: int, py: int, opts: Opts | None = None, w=None, cap: int = 1 << 16):

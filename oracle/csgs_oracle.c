@@ -359,12 +359,17 @@ typedef struct {
 
 static int near_rel(double v, double thr, double band) { return fabs(v - thr) <= band * fabs(thr); }
 
-/* Composite one pixel of one view: the definition of Sec. 3 written out. */
-static void pixel_composite(const oview* v, const or_opts* o, double px, double py, obuf* b, opix* r) {
+/* Composite one pixel of one view: the definition of Sec. 3 written out.  The
+ * candidates are all Gaussians (list == NULL) or the nlist Gaussians of list (the tiled
+ * traversal); the test, the order and the compositing are the same either way. */
+static void pixel_composite_from(const oview* v, const or_opts* o, double px, double py, const int64_t* list,
+                                 int64_t nlist, obuf* b, opix* r) {
     int64_t nc = 0;
     memset(r, 0, sizeof(*r));
     r->T = 1.0;
-    for (int64_t i = 0; i < v->n; ++i) {
+    const int64_t ncand = list ? nlist : v->n;
+    for (int64_t q = 0; q < ncand; ++q) {
+        const int64_t i = list ? list[q] : q;
         if (!v->valid[i]) continue;
         double dx = px - v->mx[i];
         if (fabs(dx) > v->rx[i]) continue;
@@ -417,6 +422,10 @@ static void pixel_composite(const oview* v, const or_opts* o, double px, double 
     r->n_terms = nt;
 }
 
+static void pixel_composite(const oview* v, const or_opts* o, double px, double py, obuf* b, opix* r) {
+    pixel_composite_from(v, o, px, py, NULL, 0, b, r);
+}
+
 /* ---------------------------------------------------------------- render */
 
 /* Render pixels of one camera.  pix: optional list of npix (x, y) pairs; when NULL
@@ -455,6 +464,78 @@ int or_render(const or_scene* sc, const float* cam, const or_opts* o, const doub
         counters[0] += viol;
         counters[1] += nflag;
     }
+    free_view(&v);
+    return 0;
+}
+
+/* The same render by tiles (the rasteriser's traversal): every valid Gaussian is listed
+ * in the tiles of tile_w x tile_h pixels its footprint box [mx - rx, mx + rx] x
+ * [my - ry, my + ry] reaches, and each pixel composites only its tile's list.  Since the
+ * box contains every pixel of the footprint test, this must equal or_render exactly
+ * (reading: results do not depend on tiling). */
+int or_render_tiled(const or_scene* sc, const float* cam, const or_opts* o, const double* w, int32_t tile_w,
+                    int32_t tile_h, double* rgb, double* Tout, int32_t* nterms) {
+    if (tile_w < 1 || tile_h < 1) return -1;
+    oview v;
+    ocam cm;
+    if (build_view(sc, cam, o, w, &v, &cm)) return -1;
+    const int tx_n = (cm.W + tile_w - 1) / tile_w, ty_n = (cm.H + tile_h - 1) / tile_h;
+    const int64_t ntiles = (int64_t)tx_n * ty_n;
+    int64_t* count = (int64_t*)calloc((size_t)ntiles + 1, sizeof(int64_t));
+    if (!count) {
+        free_view(&v);
+        return -1;
+    }
+    /* two sweeps over the Gaussians: count per tile, then fill (index order within a tile) */
+    int64_t* start = (int64_t*)calloc((size_t)ntiles + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < v.n; ++i) {
+        if (!v.valid[i]) continue;
+        int x0 = (int)floor((v.mx[i] - v.rx[i]) / tile_w), x1 = (int)floor((v.mx[i] + v.rx[i]) / tile_w);
+        int y0 = (int)floor((v.my[i] - v.ry[i]) / tile_h), y1 = (int)floor((v.my[i] + v.ry[i]) / tile_h);
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 >= tx_n) x1 = tx_n - 1;
+        if (y1 >= ty_n) y1 = ty_n - 1;
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) count[(int64_t)ty * tx_n + tx]++;
+    }
+    for (int64_t t = 0; t < ntiles; ++t) start[t + 1] = start[t] + count[t];
+    int64_t* list = (int64_t*)malloc(sizeof(int64_t) * (size_t)(start[ntiles] > 0 ? start[ntiles] : 1));
+    memset(count, 0, sizeof(int64_t) * (size_t)ntiles);
+    for (int64_t i = 0; i < v.n; ++i) {
+        if (!v.valid[i]) continue;
+        int x0 = (int)floor((v.mx[i] - v.rx[i]) / tile_w), x1 = (int)floor((v.mx[i] + v.rx[i]) / tile_w);
+        int y0 = (int)floor((v.my[i] - v.ry[i]) / tile_h), y1 = (int)floor((v.my[i] + v.ry[i]) / tile_h);
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 >= tx_n) x1 = tx_n - 1;
+        if (y1 >= ty_n) y1 = ty_n - 1;
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) {
+                const int64_t t = (int64_t)ty * tx_n + tx;
+                list[start[t] + count[t]++] = i;
+            }
+    }
+    const int64_t total = (int64_t)cm.W * cm.H;
+#pragma omp parallel
+    {
+        obuf b = {0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < total; ++q) {
+            const int px = (int)(q % cm.W), py = (int)(q / cm.W);
+            const int64_t t = (int64_t)(py / tile_h) * tx_n + px / tile_w;
+            opix r;
+            pixel_composite_from(&v, o, px, py, list + start[t], start[t + 1] - start[t], &b, &r);
+            for (int ch = 0; ch < 3; ++ch) rgb[3 * q + ch] = r.A[ch];
+            if (Tout) Tout[q] = r.T;
+            if (nterms) nterms[q] = (int32_t)r.n_terms;
+        }
+        free(b.cand);
+        free(b.terms);
+    }
+    free(list);
+    free(start);
+    free(count);
     free_view(&v);
     return 0;
 }
