@@ -34,9 +34,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "composite_score_traffic.md")
 COMPOSITE_SRC = os.path.join(ROOT, "paper_2607_02721_b300", "csrc", "k_composite.cu")
 
 # Algorithmic work of the compositing kernel: 18 FP32 instructions per evaluated (ray,
-# Gaussian) pair and pass (the per-pair figure of the scoring path's contract: quadratic
-# form, cut test, exp, clamp, alpha_min test, 1 - rho, T update, t_min test, rho T and the
-# colour / score terms), times the pairs each pass evaluates (device counters).
+# Gaussian) pair and pass (quadratic form, cut test, exp, clamp, alpha_min test, 1 - rho,
+# T update, t_min test, rho T and the colour / score terms, as a plain per-pair
+# implementation executes them), times the pairs each pass evaluates (device counters).
 OPS_PER_PAIR = 18
 # The kernel's own essential count (reported beside it): the footprint test is 6 ops
 # (5 FFMA for log2 alpha - e1^2 - e2^2, 1 FSETP); a pass-1 contribution adds 8 (FMNMX,
@@ -386,7 +386,7 @@ def run_ours(args):
     roof = {"bound": "alu", "kernel": f"k_composite<score, {args.score_resolution}>", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock); one FP32-pipe op per lane per "
-                           "clock; 18 ops per evaluated pair and pass (see DESIGN.md)",
+                           "clock; 18 FP32 instructions per evaluated (ray, Gaussian) pair and pass",
             "ops_per_launch": ops_launch, "avg_launch_ms": avg_launch_s * 1e3,
             "essential_ops_frac": (ess_achieved / peak) if ess_achieved else None,
             "pairs_per_ray": (cnt["pairs_evaluated"] / cfg["rays_per_step"]),

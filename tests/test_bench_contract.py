@@ -1,5 +1,5 @@
 """The benchmark's reference arm (the FP64 oracle on the host cores) prints one JSON line
-with the fields the benchmark contract names; runs on CPU."""
+with the benchmark's fields; runs on CPU."""
 import json
 import os
 import subprocess

@@ -30,11 +30,11 @@ STATS = {}
 
 @pytest.fixture(scope="module", autouse=True)
 def _error_stats():
-    """Collects the observed GPU-vs-oracle error magnitudes and writes them next to
-    the run's other outputs (when a gpurun_out folder exists)."""
+    """Collects the observed GPU-vs-oracle error magnitudes and writes them to
+    $CSGS_TEST_REPORT_DIR/parity_stats.json when that variable names a folder."""
     yield
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("CSGS_TEST_REPORT_DIR", "")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "parity_stats.json"), "w") as f:
             json.dump(STATS, f, indent=1)
 

@@ -10,8 +10,8 @@ it can never enter the coreset.  The test measures, on a seeded scene:
     better than an untrained network of the same shape (Spearman 0.18 against 0.00 when
     this was written: a weak but real signal from four scored views);
   - quality: the PSNR of the 90%-pruned render with the subset's scores alone, with the
-    surrogate's, and with the exact scores.  These are recorded (gpurun_out, when
-    present) and bounded loosely; on these synthetic scenes the surrogate does not beat
+    surrogate's, and with the exact scores.  These are recorded (in $CSGS_TEST_REPORT_DIR
+    when set) and bounded loosely; on these synthetic scenes the surrogate does not beat
     the subset alone in PSNR.
 """
 import json
@@ -83,8 +83,8 @@ def test_surrogate_gain_over_subset_scores(ctx, torch):
               "spearman_trained": r_trained, "spearman_untrained": r_untrained, "psnr": psnr,
               "gain_psnr_vs_subset": psnr["surrogate"] - psnr["subset_only"],
               "delta_psnr_vs_exact": psnr["surrogate"] - psnr["exact"]}
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("CSGS_TEST_REPORT_DIR", "")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "surrogate_gain.json"), "w") as f:
             json.dump(report, f, indent=1)
     assert psnr["surrogate"] > psnr["subset_only"] - 1.0, report
