@@ -73,11 +73,15 @@ struct csgs_ctx {
     cudaEvent_t ev_start = nullptr;       // enqueue start on the context's stream
     cudaEvent_t ev_proj[2] = {};          // projection of the batch in buffer set k done
     cudaEvent_t ev_setfree[2] = {};       // last compositing that read buffer set k done
+    cudaStream_t cst = nullptr;           // second compositing stream (odd views)
+    cudaEvent_t ev_csetfree[2] = {};      // ... its last compositing that read buffer set k done
+    cudaEvent_t ev_cdone = nullptr;       // ... its last compositing of a scene done
     uint32_t cap = 0;
     int sort_blocks = kSortBlocks;  // radix-sort grid (autotuned)
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
     DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
-    DevBuf mskb;        // pixel / channel resolution: warp mask per instance (pass 1 -> pass 2)
+    DevBuf mskb, mskb2;  // pixel / channel resolution: warp mask per instance (pass 1 -> pass 2), per stream
+    DevBuf tsum2;        // tile resolution: the second compositing stream's per-instance sums
     // surrogate model
     bool mlp_ready = false;
     DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1, mPart;
@@ -338,10 +342,13 @@ csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
         }
     }
     bool ev_ok = cudaStreamCreateWithFlags(&ctx->pst, cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
+                 cudaStreamCreateWithFlags(&ctx->cst, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ctx->ev_cdone, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < 2 && ev_ok; ++k)
         ev_ok = cudaEventCreateWithFlags(&ctx->ev_proj[k], cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventCreateWithFlags(&ctx->ev_setfree[k], cudaEventDisableTiming) == cudaSuccess;
+                cudaEventCreateWithFlags(&ctx->ev_setfree[k], cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_csetfree[k], cudaEventDisableTiming) == cudaSuccess;
     if (!ev_ok) {
         csgs_destroy(ctx);
         return CSGS_E_CUDA;
@@ -375,16 +382,19 @@ void csgs_destroy(csgs_ctx* ctx) {
     for (int k = 0; k < 2; ++k) {
         if (ctx->ev_proj[k]) cudaEventDestroy(ctx->ev_proj[k]);
         if (ctx->ev_setfree[k]) cudaEventDestroy(ctx->ev_setfree[k]);
+        if (ctx->ev_csetfree[k]) cudaEventDestroy(ctx->ev_csetfree[k]);
         release(ctx->splats[k]);
         release(ctx->keys[k]);
         release(ctx->rects[k]);
     }
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+    if (ctx->ev_cdone) cudaEventDestroy(ctx->ev_cdone);
     if (ctx->pst) cudaStreamDestroy(ctx->pst);
+    if (ctx->cst) cudaStreamDestroy(ctx->cst);
     DevBuf* bufs[] = {
                       &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
-                      &ctx->mskb,
+                      &ctx->mskb,   &ctx->mskb2,   &ctx->tsum2,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
                       &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
                       &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->mPart,   &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
@@ -583,8 +593,12 @@ namespace {
 //     that last read that set (batch b - 2) is done, so it runs ahead of the compositing;
 //   - binning: view k in slot k % kBinSlots on the slot's high-priority stream, after the
 //     projection of its batch and the compositing that last read the slot;
-//   - compositing and the reductions on the context's stream, each view after its
-//     binning.
+//   - compositing of even views on the context's stream and of odd views on a second
+//     stream (ctx->cst), each view after its binning, so that the last tiles of one view
+//     overlap the first of the next (the score reductions are max or sum atomics; the
+//     per-instance pass-1 buffers exist once per stream); the image resolution, whose
+//     per-view fold needs the views in turn, composites on the context's stream only;
+//   - the reductions on the context's stream, after both compositing streams.
 // Every side stream's last operation is waited on by the context's stream (the capture
 // joins them).
 csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int vb, int v0_all, int v1_all,
@@ -599,13 +613,18 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
     if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev_start, st));
     CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_start, 0));
+    const bool dual = ko.resolution != CSGS_RES_IMAGE && v1_all - v0_all > 1;
+    if (dual) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->cst, ctx->ev_start, 0));
     bool freed_recorded[kBinSlots] = {};
     bool set_used[2] = {false, false};
     int view = 0, batch = 0;
     for (int v0 = v0_all; v0 < v1_all; v0 += vb, ++batch) {
         const int nb = (v1_all - v0) < vb ? (v1_all - v0) : vb;
         const int set = batch & 1;
-        if (set_used[set]) CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_setfree[set], 0));
+        if (set_used[set]) {
+            CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_setfree[set], 0));
+            if (dual) CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_csetfree[set], 0));
+        }
         size_t e0 = pt.begin(ps);
         launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats[set]), P<uint32_t>(ctx->keys[set]),
                        P<uint2>(ctx->rects[set]), ps);
@@ -623,7 +642,9 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             const uint32_t* iv = bin_view(ctx, sl, n, keys_v, rects_v, cam, slot.st);
             pt.end(1, e1, slot.st);
             CUDA_TRY(ctx, cudaEventRecord(slot.ready, slot.st));
-            CUDA_TRY(ctx, cudaStreamWaitEvent(st, slot.ready, 0));
+            const bool second = dual && (view & 1);
+            cudaStream_t cs = second ? ctx->cst : st;
+            CUDA_TRY(ctx, cudaStreamWaitEvent(cs, slot.ready, 0));
             CompositeArgs a{};
             a.ranges = P<uint2>(slot.ranges);
             a.inst_gid = iv;
@@ -633,23 +654,28 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             a.o = ko;
             a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
             a.s_sum = ko.resolution == CSGS_RES_IMAGE ? P<float>(ctx->vbuf) : s_dev;
-            a.tile_sum = P<float>(ctx->tsum);
-            a.mskbuf = P<uint8_t>(ctx->mskb);
+            a.tile_sum = P<float>(second ? ctx->tsum2 : ctx->tsum);
+            a.mskbuf = P<uint8_t>(second ? ctx->mskb2 : ctx->mskb);
             a.ctr = ctx->d_ctr;
             a.stats = stats & 1;
             if (ko.resolution == CSGS_RES_IMAGE)
                 CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
-            size_t e2 = pt.begin(st);
-            launch_composite_score(a, st);
+            size_t e2 = pt.begin(cs);
+            launch_composite_score(a, cs);
             if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
-            pt.end(2, e2, st);
-            CUDA_TRY(ctx, cudaEventRecord(slot.freed, st));
+            pt.end(2, e2, cs);
+            CUDA_TRY(ctx, cudaEventRecord(slot.freed, cs));
             freed_recorded[sl] = true;
             ++comp_launches;
         }
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev_setfree[set], st));
+        if (dual) CUDA_TRY(ctx, cudaEventRecord(ctx->ev_csetfree[set], ctx->cst));
         set_used[set] = true;
         if ((r = launch_check(ctx, "score kernels"))) return r;
+    }
+    if (dual) {
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_cdone, ctx->cst));
+        CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_cdone, 0));
     }
     if (ko.resolution == CSGS_RES_SCENE) scene_normalise(s_dev, n, &ctx->d_ctr->sumA, st);
     sum_scores(s_dev, n, P<double>(ctx->partial), S_dev, st);
@@ -672,9 +698,11 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
     if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
     if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * (ns + 1)))) return r;
     if (ko.resolution == CSGS_RES_IMAGE && (r = ensure(ctx, ctx->vbuf, sizeof(float) * (size_t)nmax))) return r;
-    if (ko.resolution == CSGS_RES_TILE && (r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap))) return r;
+    if (ko.resolution == CSGS_RES_TILE && ((r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap)) ||
+                                           (r = ensure(ctx, ctx->tsum2, sizeof(float) * (size_t)ctx->cap))))
+        return r;
     if ((ko.resolution == CSGS_RES_PIXEL || ko.resolution == CSGS_RES_CHANNEL) &&
-        (r = ensure(ctx, ctx->mskb, (size_t)ctx->cap)))
+        ((r = ensure(ctx, ctx->mskb, (size_t)ctx->cap)) || (r = ensure(ctx, ctx->mskb2, (size_t)ctx->cap))))
         return r;
     return CSGS_OK;
 }
