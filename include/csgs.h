@@ -124,6 +124,8 @@ typedef struct {
     double composite_ms;
     int64_t entries_staged;   /* tile-list entries staged by compositing pass 1 (bit 0) */
     int64_t entries_staged2;  /* tile-list entries staged by pass 2 (bit 0) */
+    double composite_busy_ms; /* time some compositing launch was running: the union of their spans, which
+                                 overlap on the two compositing streams (bit 1) */
 } csgs_stats;
 
 /* Fill *o with the default conventions above. */

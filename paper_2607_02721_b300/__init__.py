@@ -69,7 +69,8 @@ class Stats(ctypes.Structure):
                 ("capacity_retries", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("composite_launches", ctypes.c_int64), ("queries", ctypes.c_int64), ("score_ms", ctypes.c_double),
                 ("project_ms", ctypes.c_double), ("sort_ms", ctypes.c_double), ("composite_ms", ctypes.c_double),
-                ("entries_staged", ctypes.c_int64), ("entries_staged2", ctypes.c_int64)]
+                ("entries_staged", ctypes.c_int64), ("entries_staged2", ctypes.c_int64),
+                ("composite_busy_ms", ctypes.c_double)]
 
 
 EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",

@@ -9,6 +9,7 @@
 #include <memory>
 #include <random>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "csgs_internal.cuh"
@@ -73,15 +74,16 @@ struct csgs_ctx {
     cudaEvent_t ev_start = nullptr;       // enqueue start on the context's stream
     cudaEvent_t ev_proj[2] = {};          // projection of the batch in buffer set k done
     cudaEvent_t ev_setfree[2] = {};       // last compositing that read buffer set k done
-    cudaStream_t cst = nullptr;           // second compositing stream (odd views)
-    cudaEvent_t ev_csetfree[2] = {};      // ... its last compositing that read buffer set k done
-    cudaEvent_t ev_cdone = nullptr;       // ... its last compositing of a scene done
+    // compositing streams besides the context's (view v composites on stream v % kCompStreams)
+    cudaStream_t cst[kCompStreams - 1] = {};
+    cudaEvent_t ev_csetfree[kCompStreams - 1][2] = {};  // ... last compositing that read buffer set k done
+    cudaEvent_t ev_cdone[kCompStreams - 1] = {};        // ... last compositing of a scene done
     uint32_t cap = 0;
     int sort_blocks = kSortBlocks;  // radix-sort grid (autotuned)
     DevBuf partial, Sdev, C, counts, ctmp, stmp, nout, p, wfull;
     DevBuf tsum, vbuf;  // tile resolution: per instance; image resolution: per Gaussian
-    DevBuf mskb, mskb2;  // pixel / channel resolution: warp mask per instance (pass 1 -> pass 2), per stream
-    DevBuf tsum2;        // tile resolution: the second compositing stream's per-instance sums
+    DevBuf mskb;        // pixel / channel resolution: warp mask per instance (pass 1 -> pass 2)
+    DevBuf mskbx[kCompStreams - 1], tsumx[kCompStreams - 1];  // ... and tile sums, for the other streams
     // surrogate model
     bool mlp_ready = false;
     DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1, mPart;
@@ -94,6 +96,7 @@ struct csgs_ctx {
     std::string graph_key;
     long long graph_nodes_launches = 0;
     unsigned long long buf_gen = 0;  // bumped whenever a work buffer is reallocated
+    bool wide_keys = false;          // a view's depth range overflowed the narrow keys: 32-bit keys from then on
 };
 
 namespace {
@@ -188,6 +191,7 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     k->ow2 = o->obj_w[2];
     k->resolution = o->resolution;
     k->variant = o->variant;
+    k->narrow_keys = ctx->wide_keys ? 0 : 1;
     return CSGS_OK;
 }
 
@@ -242,17 +246,19 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
 // slot `k` on stream `st`.  Returns the instance value buffer (Gaussian ids in tile,
 // depth order); the ranges are in slot k's `ranges`.
 const uint32_t* bin_view(csgs_ctx* ctx, int k, int64_t n, uint32_t* keys_v, const uint2* rects_v, const CamDev& cam,
-                         cudaStream_t st) {
+                         bool narrow, cudaStream_t st) {
     BinSlot& b = ctx->slot[k];
     unsigned long long* n_inst = &ctx->d_ctr->n_inst[k];
+    // narrow depth keys: three 9-bit passes; the float bits: four 8-bit passes
     int cur = radix_sort_pairs(keys_v, P<uint32_t>(b.dvals_a), P<uint32_t>(b.dkeys_b), P<uint32_t>(b.dvals_b),
-                               ctx->d_nconst, (uint32_t)n, 32, P<uint32_t>(b.hist), ctx->sort_blocks, true, st);
+                               ctx->d_nconst, (uint32_t)n, narrow ? kNarrowKeyBits : 32, narrow ? 9 : 8,
+                               P<uint32_t>(b.hist), ctx->sort_blocks, true, st);
     const uint32_t* order = cur ? P<uint32_t>(b.dvals_b) : P<uint32_t>(b.dvals_a);
     emit_instances(order, rects_v, (int)n, cam.tiles_x, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
                    P<uint32_t>(b.scan_tmp), ctx->d_ctr, n_inst, st);
     const int ntiles = cam.tiles_x * cam.tiles_y;
     int cur2 = radix_sort_pairs(P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), P<uint32_t>(b.ikeys_b),
-                                P<uint32_t>(b.ivals_b), n_inst, ctx->cap, ceil_log2((uint32_t)ntiles),
+                                P<uint32_t>(b.ivals_b), n_inst, ctx->cap, ceil_log2((uint32_t)ntiles), 8,
                                 P<uint32_t>(b.hist), ctx->sort_blocks, false, st);
     const uint32_t* ik = cur2 ? P<uint32_t>(b.ikeys_b) : P<uint32_t>(b.ikeys_a);
     const uint32_t* iv = cur2 ? P<uint32_t>(b.ivals_b) : P<uint32_t>(b.ivals_a);
@@ -263,6 +269,21 @@ const uint32_t* bin_view(csgs_ctx* ctx, int k, int64_t n, uint32_t* keys_v, cons
 csgs_status read_counters(csgs_ctx* ctx) {
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, ctx->st));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    return CSGS_OK;
+}
+
+csgs_status grow_capacity(csgs_ctx* ctx);
+
+// After a run that flagged an overflow: 32-bit depth keys from now on if a depth left the
+// narrow keys' range, a larger instance buffer if the instances did not fit.
+csgs_status widen_or_grow(csgs_ctx* ctx, KOpts& ko) {
+    const uint32_t e = ctx->h_ctr->err;
+    if (e & kErrDepthRange) {
+        if (!ko.narrow_keys) return fail(ctx, CSGS_E_DEVICE_CHECK, "depth key range flagged with 32-bit keys");
+        ctx->wide_keys = true;
+        ko.narrow_keys = 0;
+    }
+    if (e & kErrCapacity) return grow_capacity(ctx);
     return CSGS_OK;
 }
 
@@ -342,13 +363,15 @@ csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
         }
     }
     bool ev_ok = cudaStreamCreateWithFlags(&ctx->pst, cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaStreamCreateWithFlags(&ctx->cst, cudaStreamNonBlocking) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&ctx->ev_cdone, cudaEventDisableTiming) == cudaSuccess;
+                 cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < 2 && ev_ok; ++k)
         ev_ok = cudaEventCreateWithFlags(&ctx->ev_proj[k], cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventCreateWithFlags(&ctx->ev_setfree[k], cudaEventDisableTiming) == cudaSuccess &&
-                cudaEventCreateWithFlags(&ctx->ev_csetfree[k], cudaEventDisableTiming) == cudaSuccess;
+                cudaEventCreateWithFlags(&ctx->ev_setfree[k], cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; c < kCompStreams - 1 && ev_ok; ++c)
+        ev_ok = cudaStreamCreateWithFlags(&ctx->cst[c], cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_cdone[c], cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_csetfree[c][0], cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ctx->ev_csetfree[c][1], cudaEventDisableTiming) == cudaSuccess;
     if (!ev_ok) {
         csgs_destroy(ctx);
         return CSGS_E_CUDA;
@@ -382,19 +405,24 @@ void csgs_destroy(csgs_ctx* ctx) {
     for (int k = 0; k < 2; ++k) {
         if (ctx->ev_proj[k]) cudaEventDestroy(ctx->ev_proj[k]);
         if (ctx->ev_setfree[k]) cudaEventDestroy(ctx->ev_setfree[k]);
-        if (ctx->ev_csetfree[k]) cudaEventDestroy(ctx->ev_csetfree[k]);
         release(ctx->splats[k]);
         release(ctx->keys[k]);
         release(ctx->rects[k]);
     }
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
-    if (ctx->ev_cdone) cudaEventDestroy(ctx->ev_cdone);
     if (ctx->pst) cudaStreamDestroy(ctx->pst);
-    if (ctx->cst) cudaStreamDestroy(ctx->cst);
+    for (int c = 0; c < kCompStreams - 1; ++c) {
+        if (ctx->ev_cdone[c]) cudaEventDestroy(ctx->ev_cdone[c]);
+        for (int k = 0; k < 2; ++k)
+            if (ctx->ev_csetfree[c][k]) cudaEventDestroy(ctx->ev_csetfree[c][k]);
+        if (ctx->cst[c]) cudaStreamDestroy(ctx->cst[c]);
+        release(ctx->mskbx[c]);
+        release(ctx->tsumx[c]);
+    }
     DevBuf* bufs[] = {
                       &ctx->partial, &ctx->Sdev,   &ctx->C,       &ctx->counts,  &ctx->ctmp,
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
-                      &ctx->mskb,   &ctx->mskb2,   &ctx->tsum2,
+                      &ctx->mskb,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
                       &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
                       &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->mPart,   &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
@@ -567,6 +595,30 @@ struct PhaseTimer {
             ms3[sp.first] += t;
         }
     }
+    // Length of the union of one phase's spans (spans on several streams overlap).
+    double busy(int phase) {
+        std::vector<std::pair<double, double>> iv;
+        for (auto& sp : spans) {
+            if (sp.first != phase) continue;
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ctx->evpool[0], ctx->evpool[sp.second.first]);
+            cudaEventElapsedTime(&b, ctx->evpool[0], ctx->evpool[sp.second.second]);
+            iv.push_back({a, b});
+        }
+        std::sort(iv.begin(), iv.end());
+        double tot = 0.0, lo = 0.0, hi = -1e300;
+        for (auto& x : iv) {
+            if (x.first > hi) {
+                if (hi > lo) tot += hi - lo;
+                lo = x.first;
+                hi = x.second;
+            } else if (x.second > hi) {
+                hi = x.second;
+            }
+        }
+        if (hi > lo) tot += hi - lo;
+        return tot;
+    }
 };
 
 int auto_view_batch(int64_t n, int nv, int req) {
@@ -593,12 +645,12 @@ namespace {
 //     that last read that set (batch b - 2) is done, so it runs ahead of the compositing;
 //   - binning: view k in slot k % kBinSlots on the slot's high-priority stream, after the
 //     projection of its batch and the compositing that last read the slot;
-//   - compositing of even views on the context's stream and of odd views on a second
-//     stream (ctx->cst), each view after its binning, so that the last tiles of one view
-//     overlap the first of the next (the score reductions are max or sum atomics; the
+//   - compositing of view v on stream v % kCompStreams (0: the context's stream, others
+//     ctx->cst), each view after its binning, so that the last tiles of one view overlap
+//     the first of the next (the score reductions are max or sum atomics; the
 //     per-instance pass-1 buffers exist once per stream); the image resolution, whose
 //     per-view fold needs the views in turn, composites on the context's stream only;
-//   - the reductions on the context's stream, after both compositing streams.
+//   - the reductions on the context's stream, after every compositing stream.
 // Every side stream's last operation is waited on by the context's stream (the capture
 // joins them).
 csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int vb, int v0_all, int v1_all,
@@ -613,8 +665,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
     if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev_start, st));
     CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_start, 0));
-    const bool dual = ko.resolution != CSGS_RES_IMAGE && v1_all - v0_all > 1;
-    if (dual) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->cst, ctx->ev_start, 0));
+    const int ncs = ko.resolution == CSGS_RES_IMAGE ? 1 : kCompStreams;
+    for (int c = 0; c + 1 < ncs; ++c) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->cst[c], ctx->ev_start, 0));
     bool freed_recorded[kBinSlots] = {};
     bool set_used[2] = {false, false};
     int view = 0, batch = 0;
@@ -623,11 +675,11 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
         const int set = batch & 1;
         if (set_used[set]) {
             CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_setfree[set], 0));
-            if (dual) CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_csetfree[set], 0));
+            for (int c = 0; c + 1 < ncs; ++c) CUDA_TRY(ctx, cudaStreamWaitEvent(ps, ctx->ev_csetfree[c][set], 0));
         }
         size_t e0 = pt.begin(ps);
         launch_project(sd, s->d_cams + v0, nb, nullptr, ko, P<Splat>(ctx->splats[set]), P<uint32_t>(ctx->keys[set]),
-                       P<uint2>(ctx->rects[set]), ps);
+                       P<uint2>(ctx->rects[set]), ctx->d_ctr, ps);
         pt.end(0, e0, ps);
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev_proj[set], ps));
         for (int k = 0; k < nb; ++k, ++view) {
@@ -639,11 +691,11 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, ctx->ev_proj[set], 0));
             if (freed_recorded[sl]) CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, slot.freed, 0));
             size_t e1 = pt.begin(slot.st);
-            const uint32_t* iv = bin_view(ctx, sl, n, keys_v, rects_v, cam, slot.st);
+            const uint32_t* iv = bin_view(ctx, sl, n, keys_v, rects_v, cam, ko.narrow_keys != 0, slot.st);
             pt.end(1, e1, slot.st);
             CUDA_TRY(ctx, cudaEventRecord(slot.ready, slot.st));
-            const bool second = dual && (view & 1);
-            cudaStream_t cs = second ? ctx->cst : st;
+            const int ci = view % ncs;  // compositing stream of this view
+            cudaStream_t cs = ci ? ctx->cst[ci - 1] : st;
             CUDA_TRY(ctx, cudaStreamWaitEvent(cs, slot.ready, 0));
             CompositeArgs a{};
             a.ranges = P<uint2>(slot.ranges);
@@ -654,8 +706,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             a.o = ko;
             a.s_bits = reinterpret_cast<uint32_t*>(s_dev);
             a.s_sum = ko.resolution == CSGS_RES_IMAGE ? P<float>(ctx->vbuf) : s_dev;
-            a.tile_sum = P<float>(second ? ctx->tsum2 : ctx->tsum);
-            a.mskbuf = P<uint8_t>(second ? ctx->mskb2 : ctx->mskb);
+            a.tile_sum = P<float>(ci ? ctx->tsumx[ci - 1] : ctx->tsum);
+            a.mskbuf = P<uint8_t>(ci ? ctx->mskbx[ci - 1] : ctx->mskb);
             a.ctr = ctx->d_ctr;
             a.stats = stats & 1;
             if (ko.resolution == CSGS_RES_IMAGE)
@@ -669,13 +721,13 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             ++comp_launches;
         }
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev_setfree[set], st));
-        if (dual) CUDA_TRY(ctx, cudaEventRecord(ctx->ev_csetfree[set], ctx->cst));
+        for (int c = 0; c + 1 < ncs; ++c) CUDA_TRY(ctx, cudaEventRecord(ctx->ev_csetfree[c][set], ctx->cst[c]));
         set_used[set] = true;
         if ((r = launch_check(ctx, "score kernels"))) return r;
     }
-    if (dual) {
-        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_cdone, ctx->cst));
-        CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_cdone, 0));
+    for (int c = 0; c + 1 < ncs; ++c) {
+        CUDA_TRY(ctx, cudaEventRecord(ctx->ev_cdone[c], ctx->cst[c]));
+        CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_cdone[c], 0));
     }
     if (ko.resolution == CSGS_RES_SCENE) scene_normalise(s_dev, n, &ctx->d_ctr->sumA, st);
     sum_scores(s_dev, n, P<double>(ctx->partial), S_dev, st);
@@ -698,12 +750,14 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
     if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
     if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * (ns + 1)))) return r;
     if (ko.resolution == CSGS_RES_IMAGE && (r = ensure(ctx, ctx->vbuf, sizeof(float) * (size_t)nmax))) return r;
-    if (ko.resolution == CSGS_RES_TILE && ((r = ensure(ctx, ctx->tsum, sizeof(float) * (size_t)ctx->cap)) ||
-                                           (r = ensure(ctx, ctx->tsum2, sizeof(float) * (size_t)ctx->cap))))
-        return r;
-    if ((ko.resolution == CSGS_RES_PIXEL || ko.resolution == CSGS_RES_CHANNEL) &&
-        ((r = ensure(ctx, ctx->mskb, (size_t)ctx->cap)) || (r = ensure(ctx, ctx->mskb2, (size_t)ctx->cap))))
-        return r;
+    for (int c = 0; c < kCompStreams; ++c) {
+        DevBuf& ts = c ? ctx->tsumx[c - 1] : ctx->tsum;
+        DevBuf& mb = c ? ctx->mskbx[c - 1] : ctx->mskb;
+        if (ko.resolution == CSGS_RES_TILE && (r = ensure(ctx, ts, sizeof(float) * (size_t)ctx->cap))) return r;
+        if ((ko.resolution == CSGS_RES_PIXEL || ko.resolution == CSGS_RES_CHANNEL) &&
+            (r = ensure(ctx, mb, (size_t)ctx->cap)))
+            return r;
+    }
     return CSGS_OK;
 }
 
@@ -749,9 +803,9 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         if ((r = read_counters(ctx))) return r;
-        if (ctx->h_ctr->err & kErrCapacity) {
+        if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
             if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
-            if ((r = grow_capacity(ctx))) return r;
+            if ((r = widen_or_grow(ctx, ko))) return r;
             if ((r = prepare_scoring(ctx, &s, &vb, 1, ko))) return r;
             continue;
         }
@@ -780,6 +834,7 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
         ctx->stats.project_ms = ph[0];
         ctx->stats.sort_ms = ph[1];
         ctx->stats.composite_ms = ph[2];
+        ctx->stats.composite_busy_ms = pt.busy(2);
     }
     const double S = ctx->h_S[0];
     if (S_out) *S_out = S;
@@ -826,7 +881,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
     float ms = 0.f;
     long long replayed = 0;
     for (int attempt = 0;; ++attempt) {
-        const int64_t bmeta[3] = {(int64_t)ctx->cap, ctx->sort_blocks, (int64_t)ctx->buf_gen};
+        const int64_t bmeta[4] = {(int64_t)ctx->cap, ctx->sort_blocks, (int64_t)ctx->buf_gen, (int64_t)ko.narrow_keys};
         const std::string full_key = key + std::string((const char*)bmeta, sizeof(bmeta));
         const bool replay = use_graph && ctx->graph_exec && ctx->graph_key == full_key;
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, st));
@@ -868,9 +923,9 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
         CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, st));
         CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         if ((r = read_counters(ctx))) return r;
-        if (ctx->h_ctr->err & kErrCapacity) {
+        if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
             if (attempt > 4) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
-            if ((r = grow_capacity(ctx))) return r;
+            if ((r = widen_or_grow(ctx, ko))) return r;
             if ((r = prepare_scoring(ctx, sc.data(), vb.data(), n_scenes, ko))) return r;
             ctx->graph_key.clear();
             continue;
@@ -926,12 +981,12 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
                 if ((r = enqueue_scene_score(ctx, s, ko, vb, 0, pv, 0, s_tmp, P<double>(ctx->Sdev), off, cl))) break;
                 CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->st));
                 if ((r = read_counters(ctx))) break;
-                if (ctx->h_ctr->err & kErrCapacity) {
+                if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
                     if (++grows > 4) {
                         r = fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
                         break;
                     }
-                    if ((r = grow_capacity(ctx)) || (r = prepare_scoring(ctx, &s, &vb, 1, ko))) break;
+                    if ((r = widen_or_grow(ctx, ko)) || (r = prepare_scoring(ctx, &s, &vb, 1, ko))) break;
                     --rep;
                     continue;
                 }
@@ -1047,8 +1102,8 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
             scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         }
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
-                       P<uint2>(ctx->rects[0]), st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, st);
+                       P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, ko.narrow_keys != 0, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1063,9 +1118,9 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
         launch_composite_render(a, st);
         if ((r = launch_check(ctx, "render kernels"))) return r;
         if ((r = read_counters(ctx))) return r;
-        if (ctx->h_ctr->err & kErrCapacity) {
+        if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
             if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
-            if ((r = grow_capacity(ctx))) return r;
+            if ((r = widen_or_grow(ctx, ko))) return r;
             continue;
         }
         break;
@@ -1147,8 +1202,8 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->wfull.p, 0, sizeof(float) * (size_t)n, st));
         scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
-                       P<uint2>(ctx->rects[0]), st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, st);
+                       P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, ko.narrow_keys != 0, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1162,9 +1217,9 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         launch_composite_transfer(a, st);
         if ((r = launch_check(ctx, "transfer kernels"))) return r;
         if ((r = read_counters(ctx))) return r;
-        if (ctx->h_ctr->err & kErrCapacity) {
+        if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
             if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
-            if ((r = grow_capacity(ctx))) return r;
+            if ((r = widen_or_grow(ctx, ko))) return r;
             continue;
         }
         break;
@@ -1459,8 +1514,8 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
             scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         }
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
-                       P<uint2>(ctx->rects[0]), st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, st);
+                       P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
+        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, ko.narrow_keys != 0, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1479,9 +1534,9 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
         launch_composite_backward(a, st);
         if ((r = launch_check(ctx, "render backward kernels"))) return r;
         if ((r = read_counters(ctx))) return r;
-        if (ctx->h_ctr->err & kErrCapacity) {
+        if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
             if (++retries > 3) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
-            if ((r = grow_capacity(ctx))) return r;
+            if ((r = widen_or_grow(ctx, ko))) return r;
             continue;
         }
         break;

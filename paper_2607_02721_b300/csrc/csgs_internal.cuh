@@ -48,6 +48,7 @@ struct KOpts {
     float dilation, clamp_fov;
     float ow0, ow1, ow2;  // per-pixel objective weights
     int resolution, variant;
+    int narrow_keys;  // depth keys: 1 = narrow (27-bit, relative to the near plane), 0 = the float bits
 };
 
 // One projected Gaussian in one view (48 bytes, 16-byte aligned).
@@ -66,7 +67,15 @@ struct __align__(16) Splat {
 };
 
 // Device error word bits.
-enum : uint32_t { kErrCapacity = 1u, kErrNonFinite = 2u, kErrIndex = 4u };
+enum : uint32_t { kErrCapacity = 1u, kErrNonFinite = 2u, kErrIndex = 4u, kErrDepthRange = 8u };
+
+// Narrow depth keys: bits(z) - bits(near_z) (positive floats order as their bit patterns),
+// sorted as three 9-bit digits.  A visible Gaussian has key >= 1; culled ones get
+// kNarrowCulled, after every visible key.  A visible depth whose key would reach
+// kNarrowCulled (z beyond about 2^16 near_z) flags kErrDepthRange, and the call repeats
+// with the full 32-bit keys (four 8-bit digits).
+constexpr int kNarrowKeyBits = 27;
+constexpr uint32_t kNarrowCulled = (1u << kNarrowKeyBits) - 1u;
 
 // Device counters (one block per context).
 // Sum of 16 per-lane values over the warp's 32 lanes, one column per lane pair:
@@ -98,6 +107,7 @@ __device__ __forceinline__ float warp_colsum16(const float (&v)[16], int lane) {
 // Binning slots: scoring bins view k in slot k % kBinSlots on the slot's own stream, so
 // the binning of the next views overlaps the compositing of the current one.
 constexpr int kBinSlots = 3;
+constexpr int kCompStreams = 2;  // compositing streams of a scoring submission
 
 struct DevCounters {
     uint32_t err;
@@ -119,7 +129,7 @@ struct DevCounters {
 
 // ---- launchers (k_project.cu)
 void launch_project(const SceneDev& sc, const CamDev* d_cams, int nv, const float* d_w, const KOpts& o,
-                    Splat* splats, uint32_t* keys, uint2* rects, cudaStream_t st);
+                    Splat* splats, uint32_t* keys, uint2* rects, DevCounters* ctr, cudaStream_t st);
 void launch_debug_project(const SceneDev& sc, const CamDev* d_cam, const KOpts& o, float* out, cudaStream_t st);
 void launch_check_finite(const float* p, int64_t n, DevCounters* ctr, cudaStream_t st);
 void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const KOpts& o, float* stats, int accumulate,
@@ -136,12 +146,13 @@ void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* w
 // ---- sorting and scans (k_sort.cu)
 constexpr int kSortBlocks = 148 * 4;       // default radix-sort grid (the autotuner may pick another)
 constexpr int kSortMaxBlocks = 2048;
-constexpr int kSortHistWords = 256 * kSortMaxBlocks + 256;  // per-block digit counts + digit totals
-// Stable LSD radix sort of (key, value) pairs on key bits [0, bits).  n is read from
-// d_n (device) and clamped to n_max.  iota_vals: the values are the indices 0..n-1
-// (vals_a is not read).  Returns which buffer holds the result (0: a, 1: b).
+constexpr int kSortHistWords = 512 * kSortMaxBlocks + 512;  // per-block digit counts + digit totals
+// Stable LSD radix sort of (key, value) pairs on key bits [0, bits), digit_bits (8 or 9)
+// bits per pass.  n is read from d_n (device) and clamped to n_max.  iota_vals: the values
+// are the indices 0..n-1 (vals_a is not read).  Returns which buffer holds the result
+// (0: a, 1: b).
 int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st);
+                     uint32_t n_max, int bits, int digit_bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st);
 // Gaussians in depth order -> (tile, gid) instances in depth order; writes the
 // instance count to *n_inst (and the totals in ctr).  scan_tmp: >= ceil(n / 256) + 64 words.
 void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x,

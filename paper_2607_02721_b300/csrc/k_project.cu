@@ -192,7 +192,8 @@ __device__ __forceinline__ void load_gaussian(const SceneDev& sc, int i, const f
 template <int DEG>
 __global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __restrict__ cams, int nv,
                                                  const float* __restrict__ wts, KOpts o, Splat* __restrict__ splats,
-                                                 uint32_t* __restrict__ keys, uint2* __restrict__ rects) {
+                                                 uint32_t* __restrict__ keys, uint2* __restrict__ rects,
+                                                 DevCounters* ctr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc.n) return;
     float mu[3], cov3[6], op;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __re
         project_one<DEG>(mu, cov3, op, shc, c, o, r);
         const size_t off = (size_t)v * sc.n + i;
         if (!r.valid) {
-            keys[off] = 0xFFFFFFFFu;
+            keys[off] = o.narrow_keys ? kNarrowCulled : 0xFFFFFFFFu;
             rects[off] = make_uint2(0u, 0u);
             continue;
         }
@@ -221,7 +222,15 @@ __global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __re
         s.q = make_float4(s1, s1k, s2, thr);
         s.c = make_float4(r.rgb[0], r.rgb[1], r.rgb[2], la);
         splats[off] = s;
-        keys[off] = __float_as_uint(r.depth);
+        uint32_t key = __float_as_uint(r.depth);
+        if (o.narrow_keys) {
+            key -= __float_as_uint(c.near_z);  // >= 1: r.depth > near_z > 0
+            if (key >= kNarrowCulled) {
+                atomicOr(&ctr->err, kErrDepthRange);
+                key = kNarrowCulled - 1u;
+            }
+        }
+        keys[off] = key;
         rects[off] = make_uint2(r.tx0 | (r.ty0 << 16), r.tx1 | (r.ty1 << 16));
     }
 }
@@ -534,14 +543,14 @@ void launch_features(const SceneDev& sc, const float* stats, void* X, cudaStream
 }
 
 void launch_project(const SceneDev& sc, const CamDev* d_cams, int nv, const float* d_w, const KOpts& o, Splat* splats,
-                    uint32_t* keys, uint2* rects, cudaStream_t st) {
+                    uint32_t* keys, uint2* rects, DevCounters* ctr, cudaStream_t st) {
     const int threads = 256;
     const int blocks = (sc.n + threads - 1) / threads;
     switch (sc.deg) {
-        case 0: k_project<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
-        case 1: k_project<1><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
-        case 2: k_project<2><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
-        default: k_project<3><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects); break;
+        case 0: k_project<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects, ctr); break;
+        case 1: k_project<1><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects, ctr); break;
+        case 2: k_project<2><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects, ctr); break;
+        default: k_project<3><<<blocks, threads, 0, st>>>(sc, d_cams, nv, d_w, o, splats, keys, rects, ctr); break;
     }
     count_launches(1);
 }

@@ -5,7 +5,8 @@
 //   3. stable LSD radix sort of the instances by tile id only;
 //   4. per-tile [start, end) ranges.
 // Every tile list is therefore sorted by (depth, Gaussian index).  No CUB: the sort is
-// a reduce-then-scan radix sort with warp-level stable ranking (match.any).
+// a reduce-then-scan radix sort with 8- or 9-bit digits and warp-level stable ranking
+// (one ballot per digit bit).
 #include "csgs_internal.cuh"
 
 namespace csgs {
@@ -34,14 +35,17 @@ __device__ __forceinline__ uint32_t read_n(const unsigned long long* d_n, uint32
     return v < n_max ? (uint32_t)v : n_max;
 }
 
-// Per-block digit counts of one pass.  Each warp counts into its own shared histogram
-// with plain atomics (match.any costs grow with the number of distinct digits in the
-// warp; conflicting shared atomics only serialise on equal digits).
+// Per-block digit counts of one pass (RB-bit digits, D = 2^RB).  Each warp counts into
+// its own shared histogram with plain atomics (match.any costs grow with the number of
+// distinct digits in the warp; conflicting shared atomics only serialise on equal digits).
+template <int RB>
 __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys,
                                                           const unsigned long long* d_n, uint32_t n_max, int shift,
                                                           uint32_t* __restrict__ hist) {
-    __shared__ uint32_t wh[kSortWarps][256];
-    for (int k = threadIdx.x; k < kSortWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0u;
+    constexpr uint32_t D = 1u << RB;
+    constexpr int DPT = (int)D / kSortThreads;  // digits per thread
+    __shared__ uint32_t wh[kSortWarps][D];
+    for (int k = threadIdx.x; k < kSortWarps * (int)D; k += kSortThreads) (&wh[0][0])[k] = 0u;
     __syncthreads();
     const uint32_t n = read_n(d_n, n_max);
     uint32_t begin, end;
@@ -53,21 +57,25 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
             const uint32_t i = base + g * kSortThreads + threadIdx.x;
-            d[g] = i < end ? (__ldg(keys + i) >> shift) & 255u : 256u;
+            d[g] = i < end ? (__ldg(keys + i) >> shift) & (D - 1u) : D;
         }
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g)
-            if (d[g] < 256u) atomicAdd(h + d[g], 1u);
+            if (d[g] < D) atomicAdd(h + d[g], 1u);
     }
     __syncthreads();
-    uint32_t c = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) c += wh[w][threadIdx.x];
-    hist[threadIdx.x * gridDim.x + blockIdx.x] = c;
+    for (int e = 0; e < DPT; ++e) {
+        const int dg = threadIdx.x * DPT + e;
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) c += wh[w][dg];
+        hist[dg * gridDim.x + blockIdx.x] = c;
+    }
 }
 
 // Exclusive scan of each digit's row of the histogram (G per-block counts, G <=
-// kSortMaxBlocks), one CTA per digit; the row totals go to row_total[256].
+// kSortMaxBlocks), one CTA per digit; the row totals go to row_total[digits].
 __global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist, uint32_t* __restrict__ row_total,
                                                     int G) {
     constexpr int kPer = (kSortMaxBlocks + 255) / 256;
@@ -100,30 +108,38 @@ __global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist,
     if (threadIdx.x == 255) row_total[blockIdx.x] = pre;
 }
 
-// Stable scatter of one radix pass.  Each CTA walks its chunk in sub-tiles of 2048
-// keys: warps rank their keys per digit with match.any (stable: warp, group, lane
-// order), the CTA turns the per-warp counts into positions, places the sub-tile in
-// shared memory grouped by digit, and writes each digit's run to its global slot, so
-// global stores are contiguous runs.
-template <int NBITS>
+// Stable scatter of one radix pass (NBITS significant bits of an RB-bit digit, D = 2^RB
+// digits, DPT = D / 256 consecutive digits per thread).  Each CTA walks its chunk in
+// sub-tiles of 2048 keys: warps rank their keys per digit with one ballot per digit bit
+// (stable: warp, group, lane order), the CTA turns the per-warp counts into positions,
+// places the sub-tile in shared memory grouped by digit, and writes each digit's run to
+// its global slot, so global stores are contiguous runs.
+template <int NBITS, int RB>
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                              const unsigned long long* d_n, uint32_t n_max, int shift,
                                                              const uint32_t* __restrict__ hist,
                                                              const uint32_t* __restrict__ row_total) {
-    __shared__ uint32_t wcnt[kSortWarps][257];
-    __shared__ uint32_t gbase[256];
-    __shared__ uint32_t lstart[256];
+    constexpr uint32_t D = 1u << RB;
+    constexpr int DPT = (int)D / kSortThreads;
+    __shared__ uint32_t wcnt[kSortWarps][D + 1];
+    __shared__ uint32_t gbase[D];
+    __shared__ uint32_t lstart[D];
     __shared__ uint32_t skey[kSubTile];
     __shared__ uint32_t sval[kSubTile];
     __shared__ uint32_t ws[kSortWarps];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     {
-        // offset of digit tid = sum of the totals of the smaller digits
-        const uint32_t t = row_total[tid];
-        uint32_t x = t;
+        // offset of digit d = sum of the totals of the smaller digits
+        uint32_t t[DPT], sum = 0;
+#pragma unroll
+        for (int e = 0; e < DPT; ++e) {
+            t[e] = row_total[tid * DPT + e];
+            sum += t[e];
+        }
+        uint32_t x = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -131,11 +147,16 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
         }
         if (lane == 31) ws[warp] = x;
         __syncthreads();
-        uint32_t pre = x - t;
+        uint32_t pre = x - sum;
         for (int w = 0; w < warp; ++w) pre += ws[w];
-        gbase[tid] = pre + hist[tid * gridDim.x + blockIdx.x];
+#pragma unroll
+        for (int e = 0; e < DPT; ++e) {
+            const int dg = tid * DPT + e;
+            gbase[dg] = pre + hist[dg * gridDim.x + blockIdx.x];
+            pre += t[e];
+        }
     }
-    for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+    for (int k = tid; k < kSortWarps * (int)(D + 1); k += kSortThreads) (&wcnt[0][0])[k] = 0;
     __syncthreads();
     const uint32_t n = read_n(d_n, n_max);
     uint32_t begin, end;
@@ -149,16 +170,16 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
             const bool ok = i < end;
             key[g] = ok ? __ldg(kin + i) : 0u;
             val[g] = ok ? (vin ? __ldg(vin + i) : i) : 0u;
-            dig[g] = ok ? (key[g] >> shift) & 255u : 256u;
+            dig[g] = ok ? (key[g] >> shift) & (D - 1u) : D;
         }
         // lanes holding the same digit: one ballot per digit bit (NBITS, unrolled; match.any
-        // is slower when the digits are spread out); invalid lanes (digit 256) form their
-        // own class.  The per-warp digit counters then give stable ranks in (group, lane) order.
+        // is slower when the digits are spread out); invalid lanes (digit D) form their own
+        // class.  The per-warp digit counters then give stable ranks in (group, lane) order.
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
             const uint32_t d = dig[g];
-            uint32_t pm = __ballot_sync(0xffffffffu, d < 256u);
-            if (d >= 256u) pm = ~pm;
+            uint32_t pm = __ballot_sync(0xffffffffu, d < D);
+            if (d >= D) pm = ~pm;
 #pragma unroll
             for (int bb = 0; bb < NBITS; ++bb) {
                 const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bb) & 1u);
@@ -170,17 +191,23 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
             __syncwarp();
         }
         __syncthreads();
-        // digit tid: per-warp exclusive offsets within the digit, and the digit's count
-        uint32_t cnt_d = 0;
+        // this thread's digits: per-warp exclusive offsets within the digit, and its count
+        uint32_t cnt_d[DPT], csum = 0;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; ++w) {
-            const uint32_t c = wcnt[w][tid];
-            wcnt[w][tid] = cnt_d;
-            cnt_d += c;
+        for (int e = 0; e < DPT; ++e) {
+            const int dg = tid * DPT + e;
+            cnt_d[e] = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                const uint32_t c = wcnt[w][dg];
+                wcnt[w][dg] = cnt_d[e];
+                cnt_d[e] += c;
+            }
+            csum += cnt_d[e];
         }
-        // start of digit tid's run inside the sub-tile
+        // start of each digit's run inside the sub-tile
         {
-            uint32_t x = cnt_d;
+            uint32_t x = csum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -189,14 +216,18 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
             __syncthreads();  // ws reuse
             if (lane == 31) ws[warp] = x;
             __syncthreads();
-            uint32_t pre = x - cnt_d;
+            uint32_t pre = x - csum;
             for (int w = 0; w < warp; ++w) pre += ws[w];
-            lstart[tid] = pre;
+#pragma unroll
+            for (int e = 0; e < DPT; ++e) {
+                lstart[tid * DPT + e] = pre;
+                pre += cnt_d[e];
+            }
         }
         __syncthreads();
 #pragma unroll
         for (int g = 0; g < kSortGroups; ++g) {
-            if (dig[g] < 256u) {
+            if (dig[g] < D) {
                 const uint32_t lp = lstart[dig[g]] + wcnt[warp][dig[g]] + rank[g];
                 skey[lp] = key[g];
                 sval[lp] = val[g];
@@ -205,14 +236,15 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __r
         __syncthreads();
         for (uint32_t q = tid; q < nvalid; q += kSortThreads) {
             const uint32_t k = skey[q];
-            const uint32_t d = (k >> shift) & 255u;
+            const uint32_t d = (k >> shift) & (D - 1u);
             const uint32_t pos = gbase[d] + (q - lstart[d]);
             kout[pos] = k;
             vout[pos] = sval[q];
         }
         __syncthreads();
-        gbase[tid] += cnt_d;
-        for (int k = tid; k < kSortWarps * 257; k += kSortThreads) (&wcnt[0][0])[k] = 0;
+#pragma unroll
+        for (int e = 0; e < DPT; ++e) gbase[tid * DPT + e] += cnt_d[e];
+        for (int k = tid; k < kSortWarps * (int)(D + 1); k += kSortThreads) (&wcnt[0][0])[k] = 0;
         __syncthreads();
     }
 }
@@ -374,35 +406,51 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long 
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
 
+// One pass with RB-bit digits (NBITS of them significant).
+template <int RB>
+void radix_pass(int nbits, const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
+                const unsigned long long* d_n, uint32_t n_max, int shift, uint32_t* hist, int G, cudaStream_t st) {
+    constexpr int D = 1 << RB;
+    k_rs_hist<RB><<<G, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
+    count_launches(1);
+    k_rs_rowscan<<<D, 256, 0, st>>>(hist, hist + D * G, G);
+    count_launches(1);
+    const uint32_t* rt = hist + D * G;
+#define CSGS_SCATTER(NB) \
+    k_rs_scatter<NB, RB><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt)
+    switch (nbits) {
+        case 1: CSGS_SCATTER(1); break;
+        case 2: CSGS_SCATTER(2); break;
+        case 3: CSGS_SCATTER(3); break;
+        case 4: CSGS_SCATTER(4); break;
+        case 5: CSGS_SCATTER(5); break;
+        case 6: CSGS_SCATTER(6); break;
+        case 7: CSGS_SCATTER(7); break;
+        case 8: CSGS_SCATTER(8); break;
+        default: CSGS_SCATTER(RB); break;
+    }
+#undef CSGS_SCATTER
+    count_launches(1);
+}
+
 }  // namespace
 
 int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st) {
+                     uint32_t n_max, int bits, int digit_bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st) {
     if (G < 1) G = 1;
     if (G > kSortMaxBlocks) G = kSortMaxBlocks;
+    const int rb = digit_bits == 9 ? 9 : 8;
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = 0; shift < bits; shift += rb) {
         uint32_t* kin = cur ? kb : ka;
         uint32_t* vin = shift == 0 && iota_vals ? nullptr : (cur ? vb : va);
         uint32_t* kout = cur ? ka : kb;
         uint32_t* vout = cur ? va : vb;
-        k_rs_hist<<<G, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
-        count_launches(1);
-        k_rs_rowscan<<<256, 256, 0, st>>>(hist, hist + 256 * G, G);
-        count_launches(1);
-        const int nbits = bits - shift < 8 ? bits - shift : 8;
-        const uint32_t* rt = hist + 256 * G;
-        switch (nbits) {
-            case 1: k_rs_scatter<1><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            case 2: k_rs_scatter<2><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            case 3: k_rs_scatter<3><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            case 4: k_rs_scatter<4><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            case 5: k_rs_scatter<5><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            case 6: k_rs_scatter<6><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            case 7: k_rs_scatter<7><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-            default: k_rs_scatter<8><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt); break;
-        }
-        count_launches(1);
+        const int nbits = bits - shift < rb ? bits - shift : rb;
+        if (rb == 9)
+            radix_pass<9>(nbits, kin, vin, kout, vout, d_n, n_max, shift, hist, G, st);
+        else
+            radix_pass<8>(nbits, kin, vin, kout, vout, d_n, n_max, shift, hist, G, st);
         cur ^= 1;
     }
     return cur;

@@ -350,6 +350,36 @@ def test_instance_capacity_growth(ctx, torch):
     c2.close()
 
 
+def test_depth_keys_wide_fallback(small, torch):
+    """Depth keys are the FP32 depth bits minus the near plane's bits, sorted as three 9-bit
+    digits; they cover depths up to about 2^16 times near_z.  A view with a visible depth
+    beyond that flags the run, which repeats with the full 32-bit keys (four 8-bit
+    digits), and the context keeps those.  Both key widths order the Gaussians the same
+    way, so the scores agree bit for bit, and the wide run matches the oracle."""
+    sc, cams, _, sa = small
+    far = np.array(cams, dtype=np.float32).copy()
+    far[:, 18] = 1e-5  # every visible depth (about 1.3 to 4.7) is beyond 2^16 * 1e-5
+    narrow, wide = csgs.Context(0), csgs.Context(0)
+    try:
+        sid_w = wide.load_scene(sc)
+        wide.set_queries(sid_w, far)
+        s_far, S_far = wide.score(sid_w)
+        assert wide.stats()["capacity_retries"] >= 1  # the flagged run was repeated
+        check_scores(s_far.cpu().numpy(), S_far, oracle.score(sa, far))
+        # the same query set on both contexts: narrow keys on one, 32-bit keys on the other
+        sid_n = narrow.load_scene(sc)
+        narrow.set_queries(sid_n, cams)
+        wide.set_queries(sid_w, cams)
+        a, Sa = narrow.score(sid_n)
+        b, Sb = wide.score(sid_w)
+        assert narrow.stats()["capacity_retries"] == 0 and wide.stats()["capacity_retries"] == 0
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+        assert Sa == Sb
+    finally:
+        narrow.close()
+        wide.close()
+
+
 # ---------------------------------------------------------------- resolutions and variants (Sec. 3.5)
 
 RESOLUTIONS = [("pixel", csgs.RES_PIXEL, oracle.RES_PIXEL), ("channel", csgs.RES_CHANNEL, oracle.RES_CHANNEL),
