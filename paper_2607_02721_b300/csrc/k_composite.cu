@@ -486,7 +486,8 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     imp = fmaxf(__fmul_rn(t0, inv0), fmaxf(__fmul_rn(t1, inv1), __fmul_rn(t2, inv2)));
                 }
                 const uint32_t bits = hit ? __float_as_uint(imp) : 0u;
-                T = hit ? __fmul_rn(T, __fadd_rn(1.f, -r)) : T;
+                // pass 2 only scales imp by T (no threshold reads it): one FMA, T - T r
+                T = hit ? __fmaf_rn(-T, r, T) : T;
                 const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
                 if (lane == 0 && mx) atomicMax(&sh.red[j], mx);
             }

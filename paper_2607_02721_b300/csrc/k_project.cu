@@ -189,8 +189,11 @@ __device__ __forceinline__ void load_gaussian(const SceneDev& sc, int i, const f
         for (int ch = 0; ch < 3; ++ch) shc[3 * k + ch] = __ldg(sc.sh + (size_t)(3 * k + ch) * n + i);
 }
 
+// Three CTAs per SM (at most 80 registers; the degree-3 colour coefficients spill a little
+// to L1): the kernel runs beside compositing, and a smaller register footprint leaves room
+// for compositing CTAs (measured: 0.6% shorter scoring step than at 115 registers).
 template <int DEG>
-__global__ void __launch_bounds__(256) k_project(SceneDev sc, const CamDev* __restrict__ cams, int nv,
+__global__ void __launch_bounds__(256, 3) k_project(SceneDev sc, const CamDev* __restrict__ cams, int nv,
                                                  const float* __restrict__ wts, KOpts o, Splat* __restrict__ splats,
                                                  uint32_t* __restrict__ keys, uint2* __restrict__ rects,
                                                  DevCounters* ctr) {
