@@ -70,7 +70,9 @@ typedef struct {
     float t[3];
     float fx, fy, cx, cy;
     int32_t width, height; /* 1..16384 */
-    float near_z;   /* Gaussians with camera depth <= near_z are culled (> 0) */
+    float near_z;   /* Gaussians with camera depth <= near_z are culled (> 0).  Depths are sorted as
+                       27-bit keys relative to near_z while every visible depth stays below about
+                       2^16 near_z; a larger one makes the call repeat with 32-bit keys (same order) */
     float pad;
 } csgs_camera;
 
@@ -114,7 +116,8 @@ typedef struct {
     int64_t pairs_evaluated2; /* scoring pass 2: pairs tested (bit 0) */
     int64_t pairs_hit2;       /* scoring pass 2: contributing pairs (bit 0) */
     int64_t violations;       /* csgs_render: pairs met before the stop with w alpha k >= 1 (bit 0) */
-    int64_t capacity_retries; /* re-runs after growing the instance buffers */
+    int64_t capacity_retries; /* re-runs after growing the instance buffers, or after a visible depth beyond
+                                 about 2^16 near_z switched the context to 32-bit depth keys */
     int64_t kernel_launches;  /* kernels this library launched in the call */
     int64_t composite_launches;
     int64_t queries;          /* pixel queries with A > 0 (|Q'| of Thm. 2; pixel and channel resolutions) */
