@@ -906,7 +906,8 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
                 return er;
             }
             if (ce != cudaSuccess) return fail(ctx, CSGS_E_CUDA, "stream capture: %s", cudaGetErrorString(ce));
-            ce = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+            // keep the capturing streams' priorities (binning ahead of compositing) in the replay
+            ce = cudaGraphInstantiate(&ctx->graph_exec, g, cudaGraphInstantiateFlagUseNodePriority);
             cudaGraphDestroy(g);
             if (ce != cudaSuccess) return fail(ctx, CSGS_E_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
             ctx->graph_key = full_key;
