@@ -17,6 +17,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortGroups = 8;                               // 32-key groups per warp per sub-tile
 constexpr int kSubTile = kSortThreads * kSortGroups;          // 2048 keys
 constexpr int kScanThreads = 256;
+constexpr int kEmitBlocks = 148 * 4;  // grid bound of the emit kernels (chunks of kScanThreads Gaussians)
 
 // chunk of the key array handled by block b of a grid of G blocks (multiples of sub-tiles)
 __device__ __forceinline__ void sort_chunk(uint32_t n, int b, uint32_t& begin, uint32_t& end) {
@@ -281,16 +282,22 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return pre;
 }
 
-// Emit, phase 1: instance count per block of 256 depth-ordered Gaussians.
+// Emit, phase 1: instance count per chunk of 256 depth-ordered Gaussians.  The emit
+// kernels loop over chunks on a grid of at most kEmitBlocks CTAs: they run at binning's high
+// priority beside compositing, and a bounded grid holds fewer of the SMs' CTA slots at once
+// (measured: 0.6% shorter scoring step than one CTA per chunk).
 __global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __restrict__ order,
                                                               const uint2* __restrict__ rects, int n,
                                                               uint32_t* __restrict__ partial) {
     __shared__ uint32_t ws[32];
-    const int j = blockIdx.x * kScanThreads + threadIdx.x;
-    const uint32_t c = j < n ? tile_count(__ldg(rects + __ldg(order + j))) : 0u;
-    uint32_t tot;
-    block_exclusive_scan(c, ws, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+    const int nb = (n + kScanThreads - 1) / kScanThreads;
+    for (int cb = blockIdx.x; cb < nb; cb += gridDim.x) {
+        const int j = cb * kScanThreads + threadIdx.x;
+        const uint32_t c = j < n ? tile_count(__ldg(rects + __ldg(order + j))) : 0u;
+        uint32_t tot;
+        block_exclusive_scan(c, ws, &tot);
+        if (threadIdx.x == 0) partial[cb] = tot;
+    }
 }
 
 // Exclusive scan of the per-block totals in one CTA (any count), plus the grand total.
@@ -343,44 +350,45 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
     __shared__ uint32_t s_g[kScanThreads / 32][32];
     __shared__ uint2 s_r[kScanThreads / 32][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * kScanThreads + threadIdx.x;
-    const uint32_t gid = j < n ? __ldg(order + j) : 0u;
-    const uint2 rc = j < n ? __ldg(rects + gid) : make_uint2(0u, 0u);
-    const uint32_t c = tile_count(rc);
-    uint32_t tot;
-    const uint32_t off = block_exclusive_scan(c, ws, &tot) + partial[blockIdx.x];
-    const uint32_t wbase = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t wtot = __shfl_sync(0xffffffffu, off + c, 31) - wbase;
-    s_e[warp][lane] = off - wbase;
-    s_g[warp][lane] = gid;
-    s_r[warp][lane] = rc;
-    __syncwarp();
-    if ((unsigned long long)wbase + wtot > cap) {
-        if (lane == 0 && wtot) atomicOr(&ctr->err, kErrCapacity);
-        return;
-    }
-    for (uint32_t f = lane; f < wtot; f += 32) {
-        // owner: the largest lane whose run starts at or before f
-        int lo = 0, hi = 31;
+    const int nb = (n + kScanThreads - 1) / kScanThreads;
+    for (int cb = blockIdx.x; cb < nb; cb += gridDim.x) {
+        const int j = cb * kScanThreads + threadIdx.x;
+        const uint32_t gid = j < n ? __ldg(order + j) : 0u;
+        const uint2 rc = j < n ? __ldg(rects + gid) : make_uint2(0u, 0u);
+        const uint32_t c = tile_count(rc);
+        uint32_t tot;
+        const uint32_t off = block_exclusive_scan(c, ws, &tot) + partial[cb];
+        const uint32_t wbase = __shfl_sync(0xffffffffu, off, 0);
+        const uint32_t wtot = __shfl_sync(0xffffffffu, off + c, 31) - wbase;
+        s_e[warp][lane] = off - wbase;
+        s_g[warp][lane] = gid;
+        s_r[warp][lane] = rc;
+        __syncwarp();
+        const bool fits = (unsigned long long)wbase + wtot <= cap;
+        if (!fits && lane == 0 && wtot) atomicOr(&ctr->err, kErrCapacity);
+        for (uint32_t f = lane; fits && f < wtot; f += 32) {
+            // owner: the largest lane whose run starts at or before f
+            int lo = 0, hi = 31;
 #pragma unroll
-        for (int it = 0; it < 5; ++it) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_e[warp][mid] <= f)
-                lo = mid;
-            else
-                hi = mid - 1;
+            for (int it = 0; it < 5; ++it) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_e[warp][mid] <= f)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const uint2 r = s_r[warp][lo];
+            const uint32_t local = f - s_e[warp][lo];
+            const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu;
+            const uint32_t w = x1 - x0;
+            // local / w in FP32: (local + 0.5) / w lies at least 0.5 / w from an integer and the
+            // product with the rounded reciprocal is within (local + 0.5) 2^-23 / w of it, so
+            // the floor is exact for local < 2^22 (integer division beyond)
+            const uint32_t dy = local < (1u << 22) ? (uint32_t)(((float)local + 0.5f) * __frcp_rn((float)w)) : local / w;
+            const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
+            ikeys[wbase + f] = ty * (uint32_t)tiles_x + tx;
+            ivals[wbase + f] = s_g[warp][lo];
         }
-        const uint2 r = s_r[warp][lo];
-        const uint32_t local = f - s_e[warp][lo];
-        const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu;
-        const uint32_t w = x1 - x0;
-        // local / w in FP32: (local + 0.5) / w lies at least 0.5 / w from an integer and the
-        // product with the rounded reciprocal is within (local + 0.5) 2^-23 / w of it, so
-        // the floor is exact for local < 2^22 (integer division beyond)
-        const uint32_t dy = local < (1u << 22) ? (uint32_t)(((float)local + 0.5f) * __frcp_rn((float)w)) : local / w;
-        const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
-        ikeys[wbase + f] = ty * (uint32_t)tiles_x + tx;
-        ivals[wbase + f] = s_g[warp][lo];
     }
 }
 
@@ -459,11 +467,12 @@ int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, con
 void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x, uint32_t* ikeys, uint32_t* ivals,
                     uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr, unsigned long long* n_inst, cudaStream_t st) {
     const int nb = (n + kScanThreads - 1) / kScanThreads;
-    k_emit_reduce<<<nb, kScanThreads, 0, st>>>(order, rects, n, scan_tmp);
+    const int ng = nb < kEmitBlocks ? nb : kEmitBlocks;
+    k_emit_reduce<<<ng, kScanThreads, 0, st>>>(order, rects, n, scan_tmp);
     count_launches(1);
     k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nb, ctr, n_inst);
     count_launches(1);
-    k_emit_down<<<nb, kScanThreads, 0, st>>>(order, rects, n, tiles_x, scan_tmp, ikeys, ivals, cap, ctr);
+    k_emit_down<<<ng, kScanThreads, 0, st>>>(order, rects, n, tiles_x, scan_tmp, ikeys, ivals, cap, ctr);
     count_launches(1);
 }
 
