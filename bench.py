@@ -667,7 +667,7 @@ def run_finetune(args):
 
 def run_mlp(args):
     """Tensor-core roofline of the surrogate network alone: forward over `--mlp-rows` random
-    BF16 feature rows and the training step (64k-row batch: forward, backward, Adam)."""
+    BF16 feature rows and the training step (the surrogate's batch: forward, backward, Adam)."""
     import torch
 
     import paper_2607_02721_b300 as csgs
@@ -691,7 +691,9 @@ def run_mlp(args):
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     fwd_ms = e0.elapsed_time(e1) / args.steps
-    batch, steps = 65536, 50
+    from paper_2607_02721_b300 import surrogate
+
+    batch, steps = surrogate.SurrogateConfig().batch, 50
     ctx.mlp_train(X, t, batch=batch, steps=3, lr=1e-3, seed=1)
     torch.cuda.synchronize()
     e0.record(ctx.stream)
