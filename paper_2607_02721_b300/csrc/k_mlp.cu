@@ -529,11 +529,13 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restri
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
+        // the chunk's MMA first, so that the tensor core runs during the bias sums below (both
+        // only read the staged tiles; the wait comes after)
+        if (tid == 0) mma_tile(taddr, sA, sB, 128, tc::idesc_bf16(128, NIN), chunk > 0, &bar);
         // bias gradient: thread o < 128 sums its out's row of A over the chunk
         if (tid < 128)
             for (int r = 0; r < 128; ++r)
                 bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + tc::kmajor_off(tid, r, 128)));
-        if (tid == 0) mma_tile(taddr, sA, sB, 128, tc::idesc_bf16(128, NIN), chunk > 0, &bar);
         const bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
