@@ -41,6 +41,9 @@ extern "C" csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t 
     if (!p_dev || !idx_dev || !w_dev || !n_distinct) return CSGS_E_INVAL;
     if (n <= 0 || n > kMaxN) return CSGS_E_INVAL;
     if (m <= 0 || m >= (1ll << 31)) return CSGS_E_INVAL;
+    // An error left pending by earlier work on this thread is not this call's: report
+    // it without launching and leave it in place for its owner.
+    if (cudaPeekAtLastError() != cudaSuccess) return CSGS_E_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

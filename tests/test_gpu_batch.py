@@ -1,11 +1,13 @@
 """Multi-scene scoring in one submission (eager, captured as a CUDA graph, replayed)
 and the view-batch / sort-grid autotuner: every path returns the scores csgs_score
-returns scene by scene."""
+returns scene by scene, and the replayed graph's scores match the FP64 oracle."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2607_02721_b300 as csgs
 from paper_2607_02721_b300 import build, synth
+from parity_helpers import check_scores
 
 pytestmark = pytest.mark.gpu
 
@@ -27,18 +29,56 @@ def ctx(torch):
     c.close()
 
 
+SPEC = [(3000, 5, 96, 80, 1), (12000, 9, 128, 128, 2), (6000, 3, 200, 120, 3)]
+
+
+def make_scene(k):
+    n, v, W, H, seed = SPEC[k]
+    return synth.mixture_scene(n, 16, 3, seed, half_extent=2.0), synth.hemisphere_cameras(v, W, H, radius=7.0, seed=seed)
+
+
 @pytest.fixture(scope="module")
 def scenes(ctx):
     """Three scenes of uneven size, each with its own views (count and resolution)."""
-    spec = [(3000, 5, 96, 80, 1), (12000, 9, 128, 128, 2), (6000, 3, 200, 120, 3)]
     sids = []
-    for n, v, W, H, seed in spec:
-        sc = synth.mixture_scene(n, 16, 3, seed, half_extent=2.0)
-        cams = synth.hemisphere_cameras(v, W, H, radius=7.0, seed=seed)
+    for k in range(len(SPEC)):
+        sc, cams = make_scene(k)
         sid = ctx.load_scene(sc)
         ctx.set_queries(sid, cams)
         sids.append(sid)
     return sids
+
+
+@pytest.mark.parametrize("res", [("pixel", csgs.RES_PIXEL, oracle.RES_PIXEL), ("scene", csgs.RES_SCENE, oracle.RES_SCENE)],
+                         ids=["pixel", "scene"])
+def test_replayed_graph_matches_oracle(ctx, res):
+    """Scenes 0 and 2 of a captured submission, after a replay, against the oracle
+    scene by scene (its own context, so no earlier test changed the query sets)."""
+    c = csgs.Context(0)
+    try:
+        data = [make_scene(k) for k in range(len(SPEC))]
+        sids = []
+        for sc, cams in data:
+            sid = c.load_scene(sc)
+            c.set_queries(sid, cams)
+            sids.append(sid)
+        opts = csgs.default_opts(resolution=res[1])
+        outs, _ = c.score_batch(sids, opts, use_graph=True)       # eager pass + capture
+        for o in outs:
+            o.fill_(-1.0)
+        outs, S = c.score_batch(sids, opts, outs=outs, use_graph=True)  # replay
+        for k in (0, 2):
+            sc, cams = data[k]
+            ref = oracle.score(oracle.SceneArrays(sc), cams, oracle.Opts(resolution=res[2]))
+            s = outs[k].cpu().numpy()
+            if res[0] == "pixel":
+                check_scores(s, S[k], ref)
+            else:
+                big = ref["s"] > 1e-6
+                rel = np.abs(s[big].astype(np.float64) - ref["s"][big]) / ref["s"][big]
+                assert np.quantile(rel, 0.999) <= 1e-3 and abs(S[k] - 1.0) < 1e-4
+    finally:
+        c.close()
 
 
 def one_by_one(ctx, sids, opts):

@@ -1,13 +1,19 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (stated for the path's results):
+Tolerances (stated for the path's results; the comparison rules are in
+``parity_helpers``):
   rendered colours        1e-5 absolute
-  sensitivities           1e-3 relative where the oracle's value exceeds 1e-6
+  sensitivities           1e-3 relative where the oracle's value exceeds 1e-6, every
+                          Gaussian; S within 1e-3 relative
   coreset indices         bit-exact when the GPU sampler gets the oracle's p and seed
 Pixels where FP32 and FP64 can take a threshold decision differently (the oracle's
 straddle flags: footprint cut, alpha_min, t_min, near-equal depths) are excluded from
-the element-wise comparison and their share is bounded; Gaussians contributing to such
-pixels are compared through bounds instead.
+the element-wise render comparison and their share is bounded.
+
+Two scenes: the small workload (10,000 Gaussians, SH degree 0, eight 128x128 views)
+and an SH degree 3 mixture (24,000 Gaussians from 16 anisotropic components, 30%
+surface Gaussians, four 256x256 hemisphere views), so that the view-dependent colour
+of every SH degree reaches the element-wise comparison.
 """
 import json
 import math
@@ -23,8 +29,9 @@ from paper_2607_02721_b300 import build, synth
 
 pytestmark = pytest.mark.gpu
 
-RGB_TOL = 1e-5
-S_RTOL = 1e-3
+from parity_helpers import RGB_TOL, S_RTOL
+import parity_helpers
+
 STATS = {}
 
 
@@ -74,6 +81,27 @@ def small_sid(ctx, small):
     return sid
 
 
+@pytest.fixture(scope="module")
+def sh3():
+    sc = synth.mixture_scene(24_000, 16, 3, 5, half_extent=2.0)
+    cams = synth.hemisphere_cameras(4, 256, 256, radius=6.0, seed=5)
+    return sc, cams, 2_400, oracle.SceneArrays(sc)
+
+
+@pytest.fixture(scope="module")
+def sh3_sid(ctx, sh3):
+    sc, cams, _, _ = sh3
+    sid = ctx.load_scene(sc)
+    ctx.set_queries(sid, cams)
+    return sid
+
+
+@pytest.fixture(scope="module", params=["small", "sh3"])
+def workload(request, small, small_sid, sh3, sh3_sid):
+    """(scene, cameras, m, oracle arrays, scene id) of each parity scene."""
+    return (small + (small_sid,)) if request.param == "small" else (sh3 + (sh3_sid,))
+
+
 def render_gpu(ctx, sid, cam, view, **kw):
     H, W = int(cam[17]), int(cam[16])
     out = ctx.render(sid, view, H=H, W=W, **kw)
@@ -82,10 +110,10 @@ def render_gpu(ctx, sid, cam, view, **kw):
 
 # ---------------------------------------------------------------- projection
 
-def test_projection_matches_oracle(ctx, small, small_sid):
-    sc, cams, _, sa = small
-    for v in (0, 5):
-        g = ctx.debug_project(small_sid, v).cpu().numpy().astype(np.float64)
+def test_projection_matches_oracle(ctx, workload):
+    sc, cams, _, sa, sid = workload
+    for v in (0, len(cams) - 1):
+        g = ctx.debug_project(sid, v).cpu().numpy().astype(np.float64)
         o = oracle.project(sa, cams[v])
         ov = o[:, 0] > 0
         gv = g[:, 0] > 0
@@ -101,7 +129,13 @@ def test_projection_matches_oracle(ctx, small, small_sid):
         np.testing.assert_allclose(g[vv, 2], o[vv, 2], rtol=0, atol=2e-4)
         np.testing.assert_allclose(g[vv, 9], o[vv, 9], rtol=2e-7)
         np.testing.assert_allclose(g[vv, 6:9], o[vv, 6:9], rtol=2e-5, atol=1e-6)
-        np.testing.assert_allclose(g[vv, 3:6], o[vv, 3:6], rtol=5e-5, atol=1e-5)
+        # an entry of an inverted 2x2 matrix carries FP32 error in proportion to the
+        # matrix's scale, not its own size (the off-diagonal of a flattened Gaussian's
+        # conic is small and cancels): compare against the larger diagonal entry
+        scale = np.maximum(np.abs(o[vv, 3]), np.abs(o[vv, 5]))[:, None]
+        conic_err = np.abs(g[vv, 3:6] - o[vv, 3:6]) / scale
+        note("proj_conic_rel_scale", conic_err.max())
+        assert conic_err.max() <= 5e-5, conic_err.max()
         np.testing.assert_allclose(g[vv, 10], o[vv, 10], rtol=1e-6)
         np.testing.assert_allclose(g[vv, 11:14], o[vv, 11:14], atol=2e-6)
 
@@ -109,22 +143,13 @@ def test_projection_matches_oracle(ctx, small, small_sid):
 # ---------------------------------------------------------------- render
 
 def compare_render(rgb_gpu, ref, max_flag_frac=0.01):
-    fl = ref["flags"].astype(bool)
-    d = np.abs(rgb_gpu.astype(np.float64) - ref["rgb"])
-    assert fl.mean() <= max_flag_frac, fl.mean()
-    worst = d[~fl].max() if (~fl).any() else 0.0
-    note("render_rgb_abs_unflagged", worst)
-    note("render_flagged_frac", fl.mean())
-    if fl.any():
-        note("render_rgb_abs_flagged", d[fl].max())
-    assert worst <= RGB_TOL, (worst, np.unravel_index(np.argmax(np.where(fl[..., None], 0, d)), d.shape))
-    return worst, fl.mean()
+    return parity_helpers.compare_render(rgb_gpu, ref, max_flag_frac, note=note)
 
 
-def test_render_matches_oracle_small(ctx, small, small_sid):
-    sc, cams, _, sa = small
+def test_render_matches_oracle(ctx, workload):
+    sc, cams, _, sa, sid = workload
     for v in range(len(cams)):
-        rgb = render_gpu(ctx, small_sid, cams[v], v).cpu().numpy()
+        rgb = render_gpu(ctx, sid, cams[v], v).cpu().numpy()
         ref = oracle.render(sa, cams[v])
         compare_render(rgb, ref)
 
@@ -140,28 +165,12 @@ def test_render_transmittance_matches_oracle(ctx, small, small_sid):
 # ---------------------------------------------------------------- score
 
 def check_scores(s_gpu, S_gpu, ref, min_val=1e-6):
-    """Untouched Gaussians (no contribution to a straddling query): element-wise within
-    S_RTOL.  Touched ones: the GPU's max runs over a superset of the clean queries, so
-    it is at least s_clean; and only a small share may leave the tolerance."""
-    s_gpu = s_gpu.astype(np.float64)
-    s = ref["s"]
-    clean = ~ref["touched"] & (s > min_val)
-    rel = np.abs(s_gpu[clean] - s[clean]) / s[clean]
-    note("score_rel_untouched", rel.max())
-    note("touched_frac", ref["touched"].mean())
-    assert rel.max() <= S_RTOL, (rel.max(), np.argmax(rel))
-    t = ref["touched"] & (ref["s_clean"] > min_val)
-    assert np.all(s_gpu[t] >= ref["s_clean"][t] * (1 - S_RTOL))
-    big = ref["touched"] & (s > min_val)
-    off = np.abs(s_gpu[big] - s[big]) > S_RTOL * s[big]
-    note("touched_out_of_tol_frac", off.sum() / len(s))
-    assert off.sum() <= 0.02 * len(s)
-    assert abs(S_gpu - ref["S"]) <= 5e-3 * ref["S"]
+    parity_helpers.check_scores(s_gpu, S_gpu, ref, min_val, note=note)
 
 
-def test_score_pixel_matches_oracle_small(ctx, small, small_sid):
-    sc, cams, _, sa = small
-    s, S = ctx.score(small_sid)
+def test_score_pixel_matches_oracle(ctx, workload):
+    sc, cams, _, sa, sid = workload
+    s, S = ctx.score(sid)
     ref = oracle.score(sa, cams)
     check_scores(s.cpu().numpy(), S, ref)
     assert 1.0 <= S <= min(sc.n, ref["queries"]) * (1 + 1e-6)
@@ -242,8 +251,8 @@ def test_sampler_edge_cases(ctx, torch):
 
 # ---------------------------------------------------------------- weighted render
 
-def test_weighted_render_matches_oracle(ctx, small, small_sid, torch):
-    sc, cams, m, sa = small
+def test_weighted_render_matches_oracle(ctx, workload, torch):
+    sc, cams, m, sa, sid = workload
     ref = oracle.score(sa, cams)
     p, S = oracle.probabilities(ref["s"])
     o = oracle.sample(p, m, 11)
@@ -252,8 +261,9 @@ def test_weighted_render_matches_oracle(ctx, small, small_sid, torch):
     wfull[o["idx"]] = w32.astype(np.float64)
     idx_t = torch.tensor(o["idx"], device="cuda", dtype=torch.int32)
     w_t = torch.tensor(w32, device="cuda")
-    for v in (0, 6):
-        rgb = ctx.render(small_sid, v, idx=idx_t, w=w_t, H=128, W=128, opts=csgs.default_opts(collect_stats=1))
+    for v in (0, len(cams) - 2):
+        H, W = int(cams[v][17]), int(cams[v][16])
+        rgb = ctx.render(sid, v, idx=idx_t, w=w_t, H=H, W=W, opts=csgs.default_opts(collect_stats=1))
         st = ctx.stats()
         r = oracle.render(sa, cams[v], w=wfull)
         compare_render(rgb.cpu().numpy(), r)
@@ -390,9 +400,9 @@ VARIANTS = [("L1", csgs.VAR_L1, oracle.VAR_L1), ("L2", csgs.VAR_L2, oracle.VAR_L
 
 @pytest.mark.parametrize("res", RESOLUTIONS, ids=[r[0] for r in RESOLUTIONS])
 @pytest.mark.parametrize("var", VARIANTS, ids=[v[0] for v in VARIANTS])
-def test_resolutions_and_variants_match_oracle(ctx, small, small_sid, res, var):
-    sc, cams, _, sa = small
-    s, S = ctx.score(small_sid, csgs.default_opts(resolution=res[1], variant=var[1]))
+def test_resolutions_and_variants_match_oracle(ctx, workload, res, var):
+    sc, cams, _, sa, sid = workload
+    s, S = ctx.score(sid, csgs.default_opts(resolution=res[1], variant=var[1]))
     ref = oracle.score(sa, cams, Opts(resolution=res[2], variant=var[2], tile=16))
     s = s.cpu().numpy()
     if res[0] in ("pixel", "channel"):

@@ -85,6 +85,98 @@ def test_sh_basis_is_orthonormal():
         np.testing.assert_array_equal(oracle.sh_basis(deg, d), Y3[: (deg + 1) ** 2])
 
 
+def _real_sh_from_complex(l, m, d):
+    """Real spherical harmonic of degree l, order m along unit vector d, built from
+    scipy's complex Y_l^m (which carries the Condon-Shortley phase): sqrt(2) Re Y_l^m
+    for m > 0, Y_l^0 for m = 0, sqrt(2) Im Y_l^|m| for m < 0."""
+    from scipy.special import sph_harm_y
+
+    theta = math.acos(max(-1.0, min(1.0, d[2])))
+    phi = math.atan2(d[1], d[0])
+    Y = complex(sph_harm_y(l, abs(m), theta, phi))
+    if m == 0:
+        return Y.real
+    return math.sqrt(2.0) * (Y.real if m > 0 else Y.imag)
+
+
+def test_sh_basis_matches_complex_harmonics():
+    """Every one of the 16 basis functions (order m = -l..l at index l^2 + l + m), at
+    random directions and the six axis directions, against an evaluation that shares
+    nothing with the oracle's constants: a sign flip, a swapped order or a wrong
+    normalisation of any degree-1..3 function fails here."""
+    rng = np.random.default_rng(0)
+    dirs = rng.standard_normal((50, 3))
+    dirs = np.concatenate([dirs, np.eye(3), -np.eye(3)])
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    for d in dirs:
+        Y = oracle.sh_basis(3, d)
+        ref = [_real_sh_from_complex(l, m, d) for l in range(4) for m in range(-l, l + 1)]
+        np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-12)
+
+
+def _sh_scene(mu, coeffs, opac_logit=0.3, sig=0.05):
+    """One Gaussian with SH degree 3 colour: ``coeffs`` maps (basis index, channel) to a
+    coefficient; every other coefficient is zero."""
+    sh = np.zeros((16, 3, 1), dtype=np.float32)
+    for (k, ch), v in coeffs.items():
+        sh[k, ch, 0] = v
+    return synth.Scene(np.asarray(mu, dtype=np.float32).reshape(3, 1),
+                       np.full((3, 1), math.log(sig), dtype=np.float32),
+                       np.array([[1.0], [0.0], [0.0], [0.0]], dtype=np.float32),
+                       np.array([opac_logit], dtype=np.float32), sh)
+
+
+def test_view_direction_of_the_colour_closed_form():
+    """The colour is evaluated along the direction from the camera centre to the mean
+    (Sec. 3: view-dependent colour c_i(q)).  A Gaussian at the origin seen along the
+    world z axis from below and from above: at the poles the zonal harmonics are
+    Y_l^0 = (+-1)^l sqrt((2l + 1) / (4 pi)) (Legendre P_l(+-1) = (+-1)^l), so the
+    degree-1 and degree-3 terms change sign between the two cameras and the degree-2
+    term does not.  Seen along +x and +y, the order-(+-1) degree-1 functions are
+    -sqrt(3 / (4 pi)) x and -sqrt(3 / (4 pi)) y (Condon-Shortley phase).  The centre
+    pixel of each render is that colour times the opacity (k = 1 there)."""
+    y1 = math.sqrt(3.0 / (4.0 * math.pi))
+    y2 = math.sqrt(5.0 / (4.0 * math.pi))
+    y3 = math.sqrt(7.0 / (4.0 * math.pi))
+    dc = (0.1, -0.2, 0.3)
+    coeffs = {(0, 0): dc[0], (0, 1): dc[1], (0, 2): dc[2],
+              (2, 0): 0.3, (12, 1): 0.25, (6, 2): 0.2,   # zonal l = 1, 3, 2
+              (3, 0): 0.15, (1, 1): -0.35}                # l = 1, m = +1 (x) and m = -1 (y)
+    sc = _sh_scene([0.0, 0.0, 0.0], coeffs)
+    sh = sc.sh[:, :, 0].astype(np.float64)
+    base = C0 * sh[0] + 0.5
+    alpha = sigmoid(0.3)
+    # camera centres and world-to-camera rotations (rows = camera axes in world
+    # coordinates, right-handed), each 2 units from the Gaussian and looking at it
+    views = [
+        ((0.0, 0.0, -2.0), np.eye(3), (0, 0, 1.0)),
+        ((0.0, 0.0, 2.0), np.diag([1.0, -1.0, -1.0]), (0, 0, -1.0)),
+        ((-2.0, 0.0, 0.0), np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]]), (1.0, 0, 0)),
+        ((0.0, -2.0, 0.0), np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]), (0, 1.0, 0)),
+    ]
+    for C, R, d in views:
+        assert abs(np.linalg.det(R) - 1.0) < 1e-12
+        t = -R @ np.asarray(C)
+        cam = axis_camera(W=33, H=33, f=40.0, R=R, t=t)
+        x, y, z = d
+        expect = base.copy()
+        expect[0] += sh[2, 0] * y1 * z + sh[3, 0] * (-y1 * x)
+        expect[1] += sh[12, 1] * y3 * z ** 3 + sh[1, 1] * (-y1 * y)
+        expect[2] += sh[6, 2] * y2 * (1.5 * z * z - 0.5)
+        expect = np.maximum(expect, 0.0)
+        P = oracle.project(sc, cam)[0]
+        assert P[0] == 1 and abs(P[9] - 2.0) < 1e-12
+        np.testing.assert_allclose(P[11:14], expect, rtol=0, atol=1e-12)
+        out = oracle.render(sc, cam, Opts())
+        np.testing.assert_allclose(out["rgb"][16, 16], expect * alpha, rtol=0, atol=1e-12)
+    # the odd degrees really flip: the two z-axis colours differ by 2 y1 c_(l=1) etc.
+    P0 = oracle.project(sc, axis_camera(R=views[0][1], t=-views[0][1] @ np.asarray(views[0][0])))[0]
+    P1 = oracle.project(sc, axis_camera(R=views[1][1], t=-views[1][1] @ np.asarray(views[1][0])))[0]
+    np.testing.assert_allclose(P0[11] - P1[11], 2 * y1 * sh[2, 0], atol=1e-12)
+    np.testing.assert_allclose(P0[12] - P1[12], 2 * y3 * sh[12, 1], atol=1e-12)
+    np.testing.assert_allclose(P0[13] - P1[13], 0.0, atol=1e-12)
+
+
 def test_philox_known_answers():
     rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
     assert len(rows) == 3
@@ -220,6 +312,69 @@ def test_two_gaussians_on_axis_closed_form():
     a1l, a2l = np.dot(c1, wl) * p1, np.dot(c2, wl) * p2 * (1 - p1)
     rl = oracle.score(sc, cam[None], Opts(obj_w=wl))
     np.testing.assert_allclose(rl["s"], [np.max(a2l[m] / (a1l + a2l)[m]), np.max(a1l[m] / (a1l + a2l)[m])], rtol=1e-12)
+
+
+def test_two_gaussians_resolutions_and_variants_closed_form():
+    """Sec. 3.5's resolutions and variants written out by hand for two Gaussians on
+    the optical axis (index 1 in front), from the per-pixel closed forms
+    rho_1, rho_2, T_1 = 1, T_2 = 1 - rho_1:
+      channel  s_i = max over (pixel, lambda) with A_lambda > 0 of a_i,lambda / A_lambda
+      tile     s_i = max over 11x11 tiles of (sum_tile a_i) / (sum_tile A)
+      image    s_i = (sum_image a_i) / (sum_image A)  (one view: the scene query)
+      L2       a_i = sum_lambda (c_i,lambda rho_i T_i)^2,  no-colour  a_i = rho_i T_i
+    with A the sum of the same terms over the pixel's contributors."""
+    f, dil = 40.0, DIL
+    s1, s2, z1, z2, l1, l2 = 0.03, 0.06, 1.5, 2.5, 0.4, -0.2
+    c1, c2 = np.array([0.9, 0.1, 0.2]), np.array([0.1, 0.7, 0.6])
+    sc = one_scene([[0, 0, z2], [0, 0, z1]], [[math.log(s2)] * 3, [math.log(s1)] * 3], [c2, c1], [l2, l1])
+    c2, c1 = (C0 * sc.sh[0, :, 0].astype(np.float64) + 0.5), (C0 * sc.sh[0, :, 1].astype(np.float64) + 0.5)
+    cam = axis_camera(f=f)
+    yy, xx = np.mgrid[0:33, 0:33]
+    r2 = (xx - 16.0) ** 2 + (yy - 16.0) ** 2
+    o = Opts()
+
+    def rho(s, z, lg):
+        v = (f * eff_scale(s) / z) ** 2 + dil
+        r = np.minimum(o.rho_max, sigmoid(lg) * np.exp(-0.5 * r2 / v))
+        r[(r2 / v > 9) | (r < o.alpha_min)] = 0.0
+        return r
+
+    p1, p2 = rho(s1, z1, l1), rho(s2, z2, l2)
+    w1, w2 = p1, p2 * (1 - p1)                      # rho T of each contributor
+    a1c, a2c = c1 * w1[..., None], c2 * w2[..., None]  # per-channel L1 terms [33, 33, 3]
+
+    def score(**kw):
+        return oracle.score(sc, cam[None], Opts(**kw))["s"]  # [Gaussian 0 (back), 1 (front)]
+
+    # per-channel (L1)
+    A = a1c + a2c
+    m = A > 0
+    np.testing.assert_allclose(score(resolution=oracle.RES_CHANNEL),
+                               [np.max(a2c[m] / A[m]), np.max(a1c[m] / A[m])], rtol=1e-12)
+    # per-pixel L2 and no-colour
+    for var, t1, t2 in ((oracle.VAR_L2, (a1c ** 2).sum(-1), (a2c ** 2).sum(-1)), (oracle.VAR_NC, w1, w2)):
+        At = t1 + t2
+        mm = At > 0
+        np.testing.assert_allclose(score(variant=var), [np.max(t2[mm] / At[mm]), np.max(t1[mm] / At[mm])],
+                                   rtol=1e-12)
+    # per-channel L2: each channel's own squared terms
+    A2 = a1c ** 2 + a2c ** 2
+    m2 = A2 > 0
+    np.testing.assert_allclose(score(resolution=oracle.RES_CHANNEL, variant=oracle.VAR_L2),
+                               [np.max(a2c[m2] ** 2 / A2[m2]), np.max(a1c[m2] ** 2 / A2[m2])], rtol=1e-12)
+    # per-tile (11x11 tiles of the 33x33 image) and per-image, L1 pixel objective
+    t1, t2 = a1c.sum(-1), a2c.sum(-1)
+    tiles = []
+    for ty in range(3):
+        for tx in range(3):
+            sl = (slice(11 * ty, 11 * ty + 11), slice(11 * tx, 11 * tx + 11))
+            At = t1[sl].sum() + t2[sl].sum()
+            if At > 0:
+                tiles.append((t2[sl].sum() / At, t1[sl].sum() / At))
+    np.testing.assert_allclose(score(resolution=oracle.RES_TILE, tile=11), np.max(np.array(tiles), 0), rtol=1e-12)
+    Ai = t1.sum() + t2.sum()
+    np.testing.assert_allclose(score(resolution=oracle.RES_IMAGE), [t2.sum() / Ai, t1.sum() / Ai], rtol=1e-12)
+    np.testing.assert_allclose(score(resolution=oracle.RES_SCENE), [t2.sum() / Ai, t1.sum() / Ai], rtol=1e-12)
 
 
 def test_early_termination_and_order_invariants():
