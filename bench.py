@@ -45,6 +45,19 @@ OPS_PER_PAIR = 18
 OPS_TEST, OPS_HIT1, OPS_HIT2 = 6, 8, 5
 SMS, FP32_LANES = 148, 128
 
+# Algorithmic bytes of the HBM-bound phases (per launch of a view batch of nb views):
+#   projection: each Gaussian's attributes read once (means 12, log-scales 12, quaternion 16,
+#     opacity 4, SH (d+1)^2 x 12 bytes: 236 B at degree 3), then per (view, Gaussian) a depth
+#     key (4 B) and a tile rectangle (8 B) written, plus the 48-byte splat of a visible one;
+#   binning: depth sort of nb x N keys in three 9-bit passes (histogram read 4 B, scatter
+#     read 8 B (4 B in the first pass: the values are the indices) and write 8 B per key and
+#     pass: 56 B), the emit (depth order and rectangle read in both of its passes: 24 B per
+#     (view, Gaussian); (key, value) written: 8 B per instance) and the (view, tile) sort of
+#     the instances in two passes (20 B per instance and pass).
+PROJ_READ_PER_G = {0: 56, 1: 92, 2: 152, 3: 236}
+PROJ_WRITE_PER_VG, PROJ_WRITE_PER_VIS = 12, 48
+SORT_PER_VG, SORT_PER_INST = 56 + 24, 8 + 2 * 20
+
 
 def workload(name: str):
     from paper_2607_02721_b300 import synth
@@ -267,7 +280,7 @@ def run_ours(args):
     import torch
 
     import paper_2607_02721_b300 as csgs
-    from paper_2607_02721_b300 import build
+    from paper_2607_02721_b300 import build, sharded
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -293,7 +306,16 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=local)
     ctx = csgs.Context(local, stream=stream)
     sid = ctx.load_scene(scene)
-    ctx.set_queries(sid, cams)
+    # one workload over all ranks: each scores its round-robin share of the views, and one
+    # all-reduce per step (MAX of s; per-scene: SUM) combines them (strong scaling)
+    my_views = sharded.shard_views(len(cams), rank, world)
+    if world > 1:
+        cfg["parallelism"] = f"views sharded over {world} ranks, all-reduce of s per step"
+        cfg["views_per_rank"] = int(len(my_views))
+    else:
+        cfg["parallelism"] = "single GPU"
+    ctx.set_queries(sid, cams[my_views])
+    rays_local = int(sum(int(c[16]) * int(c[17]) for c in cams[my_views]))
     s = torch.empty(scene.n, dtype=torch.float32, device=f"cuda:{local}")
     tuned = None
     if not args.no_autotune and not args.view_batch:
@@ -304,11 +326,22 @@ def run_ours(args):
     # pair counts of one pass (untimed; counting kernels are slower)
     ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch, resolution=res_id), out=s)
     cnt = ctx.stats()
+    # visible (view, Gaussian) fraction for the projection's algorithmic bytes (untimed,
+    # four views spread over the query set)
+    vis_views = sorted({int(k * len(cams) / 4) for k in range(4)})
+    vis_frac = float(np.mean([float((ctx.debug_project(sid, v)[:, 0] > 0).float().mean()) for v in vis_views]))
+    torch.cuda.empty_cache()
     timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch, resolution=res_id)
+
+    def combine(st):
+        if dist is not None:
+            ctx.sync()
+            sharded.combine_shards(s, st["objective_sum"], res_id, dist, ctx.scale_scores)
 
     def step(seed):
         ctx.score(sid, timing, out=s)
         st = ctx.stats()
+        combine(st)
         ctx.sample_coreset(s, m, seed)
         return st
 
@@ -336,22 +369,24 @@ def run_ours(args):
     launches = csgs.kernel_launch_count() - l0
     clk = clocks.stop()
     el_ms = job_time_ms(ev0.elapsed_time(ev1), dist, torch.device("cuda", local))
-    value = job_rate(cfg["rays_per_step"] * args.steps, world, el_ms)
+    # the ranks together score the workload's rays once per step
+    value = job_rate(cfg["rays_per_step"] * args.steps / world, world, el_ms)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
         host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
                 for a in (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh)]
-        h2d = sum(h.numel() * 4 for h in host) + len(cams) * 80
+        h2d = sum(h.numel() * 4 for h in host) + len(my_views) * 80
         s_host = torch.empty(scene.n, dtype=torch.float32).pin_memory()
         idx_host = torch.empty(m, dtype=torch.int32).pin_memory()
         w_host = torch.empty(m, dtype=torch.float32).pin_memory()
 
         def e2e_step(seed):
             sid2 = ctx.load_scene_ptrs(scene.n, scene.sh_degree, [h.data_ptr() for h in host], is_device=False)
-            ctx.set_queries(sid2, cams)
+            ctx.set_queries(sid2, cams[my_views])
             s2, _ = ctx.score(sid2, csgs.default_opts(resolution=res_id), out=s)
+            combine(ctx.stats())
             idx, w = ctx.sample_coreset(s2, m, seed)
             with torch.cuda.stream(stream):
                 s_host.copy_(s2, non_blocking=True)
@@ -370,6 +405,7 @@ def run_ours(args):
             d2h = e2e_step(2000 + i)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
+        te = job_time_ms(te * 1e3, dist, torch.device("cuda", local)) / 1e3
         e2e = {"value": cfg["rays_per_step"] * ne / te, "unit": "rays/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": ne}
 
@@ -396,17 +432,39 @@ def run_ours(args):
             "essential_ops_frac": (ess_achieved / peak) if ess_achieved else None,
             "achieved_busy": achieved_busy, "frac_busy": (achieved_busy / peak) if achieved_busy else None,
             "busy_ms_per_step": busy_s * 1e3,
-            "pairs_per_ray": (cnt["pairs_evaluated"] / cfg["rays_per_step"]),
-            "pairs_per_ray_pass2": (cnt["pairs_evaluated2"] / cfg["rays_per_step"]),
-            "contributing_pairs_per_ray": (cnt["pairs_hit"] / cfg["rays_per_step"]),
+            "pairs_per_ray": (cnt["pairs_evaluated"] / rays_local),
+            "pairs_per_ray_pass2": (cnt["pairs_evaluated2"] / rays_local),
+            "contributing_pairs_per_ray": (cnt["pairs_hit"] / rays_local),
             "staged_fraction": [cnt["entries_staged"] / max(cnt["instances"], 1),
                                 cnt["entries_staged2"] / max(cnt["instances"], 1)],
+            # evaluated pairs over the lanes of the warps' list iterations (pass 1, pass 2)
+            "lane_utilization": [cnt["pairs_evaluated"] / max(32 * cnt["warp_entries"], 1),
+                                 cnt["pairs_evaluated2"] / max(32 * cnt["warp_entries2"], 1)],
             "share_of_step": comp_ms / max(el_ms, 1e-9)}
     if stale:
         roof["traffic_note"] = "ncu counters predate the current kernel source"
+    # HBM phases: algorithmic bytes per launch / the launch's mean CUDA-event duration
+    hbm_peak = peaks().get("hbm_gbs")
+    nbatch = max(1, cnt["view_batches"])
+    nvg = scene.n * len(my_views)  # (view, Gaussian) pairs per step on this rank
+    proj_bytes = (PROJ_READ_PER_G[scene.sh_degree] * scene.n * nbatch + PROJ_WRITE_PER_VG * nvg
+                  + PROJ_WRITE_PER_VIS * vis_frac * nvg)
+    sort_bytes = SORT_PER_VG * nvg + SORT_PER_INST * cnt["instances"]
+    for key, nbytes, ms, nl in (("project", proj_bytes, proj_ms, nbatch), ("sort", sort_bytes, sort_ms, len(my_views))):
+        per_launch_s = ms / args.steps / nl / 1e3
+        ach = nbytes / nl / per_launch_s / 1e9 if per_launch_s > 0 else None
+        roof[key] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": (ach / hbm_peak) if (ach and hbm_peak) else None,
+                     "bytes_per_launch": nbytes / nl, "avg_launch_ms": per_launch_s * 1e3,
+                     "launches_per_step": nl, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, read + write)"}
+    roof["project"]["visible_fraction"] = vis_frac
+    roof["project"]["note"] = "one launch projects one view batch"
+    roof["sort"]["note"] = ("one launch = the binning chain of one view (depth sort, emit, tile sort, ranges); "
+                            "chains of three views overlap each other and the compositing")
 
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
             "gpu_launches": int(launches),
             "phases_ms_per_step": {"project": proj_ms / args.steps, "sort_and_bin": sort_ms / args.steps,

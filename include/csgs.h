@@ -129,6 +129,12 @@ typedef struct {
     int64_t entries_staged2;  /* tile-list entries staged by pass 2 (bit 0) */
     double composite_busy_ms; /* time some compositing launch was running: the union of their spans, which
                                  overlap on the two compositing streams (bit 1) */
+    int64_t view_batches;     /* csgs_score: view batches (one projection launch and one binning chain each) */
+    int64_t warp_entries;     /* compositing pass 1: (warp, tile-list entry) iterations; 32 x this over
+                                 pairs_evaluated is the lanes' idle share (bit 0, pixel and channel scores) */
+    int64_t warp_entries2;    /* ... of scoring pass 2 (bit 0) */
+    double objective_sum;     /* per-scene resolution: sum over the call's queries of the objective A(q), the
+                                 denominator of its scores (lets view shards combine their scores) */
 } csgs_stats;
 
 /* Fill *o with the default conventions above. */
@@ -298,6 +304,17 @@ csgs_status csgs_adam_update(csgs_ctx* ctx, float* p_dev, const float* g_dev, fl
 /* Wait for the context's stream and report errors of asynchronous work. */
 csgs_status csgs_sync(csgs_ctx* ctx);
 
+/* s_dev[i] = s_dev[i] * factor (FP64 product rounded to FP32), device float[n], on the
+ * context's stream (asynchronous).  factor finite and >= 0 (else CSGS_E_INVAL).  The
+ * per-scene resolution of Sec. 3.5 is a ratio of sums over queries: view shards combine
+ * their scores s_r into the whole query set's by s = sum_r s_r A_r / sum_r A_r, with A_r
+ * the shard's objective total (csgs_stats.objective_sum); this scales one shard. */
+csgs_status csgs_scale_scores(csgs_ctx* ctx, float* s_dev, int64_t n, double factor);
+
+/* S = sum_i s_i (Alg. 1 step 3) in FP64, in the fixed order csgs_score uses; s_dev:
+ * device float[n].  Synchronises. */
+csgs_status csgs_total_sensitivity(csgs_ctx* ctx, const float* s_dev, int64_t n, double* S_out);
+
 /* Counters of the last score / render (synchronises). */
 csgs_status csgs_get_stats(csgs_ctx* ctx, csgs_stats* out);
 
@@ -334,6 +351,18 @@ csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t n, int64_t 
  * Synchronises; CSGS_E_TIMEOUT if the MMA completion was not observed in time. */
 csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
                                int32_t N);
+
+/* Diagnostic of the bounded device waits: csgs_debug_tc_gemm with the threads' wait for
+ * the MMA chain's completion limited to first_wait_cycles SM clock cycles (0: a single
+ * non-blocking test of the completion barrier, which an MMA chain issued a moment
+ * earlier has not reached).  A warp whose wait runs out records the error and then
+ * waits, with the kernels' full budget (about one second), for the chain to drain, so
+ * that no MMA is in flight when the kernel frees its tensor memory and returns; the
+ * context stays usable.  Returns CSGS_E_TIMEOUT when the first wait ran out (C_dev is
+ * then partly unwritten), CSGS_E_INVAL for a negative budget.  Synchronises.  The paper
+ * has no counterpart: this exercises the failure path of the library's own waits. */
+csgs_status csgs_debug_tc_gemm_wait(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                                    int32_t N, int64_t first_wait_cycles);
 
 /* Diagnostic: the surrogate network's activation as its kernels evaluate it:
  * out_dev[2i] = GELU(z_i) = z_i Phi(z_i), out_dev[2i+1] = GELU'(z_i) (erf by Abramowitz &

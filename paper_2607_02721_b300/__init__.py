@@ -70,14 +70,16 @@ class Stats(ctypes.Structure):
                 ("composite_launches", ctypes.c_int64), ("queries", ctypes.c_int64), ("score_ms", ctypes.c_double),
                 ("project_ms", ctypes.c_double), ("sort_ms", ctypes.c_double), ("composite_ms", ctypes.c_double),
                 ("entries_staged", ctypes.c_int64), ("entries_staged2", ctypes.c_int64),
-                ("composite_busy_ms", ctypes.c_double)]
+                ("composite_busy_ms", ctypes.c_double), ("view_batches", ctypes.c_int64),
+                ("warp_entries", ctypes.c_int64), ("warp_entries2", ctypes.c_int64),
+                ("objective_sum", ctypes.c_double)]
 
 
 EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
            "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
            "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
-           "csgs_debug_tc_gemm", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
+           "csgs_debug_tc_gemm", "csgs_debug_tc_gemm_wait", "csgs_scale_scores", "csgs_total_sensitivity", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
            "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
            "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update",
            "csgs_score_batch", "csgs_autotune", "csgs_debug_gelu")
@@ -119,6 +121,9 @@ def lib():
     L.csgs_theorem3_eps.argtypes = [ctypes.c_double, ctypes.c_double]
     L.csgs_theorem3_eps.restype = ctypes.c_double
     L.csgs_debug_tc_gemm.argtypes = [V, V, V, V, I32, I32]
+    L.csgs_debug_tc_gemm_wait.argtypes = [V, V, V, V, I32, I32, ctypes.c_int64]
+    L.csgs_scale_scores.argtypes = [V, V, ctypes.c_int64, ctypes.c_double]
+    L.csgs_total_sensitivity.argtypes = [V, V, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
     L.csgs_mlp_init.argtypes = [V, U64]
     L.csgs_mlp_set_params.argtypes = [V, V]
     L.csgs_mlp_get_params.argtypes = [V, V]
@@ -265,6 +270,10 @@ class Context:
         self._scenes[sid.value] = n
         return sid.value
 
+    def scene_size(self, sid: int) -> int:
+        """Number of Gaussians of a loaded scene."""
+        return self._scenes[sid]
+
     def free_scene(self, sid: int):
         self._check(lib().csgs_free_scene(self.h, sid))
         self._scenes.pop(sid, None)
@@ -286,6 +295,21 @@ class Context:
         self._check(lib().csgs_score(self.h, sid, ctypes.byref(opts), _ptr(out), ctypes.byref(S)))
         self._out()
         return out, S.value
+
+    def scale_scores(self, s, factor: float):
+        """s *= factor in place (library kernel, FP64 product rounded to FP32)."""
+        self._in()
+        self._check(lib().csgs_scale_scores(self.h, _ptr(s), s.numel(), float(factor)))
+        self._out()
+        return s
+
+    def total_sensitivity(self, s) -> float:
+        """S = sum of s in FP64 (the library's fixed-order reduction)."""
+        S = ctypes.c_double()
+        self._in()
+        self._check(lib().csgs_total_sensitivity(self.h, _ptr(s), s.numel(), ctypes.byref(S)))
+        self._out()
+        return S.value
 
     def score_batch(self, sids, opts: ScoreOpts | None = None, outs=None, use_graph: bool = True):
         """Scores of several scenes in one submission (replayed as one CUDA graph after
@@ -471,6 +495,17 @@ class Context:
         C = self._empty((A.shape[0], B.shape[0]), torch.float32)
         self._in()
         self._check(lib().csgs_debug_tc_gemm(self.h, _ptr(A), _ptr(B), _ptr(C), A.shape[1], B.shape[0]))
+        self._out()
+        return C
+
+    def debug_tc_gemm_wait(self, A, B, first_wait_cycles: int):
+        """debug_tc_gemm with the completion wait limited to ``first_wait_cycles`` clock
+        cycles (0: one non-blocking test); raises CsgsError(CSGS_E_TIMEOUT) when it ran out."""
+        torch = self.torch
+        C = self._empty((A.shape[0], B.shape[0]), torch.float32)
+        self._in()
+        self._check(lib().csgs_debug_tc_gemm_wait(self.h, _ptr(A), _ptr(B), _ptr(C), A.shape[1], B.shape[0],
+                                                  int(first_wait_cycles)))
         self._out()
         return C
 

@@ -10,6 +10,7 @@
 #include <random>
 #include <string>
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "csgs_internal.cuh"
@@ -29,10 +30,9 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-// Buffers of one view's binning (depth sort, instances, tile sort, ranges).  Scoring
-// rotates over kBinSlots slots so that the binning of the next views, each on its
-// slot's own high-priority stream, overlaps the compositing of the current one (the
-// binning kernels are latency-bound, so several binning chains also overlap each other).
+// Buffers of one view batch's binning (depth sort, instances, tile sort, ranges).  Scoring
+// alternates over kBinSlots slots so that the binning of the next view batch, on its
+// slot's own high-priority stream, overlaps the compositing of the current one.
 struct BinSlot {
     DevBuf dkeys_b, dvals_a, dvals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, ranges, hist, scan_tmp;
     cudaStream_t st = nullptr;
@@ -97,6 +97,7 @@ struct csgs_ctx {
     long long graph_nodes_launches = 0;
     unsigned long long buf_gen = 0;  // bumped whenever a work buffer is reallocated
     bool wide_keys = false;          // a view's depth range overflowed the narrow keys: 32-bit keys from then on
+    int max_tiles = 0;               // ranges per view row in the binning slots
 };
 
 namespace {
@@ -212,7 +213,8 @@ SceneDev scene_dev(const SceneRec& s) {
     return d;
 }
 
-// Per-view buffers for a batch of `vb` views and the instance buffers.
+// Per-view buffers for a batch of `vb` views and the binning slots' buffers (one view
+// each: scoring bins every view in its own chain).
 csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles) {
     csgs_status r;
     for (int k = 0; k < 2; ++k) {
@@ -227,12 +229,15 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
         ctx->cap = (uint32_t)c;
     }
     const size_t ib = sizeof(uint32_t) * (size_t)ctx->cap;
+    const size_t nv = (size_t)n;
+    // the row stride of the ranges only grows (a captured graph keeps the stride it saw)
+    if (max_tiles > ctx->max_tiles) ctx->max_tiles = max_tiles;
     for (BinSlot& b : ctx->slot) {
-        if ((r = ensure(ctx, b.dkeys_b, sizeof(uint32_t) * (size_t)n))) return r;
-        if ((r = ensure(ctx, b.dvals_a, sizeof(uint32_t) * (size_t)n))) return r;
-        if ((r = ensure(ctx, b.dvals_b, sizeof(uint32_t) * (size_t)n))) return r;
-        if ((r = ensure(ctx, b.ranges, sizeof(uint2) * (size_t)max_tiles))) return r;
-        if ((r = ensure(ctx, b.hist, sizeof(uint32_t) * kSortHistWords))) return r;
+        if ((r = ensure(ctx, b.dkeys_b, sizeof(uint32_t) * nv))) return r;
+        if ((r = ensure(ctx, b.dvals_a, sizeof(uint32_t) * nv))) return r;
+        if ((r = ensure(ctx, b.dvals_b, sizeof(uint32_t) * nv))) return r;
+        if ((r = ensure(ctx, b.ranges, sizeof(uint2) * (size_t)ctx->max_tiles))) return r;
+        if ((r = ensure(ctx, b.hist, sizeof(uint32_t) * sort_hist_stride(kSortMaxBlocks)))) return r;
         if ((r = ensure(ctx, b.scan_tmp, sizeof(uint32_t) * ((size_t)(n + 255) / 256 + 64)))) return r;
         if ((r = ensure(ctx, b.ikeys_a, ib))) return r;
         if ((r = ensure(ctx, b.ikeys_b, ib))) return r;
@@ -242,27 +247,42 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
     return CSGS_OK;
 }
 
-// Depth sort -> instances -> tile sort -> ranges for one projected view, in binning
-// slot `k` on stream `st`.  Returns the instance value buffer (Gaussian ids in tile,
-// depth order); the ranges are in slot k's `ranges`.
-const uint32_t* bin_view(csgs_ctx* ctx, int k, int64_t n, uint32_t* keys_v, const uint2* rects_v, const CamDev& cam,
-                         bool narrow, cudaStream_t st) {
+// Depth sort -> instances -> (view, tile) sort -> ranges for nv projected views (keys and
+// rectangles [nv][n], cameras cams[0..nv) on host and device) in binning slot `k` on
+// stream `st`.  Returns the instance value buffer (Gaussian ids in view, tile, depth
+// order); view v's ranges are row v (ctx->max_tiles ranges per row) of slot k's `ranges`.
+// Scoring bins one view per chain (nv = 1): one sort over a whole view batch (segments
+// per view, (view, tile) keys) measured slower, because each radix pass is bound by the
+// latency of its 2048-key sub-tiles, not by the array's size.  The slot buffers are sized
+// for nv = 1.
+const uint32_t* bin_batch(csgs_ctx* ctx, int k, int64_t n, int nv, uint32_t* keys, const uint2* rects,
+                          const CamDev* h_cams, const CamDev* d_cams, bool narrow, cudaStream_t st) {
     BinSlot& b = ctx->slot[k];
     unsigned long long* n_inst = &ctx->d_ctr->n_inst[k];
+    // one segment per view; the grid is split over the segments
+    int gseg = ctx->sort_blocks / nv;
+    if (gseg < 8) gseg = 8;
     // narrow depth keys: three 9-bit passes; the float bits: four 8-bit passes
-    int cur = radix_sort_pairs(keys_v, P<uint32_t>(b.dvals_a), P<uint32_t>(b.dkeys_b), P<uint32_t>(b.dvals_b),
+    int cur = radix_sort_pairs(keys, P<uint32_t>(b.dvals_a), P<uint32_t>(b.dkeys_b), P<uint32_t>(b.dvals_b),
                                ctx->d_nconst, (uint32_t)n, narrow ? kNarrowKeyBits : 32, narrow ? 9 : 8,
-                               P<uint32_t>(b.hist), ctx->sort_blocks, true, st);
+                               P<uint32_t>(b.hist), gseg, true, nv, (size_t)n, st);
     const uint32_t* order = cur ? P<uint32_t>(b.dvals_b) : P<uint32_t>(b.dvals_a);
-    emit_instances(order, rects_v, (int)n, cam.tiles_x, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
+    int tbits = 1;
+    for (int v = 0; v < nv; ++v) {
+        const int tb = ceil_log2((uint32_t)(h_cams[v].tiles_x * h_cams[v].tiles_y));
+        if (tb > tbits) tbits = tb;
+    }
+    emit_instances(order, rects, (int)n, nv, d_cams, tbits, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
                    P<uint32_t>(b.scan_tmp), ctx->d_ctr, n_inst, st);
-    const int ntiles = cam.tiles_x * cam.tiles_y;
+    const int kbits = tbits + ceil_log2((uint32_t)nv);
+    // 9-bit digits once the key needs more than two 8-bit passes
+    const int db = kbits > 16 ? 9 : 8;
     int cur2 = radix_sort_pairs(P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), P<uint32_t>(b.ikeys_b),
-                                P<uint32_t>(b.ivals_b), n_inst, ctx->cap, ceil_log2((uint32_t)ntiles), 8,
-                                P<uint32_t>(b.hist), ctx->sort_blocks, false, st);
+                                P<uint32_t>(b.ivals_b), n_inst, ctx->cap, kbits, db, P<uint32_t>(b.hist),
+                                ctx->sort_blocks, false, 1, 0, st);
     const uint32_t* ik = cur2 ? P<uint32_t>(b.ikeys_b) : P<uint32_t>(b.ikeys_a);
     const uint32_t* iv = cur2 ? P<uint32_t>(b.ivals_b) : P<uint32_t>(b.ivals_a);
-    tile_ranges(ik, n_inst, ctx->cap, P<uint2>(b.ranges), ntiles, st);
+    tile_ranges(ik, n_inst, ctx->cap, P<uint2>(b.ranges), nv, d_cams, tbits, ctx->max_tiles, st);
     return iv;
 }
 
@@ -691,7 +711,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, ctx->ev_proj[set], 0));
             if (freed_recorded[sl]) CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, slot.freed, 0));
             size_t e1 = pt.begin(slot.st);
-            const uint32_t* iv = bin_view(ctx, sl, n, keys_v, rects_v, cam, ko.narrow_keys != 0, slot.st);
+            const uint32_t* iv = bin_batch(ctx, sl, n, 1, keys_v, rects_v, &cam, s->d_cams + v0 + k,
+                                           ko.narrow_keys != 0, slot.st);
             pt.end(1, e1, slot.st);
             CUDA_TRY(ctx, cudaEventRecord(slot.ready, slot.st));
             const int ci = view % ncs;  // compositing stream of this view
@@ -828,6 +849,10 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     ctx->stats.queries = (int64_t)ctx->h_ctr->queries;
     ctx->stats.entries_staged = (int64_t)ctx->h_ctr->staged1;
     ctx->stats.entries_staged2 = (int64_t)ctx->h_ctr->staged2;
+    ctx->stats.view_batches = (nv + vb - 1) / vb;
+    ctx->stats.warp_entries = (int64_t)ctx->h_ctr->wentries1;
+    ctx->stats.warp_entries2 = (int64_t)ctx->h_ctr->wentries2;
+    ctx->stats.objective_sum = ctx->h_ctr->sumA;
     {
         double ph[3] = {0.0, 0.0, 0.0};
         pt.sum(ph);
@@ -1104,7 +1129,8 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
         }
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
                        P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, ko.narrow_keys != 0, st);
+        const uint32_t* iv = bin_batch(ctx, 0, n, 1, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), &cam,
+                                       s->d_cams + view, ko.narrow_keys != 0, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1142,20 +1168,32 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
 
 int64_t csgs_kernel_launch_count(void) { return (int64_t)launches(); }
 
-csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
-                               int32_t N) {
+static csgs_status tc_gemm_common(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                                  int32_t N, long long first_wait) {
     if (!ctx) return CSGS_E_INVAL;
     if (!A_dev || !B_dev || !C_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
     if (K < 16 || K > 128 || K % 16 || N < 16 || N > 256 || N % 16)
         return fail(ctx, CSGS_E_INVAL, "unsupported GEMM shape K=%d N=%d", K, N);
     cudaSetDevice(ctx->device);
     CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
-    gemm_check(A_dev, B_dev, C_dev, K, N, reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
+    gemm_check(A_dev, B_dev, C_dev, K, N, reinterpret_cast<int*>(&ctx->d_ctr->err), first_wait, ctx->st);
     csgs_status r;
     if ((r = launch_check(ctx, "tensor-core GEMM"))) return r;
     if ((r = read_counters(ctx))) return r;
+    if (ctx->h_ctr->err & 2) return fail(ctx, CSGS_E_TIMEOUT, "MMA chain did not drain within the full budget");
     if (ctx->h_ctr->err) return fail(ctx, CSGS_E_TIMEOUT, "MMA completion not observed");
     return CSGS_OK;
+}
+
+csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                               int32_t N) {
+    return tc_gemm_common(ctx, A_dev, B_dev, C_dev, K, N, -1);
+}
+
+csgs_status csgs_debug_tc_gemm_wait(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                                    int32_t N, int64_t first_wait_cycles) {
+    if (first_wait_cycles < 0) return fail(ctx, CSGS_E_INVAL, "negative wait budget");
+    return tc_gemm_common(ctx, A_dev, B_dev, C_dev, K, N, (long long)first_wait_cycles);
 }
 
 csgs_status csgs_debug_gelu(csgs_ctx* ctx, const float* z_dev, int64_t n, float* out_dev) {
@@ -1204,7 +1242,8 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         scatter_weights(idx_dev, w_dev, n_sel, P<float>(ctx->wfull), n, ctx->d_ctr, st);
         launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
                        P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, ko.narrow_keys != 0, st);
+        const uint32_t* iv = bin_batch(ctx, 0, n, 1, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), &cam,
+                                       s->d_cams + view, ko.narrow_keys != 0, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1226,6 +1265,30 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         break;
     }
     if (ctx->h_ctr->err & kErrIndex) return fail(ctx, CSGS_E_INVAL, "coreset index out of range");
+    return CSGS_OK;
+}
+
+csgs_status csgs_scale_scores(csgs_ctx* ctx, float* s_dev, int64_t n, double factor) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!s_dev || n <= 0) return fail(ctx, CSGS_E_INVAL, "bad score array");
+    if (!std::isfinite(factor) || factor < 0.0) return fail(ctx, CSGS_E_INVAL, "bad scale factor");
+    cudaSetDevice(ctx->device);
+    scale_scores(s_dev, n, factor, ctx->st);
+    return launch_check(ctx, "score scaling");
+}
+
+csgs_status csgs_total_sensitivity(csgs_ctx* ctx, const float* s_dev, int64_t n, double* S_out) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!s_dev || n <= 0 || !S_out) return fail(ctx, CSGS_E_INVAL, "bad arguments");
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
+    if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * 2))) return r;
+    sum_scores(s_dev, n, P<double>(ctx->partial), P<double>(ctx->Sdev), ctx->st);
+    if ((r = launch_check(ctx, "total sensitivity"))) return r;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    *S_out = ctx->h_S[0];
     return CSGS_OK;
 }
 
@@ -1516,7 +1579,8 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
         }
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
                        P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
-        const uint32_t* iv = bin_view(ctx, 0, n, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), cam, ko.narrow_keys != 0, st);
+        const uint32_t* iv = bin_batch(ctx, 0, n, 1, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), &cam,
+                                       s->d_cams + view, ko.narrow_keys != 0, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;

@@ -113,8 +113,8 @@ struct DevCounters {
     uint32_t err;
     uint32_t pad;
     unsigned long long n_inst[kBinSlots];  // instances of the view in each binning slot (may exceed capacity)
-    unsigned long long max_inst;    // maximum over views
-    unsigned long long inst_total;  // sum over views
+    unsigned long long max_inst;    // maximum over binning chains
+    unsigned long long inst_total;  // sum over binning chains
     unsigned long long pairs_eval;
     unsigned long long pairs_hit;
     unsigned long long pairs_eval2;
@@ -125,6 +125,8 @@ struct DevCounters {
     unsigned long long queries;     // pixel queries with A > 0 (two-pass resolutions)
     unsigned long long staged1;     // tile-list entries staged by compositing pass 1 (counting runs)
     unsigned long long staged2;     // ... and by pass 2
+    unsigned long long wentries1;   // (warp, tile-list entry) iterations of pass 1 (counting runs)
+    unsigned long long wentries2;   // ... and of pass 2
 };
 
 // ---- launchers (k_project.cu)
@@ -146,20 +148,28 @@ void scatter_weights(const int32_t* idx, const float* w, int64_t n_sel, float* w
 // ---- sorting and scans (k_sort.cu)
 constexpr int kSortBlocks = 148 * 4;       // default radix-sort grid (the autotuner may pick another)
 constexpr int kSortMaxBlocks = 2048;
-constexpr int kSortHistWords = 512 * kSortMaxBlocks + 512;  // per-block digit counts + digit totals
+// words of one segment's radix histograms (per-block digit counts + digit totals) for a
+// grid of G blocks per segment
+inline size_t sort_hist_stride(int G) { return (size_t)512 * (size_t)G + 512; }
 // Stable LSD radix sort of (key, value) pairs on key bits [0, bits), digit_bits (8 or 9)
-// bits per pass.  n is read from d_n (device) and clamped to n_max.  iota_vals: the values
-// are the indices 0..n-1 (vals_a is not read).  Returns which buffer holds the result
-// (0: a, 1: b).
+// bits per pass, of S independent segments of n keys each (segment k at offset
+// k * seg_stride in every array).  n is read from d_n (device) and clamped to n_max.
+// iota_vals: the values are the indices 0..n-1 within each segment (vals_a is not read).
+// hist: S * sort_hist_stride(G) words.  Returns which buffer holds the result (0: a, 1: b).
 int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint32_t* vals_b, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, int digit_bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st);
-// Gaussians in depth order -> (tile, gid) instances in depth order; writes the
-// instance count to *n_inst (and the totals in ctr).  scan_tmp: >= ceil(n / 256) + 64 words.
-void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x,
+                     uint32_t n_max, int bits, int digit_bits, uint32_t* hist, int G, bool iota_vals, int S,
+                     size_t seg_stride, cudaStream_t st);
+// Gaussians of nv views in depth order (order[v][n], Gaussian ids) -> instances with key
+// (v << tbits) | tile id and value Gaussian id, view by view, each view in depth order;
+// writes the instance count to *n_inst (and the totals in ctr).  cams: the nv views'
+// cameras (device).  scan_tmp: >= nv * ceil(n / 256) + 64 words.
+void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits,
                     uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     unsigned long long* n_inst, cudaStream_t st);
-void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
-                 cudaStream_t st);
+// ranges[v][tile] = [start, end) of each (view, tile) key in the sorted instance keys
+// (rows of max_tiles ranges per view).
+void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
+                 const CamDev* cams, int tbits, int max_tiles, cudaStream_t st);
 void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 
 // ---- compositing (k_composite.cu)
@@ -201,6 +211,8 @@ struct SampleTemp {
 };
 void sum_scores(const float* s, int64_t n, double* partial, double* S, cudaStream_t st);
 void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st);
+// s = (float)((double)s * f)
+void scale_scores(float* s, int64_t n, double f, cudaStream_t st);
 // image resolution: s = max(s, vbuf / A_view); vbuf = 0
 void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaStream_t st);
 void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st);
@@ -215,7 +227,10 @@ void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const Sa
                   int32_t* idx, float* w, cudaStream_t st);
 
 // ---- tensor cores (k_mlp.cu)
-int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, cudaStream_t st);
+// first_wait: clock cycles of the completion wait (< 0: the kernels' full budget, 0: one
+// non-blocking test); *d_err |= 1 when it ran out (2 if even the drain wait did)
+int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, long long first_wait,
+               cudaStream_t st);
 // out[2i] = GELU(z[i]), out[2i+1] = GELU'(z[i]) with the surrogate kernels' device functions
 void debug_gelu(const float* z, int n, float* out, cudaStream_t st);
 

@@ -209,6 +209,14 @@ __device__ __forceinline__ float pixel_objective(const KOpts& o, float A0, float
     return o.ow0 * A0 + o.ow1 * A1 + o.ow2 * A2;
 }
 
+// The per-pixel objective after pass 1: the per-pixel score accumulates it directly in A0
+// (one FMA per contributor), the other modes per channel.
+template <int MODE, int VAR>
+__device__ __forceinline__ float pass1_objective(const KOpts& o, float A0, float A1, float A2) {
+    if (MODE == kScorePixel) return A0;
+    return pixel_objective<VAR>(o, A0, A1, A2);
+}
+
 template <int MODE, int VAR, bool STATS>
 __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     __shared__ Shared sh;
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     int last = 0;
     int processed = 0;  // tile-list entries staged by pass 1 (CTA-uniform)
     bool done = !inside;
-    unsigned long long n_eval = 0, n_hit = 0, n_viol = 0;
+    unsigned long long n_eval = 0, n_hit = 0, n_viol = 0, n_went1 = 0, n_went2 = 0;
     if (tid == 0) sh.last = 0;
 
     // ---------------------------------------------------------------- pass 1
@@ -277,8 +285,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                 T = Tn;
             }
         } else if (!summed(MODE)) {
+            int kmax = 0;  // counting runs: entries this lane walked (the warp walks the maximum)
             if (!done) {
                 for (int k = 0; k < nw; ++k) {
+                    if (STATS) kmax = k + 1;
                     const int j = sh.wl[warp][k];
                     const float4 Aj = sh.A[j];
                     const float4 Bj = sh.B[j];
@@ -297,10 +307,18 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                         break;
                     }
                     const float w = __fmul_rn(r, T);
-                    accumulate<MODE, VAR>(A0, A1, A2, sh.C[j], w);
+                    if (MODE == kScorePixel)
+                        A0 = VAR == kL1 ? __fmaf_rn(Bj.w, w, A0)
+                                        : (VAR == kL2 ? __fmaf_rn(sh.C[j].w, __fmul_rn(w, w), A0) : __fadd_rn(A0, w));
+                    else
+                        accumulate<MODE, VAR>(A0, A1, A2, sh.C[j], w);
                     T = Tn;
                     last = b + j + 1;
                 }
+            }
+            if (STATS) {
+                const int wk = (int)__reduce_max_sync(0xffffffffu, (unsigned)kmax);
+                if (lane == 0) n_went1 += wk;
             }
         } else {
             // summed resolutions: warp-uniform loop over chunks of 16 entries; the warp's sum
@@ -379,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
 
     if (two_pass(MODE)) {
         // |Q'|: pixel queries with a non-zero objective
-        const bool nz = inside && pixel_objective<VAR>(a.o, A0, A1, A2) > 0.f;
+        const bool nz = inside && pass1_objective<MODE, VAR>(a.o, A0, A1, A2) > 0.f;
         const unsigned c = __popc(__ballot_sync(0xffffffffu, nz));
         if (lane == 0 && c) atomicAdd(&a.ctr->queries, (unsigned long long)c);
     }
@@ -418,7 +436,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         float inv0 = 0.f, inv1 = 0.f, inv2 = 0.f;
         bool has;
         if (MODE == kScorePixel) {
-            const float Aobj = pixel_objective<VAR>(a.o, A0, A1, A2);
+            const float Aobj = pass1_objective<MODE, VAR>(a.o, A0, A1, A2);
             has = inside && Aobj > 0.f;
             inv0 = has ? 1.f / Aobj : 0.f;
         } else {
@@ -445,6 +463,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             // the warp's list holds only entries below its lanes' largest contributor bound
             const int jw = (int)__reduce_max_sync(0xffffffffu, (unsigned)lim);
             const int nw = warp_list(sh, jw, warp, lane);
+            if (STATS && lane == 0) n_went2 += nw;
 #pragma unroll 4
             for (int k = 0; k < nw; ++k) {
                 const int j = sh.wl[warp][k];
@@ -519,6 +538,8 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             if (e2) atomicAdd(&a.ctr->pairs_eval2, e2);
             if (h2) atomicAdd(&a.ctr->pairs_hit2, h2);
             if (vv) atomicAdd(&a.ctr->violations, vv);
+            if (n_went1) atomicAdd(&a.ctr->wentries1, n_went1);
+            if (n_went2) atomicAdd(&a.ctr->wentries2, n_went2);
         }
     }
 }

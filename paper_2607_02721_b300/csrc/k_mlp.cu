@@ -10,10 +10,13 @@ constexpr long long kWaitBudget = 2000000000LL;  // ~1 s at 2 GHz; a wait beyond
 
 // C[128 x N] = A[128 x K] * B[N x K]^T, BF16 in, FP32 out; one CTA of 128 threads
 // (one warpgroup, so warp w reads TMEM lanes 32w..32w+31).  K % 16 == 0, K <= 128,
-// N % 16 == 0, 16 <= N <= 256.
+// N % 16 == 0, 16 <= N <= 256.  first_wait: clock cycles the threads wait for the MMA
+// chain's completion (0: one non-blocking test); a warp that gives up sets *err and then
+// waits the full budget for the chain to drain, so no MMA is in flight when the tensor
+// memory is freed.
 __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restrict__ A,
                                                     const __nv_bfloat16* __restrict__ B, float* __restrict__ C,
-                                                    int K, int N, int* err) {
+                                                    int K, int N, int* err, long long first_wait) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // operand tiles start on a 1024-byte boundary
     unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -52,10 +55,11 @@ __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restr
         }
         tc::commit(&bar);
     }
-    bool ok = tc::mbar_wait(&bar, 0, kWaitBudget);
+    bool ok = first_wait > 0 ? tc::mbar_wait(&bar, 0, first_wait) : tc::mbar_test(&bar, 0);
     if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) atomicOr(err, 1);
-        tc::mbar_wait(&bar, 0, kWaitBudget);  // let an in-flight MMA drain before freeing TMEM
+        // let an in-flight MMA drain before freeing TMEM
+        if (!tc::mbar_wait(&bar, 0, kWaitBudget) && lane == 0) atomicOr(err, 2);
     } else {
         tc::fence_after_sync();
         const int row = warp * 32 + lane;
@@ -73,11 +77,13 @@ __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restr
 
 }  // namespace
 
-int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, cudaStream_t st) {
+int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, long long first_wait,
+               cudaStream_t st) {
     const size_t smem = (size_t)128 * K * 2 + (size_t)N * K * 2 + 1024;
     cudaFuncSetAttribute(k_gemm_check, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gemm_check<<<1, 128, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(A),
-                                       reinterpret_cast<const __nv_bfloat16*>(B), C, K, N, d_err);
+                                       reinterpret_cast<const __nv_bfloat16*>(B), C, K, N, d_err,
+                                       first_wait < 0 ? kWaitBudget : first_wait);
     count_launches(1);
     return 0;
 }

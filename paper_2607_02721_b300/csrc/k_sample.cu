@@ -51,6 +51,11 @@ __global__ void k_scene_normalise(float* __restrict__ s, int64_t n, const double
         s[i] = A > 0.0 ? (float)((double)s[i] / A) : 0.f;
 }
 
+__global__ void k_scale(float* __restrict__ s, int64_t n, double f) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s[i] = (float)((double)s[i] * f);
+}
+
 __global__ void k_image_fold(float* __restrict__ s, float* __restrict__ vbuf, int64_t n,
                              const double* __restrict__ sumA_view) {
     const double A = *sumA_view;
@@ -282,6 +287,11 @@ void sum_scores(const float* s, int64_t n, double* partial, double* S, cudaStrea
 
 void scene_normalise(float* s, int64_t n, const double* sumA, cudaStream_t st) {
     k_scene_normalise<<<148 * 8, 256, 0, st>>>(s, n, sumA);
+    count_launches(1);
+}
+
+void scale_scores(float* s, int64_t n, double f, cudaStream_t st) {
+    k_scale<<<148 * 8, 256, 0, st>>>(s, n, f);
     count_launches(1);
 }
 

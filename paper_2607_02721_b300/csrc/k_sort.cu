@@ -1,12 +1,17 @@
 // Binning of projected Gaussians into screen tiles in front-to-back order (the order
-// "induced by the view depths", Sec. 3 "Scalar rendering function"):
-//   1. stable LSD radix sort of all Gaussians of a view by depth (ties keep index order);
-//   2. one fused scan + emit pass that writes (tile, gid) instances in depth order;
-//   3. stable LSD radix sort of the instances by tile id only;
-//   4. per-tile [start, end) ranges.
-// Every tile list is therefore sorted by (depth, Gaussian index).  No CUB: the sort is
-// a reduce-then-scan radix sort with 8- or 9-bit digits and warp-level stable ranking
-// (one ballot per digit bit).
+// "induced by the view depths", Sec. 3 "Scalar rendering function"), for a batch of
+// views at once:
+//   1. stable LSD radix sort of all Gaussians of every view by depth (ties keep index
+//      order); one segment per view, all segments in the same launches;
+//   2. one fused scan + emit pass over the batch that writes (view, tile, gid) instances,
+//      view by view, each view in depth order;
+//   3. stable LSD radix sort of the batch's instances by the key (view, tile id);
+//   4. per-(view, tile) [start, end) ranges.
+// Every tile list is therefore sorted by (depth, Gaussian index).  Sorting a whole view
+// batch per launch keeps each pass a bandwidth-bound sweep over tens of millions of keys
+// instead of a latency-bound one over a single view's.  No CUB: the sort is a
+// reduce-then-scan radix sort with 8- or 9-bit digits and warp-level stable ranking (one
+// ballot per digit bit).
 #include "csgs_internal.cuh"
 
 namespace csgs {
@@ -39,11 +44,15 @@ __device__ __forceinline__ uint32_t read_n(const unsigned long long* d_n, uint32
 // Per-block digit counts of one pass (RB-bit digits, D = 2^RB).  Each warp counts into
 // its own shared histogram with plain atomics (match.any costs grow with the number of
 // distinct digits in the warp; conflicting shared atomics only serialise on equal digits).
+// Segment blockIdx.y: keys + seg * seg_stride, histogram block hist + seg * hstride.
 template <int RB>
 __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __restrict__ keys,
                                                           const unsigned long long* d_n, uint32_t n_max, int shift,
-                                                          uint32_t* __restrict__ hist) {
+                                                          uint32_t* __restrict__ hist, size_t seg_stride,
+                                                          size_t hstride) {
     constexpr uint32_t D = 1u << RB;
+    keys += blockIdx.y * seg_stride;
+    hist += blockIdx.y * hstride;
     constexpr int DPT = (int)D / kSortThreads;  // digits per thread
     __shared__ uint32_t wh[kSortWarps][D];
     for (int k = threadIdx.x; k < kSortWarps * (int)D; k += kSortThreads) (&wh[0][0])[k] = 0u;
@@ -76,11 +85,13 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
 }
 
 // Exclusive scan of each digit's row of the histogram (G per-block counts, G <=
-// kSortMaxBlocks), one CTA per digit; the row totals go to row_total[digits].
-__global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist, uint32_t* __restrict__ row_total,
-                                                    int G) {
+// kSortMaxBlocks), one CTA per (digit, segment); the row totals of segment y go to
+// hist + y * hstride + D * G.
+__global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist, int G, int D, size_t hstride) {
     constexpr int kPer = (kSortMaxBlocks + 255) / 256;
     __shared__ uint32_t ws[8];
+    hist += blockIdx.y * hstride;
+    uint32_t* row_total = hist + (size_t)D * G;
     const int per = (G + 255) / 256;
     uint32_t* row = hist + (size_t)blockIdx.x * G;
     const int b0 = threadIdx.x * per;
@@ -115,15 +126,26 @@ __global__ void __launch_bounds__(256) k_rs_rowscan(uint32_t* __restrict__ hist,
 // (stable: warp, group, lane order), the CTA turns the per-warp counts into positions,
 // places the sub-tile in shared memory grouped by digit, and writes each digit's run to
 // its global slot, so global stores are contiguous runs.
+// Segment blockIdx.y: every key and value array + seg * seg_stride (positions are
+// within the segment), histogram block hist + seg * hstride.
 template <int NBITS, int RB>
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
                                                              const uint32_t* __restrict__ vin,
                                                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                              const unsigned long long* d_n, uint32_t n_max, int shift,
-                                                             const uint32_t* __restrict__ hist,
-                                                             const uint32_t* __restrict__ row_total) {
+                                                             const uint32_t* __restrict__ hist, size_t seg_stride,
+                                                             size_t hstride) {
     constexpr uint32_t D = 1u << RB;
     constexpr int DPT = (int)D / kSortThreads;
+    {
+        const size_t so = blockIdx.y * seg_stride;
+        kin += so;
+        if (vin) vin += so;
+        kout += so;
+        vout += so;
+        hist += blockIdx.y * hstride;
+    }
+    const uint32_t* __restrict__ row_total = hist + (size_t)D * gridDim.x;
     __shared__ uint32_t wcnt[kSortWarps][D + 1];
     __shared__ uint32_t gbase[D];
     __shared__ uint32_t lstart[D];
@@ -282,21 +304,22 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return pre;
 }
 
-// Emit, phase 1: instance count per chunk of 256 depth-ordered Gaussians.  The emit
-// kernels loop over chunks on a grid of at most kEmitBlocks CTAs: they run at binning's high
-// priority beside compositing, and a bounded grid holds fewer of the SMs' CTA slots at once
-// (measured: 0.6% shorter scoring step than one CTA per chunk).
+// Emit, phase 1: instance count per chunk of 256 depth-ordered Gaussians of one view
+// of the batch (chunk c: view c / nb, chunk c % nb of that view; nb chunks per view).
+// The emit kernels loop over chunks on a grid of at most kEmitBlocks CTAs.
 __global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __restrict__ order,
-                                                              const uint2* __restrict__ rects, int n,
+                                                              const uint2* __restrict__ rects, int n, int nv,
                                                               uint32_t* __restrict__ partial) {
     __shared__ uint32_t ws[32];
     const int nb = (n + kScanThreads - 1) / kScanThreads;
-    for (int cb = blockIdx.x; cb < nb; cb += gridDim.x) {
+    for (int c = blockIdx.x; c < nb * nv; c += gridDim.x) {
+        const int v = c / nb, cb = c - v * nb;
+        const size_t vo = (size_t)v * n;
         const int j = cb * kScanThreads + threadIdx.x;
-        const uint32_t c = j < n ? tile_count(__ldg(rects + __ldg(order + j))) : 0u;
+        const uint32_t c_ = j < n ? tile_count(__ldg(rects + vo + __ldg(order + vo + j))) : 0u;
         uint32_t tot;
-        block_exclusive_scan(c, ws, &tot);
-        if (threadIdx.x == 0) partial[cb] = tot;
+        block_exclusive_scan(c_, ws, &tot);
+        if (threadIdx.x == 0) partial[c] = tot;
     }
 }
 
@@ -339,9 +362,11 @@ __global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ pa
 
 // Emit, phase 3: every warp expands its 32 Gaussians' tile rectangles into a
 // contiguous run of instances, lane f of each round writing instance f of the run
-// (coalesced), in depth order and row-major tile order within a Gaussian.
+// (coalesced), in depth order and row-major tile order within a Gaussian.  The key is
+// (view << tbits) | tile id, the value the Gaussian id.
 __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __restrict__ order,
-                                                            const uint2* __restrict__ rects, int n, int tiles_x,
+                                                            const uint2* __restrict__ rects, int n, int nv,
+                                                            const CamDev* __restrict__ cams, int tbits,
                                                             const uint32_t* __restrict__ partial,
                                                             uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
                                                             uint32_t cap, DevCounters* ctr) {
@@ -351,15 +376,19 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
     __shared__ uint2 s_r[kScanThreads / 32][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = (n + kScanThreads - 1) / kScanThreads;
-    for (int cb = blockIdx.x; cb < nb; cb += gridDim.x) {
+    for (int c = blockIdx.x; c < nb * nv; c += gridDim.x) {
+        const int v = c / nb, cb = c - v * nb;
+        const size_t vo = (size_t)v * n;
+        const uint32_t tiles_x = (uint32_t)cams[v].tiles_x;
+        const uint32_t vkey = (uint32_t)v << tbits;
         const int j = cb * kScanThreads + threadIdx.x;
-        const uint32_t gid = j < n ? __ldg(order + j) : 0u;
-        const uint2 rc = j < n ? __ldg(rects + gid) : make_uint2(0u, 0u);
-        const uint32_t c = tile_count(rc);
+        const uint32_t gid = j < n ? __ldg(order + vo + j) : 0u;
+        const uint2 rc = j < n ? __ldg(rects + vo + gid) : make_uint2(0u, 0u);
+        const uint32_t cnt = tile_count(rc);
         uint32_t tot;
-        const uint32_t off = block_exclusive_scan(c, ws, &tot) + partial[cb];
+        const uint32_t off = block_exclusive_scan(cnt, ws, &tot) + partial[c];
         const uint32_t wbase = __shfl_sync(0xffffffffu, off, 0);
-        const uint32_t wtot = __shfl_sync(0xffffffffu, off + c, 31) - wbase;
+        const uint32_t wtot = __shfl_sync(0xffffffffu, off + cnt, 31) - wbase;
         s_e[warp][lane] = off - wbase;
         s_g[warp][lane] = gid;
         s_r[warp][lane] = rc;
@@ -386,30 +415,36 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
             // the floor is exact for local < 2^22 (integer division beyond)
             const uint32_t dy = local < (1u << 22) ? (uint32_t)(((float)local + 0.5f) * __frcp_rn((float)w)) : local / w;
             const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
-            ikeys[wbase + f] = ty * (uint32_t)tiles_x + tx;
+            ikeys[wbase + f] = vkey | (ty * tiles_x + tx);
             ivals[wbase + f] = s_g[warp][lo];
         }
     }
 }
 
-// Tile ranges from the tile-sorted instance keys: thread t finds the first instance
-// with key >= t by binary search and writes it as the start of tile t and the end of
-// tile t - 1 (thread n_tiles closes the last tile), so every range is written.
+// Tile ranges from the (view, tile)-sorted instance keys, one row of max_tiles ranges per
+// view (blockIdx.y): thread t finds the first instance with key >= (view << tbits) + t by
+// binary search and writes it as the start of tile t and the end of tile t - 1 (thread
+// n_tiles of the view closes its last tile: no instance has that key), so every range of
+// the view is written.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_n, uint32_t n_max,
-                         uint2* __restrict__ ranges, uint32_t n_tiles) {
+                         uint2* __restrict__ ranges, const CamDev* __restrict__ cams, int tbits, int max_tiles) {
+    const int v = blockIdx.y;
+    const uint32_t n_tiles = (uint32_t)(cams[v].tiles_x * cams[v].tiles_y);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t > n_tiles) return;
+    const uint32_t key = ((uint32_t)v << tbits) + t;
     const uint32_t n = read_n(d_n, n_max);
     uint32_t lo = 0, hi = n;
     while (lo < hi) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(keys + mid) < t)
+        if (__ldg(keys + mid) < key)
             lo = mid + 1;
         else
             hi = mid;
     }
-    if (t < n_tiles) ranges[t].x = lo;
-    if (t > 0) ranges[t - 1].y = lo;
+    uint2* rv = ranges + (size_t)v * max_tiles;
+    if (t < n_tiles) rv[t].x = lo;
+    if (t > 0) rv[t - 1].y = lo;
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
@@ -417,15 +452,17 @@ __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v;
 // One pass with RB-bit digits (NBITS of them significant).
 template <int RB>
 void radix_pass(int nbits, const uint32_t* kin, const uint32_t* vin, uint32_t* kout, uint32_t* vout,
-                const unsigned long long* d_n, uint32_t n_max, int shift, uint32_t* hist, int G, cudaStream_t st) {
+                const unsigned long long* d_n, uint32_t n_max, int shift, uint32_t* hist, int G, int S,
+                size_t seg_stride, cudaStream_t st) {
     constexpr int D = 1 << RB;
-    k_rs_hist<RB><<<G, kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist);
+    const size_t hs = sort_hist_stride(G);
+    k_rs_hist<RB><<<dim3(G, S), kSortThreads, 0, st>>>(kin, d_n, n_max, shift, hist, seg_stride, hs);
     count_launches(1);
-    k_rs_rowscan<<<D, 256, 0, st>>>(hist, hist + D * G, G);
+    k_rs_rowscan<<<dim3(D, S), 256, 0, st>>>(hist, G, D, hs);
     count_launches(1);
-    const uint32_t* rt = hist + D * G;
 #define CSGS_SCATTER(NB) \
-    k_rs_scatter<NB, RB><<<G, kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, rt)
+    k_rs_scatter<NB, RB><<<dim3(G, S), kSortThreads, 0, st>>>(kin, vin, kout, vout, d_n, n_max, shift, hist, \
+                                                              seg_stride, hs)
     switch (nbits) {
         case 1: CSGS_SCATTER(1); break;
         case 2: CSGS_SCATTER(2); break;
@@ -444,9 +481,11 @@ void radix_pass(int nbits, const uint32_t* kin, const uint32_t* vin, uint32_t* k
 }  // namespace
 
 int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, const unsigned long long* d_n,
-                     uint32_t n_max, int bits, int digit_bits, uint32_t* hist, int G, bool iota_vals, cudaStream_t st) {
+                     uint32_t n_max, int bits, int digit_bits, uint32_t* hist, int G, bool iota_vals, int S,
+                     size_t seg_stride, cudaStream_t st) {
     if (G < 1) G = 1;
     if (G > kSortMaxBlocks) G = kSortMaxBlocks;
+    if (S < 1) S = 1;
     const int rb = digit_bits == 9 ? 9 : 8;
     int cur = 0;
     for (int shift = 0; shift < bits; shift += rb) {
@@ -456,29 +495,31 @@ int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, con
         uint32_t* vout = cur ? va : vb;
         const int nbits = bits - shift < rb ? bits - shift : rb;
         if (rb == 9)
-            radix_pass<9>(nbits, kin, vin, kout, vout, d_n, n_max, shift, hist, G, st);
+            radix_pass<9>(nbits, kin, vin, kout, vout, d_n, n_max, shift, hist, G, S, seg_stride, st);
         else
-            radix_pass<8>(nbits, kin, vin, kout, vout, d_n, n_max, shift, hist, G, st);
+            radix_pass<8>(nbits, kin, vin, kout, vout, d_n, n_max, shift, hist, G, S, seg_stride, st);
         cur ^= 1;
     }
     return cur;
 }
 
-void emit_instances(const uint32_t* order, const uint2* rects, int n, int tiles_x, uint32_t* ikeys, uint32_t* ivals,
-                    uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr, unsigned long long* n_inst, cudaStream_t st) {
+void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits,
+                    uint32_t* ikeys, uint32_t* ivals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
+                    unsigned long long* n_inst, cudaStream_t st) {
     const int nb = (n + kScanThreads - 1) / kScanThreads;
-    const int ng = nb < kEmitBlocks ? nb : kEmitBlocks;
-    k_emit_reduce<<<ng, kScanThreads, 0, st>>>(order, rects, n, scan_tmp);
+    const int nc = nb * nv;
+    const int ng = nc < kEmitBlocks ? nc : kEmitBlocks;
+    k_emit_reduce<<<ng, kScanThreads, 0, st>>>(order, rects, n, nv, scan_tmp);
     count_launches(1);
-    k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nb, ctr, n_inst);
+    k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nc, ctr, n_inst);
     count_launches(1);
-    k_emit_down<<<ng, kScanThreads, 0, st>>>(order, rects, n, tiles_x, scan_tmp, ikeys, ivals, cap, ctr);
+    k_emit_down<<<ng, kScanThreads, 0, st>>>(order, rects, n, nv, cams, tbits, scan_tmp, ikeys, ivals, cap, ctr);
     count_launches(1);
 }
 
-void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int n_tiles,
-                 cudaStream_t st) {
-    k_ranges<<<(n_tiles + 1 + 255) / 256, 256, 0, st>>>(keys, d_n, n_max, ranges, (uint32_t)n_tiles);
+void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
+                 const CamDev* cams, int tbits, int max_tiles, cudaStream_t st) {
+    k_ranges<<<dim3((max_tiles + 1 + 255) / 256, nv), 256, 0, st>>>(keys, d_n, n_max, ranges, cams, tbits, max_tiles);
     count_launches(1);
 }
 

@@ -45,11 +45,11 @@ def test_default_opts_are_the_rasteriser_conventions(lib):
 
 
 def test_struct_layouts_match_header(lib):
-    # csgs_camera is 80 bytes; csgs_scene_desc 56; csgs_score_opts 52; csgs_stats 152
+    # csgs_camera is 80 bytes; csgs_scene_desc 56; csgs_score_opts 52; csgs_stats 184
     assert ctypes.sizeof(csgs.Camera) == 80
     assert ctypes.sizeof(csgs.SceneDesc) == 56
     assert ctypes.sizeof(csgs.ScoreOpts) == 52
-    assert ctypes.sizeof(csgs.Stats) == 152
+    assert ctypes.sizeof(csgs.Stats) == 184
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

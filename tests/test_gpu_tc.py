@@ -1,5 +1,6 @@
 """The tcgen05 tensor-core building block (BF16 x BF16 -> FP32 in tensor memory)
-against an FP64 matrix product of the same BF16 inputs."""
+against an FP64 matrix product of the same BF16 inputs, and the failure path of its
+bounded completion wait."""
 import numpy as np
 import pytest
 
@@ -32,3 +33,31 @@ def test_tc_gemm_matches_fp64(ctx, K, N):
     ref = a @ b.T
     scale = np.abs(a) @ np.abs(b).T
     assert np.all(np.abs(C - ref) <= 1e-6 * scale + 1e-12)
+
+
+def _check_product(C, A, B):
+    a, b = A.double().numpy(), B.double().numpy()
+    scale = np.abs(a) @ np.abs(b).T
+    assert np.all(np.abs(C - a @ b.T) <= 1e-6 * scale + 1e-12)
+
+
+def test_wait_budget_expiry_reports_timeout_and_context_survives(ctx):
+    """A completion wait whose budget runs out (budget 0: one non-blocking test, taken
+    before the 8-MMA chain can finish) reports CSGS_E_TIMEOUT; the kernel drains the
+    chain before freeing its tensor memory, so the same context then computes a correct
+    product, with the default and with an explicit generous budget."""
+    import torch
+
+    g = torch.Generator().manual_seed(7)
+    A = torch.randn(128, 128, generator=g).to(torch.bfloat16)
+    B = torch.randn(256, 128, generator=g).to(torch.bfloat16)
+    Ad, Bd = A.cuda(), B.cuda()
+    for _ in range(2):
+        with pytest.raises(csgs.CsgsError) as e:
+            ctx.debug_tc_gemm_wait(Ad, Bd, 0)
+        assert e.value.status == csgs.CSGS_E_TIMEOUT
+        _check_product(ctx.debug_tc_gemm(Ad, Bd).cpu().numpy().astype(np.float64), A, B)
+    _check_product(ctx.debug_tc_gemm_wait(Ad, Bd, 2_000_000_000).cpu().numpy().astype(np.float64), A, B)
+    with pytest.raises(csgs.CsgsError) as e:
+        ctx.debug_tc_gemm_wait(Ad, Bd, -1)
+    assert e.value.status == csgs.CSGS_E_INVAL
