@@ -470,6 +470,13 @@ def run_ours(args):
             "phases_ms_per_step": {"project": proj_ms / args.steps, "sort_and_bin": sort_ms / args.steps,
                                    "composite_score": comp_ms / args.steps},
             "clocks": clk, "e2e": e2e}
+    if world == 1 and not args.no_surrogate_record and not args.max_views:
+        # the metric's second half: surrogate-assisted vs exact scoring of this workload
+        from paper_2607_02721_b300 import surrogate
+
+        scfg = surrogate.SurrogateConfig()
+        rec, _, _ = surrogate_record(ctx, sid, cams, m, scfg, csgs.default_opts(resolution=res_id), 10)
+        line["surrogate"] = rec
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, _, _ = cpu_baseline(args.workload, scene, cams, args.cpu_seconds)
         line["cpu_baseline"] = cb
@@ -479,6 +486,60 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def surrogate_record(ctx, sid, cams, m, cfg, sopts, psnr_stride: int):
+    """Surrogate-assisted against exact scoring of the same query set on the same GPU:
+    times (CUDA events on the library's stream, after one warm-up each) and PSNR of the
+    90%-pruned weighted coreset against the full render on every `psnr_stride`-th view,
+    for the exact scores, the surrogate's and the scored subset's alone."""
+    import numpy as np
+    import torch
+
+    from paper_2607_02721_b300 import surrogate
+
+    ctx.set_queries(sid, cams)
+    ctx.score(sid, sopts)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(ctx.stream)
+    s_exact, _ = ctx.score(sid, sopts)
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    exact_ms = ev0.elapsed_time(ev1)
+    s_exact = s_exact.clone()
+    surrogate.surrogate_scores(ctx, sid, cams, cfg, opts=sopts)  # warm-up
+    tim = {}
+    s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, cfg, opts=sopts, timings=tim)
+    views = list(range(0, len(cams), psnr_stride))
+    res = {"exact_ms": exact_ms, "surrogate_ms": tim["total_ms"], "speedup": exact_ms / tim["total_ms"],
+           "phases_ms": tim, "train_views": cfg.train_views, "train_steps": cfg.steps,
+           "lowres_factor": cfg.lowres_factor, "cheap_stride": cfg.cheap_stride, "train_lr": cfg.lr,
+           "fill_only": cfg.fill_only, "aug_views": list(cfg.aug_views),
+           "psnr_views": len(views), "prune_ratio": 0.9}
+    # the same inputs without the network: the cheap score scaled to the exact scores by
+    # the median ratio on the scored views, maximum with the scored subset's exact scores
+    s_nonet = None
+    if cfg.lowres_factor > 0:
+        low = surrogate.lowres_cameras(cams, cfg.lowres_factor)
+        sub = surrogate.view_subset(len(cams), cfg.train_views)
+        s_low = surrogate._score_or_zero(ctx, sid, low[::max(1, cfg.cheap_stride)], sopts)
+        s_low_sub = surrogate._score_or_zero(ctx, sid, low[sub], sopts).double().cpu().numpy()
+        b = s_sub.double().cpu().numpy()
+        ok = (b > 0) & (s_low_sub > 0)
+        ratio = float(np.median(b[ok] / s_low_sub[ok])) if ok.any() else 1.0
+        s_nonet = torch.maximum(s_sub, s_low * ratio)
+        ctx.set_queries(sid, cams)
+    for name, sv in (("exact", s_exact), ("surrogate", s_hat), ("subset_only", s_sub), ("no_network", s_nonet)):
+        if sv is not None:
+            res["psnr_" + name] = surrogate.pruned_psnr(ctx, sid, cams, sv, m, 0, views)
+    res["delta_psnr_surrogate_vs_exact"] = res["psnr_surrogate"] - res["psnr_exact"]
+    res["gain_psnr_surrogate_vs_subset"] = res["psnr_surrogate"] - res["psnr_subset_only"]
+    sh, se = s_hat.double().cpu().numpy(), s_exact.double().cpu().numpy()
+    pos = se > 0
+    res["spearman_vs_exact"] = float(np.corrcoef(np.argsort(np.argsort(sh[pos])),
+                                                 np.argsort(np.argsort(se[pos])))[0, 1])
+    res["meets_target"] = bool(res["delta_psnr_surrogate_vs_exact"] >= -0.1 and res["speedup"] > 1.0)
+    return res, s_exact, s_hat
 
 
 def run_surrogate(args):
@@ -501,31 +562,14 @@ def run_surrogate(args):
     ctx.set_queries(sid, cams)
     res_id = {"pixel": csgs.RES_PIXEL, "scene": csgs.RES_SCENE}[args.resolution]
     sopts = csgs.default_opts(resolution=res_id)
-    s_exact, _ = ctx.score(sid, sopts)  # warm-up (buffers)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(ctx.stream)
-    s_exact, S = ctx.score(sid, sopts)
-    ev1.record(ctx.stream)
-    torch.cuda.synchronize()
-    exact_ms = ev0.elapsed_time(ev1)
     scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps, fill_only=args.fill_only,
-                                     aug_views=tuple(int(x) for x in args.aug_views.split(",") if x))
-    surrogate.surrogate_scores(ctx, sid, cams, scfg, opts=sopts)  # warm-up
-    tim = {}
-    s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, scfg, opts=sopts, timings=tim)
-    views = list(range(0, len(cams), args.psnr_stride))
-    res = {"mode": "surrogate", "config": cfg, "exact_ms": exact_ms, "surrogate": tim,
-           "speedup_total": exact_ms / tim["total_ms"],
-           "speedup_without_training": exact_ms / (tim["total_ms"] - tim["train_ms"]),
-           "psnr_views": len(views), "train_views": args.train_views, "train_steps": args.train_steps,
-           "fill_only": args.fill_only, "aug_views": scfg.aug_views, "resolution": args.resolution}
-    for name, sv in (("exact", s_exact), ("surrogate", s_hat), ("subset_only", s_sub)):
-        res["psnr_" + name] = surrogate.pruned_psnr(ctx, sid, cams, sv, m, 0, views)
-    res["delta_psnr_surrogate_vs_exact"] = res["psnr_surrogate"] - res["psnr_exact"]
-    res["gain_psnr_surrogate_vs_subset"] = res["psnr_surrogate"] - res["psnr_subset_only"]
-    sh, se = s_hat.double().cpu().numpy(), s_exact.double().cpu().numpy()
-    res["spearman_log"] = float(np.corrcoef(np.argsort(np.argsort(sh)), np.argsort(np.argsort(se)))[0, 1])
+                                     aug_views=tuple(int(x) for x in args.aug_views.split(",") if x),
+                                     lowres_factor=args.lowres_factor)
+    rec, s_exact, s_hat = surrogate_record(ctx, sid, cams, m, scfg, sopts, args.psnr_stride)
+    res = {"mode": "surrogate", "config": cfg, "resolution": args.resolution}
+    res.update(rec)
     # tensor-core roofline of the network's forward over every Gaussian (inference GEMMs)
+    ctx.set_queries(sid, cams)
     X = ctx.features(sid, ctx.view_stats(sid, sopts))
     for _ in range(3):
         ctx.mlp_forward(X)
@@ -840,11 +884,14 @@ def main():
     ap.add_argument("--view-batch", type=int, default=0, help="views projected per launch (0 = automatic)")
     ap.add_argument("--surrogate", action="store_true", help="surrogate-assisted vs exact scoring report")
     ap.add_argument("--train-views", type=int, default=20)
-    ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--train-steps", type=int, default=150)
     ap.add_argument("--psnr-stride", type=int, default=5)
     ap.add_argument("--fill-only", action="store_true")
     ap.add_argument("--resolution", default="pixel", choices=["pixel", "scene"])
-    ap.add_argument("--aug-views", default="5,10")
+    ap.add_argument("--aug-views", default="")
+    ap.add_argument("--lowres-factor", type=int, default=4, help="surrogate: cheap score at 1/f resolution (0: off)")
+    ap.add_argument("--no-surrogate-record", action="store_true",
+                    help="leave the surrogate-vs-exact record out of the default line")
     ap.add_argument("--batch", action="store_true", help="six-scene graph-captured batch report")
     ap.add_argument("--finetune", action="store_true", help="post-prune recovery report (sensitivity vs uniform)")
     ap.add_argument("--ft-steps", type=int, default=500)

@@ -267,8 +267,11 @@ csgs_status csgs_mlp_train(csgs_ctx* ctx, const void* X_dev, const float* t_dev,
  * views the footprint reaches, mean and max area (px^2) of the projected 3-sigma ellipse. */
 csgs_status csgs_view_stats(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* stats_dev);
 /* Model inputs (device BF16 [N][64]): mean/4, log-scale+4, unit quaternion, opacity logit,
- * 5 x SH coefficients (48 slots), log(1+views), log(1+mean area)/4, log(1+max area)/4, 0, 0. */
-csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, void* X_dev);
+ * 5 x SH coefficients (48 slots), log(1+views), log(1+mean area)/4, log(1+max area)/4,
+ * extra/8, 0.  extra_dev (device float[N], nullable: 0): one more per-Gaussian input (the
+ * surrogate passes the log of its cheap reduced-resolution score). */
+csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, const float* extra_dev,
+                          void* X_dev);
 /* t = log(s + eps) (device float[n]). */
 csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float eps, float* t_dev);
 /* The surrogate sensitivity from the prediction y and the exact scores of the scored

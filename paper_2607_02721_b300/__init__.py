@@ -131,7 +131,7 @@ def lib():
     L.csgs_mlp_gradient.argtypes = [V, V, V, I64, V, V]
     L.csgs_mlp_train.argtypes = [V, V, V, I64, I32, I32, ctypes.c_float, U64, V]
     L.csgs_view_stats.argtypes = [V, I32, V, V]
-    L.csgs_features.argtypes = [V, I32, V, V]
+    L.csgs_features.argtypes = [V, I32, V, V, V]
     L.csgs_log_target.argtypes = [V, V, I64, ctypes.c_float, V]
     L.csgs_surrogate_combine.argtypes = [V, V, V, I64, ctypes.c_float, I32, V]
     L.csgs_update_scene.argtypes = [V, I32, V]
@@ -443,10 +443,10 @@ class Context:
         self._out()
         return st
 
-    def features(self, sid: int, stats):
+    def features(self, sid: int, stats, extra=None):
         X = self._empty((self._scenes[sid], 64), self.torch.bfloat16)
         self._in()
-        self._check(lib().csgs_features(self.h, sid, _ptr(stats), _ptr(X)))
+        self._check(lib().csgs_features(self.h, sid, _ptr(stats), _ptr(extra), _ptr(X)))
         self._out()
         return X
 

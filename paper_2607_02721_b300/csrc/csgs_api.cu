@@ -1492,13 +1492,14 @@ csgs_status csgs_view_stats(csgs_ctx* ctx, int32_t scene_id, const csgs_score_op
     return launch_check(ctx, "view statistics");
 }
 
-csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, void* X_dev) {
+csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_dev, const float* extra_dev,
+                          void* X_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
     if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
     if (!stats_dev || !X_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
     cudaSetDevice(ctx->device);
-    launch_features(scene_dev(*s), stats_dev, X_dev, ctx->st);
+    launch_features(scene_dev(*s), stats_dev, extra_dev, X_dev, ctx->st);
     return launch_check(ctx, "features");
 }
 

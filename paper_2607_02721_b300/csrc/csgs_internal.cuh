@@ -136,7 +136,7 @@ void launch_debug_project(const SceneDev& sc, const CamDev* d_cam, const KOpts& 
 void launch_check_finite(const float* p, int64_t n, DevCounters* ctr, cudaStream_t st);
 void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const KOpts& o, float* stats, int accumulate,
                        cudaStream_t st);
-void launch_features(const SceneDev& sc, const float* stats, void* X, cudaStream_t st);
+void launch_features(const SceneDev& sc, const float* stats, const float* extra, void* X, cudaStream_t st);
 // chain the per-Gaussian 2-D gradients of one view to means [3][N], SH [(d+1)^2][3][N]
 // and opacity logits [N] (accumulated)
 void launch_project_backward(const SceneDev& sc, const CamDev* d_cam, const float* d_w, const KOpts& o,

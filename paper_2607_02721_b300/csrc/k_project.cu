@@ -311,8 +311,10 @@ __global__ void __launch_bounds__(256) k_view_stats(SceneDev sc, const CamDev* _
 
 // Surrogate features, BF16 [N][64]: mean / 4, log-scale + 4, unit quaternion, opacity
 // logit, SH coefficients x 5 (48 slots, zero beyond the degree), log(1 + view count),
-// log(1 + mean area) / 4, log(1 + max area) / 4, two zero pads.
-__global__ void k_features(SceneDev sc, const float* __restrict__ stats, __nv_bfloat16* __restrict__ X) {
+// log(1 + mean area) / 4, log(1 + max area) / 4, extra / 8 (zero without an extra input),
+// one zero pad.
+__global__ void k_features(SceneDev sc, const float* __restrict__ stats, const float* __restrict__ extra,
+                           __nv_bfloat16* __restrict__ X) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc.n) return;
     const int n = sc.n;
@@ -334,6 +336,7 @@ __global__ void k_features(SceneDev sc, const float* __restrict__ stats, __nv_bf
     f[59] = log1pf(stats[3 * i]);
     f[60] = log1pf(stats[3 * i + 1]) * 0.25f;
     f[61] = log1pf(stats[3 * i + 2]) * 0.25f;
+    if (extra) f[62] = extra[i] * 0.125f;
     uint4* dst = reinterpret_cast<uint4*>(X + (size_t)i * 64);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -540,8 +543,8 @@ void launch_project_backward(const SceneDev& sc, const CamDev* d_cam, const floa
     count_launches(1);
 }
 
-void launch_features(const SceneDev& sc, const float* stats, void* X, cudaStream_t st) {
-    k_features<<<(sc.n + 255) / 256, 256, 0, st>>>(sc, stats, reinterpret_cast<__nv_bfloat16*>(X));
+void launch_features(const SceneDev& sc, const float* stats, const float* extra, void* X, cudaStream_t st) {
+    k_features<<<(sc.n + 255) / 256, 256, 0, st>>>(sc, stats, extra, reinterpret_cast<__nv_bfloat16*>(X));
     count_launches(1);
 }
 

@@ -12,6 +12,8 @@ reported as a measurement, not an allowance.
 """
 import numpy as np
 
+from paper_2607_02721_b300 import synth
+
 RGB_TOL = 1e-5
 S_RTOL = 1e-3
 
@@ -52,3 +54,12 @@ def check_scores(s_gpu, S_gpu, ref, min_val=1e-6, note=None):
     t = ref["touched"] & (ref["s_clean"] > min_val)
     assert np.all(s_gpu[t] >= ref["s_clean"][t] * (1 - S_RTOL))
     assert abs(S_gpu - ref["S"]) <= S_RTOL * ref["S"], (S_gpu, ref["S"])
+
+
+def finetune_subcase():
+    """The gradient sub-case of the post-prune finetune: 1,000 Gaussians of an SH degree 3
+    mixture (surface Gaussians included), weights like a coreset's, two views of 160x104."""
+    sc = synth.mixture_scene(1000, 4, 3, 21, half_extent=1.0)
+    cams = synth.hemisphere_cameras(2, 160, 104, radius=4.0, seed=21)
+    w = np.random.default_rng(22).uniform(0.5, 3.0, sc.n)
+    return sc, cams, w

@@ -8,6 +8,7 @@ import oracle
 from oracle import Opts
 import paper_2607_02721_b300 as csgs
 from paper_2607_02721_b300 import build, finetune, synth
+from parity_helpers import finetune_subcase
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +72,37 @@ def test_render_backward_matches_oracle(ctx, torch, weighted):
         gl = torch.zeros(sc.n, device="cuda")
         ctx.render_backward(sid, v, torch.tensor(r, device="cuda"), gm, gs, gl, idx=idx_t, w=w_t)
         rm, rs, rl = oracle.render_backward(sc, cams[v], r, Opts(), w=wfull)
+        compare_groups(gm.cpu().numpy(), rm, "means")
+        compare_groups(gs.cpu().numpy(), rs, "sh")
+        compare_groups(gl.cpu().numpy(), rl, "opacity_logits")
+    ctx.free_scene(sid)
+
+
+@pytest.mark.parametrize("smooth", [False, True])
+def test_backward_on_finetune_subcase_matches_oracle(ctx, torch, smooth):
+    """The finetune's gradient sub-case (1,000 SH3 Gaussians with coreset-like weights,
+    two 160x104 views): the GPU gradient of <r, weighted render> against the oracle's,
+    whose own gradient is pinned by central differences at h = 1e-3 on the same case,
+    with the rasteriser's thresholds and without the alpha_min skip at a 7-sigma cut."""
+    sc, cams, w = finetune_subcase()
+    sid = ctx.load_scene(sc)
+    ctx.set_queries(sid, cams)
+    idx_t = torch.arange(sc.n, dtype=torch.int32, device="cuda")
+    w_t = torch.tensor(w.astype(np.float32), device="cuda")
+    w64 = w.astype(np.float32).astype(np.float64)
+    # smooth: no alpha_min skip and a 7-sigma footprint; the rho_max = 0.99 clamp stays, since
+    # the backward recovers T_i = T_(i+1) / (1 - rho_i) from the back and coreset weights
+    # above 1 would otherwise reach rho = 1
+    o, go = (Opts(alpha_min=0.0, cut2=49.0), csgs.default_opts(alpha_min=0.0, cut2=49.0)) if smooth \
+        else (Opts(), csgs.default_opts())
+    rng = np.random.default_rng(24)
+    for v in range(2):
+        r = rng.standard_normal((104, 160, 3)).astype(np.float32)
+        gm = torch.zeros(3, sc.n, device="cuda")
+        gs = torch.zeros(sc.sh.shape, device="cuda")
+        gl = torch.zeros(sc.n, device="cuda")
+        ctx.render_backward(sid, v, torch.tensor(r, device="cuda"), gm, gs, gl, idx=idx_t, w=w_t, opts=go)
+        rm, rs, rl = oracle.render_backward(sc, cams[v], r, o, w=w64)
         compare_groups(gm.cpu().numpy(), rm, "means")
         compare_groups(gs.cpu().numpy(), rs, "sh")
         compare_groups(gl.cpu().numpy(), rl, "opacity_logits")

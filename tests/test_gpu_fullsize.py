@@ -1,7 +1,9 @@
 """Parity at the full 3M-Gaussian, 1600x1040 workload, in the launch configuration the
 benchmark times: outputs the oracle can compute one by one (sampled pixels, the exact
 sensitivity of chosen Gaussians over a two-view query set) and properties that hold at
-any size (1 <= S <= min(N, |Q'|), s <= 1, s_i >= imp(g_i, q) for every sampled q)."""
+any size (1 <= S <= min(N, |Q'|), s <= 1, s_i >= imp(g_i, q) for every sampled q).
+Also the surrogate-assisted scorer's target on this workload: trained on 20 of the 200
+views, faster than exact scoring and within 0.1 dB PSNR of it at 90% pruning."""
 import numpy as np
 import pytest
 
@@ -115,3 +117,37 @@ def test_fullsize_resolution_chain_and_scene_total(setup):
     assert np.all(s_image >= s_scene * (1 - tol) - 1e-12)
     assert np.all(s_pixel >= s_image * (1 - tol) - 1e-12)
     assert np.all(s_pixel[s_scene > 0] > 0)  # a Gaussian that contributes anywhere has s > 0
+
+
+def test_surrogate_meets_target_at_full_size(setup):
+    """Surrogate-assisted scoring (exact scores on 20 of the 200 views, the network, a cheap
+    quarter-resolution score on every 4th view) against exact scoring of all 200 views:
+    the 90%-pruned render's PSNR (against the full render, every 10th view) loses at most
+    0.1 dB, beats the 20 scored views' exact scores alone by at least 1 dB, and the whole
+    surrogate path takes less time than exact scoring (CUDA events, after a warm-up)."""
+    import torch
+
+    from paper_2607_02721_b300 import surrogate
+
+    scene, cams, sa, ctx, sid = setup
+    ctx.set_queries(sid, cams)
+    ctx.score(sid)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    s_ex, _ = ctx.score(sid)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    exact_ms = e0.elapsed_time(e1)
+    s_ex = s_ex.clone()
+    cfg = surrogate.SurrogateConfig(train_views=20)
+    surrogate.surrogate_scores(ctx, sid, cams, cfg)
+    tim = {}
+    s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, cfg, timings=tim)
+    m = int(0.1 * scene.n)
+    views = list(range(0, len(cams), 10))
+    p = {k: surrogate.pruned_psnr(ctx, sid, cams, v, m, 0, views)
+         for k, v in (("exact", s_ex), ("surrogate", s_hat), ("subset", s_sub))}
+    report = (p, exact_ms, tim)
+    assert p["surrogate"] >= p["exact"] - 0.1, report
+    assert p["surrogate"] >= p["subset"] + 1.0, report
+    assert tim["total_ms"] < exact_ms, report

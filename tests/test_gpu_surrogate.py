@@ -1,18 +1,17 @@
-"""What the trained surrogate adds to exact scoring on a subset of the query views.
+"""What the trained surrogate adds to exact scoring on a subset of the query views, on a
+small seeded scene (the 3M-Gaussian workload's target is checked in test_gpu_fullsize).
 
-Surrogate-assisted scoring scores a few views exactly and fills in the rest with the
-trained BF16 network (library kernels only).  Without the network, the subset's scores
-are all there is, and every Gaussian that no subset view reaches has probability zero:
-it can never enter the coreset.  The test measures, on a seeded scene:
-  - coverage: the share of Gaussians with exact s > 0 that get p = 0 without the
-    network (positive here) and with it (zero);
-  - ranking: the trained network's predictions rank Gaussians by exact sensitivity
-    better than an untrained network of the same shape (Spearman 0.18 against 0.00 when
-    this was written: a weak but real signal from four scored views);
-  - quality: the PSNR of the 90%-pruned render with the subset's scores alone, with the
-    surrogate's, and with the exact scores.  These are recorded (in $CSGS_TEST_REPORT_DIR
-    when set) and bounded loosely; on these synthetic scenes the surrogate does not beat
-    the subset alone in PSNR.
+Surrogate-assisted scoring scores 10% of the views exactly at full resolution and
+predicts every Gaussian's per-pixel sensitivity over all views with the library's BF16
+network, from its attributes, view statistics over all views and a cheap score: the same
+per-pixel sensitivity over every 4th view rendered at a quarter of the resolution.  The
+network is trained on the scored views only.  The test asserts that no Gaussian with
+exact s > 0 gets p = 0 (without the network a few percent do) and that the 90%-pruned
+render (PSNR against the full render) beats the scored subset's exact scores alone.  It
+records, without asserting, the exact scores' PSNR and an un-learned combination of the
+same inputs (the cheap score scaled to the exact scores by the median ratio on the scored
+views, maximum with the subset's scores).  Written to
+$CSGS_TEST_REPORT_DIR/surrogate_gain.json when set.
 """
 import json
 import os
@@ -50,13 +49,13 @@ def ctx(torch):
 
 
 def test_surrogate_gain_over_subset_scores(ctx, torch):
-    sc = synth.mixture_scene(60000, 32, 3, 5, half_extent=3.0)
-    cams = synth.hemisphere_cameras(40, 160, 120, radius=10.0, seed=5)
+    sc = synth.mixture_scene(300_000, 64, 3, 5, half_extent=3.5)
+    cams = synth.hemisphere_cameras(40, 640, 416, radius=10.0, seed=5)
     sid = ctx.load_scene(sc)
     ctx.set_queries(sid, cams)
     s_ex, _ = ctx.score(sid)
     s_ex = s_ex.clone()
-    cfg = surrogate.SurrogateConfig(train_views=4, aug_views=(1, 2), steps=300, fill_only=True)
+    cfg = surrogate.SurrogateConfig(train_views=4)
     s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, cfg)
     a = s_ex.double().cpu().numpy()
     h = s_hat.double().cpu().numpy()
@@ -64,28 +63,31 @@ def test_surrogate_gain_over_subset_scores(ctx, torch):
     pos = a > 0
     lost_without = float(np.mean(b[pos] == 0))
     lost_with = float(np.mean(h[pos] == 0))
-    assert lost_without > 0.01  # the subset misses Gaussians other views reach
-    assert lost_with == 0.0  # every one of them gets a predicted score
-
-    # trained vs untrained network on the same features (all views)
-    X = ctx.features(sid, ctx.view_stats(sid))
-    y_trained = ctx.mlp_forward(X).double().cpu().numpy().ravel()
-    ctx.mlp_init(123)
-    y_untrained = ctx.mlp_forward(X).double().cpu().numpy().ravel()
-    r_trained = spearman(a[pos], y_trained[pos])
-    r_untrained = spearman(a[pos], y_untrained[pos])
-    assert r_trained > r_untrained + 0.1, (r_trained, r_untrained)
-
+    # the cheap score alone, brought to the exact scale by the median ratio on the scored
+    # views and combined with the subset's exact scores (no network)
+    low = surrogate.lowres_cameras(cams, cfg.lowres_factor)
+    ctx.set_queries(sid, low[::cfg.cheap_stride])
+    s_low = ctx.score(sid)[0].clone()
+    sub = surrogate.view_subset(len(cams), cfg.train_views)
+    ctx.set_queries(sid, low[sub])
+    s_low_sub = ctx.score(sid)[0].double().cpu().numpy()
+    ok = (b > 0) & (s_low_sub > 0)
+    ratio = float(np.median(b[ok] / s_low_sub[ok]))
+    s_nonet = torch.maximum(s_sub, s_low * ratio)
+    ctx.set_queries(sid, cams)
     m = int(0.1 * sc.n)
     psnr = {name: surrogate.pruned_psnr(ctx, sid, cams, sv, m, 0, None)
-            for name, sv in (("exact", s_ex), ("surrogate", s_hat), ("subset_only", s_sub))}
+            for name, sv in (("exact", s_ex), ("surrogate", s_hat), ("subset_only", s_sub), ("no_network", s_nonet))}
     report = {"coverage_lost_without": lost_without, "coverage_lost_with": lost_with,
-              "spearman_trained": r_trained, "spearman_untrained": r_untrained, "psnr": psnr,
+              "spearman_surrogate": spearman(a[pos], h[pos]),
+              "spearman_no_network": spearman(a[pos], s_nonet.double().cpu().numpy()[pos]), "psnr": psnr,
               "gain_psnr_vs_subset": psnr["surrogate"] - psnr["subset_only"],
               "delta_psnr_vs_exact": psnr["surrogate"] - psnr["exact"]}
     out = os.environ.get("CSGS_TEST_REPORT_DIR", "")
     if out and os.path.isdir(out):
         with open(os.path.join(out, "surrogate_gain.json"), "w") as f:
             json.dump(report, f, indent=1)
-    assert psnr["surrogate"] > psnr["subset_only"] - 1.0, report
+    assert lost_without > 0.01, report
+    assert lost_with == 0.0, report
+    assert psnr["surrogate"] > psnr["subset_only"], report
     ctx.free_scene(sid)
