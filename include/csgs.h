@@ -295,7 +295,9 @@ csgs_status csgs_update_scene(csgs_ctx* ctx, int32_t scene_id, const csgs_scene_
  * float).  Back to front through the compositing (dC/drho_i = c_i T_i - S_i / (1 -
  * rho_i), S_i the colour behind i), no gradient through the rho_max clamp or the
  * footprint and threshold decisions, then through the EWA projection and the SH colour
- * (including its view direction).  Asynchronous. */
+ * (including its view direction).  The transmittance in front of each contributor is
+ * recovered from the back, T_i = T_(i+1) / (1 - rho_i), so opts->rho_max must stay below
+ * 1 (a factor 1 - rho_i of 0 gives non-finite gradients).  Asynchronous. */
 csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int32_t* idx_dev,
                                  const float* w_dev, int64_t n_sel, const csgs_score_opts* opts, const float* grad_rgb_dev,
                                  float* g_means_dev, float* g_sh_dev, float* g_logit_dev);

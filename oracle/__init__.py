@@ -189,6 +189,30 @@ def project(scene, cam, opts: Opts | None = None, w=None) -> np.ndarray:
     return out
 
 
+def view_stats(scene, cams, opts: Opts | None = None) -> np.ndarray:
+    """Per-Gaussian view statistics of the surrogate's inputs (not in the paper), from the
+    projection above: [N, 3] = the number of views whose image the Gaussian's footprint
+    reaches (valid projection, alpha >= alpha_min, and the bounding box
+    |dx| <= sqrt(cut2 Sigma'_xx), |dy| <= sqrt(cut2 Sigma'_yy) of its ellipse overlapping
+    the pixel centres' range [0, W - 1] x [0, H - 1]), the mean over those views of the
+    ellipse's area pi cut2 sqrt(det Sigma'), and the maximum of that area."""
+    opts = opts or Opts()
+    cams = np.asarray(cams, dtype=np.float32).reshape(-1, 20)
+    n = _scene(scene).n
+    cnt, tot, mx = np.zeros(n), np.zeros(n), np.zeros(n)
+    for cam in cams:
+        P = project(scene, cam, opts)
+        W, H = float(cam[16]), float(cam[17])
+        rx, ry = np.sqrt(opts.cut2 * P[:, 6]), np.sqrt(opts.cut2 * P[:, 8])
+        vis = ((P[:, 0] > 0) & (P[:, 10] >= opts.alpha_min) & (P[:, 1] + rx >= 0) & (P[:, 1] - rx <= W - 1)
+               & (P[:, 2] + ry >= 0) & (P[:, 2] - ry <= H - 1))
+        area = np.pi * opts.cut2 * np.sqrt(np.maximum(P[:, 6] * P[:, 8] - P[:, 7] ** 2, 0.0))
+        cnt += vis
+        tot += np.where(vis, area, 0.0)
+        mx = np.maximum(mx, np.where(vis, area, 0.0))
+    return np.stack([cnt, np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0), mx], 1)
+
+
 def render(scene, cam, opts: Opts | None = None, w=None, pixels=None):
     """Render one camera (or the listed pixels).  Returns dict with rgb [H,W,3] (or
     [P,3]), T, n_terms, flags and the counters (violations, flagged pixels)."""

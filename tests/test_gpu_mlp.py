@@ -97,24 +97,12 @@ def test_view_stats_and_features(ctx, torch):
     sid = ctx.load_scene(sc)
     ctx.set_queries(sid, cams)
     st = ctx.view_stats(sid).cpu().numpy().astype(np.float64)
-    sa = oracle.SceneArrays(sc)
-    cnt = np.zeros(sc.n)
-    tot = np.zeros(sc.n)
-    mx = np.zeros(sc.n)
-    for cam in cams:
-        P = oracle.project(sa, cam)
-        W, H = int(cam[16]), int(cam[17])
-        rx, ry = np.sqrt(9 * P[:, 6]), np.sqrt(9 * P[:, 8])
-        vis = (P[:, 0] > 0) & (P[:, 1] + rx >= 0) & (P[:, 1] - rx <= W - 1) & (P[:, 2] + ry >= 0) & \
-              (P[:, 2] - ry <= H - 1) & (P[:, 10] >= 1 / 255)
-        area = math.pi * 9 * np.sqrt(np.maximum(P[:, 6] * P[:, 8] - P[:, 7] ** 2, 0))
-        cnt += vis
-        tot += np.where(vis, area, 0)
-        mx = np.maximum(mx, np.where(vis, area, 0))
+    ref = oracle.view_stats(oracle.SceneArrays(sc), cams)
+    cnt, mean_area, mx = ref[:, 0], ref[:, 1], ref[:, 2]
     agree = st[:, 0] == cnt
     assert agree.mean() > 0.995
     ok = agree & (cnt > 0)
-    np.testing.assert_allclose(st[ok, 1], tot[ok] / cnt[ok], rtol=2e-4)
+    np.testing.assert_allclose(st[ok, 1], mean_area[ok], rtol=2e-4)
     np.testing.assert_allclose(st[ok, 2], mx[ok], rtol=2e-4)
     X = ctx.features(sid, torch.tensor(st, dtype=torch.float32, device="cuda")).float().cpu().numpy()
     q = sc.quats / np.linalg.norm(sc.quats, axis=0, keepdims=True)
@@ -129,6 +117,12 @@ def test_view_stats_and_features(ctx, torch):
     exp[:, 61] = np.log1p(st[:, 2]) * 0.25
     bf = torch.tensor(exp, dtype=torch.float32).to(torch.bfloat16).float().numpy()
     np.testing.assert_allclose(X, bf, rtol=1e-2, atol=1e-2)
+    # the optional extra input lands in slot 62, divided by 8
+    extra = torch.linspace(-16.0, 0.0, sc.n, device="cuda")
+    X2 = ctx.features(sid, torch.tensor(st, dtype=torch.float32, device="cuda"), extra).float().cpu().numpy()
+    exp[:, 62] = extra.cpu().numpy() / 8
+    bf = torch.tensor(exp, dtype=torch.float32).to(torch.bfloat16).float().numpy()
+    np.testing.assert_allclose(X2, bf, rtol=1e-2, atol=1e-2)
     ctx.free_scene(sid)
 
 

@@ -255,6 +255,24 @@ def test_projection_quaternion_and_camera_rotation():
     np.testing.assert_allclose(P2[9], z)
 
 
+def test_view_stats_closed_form():
+    """Surrogate view statistics of one isotropic Gaussian: two cameras see it on their
+    axis at depths 2 and 4 (footprint variance (f sigma / z)^2 + dilation, area
+    pi 9 sqrt(det) = 9 pi var), a third looks away from it, a fourth has it far outside
+    its image.  A second Gaussian below alpha_min is counted nowhere."""
+    sig, f = 0.05, 40.0
+    sc = one_scene([[0, 0, 2.0], [0, 0.1, 2.0]], [[math.log(sig)] * 3] * 2, [[0.5] * 3] * 2, [0.3, -9.0])
+    R_back = np.diag([1.0, -1.0, -1.0])  # looks along -z from the origin: the Gaussian is behind
+    cams = np.stack([axis_camera(f=f), axis_camera(f=f, t=(0.0, 0.0, 2.0)), axis_camera(f=f, R=R_back),
+                     axis_camera(f=f, t=(5.0, 0.0, 0.0))])
+    st = oracle.view_stats(sc, cams)
+    s_eff = eff_scale(sig)
+    areas = [9 * math.pi * ((f * s_eff / z) ** 2 + DIL) for z in (2.0, 4.0)]
+    np.testing.assert_allclose(st[0], [2, np.mean(areas), max(areas)], rtol=1e-12)
+    assert sigmoid(-9.0) < Opts().alpha_min
+    np.testing.assert_array_equal(st[1], [0, 0, 0])
+
+
 # ---------------------------------------------------------------- compositing
 
 def test_single_gaussian_closed_form_render_and_score():
