@@ -286,34 +286,50 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             }
         } else if (!summed(MODE)) {
             int kmax = 0;  // counting runs: entries this lane walked (the warp walks the maximum)
+            // one list entry at pixel (X, Y): false once the pixel has stopped
+            auto step = [&](int j, const float4& Bj, float p) -> bool {
+                if (STATS) ++n_eval;
+                if (p < Bj.z) return true;
+                const float raw = ex2_approx(p);
+                const float r = fminf(rho_max, raw);
+                if (STATS) {
+                    ++n_hit;
+                    n_viol += raw >= 1.f;
+                }
+                const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
+                if (Tn < t_min) {
+                    done = true;
+                    return false;
+                }
+                const float w = __fmul_rn(r, T);
+                if (MODE == kScorePixel)
+                    A0 = VAR == kL1 ? __fmaf_rn(Bj.w, w, A0)
+                                    : (VAR == kL2 ? __fmaf_rn(sh.C[j].w, __fmul_rn(w, w), A0) : __fadd_rn(A0, w));
+                else
+                    accumulate<MODE, VAR>(A0, A1, A2, sh.C[j], w);
+                T = Tn;
+                last = b + j + 1;
+                return true;
+            };
             if (!done) {
-                for (int k = 0; k < nw; ++k) {
+                // two entries per iteration: the second entry's loads and exponent are
+                // independent of the first's contribution, so they overlap its latency; the
+                // entries are still applied in list order
+                int k = 0;
+                for (; k + 1 < nw; k += 2) {
+                    const int j0 = sh.wl[warp][k], j1 = sh.wl[warp][k + 1];
+                    const float4 Aa = sh.A[j0], Ba = sh.B[j0], Ab = sh.A[j1], Bb = sh.B[j1];
+                    const float pa = exponent2(Aa, Ba, X, Y), pb = exponent2(Ab, Bb, X, Y);
                     if (STATS) kmax = k + 1;
+                    if (!step(j0, Ba, pa)) break;
+                    if (STATS) kmax = k + 2;
+                    if (!step(j1, Bb, pb)) break;
+                }
+                if (!done && k < nw) {
                     const int j = sh.wl[warp][k];
-                    const float4 Aj = sh.A[j];
-                    const float4 Bj = sh.B[j];
-                    const float p = exponent2(Aj, Bj, X, Y);
-                    if (STATS) ++n_eval;
-                    if (p < Bj.z) continue;
-                    const float raw = ex2_approx(p);
-                    const float r = fminf(rho_max, raw);
-                    if (STATS) {
-                        ++n_hit;
-                        n_viol += raw >= 1.f;
-                    }
-                    const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
-                    if (Tn < t_min) {
-                        done = true;
-                        break;
-                    }
-                    const float w = __fmul_rn(r, T);
-                    if (MODE == kScorePixel)
-                        A0 = VAR == kL1 ? __fmaf_rn(Bj.w, w, A0)
-                                        : (VAR == kL2 ? __fmaf_rn(sh.C[j].w, __fmul_rn(w, w), A0) : __fadd_rn(A0, w));
-                    else
-                        accumulate<MODE, VAR>(A0, A1, A2, sh.C[j], w);
-                    T = Tn;
-                    last = b + j + 1;
+                    const float4 Aj = sh.A[j], Bj = sh.B[j];
+                    if (STATS) kmax = k + 1;
+                    step(j, Bj, exponent2(Aj, Bj, X, Y));
                 }
             }
             if (STATS) {
