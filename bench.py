@@ -320,7 +320,9 @@ def run_ours(args):
     tuned = None
     if not args.no_autotune and not args.view_batch:
         # view batch and radix-sort grid picked by the library's autotuner (untimed)
-        tuned = ctx.autotune(sid, csgs.default_opts(), probe_views=16)
+        # 48 probe views: with 16 the step times of the candidates differed by less than the
+        # run-to-run spread (picks of 8/592 and 16/296 gave 167.0 and 158.9 ms)
+        tuned = ctx.autotune(sid, csgs.default_opts(), probe_views=48)
         cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1]}
 
     # pair counts of one pass (untimed; counting kernels are slower)

@@ -186,7 +186,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
 /* Choose the view batch (views projected per launch) of one scene and the
  * radix-sort grid of the context by timing csgs_score's work on the first
  * probe_views query views (0: min(16, views)) for view batches {1,2,4,8,16} and sort
- * grids {296,592,1184,1776} blocks.  The result applies to later csgs_score /
+ * grids {148,296,592,1184,1776} blocks.  The result applies to later csgs_score /
  * csgs_score_batch calls whose opts->view_batch is 0; scores do not depend on it
  * (the footprint test is per pixel).  Outputs may be NULL.  Synchronises. */
 csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,

@@ -985,7 +985,9 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
     const int nv = (int)s->cams.size();
     const int pv = probe_views > 0 && probe_views < nv ? probe_views : (nv < 16 ? nv : 16);
     const int vbs[5] = {1, 2, 4, 8, 16};
-    const int gs[4] = {148 * 2, 148 * 4, 148 * 8, 148 * 12};
+    // radix-sort grids: from one CTA per SM (binning holds few SM slots beside the
+    // compositing) to twelve (binning alone as fast as it goes)
+    const int gs[5] = {148, 148 * 2, 148 * 4, 148 * 8, 148 * 12};
     float* s_tmp = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&s_tmp, sizeof(float) * (size_t)s->n));
     std::unique_ptr<float, cudaError_t (*)(void*)> s_tmp_owner(s_tmp, cudaFree);

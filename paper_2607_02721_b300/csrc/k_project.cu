@@ -521,12 +521,9 @@ void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const K
                        cudaStream_t st) {
     const int threads = 256;
     const int blocks = (sc.n + threads - 1) / threads;
-    switch (sc.deg) {
-        case 0: k_view_stats<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
-        case 1: k_view_stats<1><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
-        case 2: k_view_stats<2><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
-        default: k_view_stats<3><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate); break;
-    }
+    // validity and footprint do not depend on the colour: the degree-0 instantiation reads
+    // only the DC coefficients and evaluates no higher harmonics, whatever the scene's degree
+    k_view_stats<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate);
     count_launches(1);
 }
 
