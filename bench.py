@@ -384,32 +384,45 @@ def run_ours(args):
         idx_host = torch.empty(m, dtype=torch.int32).pin_memory()
         w_host = torch.empty(m, dtype=torch.float32).pin_memory()
 
-        def e2e_step(seed):
-            sid2 = ctx.load_scene_ptrs(scene.n, scene.sh_degree, [h.data_ptr() for h in host], is_device=False)
-            ctx.set_queries(sid2, cams[my_views])
-            s2, _ = ctx.score(sid2, csgs.default_opts(resolution=res_id), out=s)
-            combine(ctx.stats())
-            idx, w = ctx.sample_coreset(s2, m, seed)
-            with torch.cuda.stream(stream):
-                s_host.copy_(s2, non_blocking=True)
-                idx_host[: idx.numel()].copy_(idx, non_blocking=True)
-                w_host[: w.numel()].copy_(w, non_blocking=True)
-            stream.synchronize()
-            ctx.free_scene(sid2)
-            return s_host.numel() * 4 + 8 * idx.numel()
+        def load():
+            # asynchronous load from pinned memory: the upload runs on the copy engine while
+            # the previous step scores (its validation happens at the scene's first use)
+            return ctx.load_scene_ptrs(scene.n, scene.sh_degree, [h.data_ptr() for h in host], is_device=False,
+                                       asynchronous=True)
 
-        e2e_step(0)
+        def e2e_run(steps, seed0):
+            """`steps` steps, each one scene upload (issued one step ahead), queries, score,
+            coreset draw and read-back of s, idx and w.  Returns the D2H bytes of a step."""
+            d2h = 0
+            nxt = load()
+            for i in range(steps):
+                cur = nxt
+                nxt = load() if i + 1 < steps else None
+                ctx.set_queries(cur, cams[my_views])
+                s2, _ = ctx.score(cur, csgs.default_opts(resolution=res_id), out=s)
+                combine(ctx.stats())
+                idx, w = ctx.sample_coreset(s2, m, seed0 + i)
+                with torch.cuda.stream(stream):
+                    s_host.copy_(s2, non_blocking=True)
+                    idx_host[: idx.numel()].copy_(idx, non_blocking=True)
+                    w_host[: w.numel()].copy_(w, non_blocking=True)
+                stream.synchronize()
+                ctx.free_scene(cur)
+                d2h = s_host.numel() * 4 + 8 * idx.numel()
+            return d2h
+
+        e2e_run(2, 0)  # warm-up: two scenes' buffers for the context to reuse
         torch.cuda.synchronize()
         ne = max(1, min(args.steps, 5))
-        d2h = 0
         t0 = time.perf_counter()
-        for i in range(ne):
-            d2h = e2e_step(2000 + i)
+        d2h = e2e_run(ne, 2000)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         te = job_time_ms(te * 1e3, dist, torch.device("cuda", local)) / 1e3
         e2e = {"value": cfg["rays_per_step"] * ne / te, "unit": "rays/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "steps": ne}
+               "d2h_bytes_per_step": int(d2h), "steps": ne,
+               "note": "each step's scene upload is issued one step ahead (csgs_load_scene_async) and overlaps "
+                       "the previous step's scoring; all uploads are inside the timed region"}
 
     # ---- roofline of the dominant kernel (compositing + sensitivity reduction)
     pairs_step = cnt["pairs_evaluated"] + cnt["pairs_evaluated2"]
@@ -886,7 +899,7 @@ def main():
     ap.add_argument("--view-batch", type=int, default=0, help="views projected per launch (0 = automatic)")
     ap.add_argument("--surrogate", action="store_true", help="surrogate-assisted vs exact scoring report")
     ap.add_argument("--train-views", type=int, default=20)
-    ap.add_argument("--train-steps", type=int, default=150)
+    ap.add_argument("--train-steps", type=int, default=100)
     ap.add_argument("--psnr-stride", type=int, default=5)
     ap.add_argument("--fill-only", action="store_true")
     ap.add_argument("--resolution", default="pixel", choices=["pixel", "scene"])

@@ -153,10 +153,24 @@ const char* csgs_last_error(const csgs_ctx* ctx);
 
 /* Copy a scene into the context (host or device source per desc->is_device).
  * Checks sizes and that every attribute is finite (non-finite -> CSGS_E_INVAL,
- * synchronising).  *scene_id receives the handle. */
+ * synchronising).  *scene_id receives the handle.  Attribute buffers of earlier freed
+ * scenes of the same size are reused before new device memory is allocated. */
 csgs_status csgs_load_scene(csgs_ctx* ctx, const csgs_scene_desc* desc, int32_t* scene_id);
 
-/* Release a scene's device memory. */
+/* csgs_load_scene without waiting: allocates (or reuses) the buffers, enqueues the
+ * copies and the finiteness check on the context's own upload stream and returns.  The
+ * first call that uses the scene (any call taking its id, csgs_free_scene excepted)
+ * waits for the upload to finish; if an attribute is non-finite, that call fails with
+ * CSGS_E_INVAL and the scene is released (the id becomes invalid).  The source must stay
+ * unchanged until then; from pinned host memory the copies run on the copy engine
+ * beside the context's kernels, so loading the next scene overlaps scoring the current
+ * one.  At most 16 such loads may be pending (not yet used) at once (else CSGS_E_INVAL).
+ * The paper has no counterpart: this is a deployment variant of the load. */
+csgs_status csgs_load_scene_async(csgs_ctx* ctx, const csgs_scene_desc* desc, int32_t* scene_id);
+
+/* Release a scene (after the context's stream has finished with it).  Its attribute
+ * buffers stay with the context for later loads of the same size (up to 32 buffers;
+ * the oldest beyond that, and all of them at csgs_destroy, return to the device). */
 csgs_status csgs_free_scene(csgs_ctx* ctx, int32_t scene_id);
 
 /* Set the query views of a scene (Algorithm 1, step 1): every pixel of each camera

@@ -76,6 +76,7 @@ class Stats(ctypes.Structure):
 
 
 EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error", "csgs_load_scene",
+           "csgs_load_scene_async",
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
            "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
            "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
@@ -105,6 +106,7 @@ def lib():
     L.csgs_last_error.argtypes = [V]
     L.csgs_last_error.restype = ctypes.c_char_p
     L.csgs_load_scene.argtypes = [V, V, V]
+    L.csgs_load_scene_async.argtypes = [V, V, V]
     L.csgs_free_scene.argtypes = [V, I32]
     L.csgs_set_queries.argtypes = [V, I32, V, I32]
     L.csgs_score.argtypes = [V, I32, V, V, V]
@@ -262,11 +264,14 @@ class Context:
         self._scenes[sid.value] = int(keep[0].shape[1])
         return sid.value
 
-    def load_scene_ptrs(self, n: int, sh_degree: int, ptrs, is_device: bool) -> int:
+    def load_scene_ptrs(self, n: int, sh_degree: int, ptrs, is_device: bool, asynchronous: bool = False) -> int:
+        """Load a scene from raw attribute pointers.  asynchronous: csgs_load_scene_async
+        (the sources must stay unchanged until the scene's first use)."""
         d = SceneDesc(n, sh_degree, 1 if is_device else 0, *ptrs)
         sid = ctypes.c_int32()
         self._in()
-        self._check(lib().csgs_load_scene(self.h, ctypes.byref(d), ctypes.byref(sid)))
+        fn = lib().csgs_load_scene_async if asynchronous else lib().csgs_load_scene
+        self._check(fn(self.h, ctypes.byref(d), ctypes.byref(sid)))
         self._scenes[sid.value] = n
         return sid.value
 

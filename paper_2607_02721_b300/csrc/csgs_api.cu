@@ -53,6 +53,12 @@ struct SceneRec {
     CamDev* d_cams = nullptr;
     float uploaded_clamp = -1.f;  // clamp_fov of the cameras on the device (-1: none)
     int tuned_vb = 0;             // view batch chosen by csgs_autotune (0: automatic)
+    // asynchronous load: the upload (copies + finiteness check on the context's upload
+    // stream) is settled by the first call that uses the scene
+    bool pending = false;
+    cudaEvent_t uploaded = nullptr;
+    DevCounters* d_chk = nullptr;  // the upload's check word (one of the context's slots)
+    int chk_slot = -1;
 };
 
 }  // namespace
@@ -98,6 +104,15 @@ struct csgs_ctx {
     unsigned long long buf_gen = 0;  // bumped whenever a work buffer is reallocated
     bool wide_keys = false;          // a view's depth range overflowed the narrow keys: 32-bit keys from then on
     int max_tiles = 0;               // ranges per view row in the binning slots
+    // attribute buffers of freed scenes, kept for later loads of the same size (a scene
+    // loaded and freed every step then allocates and frees nothing); released at destroy
+    std::vector<std::pair<size_t, float*>> scene_pool;
+    cudaStream_t ust = nullptr;  // upload stream of csgs_load_scene_async
+    std::string scene_err;       // why the last settled asynchronous load was rejected
+    // check words of pending asynchronous loads, allocated once (a cudaFree per load would
+    // synchronise the device and wait for the next scene's upload)
+    DevCounters* d_chk_slots = nullptr;
+    uint32_t chk_used = 0;       // bit k: slot k belongs to a pending load
 };
 
 namespace {
@@ -196,9 +211,96 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     return CSGS_OK;
 }
 
-SceneRec* get_scene(csgs_ctx* ctx, int32_t id) {
+SceneRec* find_scene(csgs_ctx* ctx, int32_t id) {
     if (!ctx || id < 0 || id >= (int32_t)ctx->scenes.size() || !ctx->scenes[id].alive) return nullptr;
     return &ctx->scenes[id];
+}
+
+
+constexpr size_t kScenePoolMax = 32;
+constexpr int kMaxPendingLoads = 16;
+
+float* pool_take(csgs_ctx* ctx, size_t bytes) {
+    for (size_t k = 0; k < ctx->scene_pool.size(); ++k)
+        if (ctx->scene_pool[k].first == bytes) {
+            float* p = ctx->scene_pool[k].second;
+            ctx->scene_pool.erase(ctx->scene_pool.begin() + (long)k);
+            return p;
+        }
+    return nullptr;
+}
+
+void pool_put(csgs_ctx* ctx, size_t bytes, float* p) {
+    if (!p) return;
+    ctx->scene_pool.push_back({bytes, p});
+    if (ctx->scene_pool.size() > kScenePoolMax) {
+        cudaFree(ctx->scene_pool.front().second);
+        ctx->scene_pool.erase(ctx->scene_pool.begin());
+    }
+}
+
+// Byte sizes of a scene's five attribute buffers (means, log-scales, quaternions,
+// opacity logits, SH coefficients).
+void scene_bytes(int64_t n, int deg, size_t out[5]) {
+    const size_t nk = (size_t)(deg + 1) * (deg + 1);
+    const size_t counts[5] = {3 * (size_t)n, 3 * (size_t)n, 4 * (size_t)n, (size_t)n, 3 * nk * (size_t)n};
+    for (int k = 0; k < 5; ++k) out[k] = counts[k] * sizeof(float);
+}
+
+
+// Return a scene's attribute buffers to the context's pool and forget it.
+void drop_scene(csgs_ctx* ctx, SceneRec* s) {
+    size_t bytes[5];
+    scene_bytes(s->n, s->deg, bytes);
+    float* bufs[5] = {s->means, s->log_scales, s->quats, s->opac, s->sh};
+    for (int k = 0; k < 5; ++k) pool_put(ctx, bytes[k], bufs[k]);
+    if (s->d_cams) cudaFree(s->d_cams);
+    if (s->uploaded) cudaEventDestroy(s->uploaded);
+    if (s->chk_slot >= 0) ctx->chk_used &= ~(1u << s->chk_slot);
+    *s = SceneRec();
+}
+
+// Wait for an asynchronous load's upload and read its finiteness check; a scene with a
+// non-finite attribute is released (its id becomes invalid) and false is returned.
+bool settle_scene(csgs_ctx* ctx, SceneRec* s) {
+    if (!s->pending) return true;
+    s->pending = false;
+    uint32_t err = ~0u;
+    if (cudaEventSynchronize(s->uploaded) != cudaSuccess ||
+        cudaMemcpy(&err, &s->d_chk->err, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->scene_err = "the scene's upload failed";
+        drop_scene(ctx, s);
+        return false;
+    }
+    if (err & kErrNonFinite) {
+        ctx->scene_err = "scene attributes contain non-finite values (the scene is released)";
+        drop_scene(ctx, s);
+        return false;
+    }
+    ctx->chk_used &= ~(1u << s->chk_slot);
+    s->chk_slot = -1;
+    s->d_chk = nullptr;
+    return true;
+}
+
+// The scene with this id, its asynchronous upload (if any) settled; nullptr if the id is
+// invalid or the upload was rejected (ctx->scene_err says why).
+SceneRec* get_scene(csgs_ctx* ctx, int32_t id) {
+    SceneRec* s = find_scene(ctx, id);
+    if (!s) return nullptr;
+    if (!settle_scene(ctx, s)) return nullptr;
+    return s;
+}
+
+// The error of a call given a scene id that get_scene rejected.
+csgs_status scene_fail(csgs_ctx* ctx, int32_t id) {
+    if (!ctx->scene_err.empty()) {
+        std::string e = ctx->scene_err;
+        ctx->scene_err.clear();
+        return fail(ctx, CSGS_E_INVAL, "scene %d: %s", id, e.c_str());
+    }
+    return fail(ctx, CSGS_E_INVAL, "bad scene id %d", id);
 }
 
 SceneDev scene_dev(const SceneRec& s) {
@@ -383,6 +485,7 @@ csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
         }
     }
     bool ev_ok = cudaStreamCreateWithFlags(&ctx->pst, cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&ctx->ust, cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; k < 2 && ev_ok; ++k)
         ev_ok = cudaEventCreateWithFlags(&ctx->ev_proj[k], cudaEventDisableTiming) == cudaSuccess &&
@@ -405,8 +508,10 @@ void csgs_destroy(csgs_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->st) cudaStreamSynchronize(ctx->st);
+    if (ctx->ust) cudaStreamSynchronize(ctx->ust);
     for (auto& s : ctx->scenes) {
         if (!s.alive) continue;
+        if (s.uploaded) cudaEventDestroy(s.uploaded);
         cudaFree(s.means);
         cudaFree(s.log_scales);
         cudaFree(s.quats);
@@ -414,6 +519,9 @@ void csgs_destroy(csgs_ctx* ctx) {
         cudaFree(s.sh);
         cudaFree(s.d_cams);
     }
+    for (auto& e : ctx->scene_pool) cudaFree(e.second);
+    ctx->scene_pool.clear();
+    if (ctx->d_chk_slots) cudaFree(ctx->d_chk_slots);
     for (BinSlot& b : ctx->slot) {
         DevBuf* sb[] = {&b.dkeys_b, &b.dvals_a, &b.dvals_b, &b.ikeys_a, &b.ikeys_b,
                         &b.ivals_a, &b.ivals_b, &b.ranges,  &b.hist,    &b.scan_tmp};
@@ -431,6 +539,7 @@ void csgs_destroy(csgs_ctx* ctx) {
     }
     if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
     if (ctx->pst) cudaStreamDestroy(ctx->pst);
+    if (ctx->ust) cudaStreamDestroy(ctx->ust);
     for (int c = 0; c < kCompStreams - 1; ++c) {
         if (ctx->ev_cdone[c]) cudaEventDestroy(ctx->ev_cdone[c]);
         for (int k = 0; k < 2; ++k)
@@ -463,44 +572,56 @@ void csgs_destroy(csgs_ctx* ctx) {
 
 const char* csgs_last_error(const csgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-csgs_status csgs_load_scene(csgs_ctx* ctx, const csgs_scene_desc* d, int32_t* scene_id) {
-    if (!ctx) return CSGS_E_INVAL;
-    if (!d || !scene_id) return fail(ctx, CSGS_E_INVAL, "null argument");
+
+// Allocate (or reuse) a scene's buffers and enqueue the copies and the finiteness checks
+// on stream `st`, the check writing to chk->err.  On success *s holds the buffers.
+static csgs_status enqueue_scene_load(csgs_ctx* ctx, const csgs_scene_desc* d, SceneRec* s, DevCounters* chk,
+                                      cudaStream_t st) {
+    if (!d) return fail(ctx, CSGS_E_INVAL, "null argument");
     if (d->n <= 0 || d->n >= (1ll << 31)) return fail(ctx, CSGS_E_INVAL, "scene size %lld out of range", (long long)d->n);
     if (d->sh_degree < 0 || d->sh_degree > 3) return fail(ctx, CSGS_E_INVAL, "sh_degree %d not in 0..3", d->sh_degree);
     if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
         return fail(ctx, CSGS_E_INVAL, "null attribute pointer");
-    cudaSetDevice(ctx->device);
-    SceneRec s;
-    s.n = d->n;
-    s.deg = d->sh_degree;
+    s->n = d->n;
+    s->deg = d->sh_degree;
     const size_t n = (size_t)d->n;
     const size_t nk = (size_t)(d->sh_degree + 1) * (d->sh_degree + 1);
     struct {
         float** dst;
         const float* src;
         size_t count;
-    } parts[] = {{&s.means, d->means, 3 * n},
-                 {&s.log_scales, d->log_scales, 3 * n},
-                 {&s.quats, d->quats, 4 * n},
-                 {&s.opac, d->opacity_logits, n},
-                 {&s.sh, d->sh, 3 * nk * n}};
+    } parts[] = {{&s->means, d->means, 3 * n},
+                 {&s->log_scales, d->log_scales, 3 * n},
+                 {&s->quats, d->quats, 4 * n},
+                 {&s->opac, d->opacity_logits, n},
+                 {&s->sh, d->sh, 3 * nk * n}};
     const cudaMemcpyKind kind = d->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
+    CUDA_TRY(ctx, cudaMemsetAsync(&chk->err, 0, sizeof(uint32_t), st));
     for (auto& p : parts) {
-        if (cudaMalloc(p.dst, p.count * sizeof(float)) != cudaSuccess) {
+        *p.dst = pool_take(ctx, p.count * sizeof(float));
+        if (!*p.dst && cudaMalloc(p.dst, p.count * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
-            for (auto& q : parts)
-                if (*q.dst) cudaFree(*q.dst);
+            *p.dst = nullptr;
+            cudaStreamSynchronize(st);  // copies already enqueued into the other buffers
+            for (auto& q : parts) pool_put(ctx, q.count * sizeof(float), *q.dst);
             return fail(ctx, CSGS_E_NOMEM, "scene allocation failed");
         }
-        CUDA_TRY(ctx, cudaMemcpyAsync(*p.dst, p.src, p.count * sizeof(float), kind, ctx->st));
-        launch_check_finite(*p.dst, (int64_t)p.count, ctx->d_ctr, ctx->st);
+        CUDA_TRY(ctx, cudaMemcpyAsync(*p.dst, p.src, p.count * sizeof(float), kind, st));
+        launch_check_finite(*p.dst, (int64_t)p.count, chk, st);
     }
-    csgs_status r = read_counters(ctx);
+    return CSGS_OK;
+}
+
+csgs_status csgs_load_scene(csgs_ctx* ctx, const csgs_scene_desc* d, int32_t* scene_id) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!scene_id) return fail(ctx, CSGS_E_INVAL, "null argument");
+    cudaSetDevice(ctx->device);
+    SceneRec s;
+    csgs_status r = enqueue_scene_load(ctx, d, &s, ctx->d_ctr, ctx->st);
     if (r) return r;
+    if ((r = read_counters(ctx))) return r;
     if (ctx->h_ctr->err & kErrNonFinite) {
-        for (auto& q : parts) cudaFree(*q.dst);
+        drop_scene(ctx, &s);
         return fail(ctx, CSGS_E_INVAL, "scene attributes contain non-finite values");
     }
     s.alive = true;
@@ -509,23 +630,58 @@ csgs_status csgs_load_scene(csgs_ctx* ctx, const csgs_scene_desc* d, int32_t* sc
     return CSGS_OK;
 }
 
+csgs_status csgs_load_scene_async(csgs_ctx* ctx, const csgs_scene_desc* d, int32_t* scene_id) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!scene_id) return fail(ctx, CSGS_E_INVAL, "null argument");
+    cudaSetDevice(ctx->device);
+    SceneRec s;
+    if (!ctx->d_chk_slots) {
+        if (cudaMalloc(&ctx->d_chk_slots, sizeof(DevCounters) * kMaxPendingLoads) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->d_chk_slots = nullptr;
+            return fail(ctx, CSGS_E_NOMEM, "upload bookkeeping allocation failed");
+        }
+    }
+    for (int k = 0; k < kMaxPendingLoads; ++k)
+        if (!(ctx->chk_used & (1u << k))) {
+            s.chk_slot = k;
+            break;
+        }
+    if (s.chk_slot < 0)
+        return fail(ctx, CSGS_E_INVAL, "more than %d asynchronous loads pending: use the scenes first",
+                    kMaxPendingLoads);
+    s.d_chk = ctx->d_chk_slots + s.chk_slot;
+    if (cudaEventCreateWithFlags(&s.uploaded, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, CSGS_E_CUDA, "event creation failed");
+    }
+    csgs_status r = enqueue_scene_load(ctx, d, &s, s.d_chk, ctx->ust);
+    if (r) {
+        cudaStreamSynchronize(ctx->ust);
+        cudaEventDestroy(s.uploaded);
+        return r;
+    }
+    ctx->chk_used |= 1u << s.chk_slot;
+    CUDA_TRY(ctx, cudaEventRecord(s.uploaded, ctx->ust));
+    s.pending = true;
+    s.alive = true;
+    ctx->scenes.push_back(s);
+    *scene_id = (int32_t)ctx->scenes.size() - 1;
+    return CSGS_OK;
+}
+
 csgs_status csgs_free_scene(csgs_ctx* ctx, int32_t scene_id) {
-    SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    SceneRec* s = find_scene(ctx, scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
+    if (s->pending) cudaEventSynchronize(s->uploaded);  // its copies may still be landing
     cudaStreamSynchronize(ctx->st);
-    cudaFree(s->means);
-    cudaFree(s->log_scales);
-    cudaFree(s->quats);
-    cudaFree(s->opac);
-    cudaFree(s->sh);
-    cudaFree(s->d_cams);
-    *s = SceneRec();
+    drop_scene(ctx, s);
     return CSGS_OK;
 }
 
 csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera* cams, int32_t n_views) {
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (!cams || n_views <= 0) return fail(ctx, CSGS_E_INVAL, "no cameras");
     std::vector<CamDev> v(n_views);
     for (int i = 0; i < n_views; ++i) {
@@ -795,7 +951,7 @@ extern "C" {
 csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* s_dev, double* S_out) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (!s_dev) return fail(ctx, CSGS_E_INVAL, "s_dev is NULL");
     if (s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "no query views set");
     KOpts ko;
@@ -881,7 +1037,8 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
     int64_t rays = 0;
     for (int k = 0; k < n_scenes; ++k) {
         sc[k] = get_scene(ctx, scene_ids[k]);
-        if (!sc[k] || sc[k]->cams.empty() || !s_devs[k]) return fail(ctx, CSGS_E_INVAL, "bad scene %d in batch", k);
+        if (!sc[k]) return scene_fail(ctx, scene_ids[k]);
+        if (sc[k]->cams.empty() || !s_devs[k]) return fail(ctx, CSGS_E_INVAL, "bad scene %d in batch", k);
         vb[k] = scene_view_batch(sc[k], opts);
         for (auto& c : sc[k]->cams) rays += (int64_t)c.W * c.H;
     }
@@ -977,7 +1134,8 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
                           int32_t* view_batch_out, int32_t* sort_blocks_out) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s || s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
+    if (s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "scene %d has no query views", scene_id);
     KOpts ko;
     csgs_status r;
     if ((r = make_kopts(ctx, opts, &ko))) return r;
@@ -1100,7 +1258,7 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
                         int64_t n_sel, const csgs_score_opts* opts, float* rgb_dev, float* T_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
     if (!rgb_dev) return fail(ctx, CSGS_E_INVAL, "rgb_dev is NULL");
     if ((idx_dev == nullptr) != (w_dev == nullptr)) return fail(ctx, CSGS_E_INVAL, "idx and w must both be given");
@@ -1221,7 +1379,7 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
                           int64_t n_sel, const csgs_score_opts* opts, float* out_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
     if (!out_dev || !idx_dev || !w_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
     if (n_sel < 0 || n_sel > s->n) return fail(ctx, CSGS_E_INVAL, "n_sel out of range");
@@ -1311,7 +1469,7 @@ csgs_status csgs_debug_project(csgs_ctx* ctx, int32_t scene_id, int32_t view, co
                                float* out_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
     if (!out_dev) return fail(ctx, CSGS_E_INVAL, "out_dev is NULL");
     KOpts ko;
@@ -1479,7 +1637,7 @@ csgs_status csgs_mlp_train(csgs_ctx* ctx, const void* X_dev, const float* t_dev,
 csgs_status csgs_view_stats(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* stats_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (!stats_dev) return fail(ctx, CSGS_E_INVAL, "stats_dev is NULL");
     if (s->cams.empty()) return fail(ctx, CSGS_E_INVAL, "no query views set");
     KOpts ko;
@@ -1498,7 +1656,7 @@ csgs_status csgs_features(csgs_ctx* ctx, int32_t scene_id, const float* stats_de
                           void* X_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (!stats_dev || !X_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
     cudaSetDevice(ctx->device);
     launch_features(scene_dev(*s), stats_dev, extra_dev, X_dev, ctx->st);
@@ -1528,7 +1686,7 @@ extern "C" {
 
 csgs_status csgs_update_scene(csgs_ctx* ctx, int32_t scene_id, const csgs_scene_desc* d) {
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (!d || d->n != s->n || d->sh_degree != s->deg) return fail(ctx, CSGS_E_INVAL, "scene shape mismatch");
     if (!d->means || !d->log_scales || !d->quats || !d->opacity_logits || !d->sh)
         return fail(ctx, CSGS_E_INVAL, "null attribute pointer");
@@ -1548,7 +1706,7 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
                                  float* g_means_dev, float* g_sh_dev, float* g_logit_dev) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
-    if (!s) return fail(ctx, CSGS_E_INVAL, "bad scene id %d", scene_id);
+    if (!s) return scene_fail(ctx, scene_id);
     if (view < 0 || view >= (int32_t)s->cams.size()) return fail(ctx, CSGS_E_INVAL, "bad view %d", view);
     if (!grad_rgb_dev || !g_means_dev || !g_sh_dev || !g_logit_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
     if ((idx_dev == nullptr) != (w_dev == nullptr)) return fail(ctx, CSGS_E_INVAL, "idx and w must both be given");

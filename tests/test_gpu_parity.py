@@ -325,6 +325,39 @@ def test_empty_query_set_reports_zero_sensitivity(ctx):
     ctx.free_scene(sid)
 
 
+def test_asynchronous_load_matches_and_validates_on_first_use(ctx, small, torch):
+    """A scene loaded asynchronously from pinned host memory scores bit for bit like the
+    synchronously loaded one (also when its buffers come from a freed scene), and a
+    scene with a non-finite attribute is rejected by the first call that uses it."""
+    sc, cams, _, _ = small
+    host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+            for a in (sc.means, sc.log_scales, sc.quats, sc.opacity_logits, sc.sh)]
+    ptrs = [h.data_ptr() for h in host]
+    ref_sid = ctx.load_scene(sc)
+    ctx.set_queries(ref_sid, cams)
+    ref, Sref = ctx.score(ref_sid)
+    ref = ref.cpu().numpy()
+    for _ in range(2):  # the second load reuses the first one's freed buffers
+        sid = ctx.load_scene_ptrs(sc.n, sc.sh_degree, ptrs, is_device=False, asynchronous=True)
+        ctx.set_queries(sid, cams)
+        s, S = ctx.score(sid)
+        np.testing.assert_array_equal(s.cpu().numpy(), ref)
+        assert S == Sref
+        ctx.free_scene(sid)
+    bad = [h.clone().pin_memory() for h in host]
+    bad[1][2, 7] = float("inf")
+    sid = ctx.load_scene_ptrs(sc.n, sc.sh_degree, [h.data_ptr() for h in bad], is_device=False, asynchronous=True)
+    with pytest.raises(csgs.CsgsError) as e:
+        ctx.set_queries(sid, cams)
+    assert e.value.status == csgs.CSGS_E_INVAL and "non-finite" in str(e.value)
+    with pytest.raises(csgs.CsgsError):
+        ctx.score(sid)  # released
+    # freeing a scene whose upload may still be running is allowed
+    sid = ctx.load_scene_ptrs(sc.n, sc.sh_degree, ptrs, is_device=False, asynchronous=True)
+    ctx.free_scene(sid)
+    ctx.free_scene(ref_sid)
+
+
 def test_invalid_arguments(ctx, small_sid):
     sc = synth.uniform_cube_scene(10, seed=0)
     sc.means[0, 3] = np.nan
