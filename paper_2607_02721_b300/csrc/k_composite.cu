@@ -79,9 +79,11 @@ struct Shared {
     uint32_t gid[kThreads];
     float wsel[kThreads];  // transfer: the coreset weight w_i of the staged splat
     uint32_t msk[kThreads];
-    uint8_t wl[kWarps][kThreads];  // per-warp compacted batch indices
-    uint32_t red[kThreads];
-    float part[kWarps][kThreads];
+    uint16_t wl[kWarps][kThreads];  // per-warp compacted batch: byte offsets 16 x slot
+    union {
+        uint32_t red[4 * kThreads];     // two-pass modes: pass-2 maxima, word 0 of each 16-byte slot
+        float part[kWarps][kThreads];  // summed modes: the warps' term sums per slot
+    };
     int last;
     double sumA[kWarps];
 };
@@ -93,7 +95,7 @@ template <int MODE, int MSK = 0>
 __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32_t i, uint32_t end, float cx,
                                       float cy) {
     const int tid = threadIdx.x;
-    if (two_pass(MODE)) sh.red[tid] = 0u;
+    if (two_pass(MODE)) sh.red[4 * tid] = 0u;
     if (summed(MODE))
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) sh.part[w][tid] = 0.f;
@@ -155,7 +157,14 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
     if (MSK == 1) a.mskbuf[i] = (uint8_t)mk;
 }
 
-// Compact the staged batch into this warp's list; returns its length.
+// Staged record at byte offset off (16 x slot) of a float4 array in shared memory: the
+// warp lists hold these offsets, so a list entry addresses its records without scaling.
+__device__ __forceinline__ float4 at16(const float4* base, uint32_t off) {
+    return *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) + off);
+}
+
+// Compact the staged batch into this warp's list (byte offsets 16 x slot); returns its
+// length.
 __device__ __forceinline__ int warp_list(Shared& sh, int cnt, int warp, int lane) {
     const uint32_t lt = (1u << lane) - 1u;
     int nw = 0;
@@ -163,7 +172,7 @@ __device__ __forceinline__ int warp_list(Shared& sh, int cnt, int warp, int lane
         const int j = c0 + lane;
         const bool bit = j < cnt && ((sh.msk[j] >> warp) & 1u);
         const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-        if (bit) sh.wl[warp][nw + __popc(bal & lt)] = (uint8_t)j;
+        if (bit) sh.wl[warp][nw + __popc(bal & lt)] = (uint16_t)(j << 4);
         nw += __popc(bal);
     }
     __syncwarp();
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     float T = 1.f, A0 = 0.f, A1 = 0.f, A2 = 0.f;
     float tr[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // transfer: A_th[3], A_w[3]
     float Tw = 1.f, gam = 0.f, minf = 1.f;
-    int last = 0;
+    int last16 = 0;  // 16 x (index past the pixel's last contributor)
     int processed = 0;  // tile-list entries staged by pass 1 (CTA-uniform)
     bool done = !inside;
     unsigned long long n_eval = 0, n_hit = 0, n_viol = 0, n_went1 = 0, n_went2 = 0;
@@ -254,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         if (MODE == kTransfer) {
             // full-scene order with T and the reduced scene's T_w side by side
             for (int k = 0; k < nw && !done; ++k) {
-                const int j = sh.wl[warp][k];
+                const int j = sh.wl[warp][k] >> 4;
                 const float4 Aj = sh.A[j];
                 const float4 Bj = sh.B[j];
                 const float p = exponent2(Aj, Bj, X, Y);
@@ -286,8 +295,9 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             }
         } else if (!summed(MODE)) {
             int kmax = 0;  // counting runs: entries this lane walked (the warp walks the maximum)
-            // one list entry at pixel (X, Y): false once the pixel has stopped
-            auto step = [&](int j, const float4& Bj, float p) -> bool {
+            const int b16 = (b + 1) << 4;
+            // one list entry (byte offset jo) at pixel (X, Y): false once the pixel has stopped
+            auto step = [&](uint32_t jo, const float4& Bj, float p) -> bool {
                 if (STATS) ++n_eval;
                 if (p < Bj.z) return true;
                 const float raw = ex2_approx(p);
@@ -296,7 +306,8 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     ++n_hit;
                     n_viol += raw >= 1.f;
                 }
-                const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
+                // T (1 - rho) rounded once, as T - T rho
+                const float Tn = __fmaf_rn(-T, r, T);
                 if (Tn < t_min) {
                     done = true;
                     return false;
@@ -304,11 +315,11 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                 const float w = __fmul_rn(r, T);
                 if (MODE == kScorePixel)
                     A0 = VAR == kL1 ? __fmaf_rn(Bj.w, w, A0)
-                                    : (VAR == kL2 ? __fmaf_rn(sh.C[j].w, __fmul_rn(w, w), A0) : __fadd_rn(A0, w));
+                                    : (VAR == kL2 ? __fmaf_rn(at16(sh.C, jo).w, __fmul_rn(w, w), A0) : __fadd_rn(A0, w));
                 else
-                    accumulate<MODE, VAR>(A0, A1, A2, sh.C[j], w);
+                    accumulate<MODE, VAR>(A0, A1, A2, at16(sh.C, jo), w);
                 T = Tn;
-                last = b + j + 1;
+                last16 = b16 + (int)jo;
                 return true;
             };
             if (!done) {
@@ -317,8 +328,8 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                 // entries are still applied in list order
                 int k = 0;
                 for (; k + 1 < nw; k += 2) {
-                    const int j0 = sh.wl[warp][k], j1 = sh.wl[warp][k + 1];
-                    const float4 Aa = sh.A[j0], Ba = sh.B[j0], Ab = sh.A[j1], Bb = sh.B[j1];
+                    const uint32_t j0 = sh.wl[warp][k], j1 = sh.wl[warp][k + 1];
+                    const float4 Aa = at16(sh.A, j0), Ba = at16(sh.B, j0), Ab = at16(sh.A, j1), Bb = at16(sh.B, j1);
                     const float pa = exponent2(Aa, Ba, X, Y), pb = exponent2(Ab, Bb, X, Y);
                     if (STATS) kmax = k + 1;
                     if (!step(j0, Ba, pa)) break;
@@ -326,8 +337,8 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     if (!step(j1, Bb, pb)) break;
                 }
                 if (!done && k < nw) {
-                    const int j = sh.wl[warp][k];
-                    const float4 Aj = sh.A[j], Bj = sh.B[j];
+                    const uint32_t j = sh.wl[warp][k];
+                    const float4 Aj = at16(sh.A, j), Bj = at16(sh.B, j);
                     if (STATS) kmax = k + 1;
                     step(j, Bj, exponent2(Aj, Bj, X, Y));
                 }
@@ -347,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     for (int u = 0; u < 16; ++u) {
                         v[u] = 0.f;
                         if (k0 + u < nw && act) {
-                            const int j = sh.wl[warp][k0 + u];
+                            const int j = sh.wl[warp][k0 + u] >> 4;
                             const float4 Aj = sh.A[j];
                             const float4 Bj = sh.B[j];
                             const float p = exponent2(Aj, Bj, X, Y);
@@ -355,7 +366,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                             if (p >= Bj.z) {
                                 const float r = fminf(rho_max, ex2_approx(p));
                                 if (STATS) ++n_hit;
-                                const float Tn = __fmul_rn(T, __fadd_rn(1.f, -r));
+                                const float Tn = __fmaf_rn(-T, r, T);
                                 if (Tn < t_min) {
                                     act = false;
                                     done = true;
@@ -372,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     const float cs = warp_colsum16(v, lane);
                     const int c = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
                                   ((lane >> 1) & 1);
-                    if ((lane & 1) == 0 && k0 + c < nw) sh.part[warp][sh.wl[warp][k0 + c]] = cs;
+                    if ((lane & 1) == 0 && k0 + c < nw) sh.part[warp][sh.wl[warp][k0 + c] >> 4] = cs;
                     if (!__any_sync(0xffffffffu, act)) break;
                 }
             }
@@ -389,6 +400,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         }
     }
 
+    int last = last16 >> 4;
     if (MODE == kRender) {
         if (inside) {
             const size_t pix = (size_t)py * cam.W + px;
@@ -476,33 +488,37 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             __syncthreads();
             const int cnt = min(kThreads, n2 - b);
             const int lim = max(0, min(cnt, last - b));
+            const uint32_t lim16 = (uint32_t)lim << 4;
             // the warp's list holds only entries below its lanes' largest contributor bound
             const int jw = (int)__reduce_max_sync(0xffffffffu, (unsigned)lim);
             const int nw = warp_list(sh, jw, warp, lane);
             if (STATS && lane == 0) n_went2 += nw;
 #pragma unroll 4
             for (int k = 0; k < nw; ++k) {
-                const int j = sh.wl[warp][k];
+                const uint32_t jo = sh.wl[warp][k];
                 // branch-free: every lane evaluates the entry and keeps the result only where
                 // it is one of its pass-1 contributors (the warp takes this path anyway as
                 // soon as one lane contributes)
-                const float4 Aj = sh.A[j];
-                const float4 Bj = sh.B[j];
+                const float4 Aj = at16(sh.A, jo);
+                const float4 Bj = at16(sh.B, jo);
                 const float p = exponent2(Aj, Bj, X, Y);
-                const bool hit = j < lim && p >= Bj.z;
+                const bool hit = jo < lim16 && p >= Bj.z;
                 if (STATS) {
-                    n_eval2 += j < lim;
+                    n_eval2 += jo < lim16;
                     n_hit2 += hit;
                 }
-                const float r = fminf(rho_max, ex2_approx(p));
+                // a pair outside the pixel's contributor set gets rho = 0: its term is +0
+                // (bits 0) and T - T 0 = T exactly
+                const float r1 = fminf(rho_max, ex2_approx(p));
+                const float r = hit ? r1 : 0.f;
                 const float w = __fmul_rn(r, T);
                 float imp;
                 if (kScaled) {
                     imp = VAR == kL1 ? __fmul_rn(Bj.w, w) : w;
                 } else if (MODE == kScorePixel) {
-                    imp = __fmul_rn(pixel_term<VAR>(w, Bj, sh.C[j]), inv0);
+                    imp = __fmul_rn(pixel_term<VAR>(w, Bj, at16(sh.C, jo)), inv0);
                 } else {
-                    const float4 Cj = sh.C[j];
+                    const float4 Cj = at16(sh.C, jo);
                     float t0, t1, t2;
                     if (VAR == kL1) {
                         t0 = __fmul_rn(Cj.x, w);
@@ -520,15 +536,14 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
                     }
                     imp = fmaxf(__fmul_rn(t0, inv0), fmaxf(__fmul_rn(t1, inv1), __fmul_rn(t2, inv2)));
                 }
-                const uint32_t bits = hit ? __float_as_uint(imp) : 0u;
-                // pass 2 only scales imp by T (no threshold reads it): one FMA, T - T r
-                T = hit ? __fmaf_rn(-T, r, T) : T;
+                const uint32_t bits = __float_as_uint(imp);
+                T = __fmaf_rn(-T, r, T);
                 const uint32_t mx = __reduce_max_sync(0xffffffffu, bits);
-                if (lane == 0 && mx) atomicMax(&sh.red[j], mx);
+                if (lane == 0) atomicMax(reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sh.red) + jo), mx);
             }
             __syncthreads();
             if (tid < cnt) {
-                const uint32_t v = sh.red[tid];
+                const uint32_t v = sh.red[4 * tid];
                 if (v) atomicMax(a.s_bits + sh.gid[tid], v);
             }
         }
@@ -620,7 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_composite_bwd(const CompositeArgs 
         const int nw = warp_list(sh, cnt, warp, lane);
         const int lim = max(0, min(cnt, last - b));
         for (int k = nw - 1; k >= 0; --k) {
-            const int j = sh.wl[warp][k];
+            const int j = sh.wl[warp][k] >> 4;
             float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             bool any = false;
             if (j < lim) {
