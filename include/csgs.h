@@ -386,7 +386,10 @@ csgs_status csgs_debug_tc_gemm_wait(csgs_ctx* ctx, const void* A_dev, const void
 /* Diagnostic: the surrogate network's activation as its kernels evaluate it:
  * out_dev[2i] = GELU(z_i) = z_i Phi(z_i), out_dev[2i+1] = GELU'(z_i) (erf by Abramowitz &
  * Stegun 7.1.26, |error| <= 1.5e-7, with the hardware reciprocal and exponential).
- * z_dev: device float[n]; out_dev: device float[2n].  Asynchronous. */
+ * The epilogues evaluate GELU on pairs with packed FP32 instructions; out_dev[2i] is that
+ * packed result, checked bit for bit against the one-value evaluation (NaN if the two
+ * differ, for z_i or -z_i).  z_dev: device float[n]; out_dev: device float[2n].
+ * Asynchronous. */
 csgs_status csgs_debug_gelu(csgs_ctx* ctx, const float* z_dev, int64_t n, float* out_dev);
 
 /* Total number of kernels this library has launched in the process (all contexts);

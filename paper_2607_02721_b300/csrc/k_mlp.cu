@@ -129,6 +129,58 @@ __device__ __forceinline__ float erf_as(float x) {
 }
 // GELU(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)); GELU'(z) = Phi(z) + z phi(z)
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erf_as(z * 0.70710678118654752f)); }
+
+// Two FP32 values in one 64-bit register for the packed instructions (fma / mul / add
+// .rn.f32x2): each half is rounded exactly as the scalar instruction would round it.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2c(float a) { return f2(a, a); }
+__device__ __forceinline__ void f2split(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// gelu() of two values with the packed instructions, bit for bit the scalar result: the
+// same operations in the same order, except that the polynomial is carried negated (all
+// its coefficients negated: negation is exact, so -poly comes out exactly) and
+// (-|x|) |x| log2 e is formed as (x x)(-log2 e) (the same product).
+__device__ __forceinline__ f32x2 gelu2(f32x2 z) {
+    const f32x2 x = mul2(z, f2c(0.70710678118654752f));
+    float x0, x1;
+    f2split(x, x0, x1);
+    float d0, d1;
+    f2split(fma2(f2c(0.3275911f), f2(fabsf(x0), fabsf(x1)), f2c(1.f)), d0, d1);
+    const f32x2 t = f2(rcp_fast(d0), rcp_fast(d1));
+    f32x2 np = fma2(t, f2c(-1.061405429f), f2c(1.453152027f));
+    np = fma2(t, np, f2c(-1.421413741f));
+    np = fma2(t, np, f2c(0.284496736f));
+    np = fma2(t, np, f2c(-0.254829592f));
+    np = mul2(np, t);
+    float a0, a1;
+    f2split(mul2(mul2(x, x), f2c(-1.4426950408889634f)), a0, a1);
+    float r0, r1;
+    f2split(fma2(np, f2(ex2_fast(a0), ex2_fast(a1)), f2c(1.f)), r0, r1);
+    const f32x2 onep = add2(f2c(1.f), f2(copysignf(r0, x0), copysignf(r1, x1)));
+    return mul2(mul2(f2c(0.5f), z), onep);
+}
 __device__ __forceinline__ float gelu_d(float z) {
     return fmaf(0.5f, erf_as(z * 0.70710678118654752f), 0.5f) +
            z * ex2_fast(-0.5f * 1.4426950408889634f * z * z) * 0.39894228040143268f;
@@ -269,8 +321,16 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
             for (int c = qt * 32; c < qt * 32 + 32; c += 16) {
                 float v[16];
                 tc::tmem_ld16(tl + (uint32_t)(c_base + c), v);
+                const float4* b4 = reinterpret_cast<const float4*>(p.b1 + c_base + c);
+                f32x2 z[8];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] += p.b1[c_base + c + i];
+                for (int i = 0; i < 4; ++i) {
+                    const float4 b = __ldg(b4 + i);
+                    z[2 * i] = add2(f2(v[4 * i], v[4 * i + 1]), f2(b.x, b.y));
+                    z[2 * i + 1] = add2(f2(v[4 * i + 2], v[4 * i + 3]), f2(b.z, b.w));
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) f2split(z[i], v[2 * i], v[2 * i + 1]);
                 if (TRAIN && valid) {
                     float4* zo = reinterpret_cast<float4*>(z1o + (size_t)(r0 + row) * kH + c_base + c);
 #pragma unroll
@@ -278,7 +338,11 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
                 }
                 uint32_t pk[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(gelu(v[2 * i]), gelu(v[2 * i + 1]));
+                for (int i = 0; i < 8; ++i) {
+                    float g0, g1;
+                    f2split(gelu2(z[i]), g0, g1);
+                    pk[i] = pack_bf16(g0, g1);
+                }
                 *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c, kHc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c + 8, kHc)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 if (TRAIN && valid) {
@@ -310,8 +374,19 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
         for (int c0 = qt * 64; c0 < qt * 64 + 64; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
+            const float4* b4 = reinterpret_cast<const float4*>(p.b2 + c0);
+            const float4* w4 = reinterpret_cast<const float4*>(p.w3 + c0);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) part = fmaf(p.w3[c0 + i], gelu(v[i] + p.b2[c0 + i]), part);
+            for (int i = 0; i < 4; ++i) {
+                const float4 b = __ldg(b4 + i), w = __ldg(w4 + i);
+                float g0, g1, g2, g3;
+                f2split(gelu2(add2(f2(v[4 * i], v[4 * i + 1]), f2(b.x, b.y))), g0, g1);
+                f2split(gelu2(add2(f2(v[4 * i + 2], v[4 * i + 3]), f2(b.z, b.w))), g2, g3);
+                part = fmaf(w.x, g0, part);
+                part = fmaf(w.y, g1, part);
+                part = fmaf(w.z, g2, part);
+                part = fmaf(w.w, g3, part);
+            }
         }
         sdot[qt][row] = part;
         __syncthreads();
@@ -660,7 +735,13 @@ __global__ void k_sum_partials(const float* __restrict__ part, int splits, int n
 __global__ void k_debug_gelu(const float* __restrict__ z, int n, float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[2 * i] = gelu(z[i]);
+    // the packed evaluation the network's epilogues use, in both lanes (lane 1 holds -z);
+    // it must equal the scalar gelu() bit for bit, else the value is reported as NaN
+    float g, gm;
+    f2split(gelu2(f2(z[i], -z[i])), g, gm);
+    const bool same = __float_as_uint(g) == __float_as_uint(gelu(z[i])) &&
+                      __float_as_uint(gm) == __float_as_uint(gelu(-z[i]));
+    out[2 * i] = same ? g : __int_as_float(0x7fc00000);
     out[2 * i + 1] = gelu_d(z[i]);
 }
 }  // namespace
