@@ -35,6 +35,7 @@ struct DevBuf {
 // slot's own high-priority stream, overlaps the compositing of the current one.
 struct BinSlot {
     DevBuf dkeys_b, dvals_a, dvals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, ranges, hist, scan_tmp;
+    DevBuf torder;  // scoring: the view's tiles, longest lists first
     cudaStream_t st = nullptr;
     cudaEvent_t ready = nullptr;  // binning done
     cudaEvent_t freed = nullptr;  // the compositing that read the slot is done
@@ -339,6 +340,7 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
         if ((r = ensure(ctx, b.dvals_a, sizeof(uint32_t) * nv))) return r;
         if ((r = ensure(ctx, b.dvals_b, sizeof(uint32_t) * nv))) return r;
         if ((r = ensure(ctx, b.ranges, sizeof(uint2) * (size_t)ctx->max_tiles))) return r;
+        if ((r = ensure(ctx, b.torder, sizeof(uint32_t) * (size_t)ctx->max_tiles))) return r;
         if ((r = ensure(ctx, b.hist, sizeof(uint32_t) * sort_hist_stride(kSortMaxBlocks)))) return r;
         if ((r = ensure(ctx, b.scan_tmp, sizeof(uint32_t) * ((size_t)(n + 255) / 256 + 64)))) return r;
         if ((r = ensure(ctx, b.ikeys_a, ib))) return r;
@@ -876,6 +878,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             CUDA_TRY(ctx, cudaStreamWaitEvent(cs, slot.ready, 0));
             CompositeArgs a{};
             a.ranges = P<uint2>(slot.ranges);
+            a.order = P<uint32_t>(slot.torder);
             a.inst_gid = iv;
             a.splats = P<Splat>(ctx->splats[set]) + (size_t)k * n;
             a.n_gauss = (int)n;
@@ -889,6 +892,9 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             a.stats = stats & 1;
             if (ko.resolution == CSGS_RES_IMAGE)
                 CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
+            // the view's tiles, longest lists first (compositing stream: the binning chain,
+            // which the slot's next view waits for, stays as short as it was)
+            tile_order(P<uint2>(slot.ranges), cam.tiles_x * cam.tiles_y, P<uint32_t>(slot.torder), cs);
             size_t e2 = pt.begin(cs);
             launch_composite_score(a, cs);
             if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);

@@ -168,6 +168,9 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, co
                     unsigned long long* n_inst, cudaStream_t st);
 // ranges[v][tile] = [start, end) of each (view, tile) key in the sorted instance keys
 // (rows of max_tiles ranges per view).
+// The tiles of one view ordered by descending list length, in power-of-two classes
+// (order within a class unspecified): order[0..T) is a permutation of the tile ids.
+void tile_order(const uint2* ranges, int T, uint32_t* order, cudaStream_t st);
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
                  const CamDev* cams, int tbits, int max_tiles, cudaStream_t st);
 void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
@@ -175,6 +178,7 @@ void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 // ---- compositing (k_composite.cu)
 struct CompositeArgs {
     const uint2* ranges;
+    const uint32_t* order;  // tile of CTA b = order[b] (longest lists first), or null: tile b
     const uint32_t* inst_gid;
     const Splat* splats;
     int n_gauss;

@@ -230,7 +230,7 @@ template <int MODE, int VAR, bool STATS>
 __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     __shared__ Shared sh;
     const CamDev& cam = a.cam;
-    const int tile = blockIdx.x;
+    const int tile = a.order ? (int)__ldg(a.order + blockIdx.x) : (int)blockIdx.x;
     const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 4 + (lane >> 3);

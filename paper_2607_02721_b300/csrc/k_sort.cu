@@ -448,6 +448,44 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long 
     if (t > 0) rv[t - 1].y = lo;
 }
 
+// Tiles by descending list length (classes floor(log2 n) + 1, the longest class first), so
+// that the compositing launch starts its longest tiles in its first wave instead of its
+// last.  One CTA: class counts, class offsets, then each tile at its class's next slot;
+// the lanes of a warp with the same class share one shared-memory atomic.
+__global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int T,
+                                                     uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[34];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 34) cnt[tid] = 0u;
+    __syncthreads();
+    for (int t0 = 0; t0 < T; t0 += 1024) {
+        const int t = t0 + tid;
+        const int c = t < T ? 32 - __clz(ranges[t].y - ranges[t].x) : 33;
+        const uint32_t peers = __match_any_sync(0xffffffffu, c);
+        if (lane == __ffs(peers) - 1) atomicAdd(&cnt[c], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t s = 0;
+        for (int c = 32; c >= 0; --c) {
+            const uint32_t k = cnt[c];
+            cnt[c] = s;
+            s += k;
+        }
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < T; t0 += 1024) {
+        const int t = t0 + tid;
+        const int c = t < T ? 32 - __clz(ranges[t].y - ranges[t].x) : 33;
+        const uint32_t peers = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader && c < 33) base = atomicAdd(&cnt[c], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (c < 33) order[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)t;
+    }
+}
+
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
 
 // One pass with RB-bit digits (NBITS of them significant).
@@ -521,6 +559,11 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, co
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
                  const CamDev* cams, int tbits, int max_tiles, cudaStream_t st) {
     k_ranges<<<dim3((max_tiles + 1 + 255) / 256, nv), 256, 0, st>>>(keys, d_n, n_max, ranges, cams, tbits, max_tiles);
+    count_launches(1);
+}
+
+void tile_order(const uint2* ranges, int T, uint32_t* order, cudaStream_t st) {
+    k_tile_order<<<1, 1024, 0, st>>>(ranges, T, order);
     count_launches(1);
 }
 
