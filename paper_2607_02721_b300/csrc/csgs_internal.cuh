@@ -166,11 +166,11 @@ int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint3
 void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits,
                     uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     unsigned long long* n_inst, cudaStream_t st);
-// ranges[v][tile] = [start, end) of each (view, tile) key in the sorted instance keys
-// (rows of max_tiles ranges per view).
 // The tiles of one view ordered by descending list length, in power-of-two classes
 // (order within a class unspecified): order[0..T) is a permutation of the tile ids.
 void tile_order(const uint2* ranges, int T, uint32_t* order, cudaStream_t st);
+// ranges[v][tile] = [start, end) of each (view, tile) key in the sorted instance keys
+// (rows of max_tiles ranges per view).
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
                  const CamDev* cams, int tbits, int max_tiles, cudaStream_t st);
 void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
