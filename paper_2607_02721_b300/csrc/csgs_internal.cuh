@@ -106,7 +106,7 @@ __device__ __forceinline__ float warp_colsum16(const float (&v)[16], int lane) {
 
 // Binning slots: scoring bins view k in slot k % kBinSlots on the slot's own stream, so
 // the binning of the next views overlaps the compositing of the current one.
-constexpr int kBinSlots = 3;
+constexpr int kBinSlots = 4;
 constexpr int kCompStreams = 2;  // compositing streams of a scoring submission
 
 struct DevCounters {
