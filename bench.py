@@ -86,7 +86,7 @@ def describe(name, scene, cams):
             "resolution": "per-pixel (max over pixel-rays)", "objective": "R+G+B",
             "coreset_m": int(round(0.1 * scene.n)), "scorer": "exact",
             "l2": "inputs larger than L2 (scene %.0f MB)" % (scene_bytes(scene) / 1e6),
-            "parallelism": "replicas"}
+            "parallelism": "single GPU"}
 
 
 def scene_bytes(scene) -> int:
@@ -233,6 +233,9 @@ def run_reference(args):
 
     scene, cams = workload(args.workload)
     cfg = describe(args.workload, scene, cams)
+    if args.gpus > 1:  # the configuration of the arm it is compared with (the oracle runs on rank 0 only)
+        cfg["parallelism"] = f"views sharded over {args.gpus} ranks, all-reduce of s per step"
+        cfg["views_per_rank"] = len(range(0, len(cams), args.gpus))
     per_step = max(2.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
     sa = oracle.SceneArrays(scene)
     npx = _calibrate(sa, cams, per_step)
@@ -248,7 +251,7 @@ def run_reference(args):
     sample = ("the whole query set" if pix is None else f"{rays_step} pixel-rays centred in view 0")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "rays/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg,
             "cpu_baseline": {"value": v, "unit": "rays/s", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"each step: {sample} of the {args.workload} workload"},
