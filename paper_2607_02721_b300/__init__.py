@@ -165,16 +165,15 @@ def default_opts(**kw) -> ScoreOpts:
 
 
 def cameras(records) -> "ctypes.Array":
-    """csgs_camera array from float records [V, 20] (see synth.CAMERA_FIELDS)."""
+    """csgs_camera array from float records [V, 20] (see synth.CAMERA_FIELDS): the record's
+    20 values are the struct's 20 four-byte fields in order, width and height as int32."""
     rec = np.asarray(records, dtype=np.float32).reshape(-1, 20)
+    buf = np.ascontiguousarray(rec)
+    buf = buf.copy()
+    buf.view(np.int32)[:, 16:18] = rec[:, 16:18].astype(np.int32)
+    buf[:, 19] = 0.0
     arr = (Camera * rec.shape[0])()
-    for i, r in enumerate(rec):
-        c = arr[i]
-        c.R = (ctypes.c_float * 9)(*r[0:9])
-        c.t = (ctypes.c_float * 3)(*r[9:12])
-        c.fx, c.fy, c.cx, c.cy = (float(x) for x in r[12:16])
-        c.width, c.height = int(r[16]), int(r[17])
-        c.near_z = float(r[18])
+    ctypes.memmove(arr, buf.ctypes.data, buf.nbytes)
     return arr
 
 

@@ -52,6 +52,7 @@ struct SceneRec {
     float* sh = nullptr;
     std::vector<CamDev> cams;
     CamDev* d_cams = nullptr;
+    int cams_cap = 0;  // views d_cams holds
     float uploaded_clamp = -1.f;  // clamp_fov of the cameras on the device (-1: none)
     int tuned_vb = 0;             // view batch chosen by csgs_autotune (0: automatic)
     // asynchronous load: the upload (copies + finiteness check on the context's upload
@@ -108,11 +109,14 @@ struct csgs_ctx {
     // attribute buffers of freed scenes, kept for later loads of the same size (a scene
     // loaded and freed every step then allocates and frees nothing); released at destroy
     std::vector<std::pair<size_t, float*>> scene_pool;
+    // camera buffers of freed scenes (views held, pointer), reused the same way
+    std::vector<std::pair<int, CamDev*>> cams_pool;
     cudaStream_t ust = nullptr;  // upload stream of csgs_load_scene_async
     std::string scene_err;       // why the last settled asynchronous load was rejected
     // check words of pending asynchronous loads, allocated once (a cudaFree per load would
     // synchronise the device and wait for the next scene's upload)
     DevCounters* d_chk_slots = nullptr;
+    uint32_t* h_chk_slots = nullptr;  // pinned: each slot's check word, copied by the upload stream
     uint32_t chk_used = 0;       // bit k: slot k belongs to a pending load
 };
 
@@ -255,7 +259,13 @@ void drop_scene(csgs_ctx* ctx, SceneRec* s) {
     scene_bytes(s->n, s->deg, bytes);
     float* bufs[5] = {s->means, s->log_scales, s->quats, s->opac, s->sh};
     for (int k = 0; k < 5; ++k) pool_put(ctx, bytes[k], bufs[k]);
-    if (s->d_cams) cudaFree(s->d_cams);
+    if (s->d_cams) {
+        if (ctx->cams_pool.size() >= (size_t)kScenePoolMax) {  // keep the pool small: drop the oldest
+            cudaFree(ctx->cams_pool.front().second);
+            ctx->cams_pool.erase(ctx->cams_pool.begin());
+        }
+        ctx->cams_pool.emplace_back(s->cams_cap, s->d_cams);
+    }
     if (s->uploaded) cudaEventDestroy(s->uploaded);
     if (s->chk_slot >= 0) ctx->chk_used &= ~(1u << s->chk_slot);
     *s = SceneRec();
@@ -266,9 +276,13 @@ void drop_scene(csgs_ctx* ctx, SceneRec* s) {
 bool settle_scene(csgs_ctx* ctx, SceneRec* s) {
     if (!s->pending) return true;
     s->pending = false;
+    // the upload stream copied the check word to pinned memory before recording the event,
+    // so waiting for this scene's event is enough (no copy here that could queue behind the
+    // next scene's upload)
     uint32_t err = ~0u;
-    if (cudaEventSynchronize(s->uploaded) != cudaSuccess ||
-        cudaMemcpy(&err, &s->d_chk->err, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    if (cudaEventSynchronize(s->uploaded) == cudaSuccess)
+        err = *static_cast<volatile uint32_t*>(ctx->h_chk_slots + s->chk_slot);
+    else {
         cudaGetLastError();
         ctx->scene_err = "the scene's upload failed";
         drop_scene(ctx, s);
@@ -521,9 +535,12 @@ void csgs_destroy(csgs_ctx* ctx) {
         cudaFree(s.sh);
         cudaFree(s.d_cams);
     }
+    for (auto& e : ctx->cams_pool) cudaFree(e.second);
+    ctx->cams_pool.clear();
     for (auto& e : ctx->scene_pool) cudaFree(e.second);
     ctx->scene_pool.clear();
     if (ctx->d_chk_slots) cudaFree(ctx->d_chk_slots);
+    if (ctx->h_chk_slots) cudaFreeHost(ctx->h_chk_slots);
     for (BinSlot& b : ctx->slot) {
         DevBuf* sb[] = {&b.dkeys_b, &b.dvals_a, &b.dvals_b, &b.ikeys_a, &b.ikeys_b,
                         &b.ivals_a, &b.ivals_b, &b.ranges,  &b.hist,    &b.scan_tmp};
@@ -638,9 +655,12 @@ csgs_status csgs_load_scene_async(csgs_ctx* ctx, const csgs_scene_desc* d, int32
     cudaSetDevice(ctx->device);
     SceneRec s;
     if (!ctx->d_chk_slots) {
-        if (cudaMalloc(&ctx->d_chk_slots, sizeof(DevCounters) * kMaxPendingLoads) != cudaSuccess) {
+        if (cudaMalloc(&ctx->d_chk_slots, sizeof(DevCounters) * kMaxPendingLoads) != cudaSuccess ||
+            cudaHostAlloc(&ctx->h_chk_slots, sizeof(uint32_t) * kMaxPendingLoads, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
+            if (ctx->d_chk_slots) cudaFree(ctx->d_chk_slots);
             ctx->d_chk_slots = nullptr;
+            ctx->h_chk_slots = nullptr;
             return fail(ctx, CSGS_E_NOMEM, "upload bookkeeping allocation failed");
         }
     }
@@ -664,6 +684,8 @@ csgs_status csgs_load_scene_async(csgs_ctx* ctx, const csgs_scene_desc* d, int32
         return r;
     }
     ctx->chk_used |= 1u << s.chk_slot;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_chk_slots + s.chk_slot, &s.d_chk->err, sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, ctx->ust));
     CUDA_TRY(ctx, cudaEventRecord(s.uploaded, ctx->ust));
     s.pending = true;
     s.alive = true;
@@ -709,12 +731,28 @@ csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera*
         d.tiles_x = (c.width + kTile - 1) / kTile;
         d.tiles_y = (c.height + kTile - 1) / kTile;
     }
-    if (s->d_cams) {
-        cudaStreamSynchronize(ctx->st);
-        cudaFree(s->d_cams);
+    // The device copy is written by the next call's upload, in order on the context's stream
+    // after every earlier call's work.  A buffer that is too small goes back to the pool; a
+    // pooled buffer of a freed scene is taken before allocating (a scene loaded and freed every
+    // step then allocates nothing, and no call waits for an upload in flight).
+    if (s->d_cams && s->cams_cap < n_views) {
+        ctx->cams_pool.emplace_back(s->cams_cap, s->d_cams);
         s->d_cams = nullptr;
+        s->cams_cap = 0;
     }
-    CUDA_TRY(ctx, cudaMalloc(&s->d_cams, sizeof(CamDev) * n_views));
+    if (!s->d_cams) {
+        for (size_t k = 0; k < ctx->cams_pool.size(); ++k)
+            if (ctx->cams_pool[k].first >= n_views) {
+                s->cams_cap = ctx->cams_pool[k].first;
+                s->d_cams = ctx->cams_pool[k].second;
+                ctx->cams_pool.erase(ctx->cams_pool.begin() + (long)k);
+                break;
+            }
+    }
+    if (!s->d_cams) {
+        CUDA_TRY(ctx, cudaMalloc(&s->d_cams, sizeof(CamDev) * n_views));
+        s->cams_cap = n_views;
+    }
     s->cams = v;
     s->uploaded_clamp = -1.f;
     return CSGS_OK;
