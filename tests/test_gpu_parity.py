@@ -358,6 +358,38 @@ def test_asynchronous_load_matches_and_validates_on_first_use(ctx, small, torch)
     ctx.free_scene(ref_sid)
 
 
+def test_query_sets_of_changing_size_reuse_camera_buffers(ctx, small, torch):
+    """Camera buffers are kept per scene and pooled across freed scenes: a scene whose query
+    set shrinks, grows past its buffer, and a new scene that takes a freed scene's buffer all
+    score bit for bit like a fresh context given the same views."""
+    sc, cams, _, _ = small
+    cams = np.asarray(cams, dtype=np.float32)
+    sets = [cams[:3], cams[:8], cams[2:7], cams[:3]]
+    fresh = csgs.Context(0)
+    ref = []
+    for q in sets:
+        sid = fresh.load_scene(sc)
+        fresh.set_queries(sid, q)
+        s, S = fresh.score(sid)
+        ref.append((s.cpu().numpy(), S))
+        fresh.free_scene(sid)
+    fresh.close()
+    sid = ctx.load_scene(sc)
+    for q, (r, Sr) in zip(sets, ref):  # one scene: 3 views, past its buffer to 8, then fewer
+        ctx.set_queries(sid, q)
+        s, S = ctx.score(sid)
+        np.testing.assert_array_equal(s.cpu().numpy(), r)
+        assert S == Sr
+    ctx.free_scene(sid)
+    for q, (r, Sr) in zip(reversed(sets), reversed(ref)):  # new scenes take pooled buffers
+        sid = ctx.load_scene(sc)
+        ctx.set_queries(sid, q)
+        s, S = ctx.score(sid)
+        np.testing.assert_array_equal(s.cpu().numpy(), r)
+        assert S == Sr
+        ctx.free_scene(sid)
+
+
 def test_invalid_arguments(ctx, small_sid):
     sc = synth.uniform_cube_scene(10, seed=0)
     sc.means[0, 3] = np.nan
