@@ -201,6 +201,22 @@ struct MlpDev {
     const float* b3;
 };
 
+// stage_rows with asynchronous 16-byte copies (cp.async, no register round trip; rows
+// beyond nrows are zero-filled without a read).  Completed by stage_rows_wait().
+__device__ __forceinline__ void stage_rows_async(unsigned char* dst, const __nv_bfloat16* src, int r0, int nrows,
+                                                 int R, int K, int ld) {
+    const int chunks = R * (K / 8);
+    for (int idx = threadIdx.x; idx < chunks; idx += blockDim.x) {
+        const int r = idx / (K / 8), k8 = idx % (K / 8);
+        const bool in = r0 + r < nrows;
+        const __nv_bfloat16* g = src + (size_t)(in ? r0 + r : r0) * ld + k8 * 8;
+        const uint32_t s = tc::smem_u32(dst + tc::kmajor_off(r, k8 * 8, K));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(g), "r"(in ? 16 : 0) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_rows_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Stage an R x K row-major BF16 matrix (rows r0.., zero beyond nrows) into the K-major
 // core-matrix layout, 16 bytes per thread step.
 __device__ __forceinline__ void stage_rows(unsigned char* dst, const __nv_bfloat16* src, int r0, int nrows, int R,
@@ -271,6 +287,7 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
     __shared__ uint32_t slot;
     __shared__ float sdot[4][kRows];
     __shared__ float sgw3[kH];
+    __shared__ __align__(16) float sb1[kH], sb2[kH], sw3[kH];  // biases and output weights, read every tile
     __shared__ float sred[2][16];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, qt = warp >> 2, row = q * 32 + lane;
@@ -279,6 +296,11 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (TRAIN && tid < kH) sgw3[tid] = 0.f;
+    if (tid < kH) {
+        sb1[tid] = p.b1[tid];
+        sb2[tid] = p.b2[tid];
+        sw3[tid] = p.w3[tid];
+    }
     if (warp == 0) tc::tmem_alloc(&slot, 512);
     stage_rows(sW1, p.W1b, 0, kH, kH, kIn, kIn);
     stage_rows(sW2, p.W2b, 0, kH, kH, kH, kH);
@@ -305,6 +327,9 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
             break;
         }
         tc::fence_after_sync();
+        // layer 1 has read the X tile: fetch the next one under the epilogues
+        const int next = tile + gridDim.x;
+        if (next < ntiles) stage_rows_async(sX, X, next * kRows, B, kRows, kIn, kIn);
         for (int h = 0; h < 2; ++h) {
             const int c_base = h * kHc;
             if (h == 1) {
@@ -321,11 +346,11 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
             for (int c = qt * 32; c < qt * 32 + 32; c += 16) {
                 float v[16];
                 tc::tmem_ld16(tl + (uint32_t)(c_base + c), v);
-                const float4* b4 = reinterpret_cast<const float4*>(p.b1 + c_base + c);
+                const float4* b4 = reinterpret_cast<const float4*>(sb1 + c_base + c);
                 f32x2 z[8];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float4 b = __ldg(b4 + i);
+                    const float4 b = b4[i];
                     z[2 * i] = add2(f2(v[4 * i], v[4 * i + 1]), f2(b.x, b.y));
                     z[2 * i + 1] = add2(f2(v[4 * i + 2], v[4 * i + 3]), f2(b.z, b.w));
                 }
@@ -358,8 +383,7 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
             if (tid == 0) mma_tile_k(taddr + 256u, sH, kHc, sW2, kH, c_base, kHc, kIdesc1, h == 1, &bar);
         }
         if (failed) break;
-        const int next = tile + gridDim.x;
-        if (next < ntiles) stage_rows(sX, X, next * kRows, B, kRows, kIn, kIn);
+        stage_rows_wait();
         tc::fence_smem_to_async();
         ok = tc::mbar_wait(&bar, phase, kWaitBudget);
         phase ^= 1u;
@@ -374,11 +398,11 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
         for (int c0 = qt * 64; c0 < qt * 64 + 64; c0 += 16) {
             float v[16];
             tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
-            const float4* b4 = reinterpret_cast<const float4*>(p.b2 + c0);
-            const float4* w4 = reinterpret_cast<const float4*>(p.w3 + c0);
+            const float4* b4 = reinterpret_cast<const float4*>(sb2 + c0);
+            const float4* w4 = reinterpret_cast<const float4*>(sw3 + c0);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float4 b = __ldg(b4 + i), w = __ldg(w4 + i);
+                const float4 b = b4[i], w = w4[i];
                 float g0, g1, g2, g3;
                 f2split(gelu2(add2(f2(v[4 * i], v[4 * i + 1]), f2(b.x, b.y))), g0, g1);
                 f2split(gelu2(add2(f2(v[4 * i + 2], v[4 * i + 3]), f2(b.z, b.w))), g2, g3);
@@ -405,9 +429,9 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
                 tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const float z = v[i] + p.b2[c0 + i];
+                    const float z = v[i] + sb2[c0 + i];
                     g[i] = dy * gelu(z);  // this row's d loss / d w3
-                    v[i] = dy * p.w3[c0 + i] * gelu_d(z);
+                    v[i] = dy * sw3[c0 + i] * gelu_d(z);
                 }
                 const float cs = warp_colsum16(g, lane);
                 if ((lane & 1) == 0) {
@@ -427,6 +451,7 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
         tc::fence_before_sync();
         __syncthreads();
     }
+    stage_rows_wait();  // no copy into shared memory outstanding at exit
     if (failed && tid == 0) atomicOr(err, 1);
     if (failed) tc::mbar_wait(&bar, phase, kWaitBudget);  // drain before freeing TMEM
     if (TRAIN) {
