@@ -416,7 +416,9 @@ def run_ours(args):
 
         e2e_run(2, 0)  # warm-up: two scenes' buffers for the context to reuse
         torch.cuda.synchronize()
-        ne = max(1, min(args.steps, 5))
+        # at least 10 steps, so that the first step's exposed upload (the pipeline fill) weighs
+        # as in a longer run; at most 20 to bound the run time
+        ne = min(max(args.steps, 10), 20)
         t0 = time.perf_counter()
         d2h = e2e_run(ne, 2000)
         torch.cuda.synchronize()
