@@ -494,7 +494,7 @@ def run_ours(args):
         # the metric's second half: surrogate-assisted vs exact scoring of this workload
         from paper_2607_02721_b300 import surrogate
 
-        scfg = surrogate.SurrogateConfig()
+        scfg = surrogate.SurrogateConfig(residual=not args.surrogate_direct)
         rec, _, _ = surrogate_record(ctx, sid, cams, m, scfg, csgs.default_opts(resolution=res_id), 10)
         line["surrogate"] = rec
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -534,7 +534,7 @@ def surrogate_record(ctx, sid, cams, m, cfg, sopts, psnr_stride: int):
     res = {"exact_ms": exact_ms, "surrogate_ms": tim["total_ms"], "speedup": exact_ms / tim["total_ms"],
            "phases_ms": tim, "train_views": cfg.train_views, "train_steps": cfg.steps,
            "lowres_factor": cfg.lowres_factor, "cheap_stride": cfg.cheap_stride, "train_lr": cfg.lr,
-           "fill_only": cfg.fill_only, "aug_views": list(cfg.aug_views),
+           "fill_only": cfg.fill_only, "aug_views": list(cfg.aug_views), "residual": cfg.residual,
            "psnr_views": len(views), "prune_ratio": 0.9}
     # the same inputs without the network: the cheap score scaled to the exact scores by
     # the median ratio on the scored views, maximum with the scored subset's exact scores
@@ -584,7 +584,7 @@ def run_surrogate(args):
     sopts = csgs.default_opts(resolution=res_id)
     scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps, fill_only=args.fill_only,
                                      aug_views=tuple(int(x) for x in args.aug_views.split(",") if x),
-                                     lowres_factor=args.lowres_factor)
+                                     lowres_factor=args.lowres_factor, residual=not args.surrogate_direct)
     rec, s_exact, s_hat = surrogate_record(ctx, sid, cams, m, scfg, sopts, args.psnr_stride)
     res = {"mode": "surrogate", "config": cfg, "resolution": args.resolution}
     res.update(rec)
@@ -907,6 +907,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=100)
     ap.add_argument("--psnr-stride", type=int, default=5)
     ap.add_argument("--fill-only", action="store_true")
+    ap.add_argument("--surrogate-direct", action="store_true",
+                    help="surrogate network predicts log s itself, not its correction over the scaled cheap score")
     ap.add_argument("--resolution", default="pixel", choices=["pixel", "scene"])
     ap.add_argument("--aug-views", default="")
     ap.add_argument("--lowres-factor", type=int, default=4, help="surrogate: cheap score at 1/f resolution (0: off)")

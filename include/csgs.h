@@ -293,6 +293,22 @@ csgs_status csgs_log_target(csgs_ctx* ctx, const float* s_dev, int64_t n, float 
  * below the exact score); fill_only = 1: s_exact where it is > 0, else max(exp(y) - eps, 0). */
 csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const float* s_exact_dev, int64_t n, float eps,
                                    int32_t fill_only, float* s_out);
+/* Residual form of the surrogate (not in the paper): the network predicts the correction of
+ * log s over a prior score p (the cheap reduced-resolution score) scaled by exp(mu), mu the
+ * mean log-ratio of the exact to the prior score on the scored views.
+ * csgs_log_ratio_mean: mean over the i with a_i > 0 and b_i > 0 of log a_i - log b_i (FP64,
+ * fixed summation order) and how many i qualify (count_out nullable); 0 and 0 when none
+ * does.  a_dev, b_dev: device float[n]; mean_out, count_out: host.  Synchronises. */
+csgs_status csgs_log_ratio_mean(csgs_ctx* ctx, const float* a_dev, const float* b_dev, int64_t n, double* mean_out,
+                                int64_t* count_out);
+/* t = log(s + eps) - log(p + eps) - mu (device float[n]); mu finite. */
+csgs_status csgs_log_residual_target(csgs_ctx* ctx, const float* s_dev, const float* p_dev, int64_t n, float eps,
+                                     double mu, float* t_dev);
+/* csgs_surrogate_combine with the prediction y taken as that correction: the predicted score
+ * is max(exp(y + log(p + eps) + mu) - eps, 0). */
+csgs_status csgs_surrogate_combine_prior(csgs_ctx* ctx, const float* y_dev, const float* p_dev,
+                                         const float* s_exact_dev, int64_t n, float eps, double mu, int32_t fill_only,
+                                         float* s_out);
 
 /* ------------------------------------------------------------------ short recovery
  * The paper's short post-pruning finetune (Sec. 4, "short recovery"): gradients of a

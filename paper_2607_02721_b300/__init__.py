@@ -83,7 +83,8 @@ EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error"
            "csgs_debug_tc_gemm", "csgs_debug_tc_gemm_wait", "csgs_scale_scores", "csgs_total_sensitivity", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
            "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
            "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update",
-           "csgs_score_batch", "csgs_autotune", "csgs_debug_gelu")
+           "csgs_score_batch", "csgs_autotune", "csgs_debug_gelu", "csgs_log_ratio_mean", "csgs_log_residual_target",
+           "csgs_surrogate_combine_prior")
 
 _lib = None
 
@@ -136,6 +137,9 @@ def lib():
     L.csgs_features.argtypes = [V, I32, V, V, V]
     L.csgs_log_target.argtypes = [V, V, I64, ctypes.c_float, V]
     L.csgs_surrogate_combine.argtypes = [V, V, V, I64, ctypes.c_float, I32, V]
+    L.csgs_log_ratio_mean.argtypes = [V, V, V, I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    L.csgs_log_residual_target.argtypes = [V, V, V, I64, ctypes.c_float, ctypes.c_double, V]
+    L.csgs_surrogate_combine_prior.argtypes = [V, V, V, V, I64, ctypes.c_float, ctypes.c_double, I32, V]
     L.csgs_update_scene.argtypes = [V, I32, V]
     L.csgs_render_backward.argtypes = [V, I32, I32, V, V, I64, V, V, V, V, V]
     L.csgs_adam_update.argtypes = [V, V, V, V, V, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -466,6 +470,29 @@ class Context:
         self._in()
         self._check(lib().csgs_surrogate_combine(self.h, _ptr(y), _ptr(s_exact), y.numel(), eps, int(fill_only),
                                                  _ptr(out)))
+        self._out()
+        return out
+
+    def log_ratio_mean(self, a, b):
+        """(mean of log a - log b over the entries where both are > 0, their count)."""
+        mean, cnt = ctypes.c_double(), ctypes.c_int64()
+        self._in()
+        self._check(lib().csgs_log_ratio_mean(self.h, _ptr(a), _ptr(b), a.numel(), ctypes.byref(mean),
+                                              ctypes.byref(cnt)))
+        return mean.value, cnt.value
+
+    def log_residual_target(self, s, prior, eps: float, mu: float):
+        t = self._empty(s.numel(), self.torch.float32)
+        self._in()
+        self._check(lib().csgs_log_residual_target(self.h, _ptr(s), _ptr(prior), s.numel(), eps, mu, _ptr(t)))
+        self._out()
+        return t
+
+    def surrogate_combine_prior(self, y, prior, s_exact, eps: float, mu: float, fill_only: bool = False):
+        out = self._empty(y.numel(), self.torch.float32)
+        self._in()
+        self._check(lib().csgs_surrogate_combine_prior(self.h, _ptr(y), _ptr(prior), _ptr(s_exact), y.numel(), eps,
+                                                       mu, int(fill_only), _ptr(out)))
         self._out()
         return out
 

@@ -1722,6 +1722,41 @@ csgs_status csgs_surrogate_combine(csgs_ctx* ctx, const float* y_dev, const floa
     return launch_check(ctx, "surrogate combine");
 }
 
+csgs_status csgs_log_ratio_mean(csgs_ctx* ctx, const float* a_dev, const float* b_dev, int64_t n, double* mean_out,
+                                int64_t* count_out) {
+    if (!ctx) return CSGS_E_INVAL;
+    if (!a_dev || !b_dev || n <= 0 || !mean_out) return fail(ctx, CSGS_E_INVAL, "bad arguments");
+    cudaSetDevice(ctx->device);
+    csgs_status r;
+    if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
+    if ((r = ensure(ctx, ctx->Sdev, sizeof(double) * 2))) return r;
+    log_ratio_mean(a_dev, b_dev, n, P<double>(ctx->partial), P<double>(ctx->Sdev), ctx->st);
+    if ((r = launch_check(ctx, "log ratio mean"))) return r;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_S, ctx->Sdev.p, sizeof(double) * 2, cudaMemcpyDeviceToHost, ctx->st));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->st));
+    const double sum = ctx->h_S[0], cnt = ctx->h_S[1];
+    *mean_out = cnt > 0.0 ? sum / cnt : 0.0;
+    if (count_out) *count_out = (int64_t)cnt;
+    return CSGS_OK;
+}
+
+csgs_status csgs_log_residual_target(csgs_ctx* ctx, const float* s_dev, const float* p_dev, int64_t n, float eps,
+                                     double mu, float* t_dev) {
+    if (!ctx || !s_dev || !p_dev || !t_dev || n <= 0 || !(eps > 0.f) || !isfinite(mu)) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    residual_target(s_dev, p_dev, n, eps, (float)mu, t_dev, ctx->st);
+    return launch_check(ctx, "residual target");
+}
+
+csgs_status csgs_surrogate_combine_prior(csgs_ctx* ctx, const float* y_dev, const float* p_dev,
+                                         const float* s_exact_dev, int64_t n, float eps, double mu, int32_t fill_only,
+                                         float* s_out) {
+    if (!ctx || !y_dev || !p_dev || !s_out || n <= 0 || !(eps > 0.f) || !isfinite(mu)) return CSGS_E_INVAL;
+    cudaSetDevice(ctx->device);
+    surrogate_combine_prior(y_dev, p_dev, s_exact_dev, n, eps, (float)mu, fill_only, s_out, ctx->st);
+    return launch_check(ctx, "surrogate combine (prior)");
+}
+
 }  // extern "C"
 
 // ======================================================================= finetune support

@@ -222,6 +222,12 @@ void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaS
 void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st);
 void adam_update(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
                  int step, cudaStream_t st);
+// out[0] = sum of log a - log b over the i with a > 0 and b > 0, out[1] = their count (FP64,
+// fixed order); partial >= 1024 doubles
+void log_ratio_mean(const float* a, const float* b, int64_t n, double* partial, double* out, cudaStream_t st);
+void residual_target(const float* s, const float* p, int64_t n, float eps, float mu, float* t, cudaStream_t st);
+void surrogate_combine_prior(const float* y, const float* p, const float* s_exact, int64_t n, float eps, float mu,
+                             int fill_only, float* out, cudaStream_t st);
 void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, int fill_only, float* out,
                        cudaStream_t st);
 void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,

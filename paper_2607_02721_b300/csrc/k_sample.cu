@@ -45,6 +45,64 @@ __global__ void __launch_bounds__(kRedBlocks) k_final_sum(const double* __restri
     }
 }
 
+// Surrogate prior: per block, the sum of log a - log b over the i with a > 0 and b > 0 (FP64)
+// and their count; k_final_sum2 adds the blocks in a fixed order.
+__global__ void __launch_bounds__(kThreads) k_log_ratio_partial(const float* __restrict__ a, const float* __restrict__ b,
+                                                                int64_t n, double* __restrict__ partial) {
+    __shared__ double ws[2][kThreads / 32];
+    double acc = 0.0, cnt = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)kRedBlocks * kThreads) {
+        const float x = a[i], y = b[i];
+        if (x > 0.f && y > 0.f) {
+            acc += log((double)x) - log((double)y);
+            cnt += 1.0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ws[0][threadIdx.x >> 5] = acc;
+        ws[1][threadIdx.x >> 5] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            t0 += ws[0][w];
+            t1 += ws[1][w];
+        }
+        partial[2 * blockIdx.x] = t0;
+        partial[2 * blockIdx.x + 1] = t1;
+    }
+}
+
+__global__ void __launch_bounds__(kRedBlocks) k_final_sum2(const double* __restrict__ partial, double* out) {
+    __shared__ double ws[2][kRedBlocks / 32];
+    double v = partial[2 * threadIdx.x], c = partial[2 * threadIdx.x + 1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ws[0][threadIdx.x >> 5] = v;
+        ws[1][threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < kRedBlocks / 32; ++w) {
+            t0 += ws[0][w];
+            t1 += ws[1][w];
+        }
+        out[0] = t0;
+        out[1] = t1;
+    }
+}
+
 __global__ void k_scene_normalise(float* __restrict__ s, int64_t n, const double* __restrict__ sumA) {
     const double A = *sumA;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -87,6 +145,24 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __global__ void k_log_target(const float* __restrict__ s, int64_t n, float eps, float* __restrict__ t) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         t[i] = logf(s[i] + eps);
+}
+
+// residual target against the prior p: t = log(s + eps) - log(p + eps) - mu
+__global__ void k_residual_target(const float* __restrict__ s, const float* __restrict__ p, int64_t n, float eps,
+                                  float mu, float* __restrict__ t) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = logf(s[i] + eps) - logf(p[i] + eps) - mu;
+}
+
+// the prediction y as a residual on the prior: exp(y + log(p + eps) + mu) - eps, then as k_combine
+__global__ void k_combine_prior(const float* __restrict__ y, const float* __restrict__ p,
+                                const float* __restrict__ s_exact, int64_t n, float eps, float mu, int fill_only,
+                                float* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = fmaxf(expf(y[i] + logf(p[i] + eps) + mu) - eps, 0.f);
+        const float s = s_exact ? s_exact[i] : 0.f;
+        out[i] = fill_only ? (s > 0.f ? s : e) : fmaxf(e, s);
+    }
 }
 
 __global__ void k_combine(const float* __restrict__ y, const float* __restrict__ s_exact, int64_t n, float eps,
@@ -302,6 +378,23 @@ void image_fold(float* s, float* vbuf, int64_t n, const double* sumA_view, cudaS
 
 void log_target(const float* s, int64_t n, float eps, float* t, cudaStream_t st) {
     k_log_target<<<148 * 8, 256, 0, st>>>(s, n, eps, t);
+    count_launches(1);
+}
+
+void log_ratio_mean(const float* a, const float* b, int64_t n, double* partial, double* out, cudaStream_t st) {
+    k_log_ratio_partial<<<kRedBlocks, kThreads, 0, st>>>(a, b, n, partial);
+    k_final_sum2<<<1, kRedBlocks, 0, st>>>(partial, out);
+    count_launches(2);
+}
+
+void residual_target(const float* s, const float* p, int64_t n, float eps, float mu, float* t, cudaStream_t st) {
+    k_residual_target<<<148 * 8, 256, 0, st>>>(s, p, n, eps, mu, t);
+    count_launches(1);
+}
+
+void surrogate_combine_prior(const float* y, const float* p, const float* s_exact, int64_t n, float eps, float mu,
+                             int fill_only, float* out, cudaStream_t st) {
+    k_combine_prior<<<148 * 8, 256, 0, st>>>(y, p, s_exact, n, eps, mu, fill_only, out);
     count_launches(1);
 }
 

@@ -11,7 +11,10 @@ cheap score: the same per-pixel sensitivity over every ``cheap_stride``-th view 
 at 1/f of the resolution (1/f^2 of the pixel queries).  The cheap score reaches views
 the exact scorer skips and carries their occlusion; the network learns, on the scored
 views, how the full-resolution score follows from it, from the view statistics and
-from the Gaussian's attributes.
+from the Gaussian's attributes.  With a cheap score (``residual``, the default) the network
+predicts the correction of log s over the cheap score scaled by exp(mu), mu the mean
+log-ratio of the exact to the cheap score on the scored views: ŝ = max((s_cheap + eps)
+exp(mu + prediction) - eps, s_subset), so an output of zero gives the scaled cheap score.
 Training rows: the scored views, plus smaller subsets of them (``aug_views``), each with
 its statistics and cheap score over the same views and the exact score as the target.
 
@@ -47,6 +50,10 @@ class SurrogateConfig:
     # binning of every Gaussian); 3M workload, 20 scored views: f = 4 on every 4th view
     # 19.15 dB in 111 ms, on every view 18.87 dB in 193 ms, exact scoring 18.89 dB in 168 ms
     cheap_stride: int = 4
+    # the network predicts the correction of log s over the cheap score scaled by exp(mu)
+    # (mu: the mean log-ratio of the exact to the cheap score on the scored views), so that
+    # a zero output reproduces that scaled cheap score; False: it predicts log s itself
+    residual: bool = True
 
 
 def lowres_cameras(cams, f: int) -> np.ndarray:
@@ -101,22 +108,29 @@ def surrogate_scores(ctx, sid: int, cams, cfg: SurrogateConfig | None = None, op
         ev[name] = e
 
     def rows(views):
-        """(features, target) of one training set: statistics and cheap score over `views`,
-        the exact score over them as the target.  Returns the exact score too."""
+        """Features of one training set (statistics and cheap score over `views`), the exact
+        score over them and the cheap score (None without one)."""
         s_ex = _score_or_zero(ctx, sid, cams[views], opts)
-        extra = ctx.log_target(_score_or_zero(ctx, sid, low[views], opts), cfg.eps) if low is not None else None
+        s_low = _score_or_zero(ctx, sid, low[views], opts) if low is not None else None
+        extra = ctx.log_target(s_low, cfg.eps) if s_low is not None else None
         ctx.set_queries(sid, cams[views])
         X = ctx.features(sid, ctx.view_stats(sid, opts), extra)
-        return X, ctx.log_target(s_ex, cfg.eps), s_ex
+        return X, s_ex, s_low
 
     mark("start")
     sub = view_subset(nv, cfg.train_views)
-    X0, t0, s_sub = rows(sub)
-    X_parts, t_parts = [X0], [t0]
+    X0, s_sub, low_sub = rows(sub)
+    residual = cfg.residual and low is not None
+    mu = ctx.log_ratio_mean(s_sub, low_sub)[0] if residual else 0.0
+
+    def target(s_ex, s_low):
+        return ctx.log_residual_target(s_ex, s_low, cfg.eps, mu) if residual else ctx.log_target(s_ex, cfg.eps)
+
+    X_parts, t_parts = [X0], [target(s_sub, low_sub)]
     for k in cfg.aug_views:
-        Xk, tk, _ = rows(sub[view_subset(len(sub), k)])
+        Xk, sk, lk = rows(sub[view_subset(len(sub), k)])
         X_parts.append(Xk)
-        t_parts.append(tk)
+        t_parts.append(target(sk, lk))
     mark("scored")
     with torch.cuda.stream(ctx.stream):
         X = torch.cat(X_parts)
@@ -124,13 +138,14 @@ def surrogate_scores(ctx, sid: int, cams, cfg: SurrogateConfig | None = None, op
     ctx.mlp_init(cfg.seed)
     ctx.mlp_train(X, t, batch=cfg.batch, steps=cfg.steps, lr=cfg.lr, seed=cfg.seed + 1)
     mark("trained")
-    extra = (ctx.log_target(_score_or_zero(ctx, sid, low[::max(1, cfg.cheap_stride)], opts), cfg.eps)
-             if low is not None else None)
+    cheap = _score_or_zero(ctx, sid, low[::max(1, cfg.cheap_stride)], opts) if low is not None else None
+    extra = ctx.log_target(cheap, cfg.eps) if cheap is not None else None
     mark("cheap_all")
     ctx.set_queries(sid, cams)
     Xall = ctx.features(sid, ctx.view_stats(sid, opts), extra)
     y = ctx.mlp_forward(Xall)
-    s_hat = ctx.surrogate_combine(y, s_sub, cfg.eps, cfg.fill_only)
+    s_hat = (ctx.surrogate_combine_prior(y, cheap, s_sub, cfg.eps, mu, cfg.fill_only) if residual
+             else ctx.surrogate_combine(y, s_sub, cfg.eps, cfg.fill_only))
     mark("inferred")
     if timings is not None:
         torch.cuda.synchronize()

@@ -138,6 +138,35 @@ def test_log_target_and_combine(ctx, torch):
     np.testing.assert_allclose(out, [0.2, 0.1, 1.0 - 1e-8, 0.3], rtol=1e-6)
 
 
+def test_residual_target_and_prior_combination(ctx, torch):
+    """The surrogate's residual form: mean log-ratio over the entries where both scores are
+    positive, t = log(s + eps) - log(p + eps) - mu, and max(exp(y + log(p + eps) + mu) - eps,
+    0, s_exact) (plain definitions in FP64 as the reference)."""
+    rng = np.random.default_rng(4)
+    n = 100_003
+    a = np.where(rng.random(n) < 0.2, 0.0, rng.lognormal(-6, 2, n)).astype(np.float32)
+    b = np.where(rng.random(n) < 0.2, 0.0, rng.lognormal(-5, 2, n)).astype(np.float32)
+    ok = (a > 0) & (b > 0)
+    ref = float(np.mean(np.log(a[ok].astype(np.float64)) - np.log(b[ok].astype(np.float64))))
+    A, B = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    mean, cnt = ctx.log_ratio_mean(A, B)
+    assert cnt == int(ok.sum()) and abs(mean - ref) <= 1e-12 * max(1.0, abs(ref))
+    assert ctx.log_ratio_mean(A, torch.zeros_like(B)) == (0.0, 0)
+    eps = 1e-8
+    mu = float(mean)
+    t = ctx.log_residual_target(A, B, eps, mu).cpu().numpy().astype(np.float64)
+    tref = np.log(a.astype(np.float64) + eps) - np.log(b.astype(np.float64) + eps) - mu
+    np.testing.assert_allclose(t, tref, rtol=0, atol=2e-5 * (1 + np.abs(tref)).max())
+    y = rng.normal(0, 1, n).astype(np.float32)
+    se = np.where(rng.random(n) < 0.5, 0.0, rng.lognormal(-6, 1, n)).astype(np.float32)
+    Y, SE = torch.tensor(y, device="cuda"), torch.tensor(se, device="cuda")
+    out = ctx.surrogate_combine_prior(Y, B, SE, eps, mu).cpu().numpy().astype(np.float64)
+    e = np.maximum(np.exp(y.astype(np.float64) + np.log(b.astype(np.float64) + eps) + mu) - eps, 0.0)
+    np.testing.assert_allclose(out, np.maximum(e, se), rtol=2e-5, atol=1e-12)
+    out = ctx.surrogate_combine_prior(Y, B, SE, eps, mu, fill_only=True).cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(out, np.where(se > 0, se, e), rtol=2e-5, atol=1e-12)
+
+
 def test_gelu_device_function_matches_oracle(ctx, torch):
     """The kernels' GELU (erf by Abramowitz & Stegun 7.1.26, error <= 1.5e-7) and its
     derivative against the FP64 definitions, over the range the network sees.  The value is
