@@ -493,7 +493,10 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
             const int jw = (int)__reduce_max_sync(0xffffffffu, (unsigned)lim);
             const int nw = warp_list(sh, jw, warp, lane);
             if (STATS && lane == 0) n_went2 += nw;
-#pragma unroll 4
+            // 8 entries per unrolled iteration for the per-pixel score (413 against 418 us per
+            // view); the per-channel score stays at 4 (at 8 it needs 48 registers)
+            constexpr int kUnroll2 = MODE == kScorePixel ? 8 : 4;
+#pragma unroll kUnroll2
             for (int k = 0; k < nw; ++k) {
                 const uint32_t jo = sh.wl[warp][k];
                 // branch-free: every lane evaluates the entry and keeps the result only where
