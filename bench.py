@@ -73,6 +73,9 @@ def workload(name: str):
     return scene, cams
 
 
+# --tile-shape: library codes (CSGS_TILE_*; 0 = the autotuner's choice)
+TILE_SHAPES = {"auto": 0, "16x16": 1, "32x8": 2, "16x8": 3}
+
 # --score-resolution: (library code, description) of the query resolutions of Sec. 3.5
 SCORE_RESOLUTIONS = {"pixel": (0, "per-pixel (max over pixel-rays)"), "scene": (1, "per-scene (one query)"),
                      "channel": (2, "per-channel (max over pixel-ray channels)"),
@@ -303,6 +306,7 @@ def run_ours(args):
         cams = cams[: args.max_views]
     cfg = describe(args.workload, scene, cams)
     res_id, res_name = SCORE_RESOLUTIONS[args.score_resolution]
+    tile_id = TILE_SHAPES[args.tile_shape]
     if args.score_resolution != "pixel":
         cfg["resolution"] = res_name
     m = cfg["coreset_m"]
@@ -325,18 +329,23 @@ def run_ours(args):
         # view batch and radix-sort grid picked by the library's autotuner (untimed)
         # 48 probe views: with 16 the step times of the candidates differed by less than the
         # run-to-run spread (picks of 8/592 and 16/296 gave 167.0 and 158.9 ms)
-        tuned = ctx.autotune(sid, csgs.default_opts(), probe_views=48)
-        cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1]}
+        tuned = ctx.autotune(sid, csgs.default_opts(tile_shape=tile_id), probe_views=48)
+        cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1],
+                            "tile_shape": csgs.TILE_SHAPE_NAMES[tuned[2]]}
+    # the shape the steps use (scenes loaded later, as in the end-to-end run, take it explicitly)
+    shape = tuned[2] if tuned else (tile_id or csgs.TILE_16X16)
+    cfg["tile_shape"] = csgs.TILE_SHAPE_NAMES[shape]
 
     # pair counts of one pass (untimed; counting kernels are slower)
-    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch, resolution=res_id), out=s)
+    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch, resolution=res_id, tile_shape=shape),
+              out=s)
     cnt = ctx.stats()
     # visible (view, Gaussian) fraction for the projection's algorithmic bytes (untimed,
     # four views spread over the query set)
     vis_views = sorted({int(k * len(cams) / 4) for k in range(4)})
     vis_frac = float(np.mean([float((ctx.debug_project(sid, v)[:, 0] > 0).float().mean()) for v in vis_views]))
     torch.cuda.empty_cache()
-    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch, resolution=res_id)
+    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch, resolution=res_id, tile_shape=shape)
 
     def combine(st):
         if dist is not None:
@@ -402,7 +411,7 @@ def run_ours(args):
                 cur = nxt
                 nxt = load() if i + 1 < steps else None
                 ctx.set_queries(cur, cams[my_views])
-                s2, _ = ctx.score(cur, csgs.default_opts(resolution=res_id), out=s)
+                s2, _ = ctx.score(cur, csgs.default_opts(resolution=res_id, tile_shape=shape), out=s)
                 combine(ctx.stats())
                 idx, w = ctx.sample_coreset(s2, m, seed0 + i)
                 with torch.cuda.stream(stream):
@@ -669,7 +678,8 @@ def run_batch(args):
             "value": rays / (ms_graph / 1e3), "ms_per_step": ms_graph, "steps": args.steps, "warmup": args.warmup,
             "per_scene_calls_value": rays / (ms_eager / 1e3), "per_scene_calls_ms": ms_eager,
             "graph_kernels_per_step": graph_kernels, "host_launches_in_timed_graph_steps": launches_host,
-            "autotuned": [{"n": sc.n, "view_batch": t[0], "sort_blocks": t[1]} for (sc, _), t in zip(work, tuned)],
+            "autotuned": [{"n": sc.n, "view_batch": t[0], "sort_blocks": t[1], "tile_shape": csgs.TILE_SHAPE_NAMES[t[2]]}
+                          for (sc, _), t in zip(work, tuned)],
             "config": {"workload": "batch6", "scenes": [{"n": n, "views": v, "width": W, "height": H}
                                                          for n, v, W, H in synth.BATCH6],
                        "rays_per_step": rays},
@@ -924,6 +934,8 @@ def main():
     ap.add_argument("--mlp", action="store_true", help="surrogate network tensor-core report")
     ap.add_argument("--mlp-rows", type=int, default=3_000_000)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile-shape", default="auto", choices=list(TILE_SHAPES),
+                    help="compositing tile shape (auto: the autotuner's choice, 16x16 without it)")
     ap.add_argument("--score-resolution", default="pixel", choices=list(SCORE_RESOLUTIONS),
                     help="query resolution of the timed scoring (Sec. 3.5); the headline is per-pixel")
     args = ap.parse_args()

@@ -89,6 +89,16 @@ typedef struct {
 #define CSGS_VAR_L2 1      /* a = (c rho T)^2 */
 #define CSGS_VAR_NC 2      /* a = rho T (no colour) */
 
+/* Screen-tile shapes of the binning and compositing (one CTA per tile, one thread per
+ * pixel, warps of 8x4 pixels).  The footprint test is per pixel, so the shape decides
+ * only how the work is split; the exponent is rounded in tile-centred coordinates, so
+ * results of two shapes agree to FP32 rounding, not bit for bit.  The per-tile
+ * resolution always uses 16x16 tiles (its query), and so does csgs_render_backward. */
+#define CSGS_TILE_AUTO 0   /* the scene's shape chosen by csgs_autotune, else 16x16 */
+#define CSGS_TILE_16X16 1
+#define CSGS_TILE_32X8 2
+#define CSGS_TILE_16X8 3
+
 /* Scoring / rendering conventions.  The paper fixes only the definitions; the
  * thresholds are those of the standard 3DGS rasteriser it relies on. */
 typedef struct {
@@ -104,6 +114,7 @@ typedef struct {
     int32_t view_batch;    /* views projected per launch (0 = automatic) */
     int32_t collect_stats; /* bit 0: count evaluated and contributing pairs (slower kernels);
                               bit 1: time the phases with CUDA events on the stream */
+    int32_t tile_shape;    /* CSGS_TILE_* (CSGS_TILE_AUTO) */
 } csgs_score_opts;
 
 /* Counters of the last csgs_score / csgs_render call. */
@@ -197,14 +208,20 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
 csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* scene_ids, const csgs_score_opts* opts,
                              float* const* s_devs, double* S_out, int32_t use_graph);
 
-/* Choose the view batch (views projected per launch) of one scene and the
- * radix-sort grid of the context by timing csgs_score's work on the first
- * probe_views query views (0: min(16, views)) for view batches {1,2,4,8,16} and sort
- * grids {148,296,592,1184,1776} blocks.  The result applies to later csgs_score /
- * csgs_score_batch calls whose opts->view_batch is 0; scores do not depend on it
- * (the footprint test is per pixel).  Outputs may be NULL.  Synchronises. */
+/* Choose, for one scene, the view batch (views projected per launch), the radix-sort
+ * grid and the tile shape by timing csgs_score's work on the first probe_views query
+ * views (0: min(16, views)): view batches {1,2,4,8,16} x sort grids
+ * {148,296,592,1184,1776} blocks at the requested shape (16x16 for CSGS_TILE_AUTO),
+ * then, for CSGS_TILE_AUTO (and not the per-tile resolution), the shapes 32x8 and
+ * 16x8 at the best pair.  The choices are kept with the scene and apply to later
+ * csgs_score / csgs_score_batch calls on it (the view batch where opts->view_batch
+ * is 0, the shape where opts->tile_shape is CSGS_TILE_AUTO); the grid also becomes the
+ * context's grid for scenes that were not tuned themselves.  The view batch and the
+ * grid do not change the scores; the shape changes them only by FP32 rounding (see
+ * CSGS_TILE_*).  tile_shape_out receives a CSGS_TILE_* value.  Outputs may be NULL.
+ * Synchronises. */
 csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,
-                          int32_t* view_batch_out, int32_t* sort_blocks_out);
+                          int32_t* view_batch_out, int32_t* sort_blocks_out, int32_t* tile_shape_out);
 
 /* Sensitivity sampling (Algorithm 1, steps 3-5): S = sum s (FP64), p = s / S,
  * m i.i.d. inverse-CDF draws with Philox4x32-10 uniforms (key = seed, counter =

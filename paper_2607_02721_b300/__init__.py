@@ -59,7 +59,12 @@ class ScoreOpts(ctypes.Structure):
     _fields_ = [("resolution", ctypes.c_int32), ("variant", ctypes.c_int32), ("obj_w", ctypes.c_float * 3),
                 ("alpha_min", ctypes.c_float), ("rho_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("cut2", ctypes.c_float), ("dilation", ctypes.c_float), ("clamp_fov", ctypes.c_float),
-                ("view_batch", ctypes.c_int32), ("collect_stats", ctypes.c_int32)]
+                ("view_batch", ctypes.c_int32), ("collect_stats", ctypes.c_int32), ("tile_shape", ctypes.c_int32)]
+
+
+# Tile shapes (CSGS_TILE_*): 0 = the scene's autotuned shape (else 16x16).
+TILE_AUTO, TILE_16X16, TILE_32X8, TILE_16X8 = 0, 1, 2, 3
+TILE_SHAPE_NAMES = {TILE_16X16: "16x16", TILE_32X8: "32x8", TILE_16X8: "16x8"}
 
 
 class Stats(ctypes.Structure):
@@ -145,7 +150,7 @@ def lib():
     L.csgs_adam_update.argtypes = [V, V, V, V, V, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    I32]
     L.csgs_score_batch.argtypes = [V, I32, V, V, V, V, I32]
-    L.csgs_autotune.argtypes = [V, I32, V, I32, V, V]
+    L.csgs_autotune.argtypes = [V, I32, V, I32, V, V, V]
     L.csgs_debug_gelu.argtypes = [V, V, I64, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
@@ -339,14 +344,15 @@ class Context:
         return outs, list(S)
 
     def autotune(self, sid: int, opts: ScoreOpts | None = None, probe_views: int = 0):
-        """Tune the view batch of a scene and the sort grid; returns (view_batch, sort_blocks)."""
-        vb, g = ctypes.c_int32(), ctypes.c_int32()
+        """Tune a scene's view batch, sort grid and tile shape; returns (view_batch,
+        sort_blocks, tile_shape) with tile_shape a TILE_* value."""
+        vb, g, sh = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         opts = opts or default_opts()
         self._in()
         self._check(lib().csgs_autotune(self.h, sid, ctypes.byref(opts), probe_views, ctypes.byref(vb),
-                                        ctypes.byref(g)))
+                                        ctypes.byref(g), ctypes.byref(sh)))
         self._out()
-        return vb.value, g.value
+        return vb.value, g.value, sh.value
 
     def sample_coreset(self, s, m: int, seed: int):
         torch = self.torch

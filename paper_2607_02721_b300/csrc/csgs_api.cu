@@ -55,6 +55,8 @@ struct SceneRec {
     int cams_cap = 0;  // views d_cams holds
     float uploaded_clamp = -1.f;  // clamp_fov of the cameras on the device (-1: none)
     int tuned_vb = 0;             // view batch chosen by csgs_autotune (0: automatic)
+    int tuned_sb = 0;             // radix-sort grid chosen by csgs_autotune (0: the context's)
+    int tuned_shape = 0;          // tile shape chosen by csgs_autotune (CSGS_TILE_*, 0: 16x16)
     // asynchronous load: the upload (copies + finiteness check on the context's upload
     // stream) is settled by the first call that uses the scene
     bool pending = false;
@@ -189,6 +191,22 @@ bool finite3(const float* v, int k) {
     return true;
 }
 
+// Tile shape of a call: the per-tile resolution's query is a 16x16 tile, so it always bins
+// 16x16 tiles; CSGS_TILE_AUTO is 16x16 until a scene-level choice replaces it
+// (scene_tile_shape).
+void set_tile_shape(KOpts* k, int shape) {
+    k->tile_lw = kTileLw16;
+    k->tile_lh = kTileLh16;
+    if (k->resolution == CSGS_RES_TILE) return;
+    if (shape == CSGS_TILE_32X8) {
+        k->tile_lw = 5;
+        k->tile_lh = 3;
+    } else if (shape == CSGS_TILE_16X8) {
+        k->tile_lw = 4;
+        k->tile_lh = 3;
+    }
+}
+
 csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     if (!o) return fail(ctx, CSGS_E_INVAL, "opts is NULL");
     if (o->resolution < CSGS_RES_PIXEL || o->resolution > CSGS_RES_IMAGE)
@@ -199,6 +217,8 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
         !(o->cut2 > 0.f) || !(o->dilation >= 0.f) || !(o->clamp_fov > 0.f) || !finite3(o->obj_w, 3) ||
         o->obj_w[0] < 0.f || o->obj_w[1] < 0.f || o->obj_w[2] < 0.f || o->view_batch < 0)
         return fail(ctx, CSGS_E_INVAL, "invalid scoring options");
+    if (o->tile_shape < CSGS_TILE_AUTO || o->tile_shape > CSGS_TILE_16X8)
+        return fail(ctx, CSGS_E_INVAL, "tile_shape %d is not supported", o->tile_shape);
     k->alpha_min = o->alpha_min;
     k->rho_max = o->rho_max;
     k->t_min = o->t_min;
@@ -213,6 +233,7 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     k->resolution = o->resolution;
     k->variant = o->variant;
     k->narrow_keys = ctx->wide_keys ? 0 : 1;
+    set_tile_shape(k, o->tile_shape);
     return CSGS_OK;
 }
 
@@ -374,11 +395,12 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
 // latency of its 2048-key sub-tiles, not by the array's size.  The slot buffers are sized
 // for nv = 1.
 const uint32_t* bin_batch(csgs_ctx* ctx, int k, int64_t n, int nv, uint32_t* keys, const uint2* rects,
-                          const CamDev* h_cams, const CamDev* d_cams, bool narrow, cudaStream_t st) {
+                          const CamDev* h_cams, const CamDev* d_cams, const KOpts& ko, int grid, cudaStream_t st) {
+    const bool narrow = ko.narrow_keys != 0;
     BinSlot& b = ctx->slot[k];
     unsigned long long* n_inst = &ctx->d_ctr->n_inst[k];
     // one segment per view; the grid is split over the segments
-    int gseg = ctx->sort_blocks / nv;
+    int gseg = grid / nv;
     if (gseg < 8) gseg = 8;
     // narrow depth keys: three 9-bit passes; the float bits: four 8-bit passes
     int cur = radix_sort_pairs(keys, P<uint32_t>(b.dvals_a), P<uint32_t>(b.dkeys_b), P<uint32_t>(b.dvals_b),
@@ -387,20 +409,21 @@ const uint32_t* bin_batch(csgs_ctx* ctx, int k, int64_t n, int nv, uint32_t* key
     const uint32_t* order = cur ? P<uint32_t>(b.dvals_b) : P<uint32_t>(b.dvals_a);
     int tbits = 1;
     for (int v = 0; v < nv; ++v) {
-        const int tb = ceil_log2((uint32_t)(h_cams[v].tiles_x * h_cams[v].tiles_y));
+        const int tb = ceil_log2((uint32_t)tiles_of(h_cams[v], ko.tile_lw, ko.tile_lh));
         if (tb > tbits) tbits = tb;
     }
-    emit_instances(order, rects, (int)n, nv, d_cams, tbits, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
+    emit_instances(order, rects, (int)n, nv, d_cams, tbits, ko.tile_lw, P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), ctx->cap,
                    P<uint32_t>(b.scan_tmp), ctx->d_ctr, n_inst, st);
     const int kbits = tbits + ceil_log2((uint32_t)nv);
     // 9-bit digits once the key needs more than two 8-bit passes
     const int db = kbits > 16 ? 9 : 8;
     int cur2 = radix_sort_pairs(P<uint32_t>(b.ikeys_a), P<uint32_t>(b.ivals_a), P<uint32_t>(b.ikeys_b),
                                 P<uint32_t>(b.ivals_b), n_inst, ctx->cap, kbits, db, P<uint32_t>(b.hist),
-                                ctx->sort_blocks, false, 1, 0, st);
+                                grid, false, 1, 0, st);
     const uint32_t* ik = cur2 ? P<uint32_t>(b.ikeys_b) : P<uint32_t>(b.ikeys_a);
     const uint32_t* iv = cur2 ? P<uint32_t>(b.ivals_b) : P<uint32_t>(b.ivals_a);
-    tile_ranges(ik, n_inst, ctx->cap, P<uint2>(b.ranges), nv, d_cams, tbits, ctx->max_tiles, st);
+    tile_ranges(ik, n_inst, ctx->cap, P<uint2>(b.ranges), nv, d_cams, tbits, ko.tile_lw, ko.tile_lh, ctx->max_tiles,
+                st);
     return iv;
 }
 
@@ -459,6 +482,7 @@ void csgs_default_opts(csgs_score_opts* o) {
     o->clamp_fov = 1.3f;
     o->view_batch = 0;
     o->collect_stats = 0;
+    o->tile_shape = CSGS_TILE_AUTO;
 }
 
 csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
@@ -728,8 +752,6 @@ csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera*
             d.campos[k] = (float)(-((double)c.R[k] * c.t[0] + (double)c.R[3 + k] * c.t[1] + (double)c.R[6 + k] * c.t[2]));
         d.limx = 0.f;  // set per call from clamp_fov
         d.limy = 0.f;
-        d.tiles_x = (c.width + kTile - 1) / kTile;
-        d.tiles_y = (c.height + kTile - 1) / kTile;
     }
     // The device copy is written by the next call's upload, in order on the context's stream
     // after every earlier call's work.  A buffer that is too small goes back to the pool; a
@@ -875,6 +897,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
     cudaStream_t st = ctx->st, ps = ctx->pst;
     csgs_status r;
     const SceneDev sd = scene_dev(*s);
+    const int grid = s->tuned_sb > 0 ? s->tuned_sb : ctx->sort_blocks;
     set_u64(ctx->d_nconst, (unsigned long long)n, st);
     CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
     if (ko.resolution == CSGS_RES_SCENE) CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA, 0, sizeof(double), st));
@@ -907,8 +930,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, ctx->ev_proj[set], 0));
             if (freed_recorded[sl]) CUDA_TRY(ctx, cudaStreamWaitEvent(slot.st, slot.freed, 0));
             size_t e1 = pt.begin(slot.st);
-            const uint32_t* iv = bin_batch(ctx, sl, n, 1, keys_v, rects_v, &cam, s->d_cams + v0 + k,
-                                           ko.narrow_keys != 0, slot.st);
+            const uint32_t* iv = bin_batch(ctx, sl, n, 1, keys_v, rects_v, &cam, s->d_cams + v0 + k, ko, grid, slot.st);
             pt.end(1, e1, slot.st);
             CUDA_TRY(ctx, cudaEventRecord(slot.ready, slot.st));
             const int ci = view % ncs;  // compositing stream of this view
@@ -932,7 +954,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
                 CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
             // the view's tiles, longest lists first (compositing stream: the binning chain,
             // which the slot's next view waits for, stays as short as it was)
-            tile_order(P<uint2>(slot.ranges), cam.tiles_x * cam.tiles_y, P<uint32_t>(slot.torder), cs);
+            tile_order(P<uint2>(slot.ranges), tiles_of(cam, ko.tile_lw, ko.tile_lh), P<uint32_t>(slot.torder), cs);
             size_t e2 = pt.begin(cs);
             launch_composite_score(a, cs);
             if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
@@ -964,8 +986,9 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
         if ((r = upload_cams(ctx, sc[k], ko))) return r;
         if (sc[k]->n > nmax) nmax = sc[k]->n;
         if (vb[k] > vbmax) vbmax = vb[k];
+        // ranges for the shape with the most tiles (16x8), so that any scene's shape fits
         for (auto& c : sc[k]->cams)
-            if (c.tiles_x * c.tiles_y > tiles) tiles = c.tiles_x * c.tiles_y;
+            if (tiles_of(c, 4, 3) > tiles) tiles = tiles_of(c, 4, 3);
     }
     if ((r = ensure_view_buffers(ctx, nmax, vbmax, tiles))) return r;
     if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
@@ -980,6 +1003,14 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
             return r;
     }
     return CSGS_OK;
+}
+
+// The call's conventions with the scene's tuned tile shape where the caller left the shape
+// to the library (CSGS_TILE_AUTO).
+KOpts scene_kopts(const KOpts& ko, const SceneRec* s, const csgs_score_opts* opts) {
+    KOpts k = ko;
+    if (opts->tile_shape == CSGS_TILE_AUTO && s->tuned_shape) set_tile_shape(&k, s->tuned_shape);
+    return k;
 }
 
 int scene_view_batch(const SceneRec* s, const csgs_score_opts* opts) {
@@ -1001,6 +1032,7 @@ csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* o
     KOpts ko;
     csgs_status r;
     if ((r = make_kopts(ctx, opts, &ko))) return r;
+    ko = scene_kopts(ko, s, opts);
     cudaSetDevice(ctx->device);
     const int nv = (int)s->cams.size();
     const int vb = scene_view_batch(s, opts);
@@ -1078,12 +1110,14 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
     cudaSetDevice(ctx->device);
     std::vector<SceneRec*> sc(n_scenes);
     std::vector<int> vb(n_scenes);
+    std::vector<KOpts> kos(n_scenes);  // per scene: its tile shape
     int64_t rays = 0;
     for (int k = 0; k < n_scenes; ++k) {
         sc[k] = get_scene(ctx, scene_ids[k]);
         if (!sc[k]) return scene_fail(ctx, scene_ids[k]);
         if (sc[k]->cams.empty() || !s_devs[k]) return fail(ctx, CSGS_E_INVAL, "bad scene %d in batch", k);
         vb[k] = scene_view_batch(sc[k], opts);
+        kos[k] = scene_kopts(ko, sc[k], opts);
         for (auto& c : sc[k]->cams) rays += (int64_t)c.W * c.H;
     }
     if ((r = prepare_scoring(ctx, sc.data(), vb.data(), n_scenes, ko))) return r;
@@ -1095,7 +1129,8 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
     // (the launches bake in the scene pointers, the host copies of the cameras and every
     // work-buffer address, so all of them are part of the key)
     for (int k = 0; k < n_scenes; ++k) {
-        const int64_t meta[3] = {(int64_t)sc[k]->cams.size(), vb[k], (int64_t)(uintptr_t)sc[k]->d_cams};
+        const int64_t meta[6] = {(int64_t)sc[k]->cams.size(), vb[k], (int64_t)(uintptr_t)sc[k]->d_cams,
+                                 sc[k]->tuned_sb, kos[k].tile_lw, kos[k].tile_lh};
         key.append((const char*)meta, sizeof(meta));
         const SceneDev sd = scene_dev(*sc[k]);
         key.append((const char*)&sd, sizeof(sd));
@@ -1107,6 +1142,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
     float ms = 0.f;
     long long replayed = 0;
     for (int attempt = 0;; ++attempt) {
+        for (int k = 0; k < n_scenes; ++k) kos[k].narrow_keys = ko.narrow_keys;
         const int64_t bmeta[4] = {(int64_t)ctx->cap, ctx->sort_blocks, (int64_t)ctx->buf_gen, (int64_t)ko.narrow_keys};
         const std::string full_key = key + std::string((const char*)bmeta, sizeof(bmeta));
         const bool replay = use_graph && ctx->graph_exec && ctx->graph_key == full_key;
@@ -1124,7 +1160,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
             csgs_status er = CSGS_OK;
             cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st);
             for (int k = 0; k < n_scenes && !er; ++k)
-                er = enqueue_scene_score(ctx, sc[k], ko, vb[k], 0, (int)sc[k]->cams.size(), 0, s_devs[k],
+                er = enqueue_scene_score(ctx, sc[k], kos[k], vb[k], 0, (int)sc[k]->cams.size(), 0, s_devs[k],
                                          P<double>(ctx->Sdev) + k, off, cl);
             cudaError_t ce = cudaStreamEndCapture(st, &g);
             if (er) {
@@ -1143,7 +1179,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
             // eager pass: settles the instance capacity before a capture
             CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), st));
             for (int k = 0; k < n_scenes; ++k)
-                if ((r = enqueue_scene_score(ctx, sc[k], ko, vb[k], 0, (int)sc[k]->cams.size(), 0, s_devs[k],
+                if ((r = enqueue_scene_score(ctx, sc[k], kos[k], vb[k], 0, (int)sc[k]->cams.size(), 0, s_devs[k],
                                              P<double>(ctx->Sdev) + k, off, cl)))
                     return r;
         }
@@ -1175,7 +1211,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
 }
 
 csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,
-                          int32_t* view_batch_out, int32_t* sort_blocks_out) {
+                          int32_t* view_batch_out, int32_t* sort_blocks_out, int32_t* tile_shape_out) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
     if (!s) return scene_fail(ctx, scene_id);
@@ -1193,38 +1229,52 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
     float* s_tmp = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&s_tmp, sizeof(float) * (size_t)s->n));
     std::unique_ptr<float, cudaError_t (*)(void*)> s_tmp_owner(s_tmp, cudaFree);
-    float best = 1e30f;
-    int best_vb = auto_view_batch(s->n, nv, 0), best_g = ctx->sort_blocks;
     PhaseTimer off{ctx, false};
     long long cl = 0;
     int grows = 0;
+    const int saved_sb = s->tuned_sb;
+    // time the scoring of the first pv views with view batch vb, sort grid g and the tile
+    // shape of kk (best of two runs after a warm-up that also settles the capacity)
+    auto trial = [&](int vb, int g, KOpts& kk, float* t_out) -> csgs_status {
+        csgs_status e;
+        s->tuned_sb = g;
+        if ((e = prepare_scoring(ctx, &s, &vb, 1, kk))) return e;
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->st));
+            CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->st));
+            if ((e = enqueue_scene_score(ctx, s, kk, vb, 0, pv, 0, s_tmp, P<double>(ctx->Sdev), off, cl))) return e;
+            CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->st));
+            if ((e = read_counters(ctx))) return e;
+            if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
+                if (++grows > 4) return fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
+                if ((e = widen_or_grow(ctx, kk)) || (e = prepare_scoring(ctx, &s, &vb, 1, kk))) return e;
+                ko.narrow_keys = kk.narrow_keys;
+                --rep;
+                continue;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            if (rep > 0 && ms < t) t = ms;
+        }
+        *t_out = t;
+        return CSGS_OK;
+    };
+    // view batch x sort grid at the requested shape (16x16 when left to the library), then
+    // the tile shapes at the best pair
+    float best = 1e30f;
+    int best_vb = auto_view_batch(s->n, nv, 0), best_g = saved_sb > 0 ? saved_sb : ctx->sort_blocks;
+    int best_shape = opts->tile_shape == CSGS_TILE_AUTO ? CSGS_TILE_16X16 : opts->tile_shape;
+    KOpts k0 = ko;
+    set_tile_shape(&k0, best_shape);
+    r = CSGS_OK;
     for (int vb : vbs) {
         if (vb > pv) continue;
         if ((int64_t)vb * s->n * (int64_t)(sizeof(Splat) + 12) > ((int64_t)4 << 30)) continue;
         for (int g : gs) {
-            ctx->sort_blocks = g;
-            if ((r = prepare_scoring(ctx, &s, &vb, 1, ko))) break;
             float t = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up (and settles capacity)
-                CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->st));
-                CUDA_TRY(ctx, cudaEventRecord(ctx->ev0, ctx->st));
-                if ((r = enqueue_scene_score(ctx, s, ko, vb, 0, pv, 0, s_tmp, P<double>(ctx->Sdev), off, cl))) break;
-                CUDA_TRY(ctx, cudaEventRecord(ctx->ev1, ctx->st));
-                if ((r = read_counters(ctx))) break;
-                if (ctx->h_ctr->err & (kErrCapacity | kErrDepthRange)) {
-                    if (++grows > 4) {
-                        r = fail(ctx, CSGS_E_DEVICE_CHECK, "instance capacity overflow persists");
-                        break;
-                    }
-                    if ((r = widen_or_grow(ctx, ko)) || (r = prepare_scoring(ctx, &s, &vb, 1, ko))) break;
-                    --rep;
-                    continue;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-                if (rep > 0 && ms < t) t = ms;
-            }
-            if (r) break;
+            k0.narrow_keys = ko.narrow_keys;
+            if ((r = trial(vb, g, k0, &t))) break;
             if (t < best) {
                 best = t;
                 best_vb = vb;
@@ -1233,12 +1283,30 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
         }
         if (r) break;
     }
-    if (r) return r;
-    ctx->sort_blocks = best_g;
+    if (!r && opts->tile_shape == CSGS_TILE_AUTO && ko.resolution != CSGS_RES_TILE) {
+        for (int shape : {CSGS_TILE_32X8, CSGS_TILE_16X8}) {
+            KOpts kk = ko;
+            set_tile_shape(&kk, shape);
+            float t = 1e30f;
+            if ((r = trial(best_vb, best_g, kk, &t))) break;
+            if (t < best) {
+                best = t;
+                best_shape = shape;
+            }
+        }
+    }
+    if (r) {
+        s->tuned_sb = saved_sb;
+        return r;
+    }
+    s->tuned_sb = best_g;
     s->tuned_vb = best_vb;
+    ctx->sort_blocks = best_g;  // also the grid of scenes not tuned themselves
+    if (opts->tile_shape == CSGS_TILE_AUTO && ko.resolution != CSGS_RES_TILE) s->tuned_shape = best_shape;
     ctx->graph_key.clear();
     if (view_batch_out) *view_batch_out = best_vb;
     if (sort_blocks_out) *sort_blocks_out = best_g;
+    if (tile_shape_out) *tile_shape_out = best_shape;
     return CSGS_OK;
 }
 
@@ -1310,11 +1378,12 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
     KOpts ko;
     csgs_status r;
     if ((r = make_kopts(ctx, opts, &ko))) return r;
+    ko = scene_kopts(ko, s, opts);
     cudaSetDevice(ctx->device);
     if ((r = upload_cams(ctx, s, ko))) return r;
     const int64_t n = s->n;
     const CamDev& cam = s->cams[view];
-    if ((r = ensure_view_buffers(ctx, n, 1, cam.tiles_x * cam.tiles_y))) return r;
+    if ((r = ensure_view_buffers(ctx, n, 1, tiles_of(cam, ko.tile_lw, ko.tile_lh)))) return r;
     cudaStream_t st = ctx->st;
     const float* wts = nullptr;
     if (idx_dev) {
@@ -1334,7 +1403,7 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
                        P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
         const uint32_t* iv = bin_batch(ctx, 0, n, 1, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), &cam,
-                                       s->d_cams + view, ko.narrow_keys != 0, st);
+                                       s->d_cams + view, ko, ctx->sort_blocks, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1430,11 +1499,12 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
     KOpts ko;
     csgs_status r;
     if ((r = make_kopts(ctx, opts, &ko))) return r;
+    ko = scene_kopts(ko, s, opts);
     cudaSetDevice(ctx->device);
     if ((r = upload_cams(ctx, s, ko))) return r;
     const int64_t n = s->n;
     const CamDev& cam = s->cams[view];
-    if ((r = ensure_view_buffers(ctx, n, 1, cam.tiles_x * cam.tiles_y))) return r;
+    if ((r = ensure_view_buffers(ctx, n, 1, tiles_of(cam, ko.tile_lw, ko.tile_lh)))) return r;
     if ((r = ensure(ctx, ctx->wfull, sizeof(float) * (size_t)n))) return r;
     cudaStream_t st = ctx->st;
     set_u64(ctx->d_nconst, (unsigned long long)n, st);
@@ -1447,7 +1517,7 @@ csgs_status csgs_transfer(csgs_ctx* ctx, int32_t scene_id, int32_t view, const i
         launch_project(sd, s->d_cams + view, 1, nullptr, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
                        P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
         const uint32_t* iv = bin_batch(ctx, 0, n, 1, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), &cam,
-                                       s->d_cams + view, ko.narrow_keys != 0, st);
+                                       s->d_cams + view, ko, ctx->sort_blocks, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;
@@ -1793,12 +1863,14 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
     KOpts ko;
     csgs_status r;
     if ((r = make_kopts(ctx, opts, &ko))) return r;
+    ko.tile_lw = kTileLw16;  // the backward kernel composites 16x16 tiles
+    ko.tile_lh = kTileLh16;
     cudaSetDevice(ctx->device);
     if ((r = upload_cams(ctx, s, ko))) return r;
     const int64_t n = s->n;
     const CamDev& cam = s->cams[view];
     const size_t npx = (size_t)cam.W * cam.H;
-    if ((r = ensure_view_buffers(ctx, n, 1, cam.tiles_x * cam.tiles_y))) return r;
+    if ((r = ensure_view_buffers(ctx, n, 1, tiles_of(cam, ko.tile_lw, ko.tile_lh)))) return r;
     if ((r = ensure(ctx, ctx->bRgb, sizeof(float) * 3 * npx)) || (r = ensure(ctx, ctx->bT, sizeof(float) * npx)) ||
         (r = ensure(ctx, ctx->bLast, sizeof(int) * npx)) || (r = ensure(ctx, ctx->g2d, sizeof(float) * 9 * (size_t)n)))
         return r;
@@ -1820,7 +1892,7 @@ csgs_status csgs_render_backward(csgs_ctx* ctx, int32_t scene_id, int32_t view, 
         launch_project(sd, s->d_cams + view, 1, wts, ko, P<Splat>(ctx->splats[0]), P<uint32_t>(ctx->keys[0]),
                        P<uint2>(ctx->rects[0]), ctx->d_ctr, st);
         const uint32_t* iv = bin_batch(ctx, 0, n, 1, P<uint32_t>(ctx->keys[0]), P<uint2>(ctx->rects[0]), &cam,
-                                       s->d_cams + view, ko.narrow_keys != 0, st);
+                                       s->d_cams + view, ko, ctx->sort_blocks, st);
         CompositeArgs a{};
         a.ranges = P<uint2>(ctx->slot[0].ranges);
         a.inst_gid = iv;

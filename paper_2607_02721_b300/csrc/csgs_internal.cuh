@@ -13,8 +13,11 @@ namespace csgs {
 void count_launches(long long k);
 long long launches();
 
-constexpr int kTile = 16;          // screen tile edge (pixels); one CTA composites one tile
-constexpr int kTilePix = kTile * kTile;
+// Screen tiles: one CTA composites one tile of 2^lw x 2^lh pixels.  Shapes (CSGS_TILE_*):
+// 16x16 (the default, and the query of the per-tile resolution), 32x8 and 16x8; the
+// footprint test is per pixel, so the shape changes only the work split, not which pairs
+// contribute.
+constexpr int kTileLw16 = 4, kTileLh16 = 4;
 constexpr float kLog2e = 1.4426950408889634f;
 
 // Per-view camera, precomputed on the host from csgs_camera.
@@ -26,8 +29,12 @@ struct CamDev {
     float near_z;
     float campos[3];   // -R^T t
     float limx, limy;  // clamp_fov * tan(half FOV) per axis
-    int tiles_x, tiles_y;
 };
+
+// Tiles of a view per row / column for tiles of 2^lw x 2^lh pixels.
+__host__ __device__ inline int tiles_x_of(const CamDev& c, int lw) { return (c.W + (1 << lw) - 1) >> lw; }
+__host__ __device__ inline int tiles_y_of(const CamDev& c, int lh) { return (c.H + (1 << lh) - 1) >> lh; }
+__host__ __device__ inline int tiles_of(const CamDev& c, int lw, int lh) { return tiles_x_of(c, lw) * tiles_y_of(c, lh); }
 
 struct SceneDev {
     int n;
@@ -49,6 +56,7 @@ struct KOpts {
     float ow0, ow1, ow2;  // per-pixel objective weights
     int resolution, variant;
     int narrow_keys;  // depth keys: 1 = narrow (27-bit, relative to the near plane), 0 = the float bits
+    int tile_lw, tile_lh;  // tile shape: 2^tile_lw x 2^tile_lh pixels
 };
 
 // One projected Gaussian in one view (48 bytes, 16-byte aligned).
@@ -162,17 +170,18 @@ int radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b, uint3
 // Gaussians of nv views in depth order (order[v][n], Gaussian ids) -> instances with key
 // (v << tbits) | tile id and value Gaussian id, view by view, each view in depth order;
 // writes the instance count to *n_inst (and the totals in ctr).  cams: the nv views'
-// cameras (device).  scan_tmp: >= nv * ceil(n / 256) + 64 words.
-void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits,
+// cameras (device); tiles 2^lw pixels wide (the rectangles are in tile units).
+// scan_tmp: >= nv * ceil(n / 256) + 64 words.
+void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits, int lw,
                     uint32_t* inst_keys, uint32_t* inst_vals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     unsigned long long* n_inst, cudaStream_t st);
 // The tiles of one view ordered by descending list length, in power-of-two classes
 // (order within a class unspecified): order[0..T) is a permutation of the tile ids.
 void tile_order(const uint2* ranges, int T, uint32_t* order, cudaStream_t st);
 // ranges[v][tile] = [start, end) of each (view, tile) key in the sorted instance keys
-// (rows of max_tiles ranges per view).
+// (rows of max_tiles ranges per view; tiles of 2^lw x 2^lh pixels).
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
-                 const CamDev* cams, int tbits, int max_tiles, cudaStream_t st);
+                 const CamDev* cams, int tbits, int lw, int lh, int max_tiles, cudaStream_t st);
 void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 
 // ---- compositing (k_composite.cu)

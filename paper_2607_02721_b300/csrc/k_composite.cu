@@ -32,8 +32,22 @@
 namespace csgs {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+// CTA layout for tiles of 2^LW x 2^LH pixels: one thread per pixel, 8x4-pixel warps in
+// kCols columns and kBands 4-row bands (warp w = column + kCols band), so a warp mask has
+// kWarps <= 8 bits.
+template <int LW, int LH>
+struct TileCfg {
+    static constexpr int kLw = LW, kLh = LH;
+    static constexpr int kW = 1 << LW, kH = 1 << LH;
+    static constexpr int kCols = kW / 8, kBands = kH / 4;
+    static constexpr int kWarps = kCols * kBands, kThreads = 32 * kWarps;
+    // pixel (lx, ly) of the tile sits at (lx - kHx, ly - kHy) from the tile centre
+    static constexpr float kHx = 0.5f * (float)(kW - 1), kHy = 0.5f * (float)(kH - 1);
+    static_assert(kCols >= 1 && kBands >= 1 && kWarps <= 8, "warp masks are 8 bits per tile-list entry");
+};
+using Tile16x16 = TileCfg<4, 4>;
+using Tile32x8 = TileCfg<5, 3>;
+using Tile16x8 = TileCfg<4, 3>;
 
 // Modes: the render, and the query resolutions of Sec. 3.5.  Pixel and channel
 // resolutions run two passes (A(q) first); tile, image and scene are one pass that
@@ -72,33 +86,35 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     return y;
 }
 
+template <class TC>
 struct Shared {
-    float4 A[kThreads];  // s1, s1k, c1, s2
-    float4 B[kThreads];  // c2, log2 alpha, thr, cw = obj_w . rgb
-    float4 C[kThreads];  // r, g, b, cw2 = obj_w . rgb^2
-    uint32_t gid[kThreads];
-    float wsel[kThreads];  // transfer: the coreset weight w_i of the staged splat
-    uint32_t msk[kThreads];
-    uint16_t wl[kWarps][kThreads];  // per-warp compacted batch: byte offsets 16 x slot
+    static constexpr int NT = TC::kThreads, NW = TC::kWarps;
+    float4 A[NT];  // s1, s1k, c1, s2
+    float4 B[NT];  // c2, log2 alpha, thr, cw = obj_w . rgb
+    float4 C[NT];  // r, g, b, cw2 = obj_w . rgb^2
+    uint32_t gid[NT];
+    float wsel[NT];  // transfer: the coreset weight w_i of the staged splat
+    uint32_t msk[NT];
+    uint16_t wl[NW][NT];  // per-warp compacted batch: byte offsets 16 x slot
     union {
-        uint32_t red[4 * kThreads];     // two-pass modes: pass-2 maxima, word 0 of each 16-byte slot
-        float part[kWarps][kThreads];  // summed modes: the warps' term sums per slot
+        uint32_t red[4 * NT];  // two-pass modes: pass-2 maxima, word 0 of each 16-byte slot
+        float part[NW][NT];    // summed modes: the warps' term sums per slot
     };
     int last;
-    double sumA[kWarps];
+    double sumA[NW];
 };
 
 // Stage splat i of the tile list into slot threadIdx.x (tile centre (cx, cy)).  MSK = 1:
 // also store the warp mask per tile-list entry (pass 1 of the two-pass modes); MSK = 2:
 // load it instead of recomputing it (pass 2).
-template <int MODE, int MSK = 0>
-__device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32_t i, uint32_t end, float cx,
+template <int MODE, int MSK, class TC>
+__device__ __forceinline__ void stage(const CompositeArgs& a, Shared<TC>& sh, uint32_t i, uint32_t end, float cx,
                                       float cy) {
     const int tid = threadIdx.x;
     if (two_pass(MODE)) sh.red[4 * tid] = 0u;
     if (summed(MODE))
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) sh.part[w][tid] = 0.f;
+        for (int w = 0; w < TC::kWarps; ++w) sh.part[w][tid] = 0.f;
     sh.msk[tid] = 0u;
     if (i >= end) return;
     const uint32_t g = __ldg(a.inst_gid + i);
@@ -135,10 +151,13 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
     const float vmax = sR * i2 * 1.001f + 0.01f;
     const float vstar = -s1k * sR * i2 * rsqrt_approx(fmaf(s1k, s1k, s2 * s2));
     uint32_t mk = 0u;
+    // band r covers the rows 4r .. 4r + 3 (y = 4r - kHy .. 4r + 3 - kHy from the centre), warp
+    // column c the columns 8c .. 8c + 7; the bounds are padded by 0.02 px
+    constexpr float y0 = -TC::kHy - 0.02f, y1 = 3.f - TC::kHy + 0.02f;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const float va = fmaxf(-7.52f + 4.f * r - my, -vmax);
-        const float vb = fminf(-4.48f + 4.f * r - my, vmax);
+    for (int r = 0; r < TC::kBands; ++r) {
+        const float va = fmaxf(y0 + 4.f * r - my, -vmax);
+        const float vb = fminf(y1 + 4.f * r - my, vmax);
         if (!(va <= vb)) continue;
         const float vr = fminf(fmaxf(vstar, va), vb);
         const float vl = fminf(fmaxf(-vstar, va), vb);
@@ -149,9 +168,12 @@ __device__ __forceinline__ void stage(const CompositeArgs& a, Shared& sh, uint32
         const float xl = mx - (wl + s1k * vl) * i1;
         const float pad = 0.02f + 1e-3f * (wr + wl) * i1;
         uint32_t cols = 0u;
-        cols |= (xl - pad <= -0.5f && xr + pad >= -7.5f) ? 1u : 0u;
-        cols |= (xl - pad <= 7.5f && xr + pad >= 0.5f) ? 2u : 0u;
-        mk |= cols << (2 * r);
+#pragma unroll
+        for (int c = 0; c < TC::kCols; ++c) {
+            const float xa = 8.f * c - TC::kHx, xb = 8.f * c + 7.f - TC::kHx;
+            cols |= (xl - pad <= xb && xr + pad >= xa) ? 1u << c : 0u;
+        }
+        mk |= cols << (TC::kCols * r);
     }
     sh.msk[tid] = mk;
     if (MSK == 1) a.mskbuf[i] = (uint8_t)mk;
@@ -165,7 +187,8 @@ __device__ __forceinline__ float4 at16(const float4* base, uint32_t off) {
 
 // Compact the staged batch into this warp's list (byte offsets 16 x slot); returns its
 // length.
-__device__ __forceinline__ int warp_list(Shared& sh, int cnt, int warp, int lane) {
+template <class TC>
+__device__ __forceinline__ int warp_list(Shared<TC>& sh, int cnt, int warp, int lane) {
     const uint32_t lt = (1u << lane) - 1u;
     int nw = 0;
     for (int c0 = 0; c0 < cnt; c0 += 32) {
@@ -226,18 +249,20 @@ __device__ __forceinline__ float pass1_objective(const KOpts& o, float A0, float
     return pixel_objective<VAR>(o, A0, A1, A2);
 }
 
-template <int MODE, int VAR, bool STATS>
-__global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
-    __shared__ Shared sh;
+template <int MODE, int VAR, bool STATS, class TC>
+__global__ void __launch_bounds__(TC::kThreads) k_composite(const CompositeArgs a) {
+    constexpr int kThreads = TC::kThreads, kWarps = TC::kWarps;
+    __shared__ Shared<TC> sh;
     const CamDev& cam = a.cam;
     const int tile = a.order ? (int)__ldg(a.order + blockIdx.x) : (int)blockIdx.x;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int ntx = tiles_x_of(cam, TC::kLw);
+    const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 4 + (lane >> 3);
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const int lx = (warp % TC::kCols) * 8 + (lane & 7), ly = (warp / TC::kCols) * 4 + (lane >> 3);
+    const int px = (tx << TC::kLw) + lx, py = (ty << TC::kLh) + ly;
     const bool inside = px < cam.W && py < cam.H;
-    const float X = (float)lx - 7.5f, Y = (float)ly - 7.5f;
-    const float cx = (float)(tx * kTile) + 7.5f, cy = (float)(ty * kTile) + 7.5f;
+    const float X = (float)lx - TC::kHx, Y = (float)ly - TC::kHy;
+    const float cx = (float)(tx << TC::kLw) + TC::kHx, cy = (float)(ty << TC::kLh) + TC::kHy;
     const uint2 rg = a.ranges[tile];
     const uint32_t start = rg.x;
     const int n = (int)(rg.y - rg.x);
@@ -255,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
     // ---------------------------------------------------------------- pass 1
     for (int b = 0; b < n; b += kThreads) {
         if (__syncthreads_count(done) == kThreads) break;
-        stage<MODE, two_pass(MODE) ? 1 : 0>(a, sh, start + b + tid, rg.y, cx, cy);
+        stage<MODE, two_pass(MODE) ? 1 : 0, TC>(a, sh, start + b + tid, rg.y, cx, cy);
         __syncthreads();
         const int cnt = min(kThreads, n - b);
         processed = b + cnt;
@@ -484,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
         const int n2 = sh.last;
         for (int b = 0; b < n2; b += kThreads) {
             __syncthreads();
-            stage<MODE, 2>(a, sh, start + b + tid, rg.y, cx, cy);
+            stage<MODE, 2, TC>(a, sh, start + b + tid, rg.y, cx, cy);
             __syncthreads();
             const int cnt = min(kThreads, n2 - b);
             const int lim = max(0, min(cnt, last - b));
@@ -586,20 +611,23 @@ __global__ void __launch_bounds__(kThreads) k_composite(const CompositeArgs a) {
 // the contributor set is the forward's (the pixel's last contributor).  Per-Gaussian
 // sums over the tile's pixels: warp sums, shared-memory sums, one global add per
 // (tile, Gaussian) and component.
-__global__ void __launch_bounds__(kThreads) k_composite_bwd(const CompositeArgs a) {
-    __shared__ Shared sh;
+__global__ void __launch_bounds__(Tile16x16::kThreads) k_composite_bwd(const CompositeArgs a) {
+    using TC = Tile16x16;
+    constexpr int kThreads = TC::kThreads;
+    __shared__ Shared<TC> sh;
     __shared__ float4 sD[kThreads];      // mean x, mean y (tile-centred), Q xx, Q xy
     __shared__ float2 sE[kThreads];      // Q yy, alpha
     __shared__ float acc[kThreads][9];
     const CamDev& cam = a.cam;
     const int tile = blockIdx.x;
-    const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
+    const int ntx = tiles_x_of(cam, TC::kLw);
+    const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lx = (warp & 1) * 8 + (lane & 7), ly = (warp >> 1) * 4 + (lane >> 3);
-    const int px = tx * kTile + lx, py = ty * kTile + ly;
+    const int lx = (warp % TC::kCols) * 8 + (lane & 7), ly = (warp / TC::kCols) * 4 + (lane >> 3);
+    const int px = (tx << TC::kLw) + lx, py = (ty << TC::kLh) + ly;
     const bool inside = px < cam.W && py < cam.H;
-    const float X = (float)lx - 7.5f, Y = (float)ly - 7.5f;
-    const float cx = (float)(tx * kTile) + 7.5f, cy = (float)(ty * kTile) + 7.5f;
+    const float X = (float)lx - TC::kHx, Y = (float)ly - TC::kHy;
+    const float cx = (float)(tx << TC::kLw) + TC::kHx, cy = (float)(ty << TC::kLh) + TC::kHy;
     const uint2 rg = a.ranges[tile];
     const uint32_t start = rg.x;
     const float rho_max = a.o.rho_max;
@@ -621,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_composite_bwd(const CompositeArgs 
     const int n2 = sh.last;
     for (int b = ((n2 - 1) / kThreads) * kThreads; n2 > 0 && b >= 0; b -= kThreads) {
         __syncthreads();
-        stage<kRender>(a, sh, start + b + tid, rg.y, cx, cy);
+        stage<kRender, 0, TC>(a, sh, start + b + tid, rg.y, cx, cy);
         {
             const float4 Aj = sh.A[tid];
             // tile-centred mean and natural-unit conic back from the Cholesky form
@@ -698,52 +726,66 @@ __global__ void __launch_bounds__(kThreads) k_composite_bwd(const CompositeArgs 
 
 }  // namespace
 
+// The backward and the per-tile resolution (whose query is a 16x16 tile) run on 16x16 tiles
+// only; the other modes on the shape in a.o (tile_lw, tile_lh).
 void launch_composite_backward(const CompositeArgs& a, cudaStream_t st) {
-    const int tiles = a.cam.tiles_x * a.cam.tiles_y;
-    k_composite_bwd<<<tiles, kThreads, 0, st>>>(a);
+    const int tiles = tiles_of(a.cam, Tile16x16::kLw, Tile16x16::kLh);
+    k_composite_bwd<<<tiles, Tile16x16::kThreads, 0, st>>>(a);
     count_launches(1);
 }
 
+template <int MODE, int VAR, bool STATS, class TC>
+static void launch_one(const CompositeArgs& a, cudaStream_t st) {
+    k_composite<MODE, VAR, STATS, TC><<<tiles_of(a.cam, TC::kLw, TC::kLh), TC::kThreads, 0, st>>>(a);
+}
+
+template <int MODE, int VAR, bool STATS>
+static void launch_shape(const CompositeArgs& a, cudaStream_t st) {
+    if (MODE != kScoreTile && a.o.tile_lw == 5 && a.o.tile_lh == 3)
+        launch_one<MODE, VAR, STATS, Tile32x8>(a, st);
+    else if (MODE != kScoreTile && a.o.tile_lw == 4 && a.o.tile_lh == 3)
+        launch_one<MODE, VAR, STATS, Tile16x8>(a, st);
+    else
+        launch_one<MODE, VAR, STATS, Tile16x16>(a, st);
+}
+
 void launch_composite_transfer(const CompositeArgs& a, cudaStream_t st) {
-    const int tiles = a.cam.tiles_x * a.cam.tiles_y;
-    k_composite<kTransfer, kL1, false><<<tiles, kThreads, 0, st>>>(a);
+    launch_shape<kTransfer, kL1, false>(a, st);
     count_launches(1);
 }
 
 void launch_composite_render(const CompositeArgs& a, cudaStream_t st) {
-    const int tiles = a.cam.tiles_x * a.cam.tiles_y;
     if (a.stats)
-        k_composite<kRender, kL1, true><<<tiles, kThreads, 0, st>>>(a);
+        launch_shape<kRender, kL1, true>(a, st);
     else
-        k_composite<kRender, kL1, false><<<tiles, kThreads, 0, st>>>(a);
+        launch_shape<kRender, kL1, false>(a, st);
     count_launches(1);
 }
 
 template <int MODE, int VAR>
-static void launch_mode(const CompositeArgs& a, int tiles, cudaStream_t st) {
+static void launch_mode(const CompositeArgs& a, cudaStream_t st) {
     if (a.stats)
-        k_composite<MODE, VAR, true><<<tiles, kThreads, 0, st>>>(a);
+        launch_shape<MODE, VAR, true>(a, st);
     else
-        k_composite<MODE, VAR, false><<<tiles, kThreads, 0, st>>>(a);
+        launch_shape<MODE, VAR, false>(a, st);
 }
 
 template <int MODE>
-static void launch_var(const CompositeArgs& a, int tiles, cudaStream_t st) {
+static void launch_var(const CompositeArgs& a, cudaStream_t st) {
     switch (a.o.variant) {
-        case CSGS_VAR_L2: launch_mode<MODE, kL2>(a, tiles, st); break;
-        case CSGS_VAR_NC: launch_mode<MODE, kNC>(a, tiles, st); break;
-        default: launch_mode<MODE, kL1>(a, tiles, st); break;
+        case CSGS_VAR_L2: launch_mode<MODE, kL2>(a, st); break;
+        case CSGS_VAR_NC: launch_mode<MODE, kNC>(a, st); break;
+        default: launch_mode<MODE, kL1>(a, st); break;
     }
 }
 
 void launch_composite_score(const CompositeArgs& a, cudaStream_t st) {
-    const int tiles = a.cam.tiles_x * a.cam.tiles_y;
     switch (a.o.resolution) {
-        case CSGS_RES_SCENE: launch_var<kScoreScene>(a, tiles, st); break;
-        case CSGS_RES_CHANNEL: launch_var<kScoreChannel>(a, tiles, st); break;
-        case CSGS_RES_TILE: launch_var<kScoreTile>(a, tiles, st); break;
-        case CSGS_RES_IMAGE: launch_var<kScoreImage>(a, tiles, st); break;
-        default: launch_var<kScorePixel>(a, tiles, st); break;
+        case CSGS_RES_SCENE: launch_var<kScoreScene>(a, st); break;
+        case CSGS_RES_CHANNEL: launch_var<kScoreChannel>(a, st); break;
+        case CSGS_RES_TILE: launch_var<kScoreTile>(a, st); break;
+        case CSGS_RES_IMAGE: launch_var<kScoreImage>(a, st); break;
+        default: launch_var<kScorePixel>(a, st); break;
     }
     count_launches(1);
 }

@@ -125,10 +125,10 @@ __device__ __forceinline__ void project_one(const float mu[3], const float cov3[
     fx1 = fminf(fx1, (float)(c.W - 1));
     fy1 = fminf(fy1, (float)(c.H - 1));
     if (!(fx0 <= fx1) || !(fy0 <= fy1)) return;
-    r.tx0 = (uint32_t)fx0 / kTile;
-    r.ty0 = (uint32_t)fy0 / kTile;
-    r.tx1 = (uint32_t)fx1 / kTile + 1;
-    r.ty1 = (uint32_t)fy1 / kTile + 1;
+    r.tx0 = (uint32_t)fx0 >> o.tile_lw;
+    r.ty0 = (uint32_t)fy0 >> o.tile_lh;
+    r.tx1 = ((uint32_t)fx1 >> o.tile_lw) + 1;
+    r.ty1 = ((uint32_t)fy1 >> o.tile_lh) + 1;
 
     // colour along camera centre -> mean
     float dx = mu[0] - c.campos[0], dy = mu[1] - c.campos[1], dz = mu[2] - c.campos[2];

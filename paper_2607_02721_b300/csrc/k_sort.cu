@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ pa
 // (view << tbits) | tile id, the value the Gaussian id.
 __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __restrict__ order,
                                                             const uint2* __restrict__ rects, int n, int nv,
-                                                            const CamDev* __restrict__ cams, int tbits,
+                                                            const CamDev* __restrict__ cams, int tbits, int lw,
                                                             const uint32_t* __restrict__ partial,
                                                             uint32_t* __restrict__ ikeys, uint32_t* __restrict__ ivals,
                                                             uint32_t cap, DevCounters* ctr) {
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
     for (int c = blockIdx.x; c < nb * nv; c += gridDim.x) {
         const int v = c / nb, cb = c - v * nb;
         const size_t vo = (size_t)v * n;
-        const uint32_t tiles_x = (uint32_t)cams[v].tiles_x;
+        const uint32_t tiles_x = (uint32_t)tiles_x_of(cams[v], lw);
         const uint32_t vkey = (uint32_t)v << tbits;
         const int j = cb * kScanThreads + threadIdx.x;
         const uint32_t gid = j < n ? __ldg(order + vo + j) : 0u;
@@ -428,9 +428,10 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
 // n_tiles of the view closes its last tile: no instance has that key), so every range of
 // the view is written.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long long* d_n, uint32_t n_max,
-                         uint2* __restrict__ ranges, const CamDev* __restrict__ cams, int tbits, int max_tiles) {
+                         uint2* __restrict__ ranges, const CamDev* __restrict__ cams, int tbits, int lw, int lh,
+                         int max_tiles) {
     const int v = blockIdx.y;
-    const uint32_t n_tiles = (uint32_t)(cams[v].tiles_x * cams[v].tiles_y);
+    const uint32_t n_tiles = (uint32_t)tiles_of(cams[v], lw, lh);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t > n_tiles) return;
     const uint32_t key = ((uint32_t)v << tbits) + t;
@@ -542,7 +543,7 @@ int radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, con
     return cur;
 }
 
-void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits,
+void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, const CamDev* cams, int tbits, int lw,
                     uint32_t* ikeys, uint32_t* ivals, uint32_t cap, uint32_t* scan_tmp, DevCounters* ctr,
                     unsigned long long* n_inst, cudaStream_t st) {
     const int nb = (n + kScanThreads - 1) / kScanThreads;
@@ -552,13 +553,14 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, co
     count_launches(1);
     k_scan_top_u32<<<1, 1024, 0, st>>>(scan_tmp, nc, ctr, n_inst);
     count_launches(1);
-    k_emit_down<<<ng, kScanThreads, 0, st>>>(order, rects, n, nv, cams, tbits, scan_tmp, ikeys, ivals, cap, ctr);
+    k_emit_down<<<ng, kScanThreads, 0, st>>>(order, rects, n, nv, cams, tbits, lw, scan_tmp, ikeys, ivals, cap, ctr);
     count_launches(1);
 }
 
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
-                 const CamDev* cams, int tbits, int max_tiles, cudaStream_t st) {
-    k_ranges<<<dim3((max_tiles + 1 + 255) / 256, nv), 256, 0, st>>>(keys, d_n, n_max, ranges, cams, tbits, max_tiles);
+                 const CamDev* cams, int tbits, int lw, int lh, int max_tiles, cudaStream_t st) {
+    k_ranges<<<dim3((max_tiles + 1 + 255) / 256, nv), 256, 0, st>>>(keys, d_n, n_max, ranges, cams, tbits, lw, lh,
+                                                                    max_tiles);
     count_launches(1);
 }
 

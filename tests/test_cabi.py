@@ -42,14 +42,37 @@ def test_default_opts_are_the_rasteriser_conventions(lib):
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.rho_max - 0.99) < 1e-7
     assert abs(o.t_min - 1e-4) < 1e-10 and o.cut2 == 9.0 and abs(o.dilation - 0.3) < 1e-7
     assert list(o.obj_w) == [1.0, 1.0, 1.0]
+    assert o.tile_shape == csgs.TILE_AUTO and o.view_batch == 0
 
 
-def test_struct_layouts_match_header(lib):
-    # csgs_camera is 80 bytes; csgs_scene_desc 56; csgs_score_opts 52; csgs_stats 184
-    assert ctypes.sizeof(csgs.Camera) == 80
-    assert ctypes.sizeof(csgs.SceneDesc) == 56
-    assert ctypes.sizeof(csgs.ScoreOpts) == 52
-    assert ctypes.sizeof(csgs.Stats) == 184
+def test_struct_layouts_match_header(lib, tmp_path):
+    """Every field offset and struct size of the binding's ctypes structs equals the C
+    compiler's layout of include/csgs.h (a small C program built with gcc prints them)."""
+    import shutil
+    import subprocess
+
+    structs = {"csgs_camera": csgs.Camera, "csgs_scene_desc": csgs.SceneDesc,
+               "csgs_score_opts": csgs.ScoreOpts, "csgs_stats": csgs.Stats}
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "csgs.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+    assert ctypes.sizeof(csgs.ScoreOpts) == 56
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

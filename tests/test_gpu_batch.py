@@ -1,5 +1,5 @@
 """Multi-scene scoring in one submission (eager, captured as a CUDA graph, replayed)
-and the view-batch / sort-grid autotuner: every path returns the scores csgs_score
+and the view-batch / sort-grid / tile-shape autotuner: every path returns the scores csgs_score
 returns scene by scene, and the replayed graph's scores match the FP64 oracle."""
 import numpy as np
 import pytest
@@ -141,14 +141,43 @@ def test_batch_scene_resolution(ctx, scenes):
 
 
 def test_autotune_keeps_scores(ctx, scenes):
-    opts = csgs.default_opts()
-    ref, Sref = ctx.score(scenes[1], opts)
+    """The view batch and the sort grid leave the scores bit for bit; the tuned tile shape
+    is what later CSGS_TILE_AUTO calls use."""
+    fixed = csgs.default_opts(tile_shape=csgs.TILE_16X16)
+    ref, Sref = ctx.score(scenes[1], fixed)
     ref = ref.cpu().numpy()
-    vb, g = ctx.autotune(scenes[1], opts, probe_views=4)
+    vb, g, shape = ctx.autotune(scenes[1], csgs.default_opts(), probe_views=4)
     assert vb in (1, 2, 4) and g in (148, 296, 592, 1184, 1776)
-    s, S = ctx.score(scenes[1], opts)
+    assert shape in (csgs.TILE_16X16, csgs.TILE_32X8, csgs.TILE_16X8)
+    s, S = ctx.score(scenes[1], fixed)
     np.testing.assert_array_equal(s.cpu().numpy(), ref)
     assert S == Sref
+    auto, Sa = ctx.score(scenes[1], csgs.default_opts())
+    expl, Se = ctx.score(scenes[1], csgs.default_opts(tile_shape=shape))
+    np.testing.assert_array_equal(auto.cpu().numpy(), expl.cpu().numpy())
+    assert Sa == Se
+
+
+@pytest.mark.parametrize("shape", [csgs.TILE_32X8, csgs.TILE_16X8], ids=["32x8", "16x8"])
+def test_batch_tile_shapes_match_single_scene_and_oracle(ctx, scenes, shape):
+    """A captured batch in another tile shape returns csgs_score's scores scene by scene,
+    and the ragged 200x120 scene matches the oracle."""
+    opts = csgs.default_opts(tile_shape=shape)
+    ref_s, ref_S = one_by_one(ctx, scenes, opts)
+    outs, _ = ctx.score_batch(scenes, opts, use_graph=True)
+    outs, S = ctx.score_batch(scenes, opts, outs=outs, use_graph=True)
+    for k in range(len(scenes)):
+        np.testing.assert_array_equal(outs[k].cpu().numpy(), ref_s[k])
+        assert S[k] == ref_S[k]
+    c = csgs.Context(0)
+    try:
+        sc, cams = make_scene(2)
+        sid = c.load_scene(sc)
+        c.set_queries(sid, cams)
+        s, S2 = c.score(sid, opts)
+        check_scores(s.cpu().numpy(), S2, oracle.score(oracle.SceneArrays(sc), cams))
+    finally:
+        c.close()
 
 
 def test_batch_rejects_bad_arguments(ctx, scenes):

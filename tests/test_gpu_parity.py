@@ -285,21 +285,57 @@ def test_unit_weights_render_bit_identical(ctx, small, small_sid, torch):
 
 # ---------------------------------------------------------------- edge cases
 
-def test_ragged_image_and_tiny_scene(ctx, torch):
+TILE_SHAPES = [("16x16", csgs.TILE_16X16), ("32x8", csgs.TILE_32X8), ("16x8", csgs.TILE_16X8)]
+
+
+@pytest.mark.parametrize("shape", TILE_SHAPES, ids=[s[0] for s in TILE_SHAPES])
+def test_ragged_image_and_tiny_scene(ctx, torch, shape):
+    """Images smaller than one tile and with ragged right / bottom tiles, in every tile
+    shape."""
     sc = synth.uniform_cube_scene(300, seed=4)
     R, t = synth.look_at([0.0, -3.0, 0.5])
     cams = np.stack([synth.make_camera(R, t, 37, 23), synth.make_camera(R, t, 1, 1), synth.make_camera(R, t, 70, 17)])
     sid = ctx.load_scene(sc)
     ctx.set_queries(sid, cams)
     sa = oracle.SceneArrays(sc)
+    opts = csgs.default_opts(tile_shape=shape[1])
     for v in range(3):
         H, W = int(cams[v][17]), int(cams[v][16])
-        rgb = ctx.render(sid, v, H=H, W=W).cpu().numpy()
+        rgb = ctx.render(sid, v, opts=opts, H=H, W=W).cpu().numpy()
         compare_render(rgb, oracle.render(sa, cams[v]), max_flag_frac=0.05)
-    s, S = ctx.score(sid)
+    s, S = ctx.score(sid, opts)
     ref = oracle.score(sa, cams)
     check_scores(s.cpu().numpy(), S, ref)
     ctx.free_scene(sid)
+
+
+@pytest.mark.parametrize("shape", TILE_SHAPES[1:], ids=[s[0] for s in TILE_SHAPES[1:]])
+def test_tile_shapes_match_oracle(ctx, workload, shape):
+    """32x8 tiles (warps of 8x4 pixels in four columns and two bands) and 16x8 tiles (two
+    columns, two bands, 128-thread CTAs): the per-pixel and per-channel scores, the
+    per-scene sums and renders against the oracle.  The footprint test is per pixel, so
+    the shape changes only the FP32 rounding of the tile-centred exponent."""
+    sc, cams, _, sa, sid = workload
+    s, S = ctx.score(sid, csgs.default_opts(tile_shape=shape[1]))
+    check_scores(s.cpu().numpy(), S, oracle.score(sa, cams))
+    s, S = ctx.score(sid, csgs.default_opts(tile_shape=shape[1], resolution=csgs.RES_CHANNEL))
+    check_scores(s.cpu().numpy(), S, oracle.score(sa, cams, Opts(resolution=oracle.RES_CHANNEL)))
+    s, S = ctx.score(sid, csgs.default_opts(tile_shape=shape[1], resolution=csgs.RES_SCENE))
+    ref = oracle.score(sa, cams, Opts(resolution=oracle.RES_SCENE))
+    s = s.cpu().numpy().astype(np.float64)
+    big = ref["s"] > 1e-6
+    assert np.quantile(np.abs(s[big] - ref["s"][big]) / ref["s"][big], 0.999) <= S_RTOL and abs(S - 1.0) < 1e-4
+    for v in (0, len(cams) - 1):
+        rgb = render_gpu(ctx, sid, cams[v], v, opts=csgs.default_opts(tile_shape=shape[1])).cpu().numpy()
+        compare_render(rgb, oracle.render(sa, cams[v]))
+
+
+def test_tile_resolution_ignores_the_tile_shape(ctx, small_sid):
+    """The per-tile resolution's query is a 16x16 tile whatever shape is requested."""
+    a, Sa = ctx.score(small_sid, csgs.default_opts(resolution=csgs.RES_TILE))
+    b, Sb = ctx.score(small_sid, csgs.default_opts(resolution=csgs.RES_TILE, tile_shape=csgs.TILE_16X8))
+    np.testing.assert_allclose(b.cpu().numpy(), a.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    assert abs(Sa - Sb) <= 1e-5 * Sa
 
 
 def test_single_gaussian_has_unit_sensitivity(ctx):
