@@ -329,23 +329,29 @@ def run_ours(args):
         # view batch and radix-sort grid picked by the library's autotuner (untimed)
         # 48 probe views: with 16 the step times of the candidates differed by less than the
         # run-to-run spread (picks of 8/592 and 16/296 gave 167.0 and 158.9 ms)
-        tuned = ctx.autotune(sid, csgs.default_opts(tile_shape=tile_id), probe_views=48)
-        cfg["autotuned"] = {"view_batch": tuned[0], "sort_blocks": tuned[1],
-                            "tile_shape": csgs.TILE_SHAPE_NAMES[tuned[2]]}
-    # the shape the steps use (scenes loaded later, as in the end-to-end run, take it explicitly)
-    shape = tuned[2] if tuned else (tile_id or csgs.TILE_16X16)
+        tuned = ctx.autotune(sid, csgs.default_opts(tile_shape=tile_id, persist_ctas=args.persist_ctas),
+                             probe_views=48)
+        cfg["autotuned"] = {"view_batch": tuned["view_batch"], "sort_blocks": tuned["sort_blocks"],
+                            "tile_shape": csgs.TILE_SHAPE_NAMES[tuned["tile_shape"]],
+                            "persist_ctas": tuned["persist_ctas"]}
+    # the shape and compositing grid the steps use (scenes loaded later, as in the end-to-end
+    # run, take them explicitly)
+    shape = tuned["tile_shape"] if tuned else (tile_id or csgs.TILE_16X16)
+    persist = (tuned["persist_ctas"] or -1) if tuned else args.persist_ctas
     cfg["tile_shape"] = csgs.TILE_SHAPE_NAMES[shape]
+    cfg["composite_launch"] = f"persistent, {persist} CTAs" if persist > 0 else "one CTA per tile"
 
     # pair counts of one pass (untimed; counting kernels are slower)
-    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch, resolution=res_id, tile_shape=shape),
-              out=s)
+    ctx.score(sid, csgs.default_opts(collect_stats=1, view_batch=args.view_batch, resolution=res_id, tile_shape=shape,
+                                     persist_ctas=persist), out=s)
     cnt = ctx.stats()
     # visible (view, Gaussian) fraction for the projection's algorithmic bytes (untimed,
     # four views spread over the query set)
     vis_views = sorted({int(k * len(cams) / 4) for k in range(4)})
     vis_frac = float(np.mean([float((ctx.debug_project(sid, v)[:, 0] > 0).float().mean()) for v in vis_views]))
     torch.cuda.empty_cache()
-    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch, resolution=res_id, tile_shape=shape)
+    timing = csgs.default_opts(collect_stats=2, view_batch=args.view_batch, resolution=res_id, tile_shape=shape,
+                               persist_ctas=persist)
 
     def combine(st):
         if dist is not None:
@@ -411,7 +417,8 @@ def run_ours(args):
                 cur = nxt
                 nxt = load() if i + 1 < steps else None
                 ctx.set_queries(cur, cams[my_views])
-                s2, _ = ctx.score(cur, csgs.default_opts(resolution=res_id, tile_shape=shape), out=s)
+                s2, _ = ctx.score(cur, csgs.default_opts(resolution=res_id, tile_shape=shape, persist_ctas=persist),
+                                  out=s)
                 combine(ctx.stats())
                 idx, w = ctx.sample_coreset(s2, m, seed0 + i)
                 with torch.cuda.stream(stream):
@@ -678,7 +685,8 @@ def run_batch(args):
             "value": rays / (ms_graph / 1e3), "ms_per_step": ms_graph, "steps": args.steps, "warmup": args.warmup,
             "per_scene_calls_value": rays / (ms_eager / 1e3), "per_scene_calls_ms": ms_eager,
             "graph_kernels_per_step": graph_kernels, "host_launches_in_timed_graph_steps": launches_host,
-            "autotuned": [{"n": sc.n, "view_batch": t[0], "sort_blocks": t[1], "tile_shape": csgs.TILE_SHAPE_NAMES[t[2]]}
+            "autotuned": [{"n": sc.n, "view_batch": t["view_batch"], "sort_blocks": t["sort_blocks"],
+                           "tile_shape": csgs.TILE_SHAPE_NAMES[t["tile_shape"]], "persist_ctas": t["persist_ctas"]}
                           for (sc, _), t in zip(work, tuned)],
             "config": {"workload": "batch6", "scenes": [{"n": n, "views": v, "width": W, "height": H}
                                                          for n, v, W, H in synth.BATCH6],
@@ -936,6 +944,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tile-shape", default="auto", choices=list(TILE_SHAPES),
                     help="compositing tile shape (auto: the autotuner's choice, 16x16 without it)")
+    ap.add_argument("--persist-ctas", type=int, default=0,
+                    help="persistent compositing CTAs (0: the autotuner's choice, -1: one CTA per tile)")
     ap.add_argument("--score-resolution", default="pixel", choices=list(SCORE_RESOLUTIONS),
                     help="query resolution of the timed scoring (Sec. 3.5); the headline is per-pixel")
     args = ap.parse_args()

@@ -115,7 +115,21 @@ typedef struct {
     int32_t collect_stats; /* bit 0: count evaluated and contributing pairs (slower kernels);
                               bit 1: time the phases with CUDA events on the stream */
     int32_t tile_shape;    /* CSGS_TILE_* (CSGS_TILE_AUTO) */
+    int32_t persist_ctas;  /* per-pixel score: compositing as one persistent launch per view of
+                              persist_ctas CTAs, each taking the next tile (longest lists first)
+                              from a queue until none is left; 0 = the scene's choice by
+                              csgs_autotune (else one CTA per tile), -1 = one CTA per tile.
+                              Scores do not depend on it */
 } csgs_score_opts;
+
+/* What csgs_autotune chose for a scene. */
+typedef struct {
+    int32_t view_batch;    /* views projected per launch */
+    int32_t sort_blocks;   /* radix-sort grid (CTAs) */
+    int32_t tile_shape;    /* CSGS_TILE_16X16, CSGS_TILE_32X8 or CSGS_TILE_16X8 */
+    int32_t persist_ctas;  /* persistent compositing CTAs, 0 = one CTA per tile */
+    float probe_ms;        /* the chosen configuration's time for the probe views */
+} csgs_tuning;
 
 /* Counters of the last csgs_score / csgs_render call. */
 typedef struct {
@@ -209,19 +223,22 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
                              float* const* s_devs, double* S_out, int32_t use_graph);
 
 /* Choose, for one scene, the view batch (views projected per launch), the radix-sort
- * grid and the tile shape by timing csgs_score's work on the first probe_views query
- * views (0: min(16, views)): view batches {1,2,4,8,16} x sort grids
- * {148,296,592,1184,1776} blocks at the requested shape (16x16 for CSGS_TILE_AUTO),
- * then, for CSGS_TILE_AUTO (and not the per-tile resolution), the shapes 32x8 and
- * 16x8 at the best pair.  The choices are kept with the scene and apply to later
- * csgs_score / csgs_score_batch calls on it (the view batch where opts->view_batch
- * is 0, the shape where opts->tile_shape is CSGS_TILE_AUTO); the grid also becomes the
- * context's grid for scenes that were not tuned themselves.  The view batch and the
- * grid do not change the scores; the shape changes them only by FP32 rounding (see
- * CSGS_TILE_*).  tile_shape_out receives a CSGS_TILE_* value.  Outputs may be NULL.
+ * grid, the tile shape and the persistent compositing grid by timing csgs_score's work
+ * on the first probe_views query views (0: min(16, views)), one dimension after the
+ * other: view batches {1,2,4,8,16} x sort grids {148,296,592,1184,1776} blocks at the
+ * requested shape (16x16 for CSGS_TILE_AUTO); then, for CSGS_TILE_AUTO (and not the
+ * per-tile resolution), the shapes 32x8 and 16x8 at the best pair; then, for the
+ * per-pixel score with opts->persist_ctas 0, persistent launches of r, r - 1 and r - 2
+ * CTAs per SM (r: the kernel's resident limit) against one CTA per tile.  The choices
+ * are kept with the scene and apply to later csgs_score / csgs_score_batch calls on it
+ * (the view batch where opts->view_batch is 0, the shape where opts->tile_shape is
+ * CSGS_TILE_AUTO, the persistent grid where opts->persist_ctas is 0); the sort grid also
+ * becomes the context's grid for scenes that were not tuned themselves.  The view batch,
+ * the grid and the persistent launch do not change the scores; the shape changes them
+ * only by FP32 rounding (see CSGS_TILE_*).  out (may be NULL) receives the choices.
  * Synchronises. */
 csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,
-                          int32_t* view_batch_out, int32_t* sort_blocks_out, int32_t* tile_shape_out);
+                          csgs_tuning* out);
 
 /* Sensitivity sampling (Algorithm 1, steps 3-5): S = sum s (FP64), p = s / S,
  * m i.i.d. inverse-CDF draws with Philox4x32-10 uniforms (key = seed, counter =

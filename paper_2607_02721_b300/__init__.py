@@ -59,7 +59,13 @@ class ScoreOpts(ctypes.Structure):
     _fields_ = [("resolution", ctypes.c_int32), ("variant", ctypes.c_int32), ("obj_w", ctypes.c_float * 3),
                 ("alpha_min", ctypes.c_float), ("rho_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("cut2", ctypes.c_float), ("dilation", ctypes.c_float), ("clamp_fov", ctypes.c_float),
-                ("view_batch", ctypes.c_int32), ("collect_stats", ctypes.c_int32), ("tile_shape", ctypes.c_int32)]
+                ("view_batch", ctypes.c_int32), ("collect_stats", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
+                ("persist_ctas", ctypes.c_int32)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("view_batch", ctypes.c_int32), ("sort_blocks", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
+                ("persist_ctas", ctypes.c_int32), ("probe_ms", ctypes.c_float)]
 
 
 # Tile shapes (CSGS_TILE_*): 0 = the scene's autotuned shape (else 16x16).
@@ -150,7 +156,7 @@ def lib():
     L.csgs_adam_update.argtypes = [V, V, V, V, V, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                    I32]
     L.csgs_score_batch.argtypes = [V, I32, V, V, V, V, I32]
-    L.csgs_autotune.argtypes = [V, I32, V, I32, V, V, V]
+    L.csgs_autotune.argtypes = [V, I32, V, I32, V]
     L.csgs_debug_gelu.argtypes = [V, V, I64, V]
     L.csgs_kernel_launch_count.argtypes = []
     L.csgs_kernel_launch_count.restype = I64
@@ -343,16 +349,15 @@ class Context:
         self._out()
         return outs, list(S)
 
-    def autotune(self, sid: int, opts: ScoreOpts | None = None, probe_views: int = 0):
-        """Tune a scene's view batch, sort grid and tile shape; returns (view_batch,
-        sort_blocks, tile_shape) with tile_shape a TILE_* value."""
-        vb, g, sh = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    def autotune(self, sid: int, opts: ScoreOpts | None = None, probe_views: int = 0) -> dict:
+        """Tune a scene's view batch, sort grid, tile shape (a TILE_* value) and persistent
+        compositing grid; returns the csgs_tuning fields as a dict."""
+        out = Tuning()
         opts = opts or default_opts()
         self._in()
-        self._check(lib().csgs_autotune(self.h, sid, ctypes.byref(opts), probe_views, ctypes.byref(vb),
-                                        ctypes.byref(g), ctypes.byref(sh)))
+        self._check(lib().csgs_autotune(self.h, sid, ctypes.byref(opts), probe_views, ctypes.byref(out)))
         self._out()
-        return vb.value, g.value, sh.value
+        return {f: getattr(out, f) for f, _ in Tuning._fields_}
 
     def sample_coreset(self, s, m: int, seed: int):
         torch = self.torch

@@ -35,7 +35,7 @@ struct DevBuf {
 // slot's own high-priority stream, overlaps the compositing of the current one.
 struct BinSlot {
     DevBuf dkeys_b, dvals_a, dvals_b, ikeys_a, ikeys_b, ivals_a, ivals_b, ranges, hist, scan_tmp;
-    DevBuf torder;  // scoring: the view's tiles, longest lists first
+    DevBuf torder;  // scoring: a persistent launch's queue counter, then the view's tiles, longest lists first
     cudaStream_t st = nullptr;
     cudaEvent_t ready = nullptr;  // binning done
     cudaEvent_t freed = nullptr;  // the compositing that read the slot is done
@@ -57,6 +57,7 @@ struct SceneRec {
     int tuned_vb = 0;             // view batch chosen by csgs_autotune (0: automatic)
     int tuned_sb = 0;             // radix-sort grid chosen by csgs_autotune (0: the context's)
     int tuned_shape = 0;          // tile shape chosen by csgs_autotune (CSGS_TILE_*, 0: 16x16)
+    int tuned_persist = 0;        // persistent compositing CTAs chosen by csgs_autotune (0: one per tile)
     // asynchronous load: the upload (copies + finiteness check on the context's upload
     // stream) is settled by the first call that uses the scene
     bool pending = false;
@@ -219,6 +220,8 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
         return fail(ctx, CSGS_E_INVAL, "invalid scoring options");
     if (o->tile_shape < CSGS_TILE_AUTO || o->tile_shape > CSGS_TILE_16X8)
         return fail(ctx, CSGS_E_INVAL, "tile_shape %d is not supported", o->tile_shape);
+    if (o->persist_ctas < -1 || o->persist_ctas > (1 << 20))
+        return fail(ctx, CSGS_E_INVAL, "persist_ctas %d is out of range", o->persist_ctas);
     k->alpha_min = o->alpha_min;
     k->rho_max = o->rho_max;
     k->t_min = o->t_min;
@@ -234,6 +237,7 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     k->variant = o->variant;
     k->narrow_keys = ctx->wide_keys ? 0 : 1;
     set_tile_shape(k, o->tile_shape);
+    k->persist_ctas = o->persist_ctas > 0 ? o->persist_ctas : 0;
     return CSGS_OK;
 }
 
@@ -375,7 +379,7 @@ csgs_status ensure_view_buffers(csgs_ctx* ctx, int64_t n, int vb, int max_tiles)
         if ((r = ensure(ctx, b.dvals_a, sizeof(uint32_t) * nv))) return r;
         if ((r = ensure(ctx, b.dvals_b, sizeof(uint32_t) * nv))) return r;
         if ((r = ensure(ctx, b.ranges, sizeof(uint2) * (size_t)ctx->max_tiles))) return r;
-        if ((r = ensure(ctx, b.torder, sizeof(uint32_t) * (size_t)ctx->max_tiles))) return r;
+        if ((r = ensure(ctx, b.torder, sizeof(uint32_t) * ((size_t)ctx->max_tiles + 1)))) return r;
         if ((r = ensure(ctx, b.hist, sizeof(uint32_t) * sort_hist_stride(kSortMaxBlocks)))) return r;
         if ((r = ensure(ctx, b.scan_tmp, sizeof(uint32_t) * ((size_t)(n + 255) / 256 + 64)))) return r;
         if ((r = ensure(ctx, b.ikeys_a, ib))) return r;
@@ -483,6 +487,7 @@ void csgs_default_opts(csgs_score_opts* o) {
     o->view_batch = 0;
     o->collect_stats = 0;
     o->tile_shape = CSGS_TILE_AUTO;
+    o->persist_ctas = 0;
 }
 
 csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
@@ -938,7 +943,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             CUDA_TRY(ctx, cudaStreamWaitEvent(cs, slot.ready, 0));
             CompositeArgs a{};
             a.ranges = P<uint2>(slot.ranges);
-            a.order = P<uint32_t>(slot.torder);
+            a.work = P<uint32_t>(slot.torder);
+            a.order = P<uint32_t>(slot.torder) + 1;
             a.inst_gid = iv;
             a.splats = P<Splat>(ctx->splats[set]) + (size_t)k * n;
             a.n_gauss = (int)n;
@@ -954,7 +960,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
                 CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
             // the view's tiles, longest lists first (compositing stream: the binning chain,
             // which the slot's next view waits for, stays as short as it was)
-            tile_order(P<uint2>(slot.ranges), tiles_of(cam, ko.tile_lw, ko.tile_lh), P<uint32_t>(slot.torder), cs);
+            tile_order(P<uint2>(slot.ranges), tiles_of(cam, ko.tile_lw, ko.tile_lh), P<uint32_t>(slot.torder) + 1,
+                       P<uint32_t>(slot.torder), cs);
             size_t e2 = pt.begin(cs);
             launch_composite_score(a, cs);
             if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
@@ -1005,11 +1012,12 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
     return CSGS_OK;
 }
 
-// The call's conventions with the scene's tuned tile shape where the caller left the shape
-// to the library (CSGS_TILE_AUTO).
+// The call's conventions with the scene's tuned tile shape and persistent grid where the
+// caller left them to the library (CSGS_TILE_AUTO, persist_ctas 0).
 KOpts scene_kopts(const KOpts& ko, const SceneRec* s, const csgs_score_opts* opts) {
     KOpts k = ko;
     if (opts->tile_shape == CSGS_TILE_AUTO && s->tuned_shape) set_tile_shape(&k, s->tuned_shape);
+    if (opts->persist_ctas == 0) k.persist_ctas = s->tuned_persist;
     return k;
 }
 
@@ -1129,8 +1137,8 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
     // (the launches bake in the scene pointers, the host copies of the cameras and every
     // work-buffer address, so all of them are part of the key)
     for (int k = 0; k < n_scenes; ++k) {
-        const int64_t meta[6] = {(int64_t)sc[k]->cams.size(), vb[k], (int64_t)(uintptr_t)sc[k]->d_cams,
-                                 sc[k]->tuned_sb, kos[k].tile_lw, kos[k].tile_lh};
+        const int64_t meta[7] = {(int64_t)sc[k]->cams.size(), vb[k], (int64_t)(uintptr_t)sc[k]->d_cams,
+                                 sc[k]->tuned_sb, kos[k].tile_lw, kos[k].tile_lh, kos[k].persist_ctas};
         key.append((const char*)meta, sizeof(meta));
         const SceneDev sd = scene_dev(*sc[k]);
         key.append((const char*)&sd, sizeof(sd));
@@ -1211,7 +1219,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
 }
 
 csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, int32_t probe_views,
-                          int32_t* view_batch_out, int32_t* sort_blocks_out, int32_t* tile_shape_out) {
+                          csgs_tuning* out) {
     if (!ctx) return CSGS_E_INVAL;
     SceneRec* s = get_scene(ctx, scene_id);
     if (!s) return scene_fail(ctx, scene_id);
@@ -1295,6 +1303,26 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
             }
         }
     }
+    // persistent compositing launches (per-pixel score) of r, r - 1 and r - 2 CTAs per SM,
+    // r the kernel's resident limit (fewer leave SM slots to the binning that runs beside it)
+    int best_persist = ko.persist_ctas;
+    if (!r && opts->persist_ctas == 0 && ko.resolution == CSGS_RES_PIXEL) {
+        KOpts kk = ko;
+        set_tile_shape(&kk, best_shape);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        const int res = composite_resident_ctas(kk.tile_lw, kk.tile_lh);
+        for (int m = res; m >= res - 2 && m >= 1 && sms > 0; --m) {
+            kk.persist_ctas = m * sms;
+            kk.narrow_keys = ko.narrow_keys;
+            float t = 1e30f;
+            if ((r = trial(best_vb, best_g, kk, &t))) break;
+            if (t < best) {
+                best = t;
+                best_persist = kk.persist_ctas;
+            }
+        }
+    }
     if (r) {
         s->tuned_sb = saved_sb;
         return r;
@@ -1303,10 +1331,15 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
     s->tuned_vb = best_vb;
     ctx->sort_blocks = best_g;  // also the grid of scenes not tuned themselves
     if (opts->tile_shape == CSGS_TILE_AUTO && ko.resolution != CSGS_RES_TILE) s->tuned_shape = best_shape;
+    if (opts->persist_ctas == 0 && ko.resolution == CSGS_RES_PIXEL) s->tuned_persist = best_persist;
     ctx->graph_key.clear();
-    if (view_batch_out) *view_batch_out = best_vb;
-    if (sort_blocks_out) *sort_blocks_out = best_g;
-    if (tile_shape_out) *tile_shape_out = best_shape;
+    if (out) {
+        out->view_batch = best_vb;
+        out->sort_blocks = best_g;
+        out->tile_shape = best_shape;
+        out->persist_ctas = best_persist;
+        out->probe_ms = best;
+    }
     return CSGS_OK;
 }
 

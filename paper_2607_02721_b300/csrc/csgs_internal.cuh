@@ -57,6 +57,7 @@ struct KOpts {
     int resolution, variant;
     int narrow_keys;  // depth keys: 1 = narrow (27-bit, relative to the near plane), 0 = the float bits
     int tile_lw, tile_lh;  // tile shape: 2^tile_lw x 2^tile_lh pixels
+    int persist_ctas;      // per-pixel score: CTAs of a persistent compositing launch (0: one per tile)
 };
 
 // One projected Gaussian in one view (48 bytes, 16-byte aligned).
@@ -177,7 +178,8 @@ void emit_instances(const uint32_t* order, const uint2* rects, int n, int nv, co
                     unsigned long long* n_inst, cudaStream_t st);
 // The tiles of one view ordered by descending list length, in power-of-two classes
 // (order within a class unspecified): order[0..T) is a permutation of the tile ids.
-void tile_order(const uint2* ranges, int T, uint32_t* order, cudaStream_t st);
+// work (may be null): a persistent compositing launch's queue counter, set to zero.
+void tile_order(const uint2* ranges, int T, uint32_t* order, uint32_t* work, cudaStream_t st);
 // ranges[v][tile] = [start, end) of each (view, tile) key in the sorted instance keys
 // (rows of max_tiles ranges per view; tiles of 2^lw x 2^lh pixels).
 void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n_max, uint2* ranges, int nv,
@@ -188,6 +190,7 @@ void set_u64(unsigned long long* p, unsigned long long v, cudaStream_t st);
 struct CompositeArgs {
     const uint2* ranges;
     const uint32_t* order;  // tile of CTA b = order[b] (longest lists first), or null: tile b
+    uint32_t* work;         // persistent launch: queue counter (zero at launch), or null
     const uint32_t* inst_gid;
     const Splat* splats;
     int n_gauss;
@@ -211,6 +214,8 @@ void launch_composite_render(const CompositeArgs& a, cudaStream_t st);
 void launch_composite_score(const CompositeArgs& a, cudaStream_t st);
 void launch_composite_transfer(const CompositeArgs& a, cudaStream_t st);
 void launch_composite_backward(const CompositeArgs& a, cudaStream_t st);
+// Resident CTAs per SM of the persistent per-pixel score kernel for tiles of 2^lw x 2^lh.
+int composite_resident_ctas(int lw, int lh);
 
 // ---- sampling (k_sample.cu)
 struct SampleTemp {

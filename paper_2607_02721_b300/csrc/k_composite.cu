@@ -101,6 +101,7 @@ struct Shared {
         float part[NW][NT];    // summed modes: the warps' term sums per slot
     };
     int last;
+    int item;  // persistent launch: the queue position the CTA took
     double sumA[NW];
 };
 
@@ -249,12 +250,11 @@ __device__ __forceinline__ float pass1_objective(const KOpts& o, float A0, float
     return pixel_objective<VAR>(o, A0, A1, A2);
 }
 
+// One tile of the view (all threads of the CTA; shared memory is free again on return).
 template <int MODE, int VAR, bool STATS, class TC>
-__global__ void __launch_bounds__(TC::kThreads) k_composite(const CompositeArgs a) {
+__device__ __forceinline__ void composite_tile(const CompositeArgs& a, Shared<TC>& sh, const int tile) {
     constexpr int kThreads = TC::kThreads, kWarps = TC::kWarps;
-    __shared__ Shared<TC> sh;
     const CamDev& cam = a.cam;
-    const int tile = a.order ? (int)__ldg(a.order + blockIdx.x) : (int)blockIdx.x;
     const int ntx = tiles_x_of(cam, TC::kLw);
     const int tx = tile % ntx, ty = tile / ntx;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -603,6 +603,27 @@ __global__ void __launch_bounds__(TC::kThreads) k_composite(const CompositeArgs 
     }
 }
 
+// A launch of one CTA per tile (CTA b takes tile order[b]), or a persistent launch
+// (PERSIST): fewer CTAs, each taking the next position of the order from a counter
+// (a.work, zero at launch) until the view's tiles are used up.
+template <int MODE, int VAR, bool STATS, class TC, bool PERSIST>
+__global__ void __launch_bounds__(TC::kThreads) k_composite(const CompositeArgs a) {
+    __shared__ Shared<TC> sh;
+    if (!PERSIST) {
+        composite_tile<MODE, VAR, STATS, TC>(a, sh, a.order ? (int)__ldg(a.order + blockIdx.x) : (int)blockIdx.x);
+        return;
+    }
+    const int T = tiles_of(a.cam, TC::kLw, TC::kLh);
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = (int)atomicAdd(a.work, 1u);
+        __syncthreads();
+        const int item = sh.item;
+        __syncthreads();  // every thread has read the position before the next one is taken
+        if (item >= T) break;
+        composite_tile<MODE, VAR, STATS, TC>(a, sh, a.order ? (int)__ldg(a.order + item) : item);
+    }
+}
+
 // Backward of the render (Sec. 3's compositing, back to front): for contributor i of a
 // pixel, with S the colour composited behind it,
 //   dC/dc_i = rho_i T_i,  dC/drho_i = c_i T_i - S / (1 - rho_i),  T_i = T_{i+1} / (1 - rho_i),
@@ -728,6 +749,20 @@ __global__ void __launch_bounds__(Tile16x16::kThreads) k_composite_bwd(const Com
 
 // The backward and the per-tile resolution (whose query is a 16x16 tile) run on 16x16 tiles
 // only; the other modes on the shape in a.o (tile_lw, tile_lh).
+int composite_resident_ctas(int lw, int lh) {
+    int r = 0;
+    if (lw == 5 && lh == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_composite<kScorePixel, kL1, false, Tile32x8, true>,
+                                                      Tile32x8::kThreads, 0);
+    else if (lw == 4 && lh == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_composite<kScorePixel, kL1, false, Tile16x8, true>,
+                                                      Tile16x8::kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_composite<kScorePixel, kL1, false, Tile16x16, true>,
+                                                      Tile16x16::kThreads, 0);
+    return r;
+}
+
 void launch_composite_backward(const CompositeArgs& a, cudaStream_t st) {
     const int tiles = tiles_of(a.cam, Tile16x16::kLw, Tile16x16::kLh);
     k_composite_bwd<<<tiles, Tile16x16::kThreads, 0, st>>>(a);
@@ -736,7 +771,13 @@ void launch_composite_backward(const CompositeArgs& a, cudaStream_t st) {
 
 template <int MODE, int VAR, bool STATS, class TC>
 static void launch_one(const CompositeArgs& a, cudaStream_t st) {
-    k_composite<MODE, VAR, STATS, TC><<<tiles_of(a.cam, TC::kLw, TC::kLh), TC::kThreads, 0, st>>>(a);
+    const int tiles = tiles_of(a.cam, TC::kLw, TC::kLh);
+    // persistent launches for the per-pixel score (the timed path); the other modes take
+    // one CTA per tile
+    if (MODE == kScorePixel && a.work && a.o.persist_ctas > 0 && a.o.persist_ctas < tiles)
+        k_composite<MODE, VAR, STATS, TC, MODE == kScorePixel><<<a.o.persist_ctas, TC::kThreads, 0, st>>>(a);
+    else
+        k_composite<MODE, VAR, STATS, TC, false><<<tiles, TC::kThreads, 0, st>>>(a);
 }
 
 template <int MODE, int VAR, bool STATS>

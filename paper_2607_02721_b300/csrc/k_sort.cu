@@ -454,10 +454,11 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const unsigned long 
 // last.  One CTA: class counts, class offsets, then each tile at its class's next slot;
 // the lanes of a warp with the same class share one shared-memory atomic.
 __global__ void __launch_bounds__(1024) k_tile_order(const uint2* __restrict__ ranges, int T,
-                                                     uint32_t* __restrict__ order) {
+                                                     uint32_t* __restrict__ order, uint32_t* __restrict__ work) {
     __shared__ uint32_t cnt[34];
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 34) cnt[tid] = 0u;
+    if (tid == 0 && work) *work = 0u;
     __syncthreads();
     for (int t0 = 0; t0 < T; t0 += 1024) {
         const int t = t0 + tid;
@@ -564,8 +565,8 @@ void tile_ranges(const uint32_t* keys, const unsigned long long* d_n, uint32_t n
     count_launches(1);
 }
 
-void tile_order(const uint2* ranges, int T, uint32_t* order, cudaStream_t st) {
-    k_tile_order<<<1, 1024, 0, st>>>(ranges, T, order);
+void tile_order(const uint2* ranges, int T, uint32_t* order, uint32_t* work, cudaStream_t st) {
+    k_tile_order<<<1, 1024, 0, st>>>(ranges, T, order, work);
     count_launches(1);
 }
 

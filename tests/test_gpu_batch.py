@@ -146,16 +146,38 @@ def test_autotune_keeps_scores(ctx, scenes):
     fixed = csgs.default_opts(tile_shape=csgs.TILE_16X16)
     ref, Sref = ctx.score(scenes[1], fixed)
     ref = ref.cpu().numpy()
-    vb, g, shape = ctx.autotune(scenes[1], csgs.default_opts(), probe_views=4)
-    assert vb in (1, 2, 4) and g in (148, 296, 592, 1184, 1776)
-    assert shape in (csgs.TILE_16X16, csgs.TILE_32X8, csgs.TILE_16X8)
+    tu = ctx.autotune(scenes[1], csgs.default_opts(), probe_views=4)
+    assert tu["view_batch"] in (1, 2, 4) and tu["sort_blocks"] in (148, 296, 592, 1184, 1776)
+    assert tu["tile_shape"] in (csgs.TILE_16X16, csgs.TILE_32X8, csgs.TILE_16X8)
+    assert tu["persist_ctas"] == 0 or tu["persist_ctas"] % 148 == 0 and tu["probe_ms"] > 0
     s, S = ctx.score(scenes[1], fixed)
     np.testing.assert_array_equal(s.cpu().numpy(), ref)
     assert S == Sref
     auto, Sa = ctx.score(scenes[1], csgs.default_opts())
-    expl, Se = ctx.score(scenes[1], csgs.default_opts(tile_shape=shape))
+    expl, Se = ctx.score(scenes[1], csgs.default_opts(tile_shape=tu["tile_shape"]))
     np.testing.assert_array_equal(auto.cpu().numpy(), expl.cpu().numpy())
     assert Sa == Se
+
+
+@pytest.mark.parametrize("shape", [csgs.TILE_16X16, csgs.TILE_16X8], ids=["16x16", "16x8"])
+def test_persistent_compositing_matches_one_cta_per_tile(ctx, scenes, shape):
+    """The persistent launch (few CTAs taking tiles from a queue, longest lists first) gives
+    the per-tile launch's per-pixel scores bit for bit, for grids below, at and above the
+    tile count, in a single call and in a replayed batch graph."""
+    base = csgs.default_opts(tile_shape=shape, persist_ctas=-1)
+    ref_s, ref_S = one_by_one(ctx, scenes, base)
+    for grid in (1, 37, 148, 100000):
+        opts = csgs.default_opts(tile_shape=shape, persist_ctas=grid)
+        s, S = one_by_one(ctx, scenes, opts)
+        for k in range(len(scenes)):
+            np.testing.assert_array_equal(s[k], ref_s[k])
+            assert S[k] == ref_S[k]
+    opts = csgs.default_opts(tile_shape=shape, persist_ctas=37)
+    outs, _ = ctx.score_batch(scenes, opts, use_graph=True)
+    outs, S = ctx.score_batch(scenes, opts, outs=outs, use_graph=True)
+    for k in range(len(scenes)):
+        np.testing.assert_array_equal(outs[k].cpu().numpy(), ref_s[k])
+        assert S[k] == ref_S[k]
 
 
 @pytest.mark.parametrize("shape", [csgs.TILE_32X8, csgs.TILE_16X8], ids=["32x8", "16x8"])
