@@ -548,7 +548,7 @@ def surrogate_record(ctx, sid, cams, m, cfg, sopts, psnr_stride: int):
     s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, cfg, opts=sopts, timings=tim)
     views = list(range(0, len(cams), psnr_stride))
     res = {"exact_ms": exact_ms, "surrogate_ms": tim["total_ms"], "speedup": exact_ms / tim["total_ms"],
-           "phases_ms": tim, "train_views": cfg.train_views, "train_steps": cfg.steps,
+           "phases_ms": tim, "train_views": cfg.train_views, "train_steps": cfg.steps, "train_batch": cfg.batch,
            "lowres_factor": cfg.lowres_factor, "cheap_stride": cfg.cheap_stride, "train_lr": cfg.lr,
            "fill_only": cfg.fill_only, "aug_views": list(cfg.aug_views), "residual": cfg.residual,
            "psnr_views": len(views), "prune_ratio": 0.9}
@@ -601,6 +601,10 @@ def run_surrogate(args):
     scfg = surrogate.SurrogateConfig(train_views=args.train_views, steps=args.train_steps, fill_only=args.fill_only,
                                      aug_views=tuple(int(x) for x in args.aug_views.split(",") if x),
                                      lowres_factor=args.lowres_factor, residual=not args.surrogate_direct)
+    if args.train_batch:
+        scfg.batch = args.train_batch
+    if args.train_lr:
+        scfg.lr = args.train_lr
     rec, s_exact, s_hat = surrogate_record(ctx, sid, cams, m, scfg, sopts, args.psnr_stride)
     res = {"mode": "surrogate", "config": cfg, "resolution": args.resolution}
     res.update(rec)
@@ -923,6 +927,8 @@ def main():
     ap.add_argument("--surrogate", action="store_true", help="surrogate-assisted vs exact scoring report")
     ap.add_argument("--train-views", type=int, default=20)
     ap.add_argument("--train-steps", type=int, default=100)
+    ap.add_argument("--train-batch", type=int, default=0, help="surrogate training rows per step (0: default)")
+    ap.add_argument("--train-lr", type=float, default=0.0, help="surrogate learning rate (0: default)")
     ap.add_argument("--psnr-stride", type=int, default=5)
     ap.add_argument("--fill-only", action="store_true")
     ap.add_argument("--surrogate-direct", action="store_true",

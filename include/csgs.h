@@ -225,7 +225,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
 /* Choose, for one scene, the view batch (views projected per launch), the radix-sort
  * grid, the tile shape and the persistent compositing grid by timing csgs_score's work
  * on the first probe_views query views (0: min(16, views)), one dimension after the
- * other: view batches {1,2,4,8,16} x sort grids {148,296,592,1184,1776} blocks at the
+ * other: view batches {1,2,4,8,16} x sort grids {74,148,296,592,1184,1776} blocks at the
  * requested shape (16x16 for CSGS_TILE_AUTO); then, for CSGS_TILE_AUTO (and not the
  * per-tile resolution), the shapes 32x8 and 16x8 at the best pair; then, for the
  * per-pixel score with opts->persist_ctas 0, persistent launches of r, r - 1 and r - 2

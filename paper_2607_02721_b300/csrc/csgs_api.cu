@@ -97,7 +97,7 @@ struct csgs_ctx {
     DevBuf mskbx[kCompStreams - 1], tsumx[kCompStreams - 1];  // ... and tile sums, for the other streams
     // surrogate model
     bool mlp_ready = false;
-    DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mZ1, mH1, mDz2, mDz1, mPart;
+    DevBuf mP, mM, mV, mG, mW1b, mW2b, mW2Tb, mY, mXb, mTb, mLoss, mGd1, mH1, mDz2, mDz1, mPart;
     int64_t mlp_rows = 0;
     DevBuf bRgb, bT, bLast, g2d;  // render backward
     csgs_stats stats{};
@@ -601,7 +601,7 @@ void csgs_destroy(csgs_ctx* ctx) {
                       &ctx->stmp,   &ctx->nout,    &ctx->p,       &ctx->wfull,   &ctx->tsum,    &ctx->vbuf,
                       &ctx->mskb,
                       &ctx->mP,     &ctx->mM,      &ctx->mV,      &ctx->mG,      &ctx->mW1b,    &ctx->mW2b,
-                      &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mZ1,
+                      &ctx->mW2Tb,  &ctx->mY,      &ctx->mXb,     &ctx->mTb,     &ctx->mLoss,   &ctx->mGd1,
                       &ctx->mH1,    &ctx->mDz2,    &ctx->mDz1,    &ctx->mPart,   &ctx->bRgb,    &ctx->bT,      &ctx->bLast,
                       &ctx->g2d};
     for (DevBuf* b : bufs) release(*b);
@@ -1231,9 +1231,9 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
     const int nv = (int)s->cams.size();
     const int pv = probe_views > 0 && probe_views < nv ? probe_views : (nv < 16 ? nv : 16);
     const int vbs[5] = {1, 2, 4, 8, 16};
-    // radix-sort grids: from one CTA per SM (binning holds few SM slots beside the
-    // compositing) to twelve (binning alone as fast as it goes)
-    const int gs[5] = {148, 148 * 2, 148 * 4, 148 * 8, 148 * 12};
+    // radix-sort grids: from one CTA per two SMs (binning holds few SM slots beside the
+    // compositing) to twelve per SM (binning alone as fast as it goes)
+    const int gs[6] = {74, 148, 148 * 2, 148 * 4, 148 * 8, 148 * 12};
     float* s_tmp = nullptr;
     CUDA_TRY(ctx, cudaMalloc(&s_tmp, sizeof(float) * (size_t)s->n));
     std::unique_ptr<float, cudaError_t (*)(void*)> s_tmp_owner(s_tmp, cudaFree);
@@ -1648,7 +1648,7 @@ csgs_status mlp_alloc(csgs_ctx* ctx) {
 csgs_status mlp_rows_buffers(csgs_ctx* ctx, int64_t B) {
     csgs_status r;
     if ((r = ensure(ctx, ctx->mY, sizeof(float) * B)) || (r = ensure(ctx, ctx->mXb, 2 * 64 * (size_t)B)) ||
-        (r = ensure(ctx, ctx->mTb, sizeof(float) * B)) || (r = ensure(ctx, ctx->mZ1, sizeof(float) * 256 * (size_t)B)) ||
+        (r = ensure(ctx, ctx->mTb, sizeof(float) * B)) || (r = ensure(ctx, ctx->mGd1, sizeof(float) * 256 * (size_t)B)) ||
         (r = ensure(ctx, ctx->mH1, 2 * 256 * (size_t)B)) || (r = ensure(ctx, ctx->mDz2, 2 * 256 * (size_t)B)) ||
         (r = ensure(ctx, ctx->mDz1, 2 * 256 * (size_t)B)) ||
         (r = ensure(ctx, ctx->mPart, sizeof(float) * (size_t)mlp_wgrad_splits(B) * (256 * 256 + 256 * 64))))
@@ -1663,7 +1663,7 @@ MlpBufs mlp_bufs(csgs_ctx* ctx) {
 
 MlpTemp mlp_temp(csgs_ctx* ctx) {
     MlpTemp t;
-    t.z1 = P<float>(ctx->mZ1);
+    t.gd1 = P<float>(ctx->mGd1);
     t.h1 = P<__nv_bfloat16>(ctx->mH1);
     t.dz2 = P<__nv_bfloat16>(ctx->mDz2);
     t.dz1 = P<__nv_bfloat16>(ctx->mDz1);

@@ -267,7 +267,7 @@ struct MlpBufs {
     __nv_bfloat16* W2Tb;  // [256][256] transpose of W2
 };
 struct MlpTemp {
-    float* z1;            // [B][256]
+    float* gd1;           // [B][256] GELU'(z1)
     __nv_bfloat16* h1;    // [B][256]
     __nv_bfloat16* dz2;   // [B][256]
     __nv_bfloat16* dz1;   // [B][256]

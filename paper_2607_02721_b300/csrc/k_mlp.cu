@@ -181,9 +181,51 @@ __device__ __forceinline__ f32x2 gelu2(f32x2 z) {
     const f32x2 onep = add2(f2c(1.f), f2(copysignf(r0, x0), copysignf(r1, x1)));
     return mul2(mul2(f2c(0.5f), z), onep);
 }
+// GELU and its derivative from one reciprocal and one exponential: with x = z / sqrt 2,
+// erf's factor exp(-x^2) = exp(-z^2 / 2) is also sqrt(2 pi) phi(z).  g is gelu(z) bit for
+// bit (the same operations); gd = Phi(z) + z phi(z).
+__device__ __forceinline__ void gelu_both(float z, float& g, float& gd) {
+    const float x = z * 0.70710678118654752f;
+    const float ax = fabsf(x);
+    const float t = rcp_fast(fmaf(0.3275911f, ax, 1.f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    poly *= t;
+    const float e = ex2_fast(-ax * ax * 1.4426950408889634f);
+    const float er = copysignf(fmaf(-poly, e, 1.f), x);
+    g = 0.5f * z * (1.f + er);
+    gd = fmaf(0.5f, er, 0.5f) + z * e * 0.39894228040143268f;
+}
 __device__ __forceinline__ float gelu_d(float z) {
-    return fmaf(0.5f, erf_as(z * 0.70710678118654752f), 0.5f) +
-           z * ex2_fast(-0.5f * 1.4426950408889634f * z * z) * 0.39894228040143268f;
+    float g, gd;
+    gelu_both(z, g, gd);
+    return gd;
+}
+
+// gelu_both() of two values with the packed instructions, bit for bit the scalar results
+// (the operations of gelu2, then gd as in gelu_both).
+__device__ __forceinline__ void gelu2_both(f32x2 z, f32x2& g, f32x2& gd) {
+    const f32x2 x = mul2(z, f2c(0.70710678118654752f));
+    float x0, x1;
+    f2split(x, x0, x1);
+    float d0, d1;
+    f2split(fma2(f2c(0.3275911f), f2(fabsf(x0), fabsf(x1)), f2c(1.f)), d0, d1);
+    const f32x2 t = f2(rcp_fast(d0), rcp_fast(d1));
+    f32x2 np = fma2(t, f2c(-1.061405429f), f2c(1.453152027f));
+    np = fma2(t, np, f2c(-1.421413741f));
+    np = fma2(t, np, f2c(0.284496736f));
+    np = fma2(t, np, f2c(-0.254829592f));
+    np = mul2(np, t);
+    float a0, a1;
+    f2split(mul2(mul2(x, x), f2c(-1.4426950408889634f)), a0, a1);
+    const f32x2 e = f2(ex2_fast(a0), ex2_fast(a1));
+    float r0, r1;
+    f2split(fma2(np, e, f2c(1.f)), r0, r1);
+    const f32x2 er = f2(copysignf(r0, x0), copysignf(r1, x1));
+    g = mul2(mul2(f2c(0.5f), z), add2(f2c(1.f), er));
+    gd = add2(fma2(f2c(0.5f), er, f2c(0.5f)), mul2(mul2(z, e), f2c(0.39894228040143268f)));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -268,12 +310,12 @@ __device__ __forceinline__ void mma_tile_k(uint32_t d, const unsigned char* a, i
 }
 
 // 512 threads: warp w reads TMEM lanes 32 (w % 4).. and handles column quarter w / 4.
-// TRAIN additionally stores z1 (FP32), h1 (BF16) and dz2 = d loss / d z2 (BF16) per row
+// TRAIN additionally stores GELU'(z1) (FP32), h1 (BF16) and dz2 = d loss / d z2 (BF16) per row
 // (loss = mean (y - t)^2 over the B rows) and accumulates d/dw3, d/db3 and the loss.
 template <bool TRAIN>
 __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __restrict__ X, int B, MlpDev p,
                                                      float* __restrict__ y, const float* __restrict__ t,
-                                                     float* __restrict__ z1o, __nv_bfloat16* __restrict__ h1o,
+                                                     float* __restrict__ gd1o, __nv_bfloat16* __restrict__ h1o,
                                                      __nv_bfloat16* __restrict__ dz2o, float* __restrict__ gw3,
                                                      float* __restrict__ gb3, float* __restrict__ loss, float inv_B,
                                                      int* err) {
@@ -354,19 +396,31 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
                     z[2 * i] = add2(f2(v[4 * i], v[4 * i + 1]), f2(b.x, b.y));
                     z[2 * i + 1] = add2(f2(v[4 * i + 2], v[4 * i + 3]), f2(b.z, b.w));
                 }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) f2split(z[i], v[2 * i], v[2 * i + 1]);
-                if (TRAIN && valid) {
-                    float4* zo = reinterpret_cast<float4*>(z1o + (size_t)(r0 + row) * kH + c_base + c);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) zo[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                }
                 uint32_t pk[8];
+                if (TRAIN) {
+                    // GELU'(z1) for the backward, from the same reciprocal and exponential
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    float g0, g1;
-                    f2split(gelu2(z[i]), g0, g1);
-                    pk[i] = pack_bf16(g0, g1);
+                    for (int i = 0; i < 8; ++i) {
+                        f32x2 g, gd;
+                        gelu2_both(z[i], g, gd);
+                        float g0, g1;
+                        f2split(g, g0, g1);
+                        pk[i] = pack_bf16(g0, g1);
+                        f2split(gd, v[2 * i], v[2 * i + 1]);
+                    }
+                    if (valid) {
+                        float4* go = reinterpret_cast<float4*>(gd1o + (size_t)(r0 + row) * kH + c_base + c);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            go[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        float g0, g1;
+                        f2split(gelu2(z[i]), g0, g1);
+                        pk[i] = pack_bf16(g0, g1);
+                    }
                 }
                 *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c, kHc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 *reinterpret_cast<uint4*>(sH + tc::kmajor_off(row, c + 8, kHc)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -429,9 +483,10 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
                 tc::tmem_ld16(tl + 256u + (uint32_t)c0, v);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const float z = v[i] + sb2[c0 + i];
-                    g[i] = dy * gelu(z);  // this row's d loss / d w3
-                    v[i] = dy * sw3[c0 + i] * gelu_d(z);
+                    float ge, gd;
+                    gelu_both(v[i] + sb2[c0 + i], ge, gd);
+                    g[i] = dy * ge;  // this row's d loss / d w3
+                    v[i] = dy * sw3[c0 + i] * gd;
                 }
                 const float cs = warp_colsum16(g, lane);
                 if ((lane & 1) == 0) {
@@ -482,11 +537,12 @@ __global__ void __launch_bounds__(512, 1) k_mlp_fwd2(const __nv_bfloat16* __rest
     if (warp == 0) tc::tmem_dealloc(taddr, 512);
 }
 
-// dz1 = (dz2 W2) * GELU'(z1), BF16 out; smem A = dz2 tile (64 KB), B = W2^T (128 KB,
+// dz1 = (dz2 W2) * GELU'(z1) (GELU'(z1) stored by the training forward), BF16 out; smem
+// A = dz2 tile (64 KB), B = W2^T (128 KB,
 // resident).  512 threads: warp w reads TMEM lanes 32 (w % 4).. and handles column
 // quarter w / 4; the next tile's dz2 rows are loaded into registers while the tensor
 // core works on the current one.
-__global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restrict__ dz2, const float* __restrict__ z1,
+__global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restrict__ dz2, const float* __restrict__ gd1,
                                                     int B, MlpDev p, __nv_bfloat16* __restrict__ dz1, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = align1k(smem_raw);
@@ -547,19 +603,19 @@ __global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restr
             float v[16];
             tc::tmem_ld16(tl + (uint32_t)c0, v);
             if (valid) {
-                const float4* zr = reinterpret_cast<const float4*>(z1 + (size_t)(r0 + row) * kH + c0);
-                float zz[16];
+                const float4* gr = reinterpret_cast<const float4*>(gd1 + (size_t)(r0 + row) * kH + c0);
+                float gd[16];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float4 f = zr[i];
-                    zz[4 * i] = f.x;
-                    zz[4 * i + 1] = f.y;
-                    zz[4 * i + 2] = f.z;
-                    zz[4 * i + 3] = f.w;
+                    const float4 f = gr[i];
+                    gd[4 * i] = f.x;
+                    gd[4 * i + 1] = f.y;
+                    gd[4 * i + 2] = f.z;
+                    gd[4 * i + 3] = f.w;
                 }
                 uint32_t pk[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i] * gelu_d(zz[2 * i]), v[2 * i + 1] * gelu_d(zz[2 * i + 1]));
+                for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i] * gd[2 * i], v[2 * i + 1] * gd[2 * i + 1]);
                 uint4* o = reinterpret_cast<uint4*>(dz1 + (size_t)(r0 + row) * kH + c0);
                 o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
@@ -760,12 +816,24 @@ __global__ void k_sum_partials(const float* __restrict__ part, int splits, int n
 __global__ void k_debug_gelu(const float* __restrict__ z, int n, float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    // the packed evaluation the network's epilogues use, in both lanes (lane 1 holds -z);
-    // it must equal the scalar gelu() bit for bit, else the value is reported as NaN
-    float g, gm;
+    // the packed evaluations the network's epilogues use, in both lanes (lane 1 holds -z);
+    // they must equal the scalar gelu() / gelu_d() bit for bit, else the value is reported
+    // as NaN
+    float g, gm, b0, b1, d0, d1;
     f2split(gelu2(f2(z[i], -z[i])), g, gm);
+    f32x2 gb, gdb;
+    gelu2_both(f2(z[i], -z[i]), gb, gdb);
+    f2split(gb, b0, b1);
+    f2split(gdb, d0, d1);
+    float s0, sd0, s1, sd1;
+    gelu_both(z[i], s0, sd0);
+    gelu_both(-z[i], s1, sd1);
     const bool same = __float_as_uint(g) == __float_as_uint(gelu(z[i])) &&
-                      __float_as_uint(gm) == __float_as_uint(gelu(-z[i]));
+                      __float_as_uint(gm) == __float_as_uint(gelu(-z[i])) &&
+                      __float_as_uint(b0) == __float_as_uint(g) && __float_as_uint(b1) == __float_as_uint(gm) &&
+                      __float_as_uint(s0) == __float_as_uint(g) && __float_as_uint(s1) == __float_as_uint(gm) &&
+                      __float_as_uint(d0) == __float_as_uint(sd0) && __float_as_uint(d1) == __float_as_uint(sd1) &&
+                      __float_as_uint(sd0) == __float_as_uint(gelu_d(z[i]));
     out[2 * i] = same ? g : __int_as_float(0x7fc00000);
     out[2 * i + 1] = gelu_d(z[i]);
 }
@@ -806,11 +874,11 @@ void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float*
     const size_t smem_f = (size_t)kH * kIn * 2 + (size_t)kH * kH * 2 + (size_t)kRows * kIn * 2 +
                           (size_t)kRows * kHc * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_fwd2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
-    k_mlp_fwd2<true><<<fwd_grid(B), 512, smem_f, st>>>(Xb, B, d, y, t, tmp.z1, tmp.h1, tmp.dz2, gw3, gb3, loss,
+    k_mlp_fwd2<true><<<fwd_grid(B), 512, smem_f, st>>>(Xb, B, d, y, t, tmp.gd1, tmp.h1, tmp.dz2, gw3, gb3, loss,
                                                        1.f / (float)B, err);
     const size_t smem_d = (size_t)kRows * kH * 2 + (size_t)kH * kH * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_dh1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
-    k_mlp_dh1<<<fwd_grid(B), 512, smem_d, st>>>(tmp.dz2, tmp.z1, B, d, tmp.dz1, err);
+    k_mlp_dh1<<<fwd_grid(B), 512, smem_d, st>>>(tmp.dz2, tmp.gd1, B, d, tmp.dz1, err);
     const int splits = mlp_wgrad_splits(B);
     const int rows_per_cta = (B + splits - 1) / splits;
     float* part2 = tmp.wpart;
