@@ -421,6 +421,13 @@ csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t n, int64_t 
 csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
                                int32_t N);
 
+/* Diagnostic of the MN-major operand layout (used by the network's weight gradients):
+ * C[128][N] = A^T B with A given as [K][128] and B as [K][N] (BF16, device, row-major),
+ * both staged in the no-swizzle MN-major layout, FP32 C (device).  Shapes and errors as
+ * csgs_debug_tc_gemm. */
+csgs_status csgs_debug_tc_gemm_mn(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                                  int32_t N);
+
 /* Diagnostic of the bounded device waits: csgs_debug_tc_gemm with the threads' wait for
  * the MMA chain's completion limited to first_wait_cycles SM clock cycles (0: a single
  * non-blocking test of the completion barrier, which an MMA chain issued a moment

@@ -91,7 +91,7 @@ EXPORTS = ("csgs_default_opts", "csgs_create", "csgs_destroy", "csgs_last_error"
            "csgs_free_scene", "csgs_set_queries", "csgs_score", "csgs_sample_coreset", "csgs_sample_coreset_p",
            "csgs_render", "csgs_sync", "csgs_get_stats", "csgs_debug_project", "csgs_kernel_launch_count",
            "csgs_sample_coreset_noalloc", "csgs_transfer", "csgs_theorem2_sample_size", "csgs_theorem3_eps",
-           "csgs_debug_tc_gemm", "csgs_debug_tc_gemm_wait", "csgs_scale_scores", "csgs_total_sensitivity", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
+           "csgs_debug_tc_gemm", "csgs_debug_tc_gemm_mn", "csgs_debug_tc_gemm_wait", "csgs_scale_scores", "csgs_total_sensitivity", "csgs_mlp_init", "csgs_mlp_set_params", "csgs_mlp_get_params", "csgs_mlp_forward",
            "csgs_mlp_gradient", "csgs_mlp_train", "csgs_view_stats", "csgs_features", "csgs_log_target",
            "csgs_surrogate_combine", "csgs_update_scene", "csgs_render_backward", "csgs_adam_update",
            "csgs_score_batch", "csgs_autotune", "csgs_debug_gelu", "csgs_log_ratio_mean", "csgs_log_residual_target",
@@ -135,6 +135,7 @@ def lib():
     L.csgs_theorem3_eps.argtypes = [ctypes.c_double, ctypes.c_double]
     L.csgs_theorem3_eps.restype = ctypes.c_double
     L.csgs_debug_tc_gemm.argtypes = [V, V, V, V, I32, I32]
+    L.csgs_debug_tc_gemm_mn.argtypes = [V, V, V, V, I32, I32]
     L.csgs_debug_tc_gemm_wait.argtypes = [V, V, V, V, I32, I32, ctypes.c_int64]
     L.csgs_scale_scores.argtypes = [V, V, ctypes.c_int64, ctypes.c_double]
     L.csgs_total_sensitivity.argtypes = [V, V, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
@@ -537,6 +538,16 @@ class Context:
         C = self._empty((A.shape[0], B.shape[0]), torch.float32)
         self._in()
         self._check(lib().csgs_debug_tc_gemm(self.h, _ptr(A), _ptr(B), _ptr(C), A.shape[1], B.shape[0]))
+        self._out()
+        return C
+
+    def debug_tc_gemm_mn(self, At, Bt):
+        """C = At^T @ Bt on the tensor cores with MN-major operands (At: [K, 128] bf16,
+        Bt: [K, N] bf16)."""
+        torch = self.torch
+        C = self._empty((At.shape[1], Bt.shape[1]), torch.float32)
+        self._in()
+        self._check(lib().csgs_debug_tc_gemm_mn(self.h, _ptr(At), _ptr(Bt), _ptr(C), At.shape[0], Bt.shape[1]))
         self._out()
         return C
 

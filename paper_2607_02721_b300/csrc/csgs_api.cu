@@ -1475,14 +1475,14 @@ csgs_status csgs_render(csgs_ctx* ctx, int32_t scene_id, int32_t view, const int
 int64_t csgs_kernel_launch_count(void) { return (int64_t)launches(); }
 
 static csgs_status tc_gemm_common(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
-                                  int32_t N, long long first_wait) {
+                                  int32_t N, long long first_wait, int mn_major = 0) {
     if (!ctx) return CSGS_E_INVAL;
     if (!A_dev || !B_dev || !C_dev) return fail(ctx, CSGS_E_INVAL, "null argument");
     if (K < 16 || K > 128 || K % 16 || N < 16 || N > 256 || N % 16)
         return fail(ctx, CSGS_E_INVAL, "unsupported GEMM shape K=%d N=%d", K, N);
     cudaSetDevice(ctx->device);
     CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
-    gemm_check(A_dev, B_dev, C_dev, K, N, reinterpret_cast<int*>(&ctx->d_ctr->err), first_wait, ctx->st);
+    gemm_check(A_dev, B_dev, C_dev, K, N, reinterpret_cast<int*>(&ctx->d_ctr->err), first_wait, mn_major, ctx->st);
     csgs_status r;
     if ((r = launch_check(ctx, "tensor-core GEMM"))) return r;
     if ((r = read_counters(ctx))) return r;
@@ -1494,6 +1494,11 @@ static csgs_status tc_gemm_common(csgs_ctx* ctx, const void* A_dev, const void* 
 csgs_status csgs_debug_tc_gemm(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
                                int32_t N) {
     return tc_gemm_common(ctx, A_dev, B_dev, C_dev, K, N, -1);
+}
+
+csgs_status csgs_debug_tc_gemm_mn(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,
+                                  int32_t N) {
+    return tc_gemm_common(ctx, A_dev, B_dev, C_dev, K, N, -1, 1);
 }
 
 csgs_status csgs_debug_tc_gemm_wait(csgs_ctx* ctx, const void* A_dev, const void* B_dev, float* C_dev, int32_t K,

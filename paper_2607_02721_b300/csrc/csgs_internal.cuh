@@ -253,7 +253,7 @@ void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const Sa
 // ---- tensor cores (k_mlp.cu)
 // first_wait: clock cycles of the completion wait (< 0: the kernels' full budget, 0: one
 // non-blocking test); *d_err |= 1 when it ran out (2 if even the drain wait did)
-int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, long long first_wait,
+int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, long long first_wait, int mn_major,
                cudaStream_t st);
 // out[2i] = GELU(z[i]), out[2i+1] = GELU'(z[i]) with the surrogate kernels' device functions
 void debug_gelu(const float* z, int n, float* out, cudaStream_t st);

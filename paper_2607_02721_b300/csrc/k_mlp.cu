@@ -13,10 +13,11 @@ constexpr long long kWaitBudget = 2000000000LL;  // ~1 s at 2 GHz; a wait beyond
 // N % 16 == 0, 16 <= N <= 256.  first_wait: clock cycles the threads wait for the MMA
 // chain's completion (0: one non-blocking test); a warp that gives up sets *err and then
 // waits the full budget for the chain to drain, so no MMA is in flight when the tensor
-// memory is freed.
+// memory is freed.  mn_major: A is given as [K][128] and B as [K][N] (C = A^T B) and both
+// are staged in the MN-major layout.
 __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restrict__ A,
                                                     const __nv_bfloat16* __restrict__ B, float* __restrict__ C,
-                                                    int K, int N, int* err, long long first_wait) {
+                                                    int K, int N, int* err, long long first_wait, int mn_major) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // operand tiles start on a 1024-byte boundary
     unsigned char* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -29,16 +30,30 @@ __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restr
         tc::mbar_init(&bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // stage A (row tid) and B (rows tid, tid + 128) in the K-major core-matrix layout
-    for (int k8 = 0; k8 < K / 8; ++k8) {
-        const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)tid * K + k8 * 8);
-        *reinterpret_cast<uint4*>(sA + tc::kmajor_off(tid, k8 * 8, K)) = v;
-    }
-    for (int r = tid; r < N; r += 128)
+    if (!mn_major) {
+        // stage A (row tid) and B (rows tid, tid + 128) in the K-major core-matrix layout
         for (int k8 = 0; k8 < K / 8; ++k8) {
-            const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)r * K + k8 * 8);
-            *reinterpret_cast<uint4*>(sB + tc::kmajor_off(r, k8 * 8, K)) = v;
+            const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)tid * K + k8 * 8);
+            *reinterpret_cast<uint4*>(sA + tc::kmajor_off(tid, k8 * 8, K)) = v;
         }
+        for (int r = tid; r < N; r += 128)
+            for (int k8 = 0; k8 < K / 8; ++k8) {
+                const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)r * K + k8 * 8);
+                *reinterpret_cast<uint4*>(sB + tc::kmajor_off(r, k8 * 8, K)) = v;
+            }
+    } else {
+        // 16-byte runs of 8 consecutive m (n) at one k, copied as they are
+        for (int c = tid; c < K * 16; c += 128) {
+            const int k = c >> 4, m8 = c & 15;
+            const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)k * 128 + m8 * 8);
+            *reinterpret_cast<uint4*>(sA + tc::mnmajor_off(m8 * 8, k, 128)) = v;
+        }
+        for (int c = tid; c < K * (N / 8); c += 128) {
+            const int k = c / (N / 8), n8 = c % (N / 8);
+            const uint4 v = *reinterpret_cast<const uint4*>(B + (size_t)k * N + n8 * 8);
+            *reinterpret_cast<uint4*>(sB + tc::mnmajor_off(n8 * 8, k, N)) = v;
+        }
+    }
     tc::fence_smem_to_async();
     if (warp == 0) tc::tmem_alloc(&slot, 256);
     tc::fence_before_sync();
@@ -47,11 +62,22 @@ __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restr
     const uint32_t taddr = slot;
     if (tid == 0) {
         const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-        const uint32_t sbo = (uint32_t)(K / 8) * 128u;
-        for (int kk = 0; kk < K / 16; ++kk) {
-            const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, sbo);
-            const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, sbo);
-            tc::mma(taddr, ad, bd, tc::idesc_bf16(128, (uint32_t)N), kk > 0 ? 1u : 0u);
+        if (!mn_major) {
+            const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+            for (int kk = 0; kk < K / 16; ++kk) {
+                const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, sbo);
+                const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, sbo);
+                tc::mma(taddr, ad, bd, tc::idesc_bf16(128, (uint32_t)N), kk > 0 ? 1u : 0u);
+            }
+        } else {
+            // K-direction core-matrix strides (LBO); M/N-direction 128 bytes (SBO); each MMA
+            // takes two K-groups
+            const uint32_t la = 16u * 128u, lb = (uint32_t)(N / 8) * 128u;
+            for (int kk = 0; kk < K / 16; ++kk) {
+                const uint64_t ad = tc::smem_desc(a0 + kk * 2 * la, la, 128);
+                const uint64_t bd = tc::smem_desc(b0 + kk * 2 * lb, lb, 128);
+                tc::mma(taddr, ad, bd, tc::idesc_bf16_mn(128, (uint32_t)N), kk > 0 ? 1u : 0u);
+            }
         }
         tc::commit(&bar);
     }
@@ -77,13 +103,15 @@ __global__ void __launch_bounds__(128) k_gemm_check(const __nv_bfloat16* __restr
 
 }  // namespace
 
-int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, long long first_wait,
+int gemm_check(const void* A, const void* B, float* C, int K, int N, int* d_err, long long first_wait, int mn_major,
                cudaStream_t st) {
-    const size_t smem = (size_t)128 * K * 2 + (size_t)N * K * 2 + 1024;
+    // the MN-major check takes the largest allocation, so that the tensor core's reads stay
+    // inside the CTA's shared memory for any reading of the descriptor's two strides
+    const size_t smem = mn_major ? (size_t)226 * 1024 : (size_t)128 * K * 2 + (size_t)N * K * 2 + 1024;
     cudaFuncSetAttribute(k_gemm_check, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_gemm_check<<<1, 128, smem, st>>>(reinterpret_cast<const __nv_bfloat16*>(A),
                                        reinterpret_cast<const __nv_bfloat16*>(B), C, K, N, d_err,
-                                       first_wait < 0 ? kWaitBudget : first_wait);
+                                       first_wait < 0 ? kWaitBudget : first_wait, mn_major);
     count_launches(1);
     return 0;
 }
@@ -631,16 +659,25 @@ __global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restr
     if (warp == 0) tc::tmem_dealloc(taddr, 256);
 }
 
+// Weight gradient of one layer over the CTA's rows, split-K by rows: part[cta] = dz^T act
+// for the 128 outputs of block blockIdx.y, and the bias gradient sum_rows dz (atomics).
+// Both operands are MN-major in shared memory (outputs resp. inputs contiguous, one row
+// per k), so a 16-byte run of a dz or act row is copied as it is; thread t always stages
+// the same 8 outputs (t % 16) of A, which gives it the bias sums from its registers.  The
+// next 128-row chunk is loaded into registers while the tensor core works on the current.
 template <int NIN>
 __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restrict__ dz,
                                                    const __nv_bfloat16* __restrict__ act, int B, int rows_per_cta,
                                                    float* __restrict__ part, float* __restrict__ gb, int* err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = align1k(smem_raw);
-    unsigned char* sA = sm;                 // [128 out][128 rows]
-    unsigned char* sB = sm + 128 * 128 * 2;  // [NIN in][128 rows]
+    unsigned char* sA = sm;                  // MN-major, 128 outs x 128 rows
+    unsigned char* sB = sm + 128 * 128 * 2;  // MN-major, NIN ins x 128 rows
+    constexpr int kCA = 128 * 16 / 256;      // 16-byte runs of A per thread and chunk (8)
+    constexpr int kCB = 128 * (NIN / 8) / 256;  // of B (16 or 4)
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t slot;
+    __shared__ float sbias[8][128];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ob = blockIdx.y;
     if (tid == 0) {
@@ -654,56 +691,63 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restri
     const uint32_t taddr = slot;
     uint32_t phase = 0;
     bool failed = false;
-    float bsum = 0.f;
+    float bs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     const int rbeg = blockIdx.x * rows_per_cta;
     const int rend = min(B, rbeg + rows_per_cta);
+    const int o8 = tid & 15;  // this thread's 8 outputs of A: o8 * 8 ..
+    uint4 ra[kCA], rb[kCB];
+    auto load = [&](int r0) {
+#pragma unroll
+        for (int j = 0; j < kCA; ++j) {
+            const int row = (tid >> 4) + 16 * j;
+            ra[j] = r0 + row < rend
+                        ? *reinterpret_cast<const uint4*>(dz + (size_t)(r0 + row) * kH + ob * 128 + o8 * 8)
+                        : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int j = 0; j < kCB; ++j) {
+            const int c = tid + 256 * j, row = c / (NIN / 8), i8 = c % (NIN / 8);
+            rb[j] = r0 + row < rend ? *reinterpret_cast<const uint4*>(act + (size_t)(r0 + row) * NIN + i8 * 8)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    if (rbeg < rend) load(rbeg);
+    // K-direction core-matrix strides of the two operands; M/N-direction 128 bytes
+    constexpr uint32_t la = 16u * 128u, lb = (uint32_t)(NIN / 8) * 128u;
     int chunk = 0;
     for (int r0 = rbeg; r0 < rend; r0 += 128, ++chunk) {
-        // A: thread t stages rows r0 + t / 2, outs (t % 2) * 64 .. + 64 of this block
-        {
-            const int rl = tid >> 1, o0 = (tid & 1) * 64;
-            const bool ok = r0 + rl < rend;
-            const __nv_bfloat16* src = dz + (size_t)(r0 + rl) * kH + ob * 128 + o0;
-            for (int k8 = 0; k8 < 8; ++k8) {
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (ok) v = *reinterpret_cast<const uint4*>(src + k8 * 8);
-                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_off(o0 + k8 * 8 + i, rl, 128)) = e[i];
-            }
+        for (int j = 0; j < kCA; ++j) {
+            const int row = (tid >> 4) + 16 * j;
+            *reinterpret_cast<uint4*>(sA + tc::mnmajor_off(o8 * 8, row, 128)) = ra[j];
+            const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&ra[j]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) bs[i] += __bfloat162float(e[i]);
         }
-        // B: thread t stages row r0 + t / 2, inputs (t % 2) * NIN/2 .. + NIN/2
-        {
-            const int rl = tid >> 1, i0 = (tid & 1) * (NIN / 2);
-            const bool ok = r0 + rl < rend;
-            const __nv_bfloat16* src = act + (size_t)(r0 + rl) * NIN + i0;
-            for (int k8 = 0; k8 < NIN / 16; ++k8) {
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (ok) v = *reinterpret_cast<const uint4*>(src + k8 * 8);
-                const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_off(i0 + k8 * 8 + i, rl, 128)) = e[i];
-            }
+        for (int j = 0; j < kCB; ++j) {
+            const int c = tid + 256 * j, row = c / (NIN / 8), i8 = c % (NIN / 8);
+            *reinterpret_cast<uint4*>(sB + tc::mnmajor_off(i8 * 8, row, NIN)) = rb[j];
         }
         tc::fence_smem_to_async();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        // the chunk's MMA first, so that the tensor core runs during the bias sums below (both
-        // only read the staged tiles; the wait comes after)
-        if (tid == 0) mma_tile(taddr, sA, sB, 128, tc::idesc_bf16(128, NIN), chunk > 0, &bar);
-        // bias gradient: thread o < 128 sums its out's row of A over the chunk
-        if (tid < 128)
-            for (int r = 0; r < 128; ++r)
-                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(sA + tc::kmajor_off(tid, r, 128)));
+        if (tid == 0) {
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+            for (int kk = 0; kk < 8; ++kk)
+                tc::mma(taddr, tc::smem_desc(a0 + kk * 2 * la, la, 128), tc::smem_desc(b0 + kk * 2 * lb, lb, 128),
+                        tc::idesc_bf16_mn(128, NIN), (kk > 0 || chunk > 0) ? 1u : 0u);
+            tc::commit(&bar);
+        }
+        if (r0 + 128 < rend) load(r0 + 128);
         const bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
             failed = true;
             break;
         }
+        tc::fence_after_sync();
     }
     if (failed) {
         if (tid == 0) atomicOr(err, 1);
@@ -712,7 +756,6 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restri
         float* dst = part + (size_t)blockIdx.x * kH * NIN + (size_t)ob * 128 * NIN;
         for (int i = tid; i < 128 * NIN; i += 256) dst[i] = 0.f;
     } else {
-        tc::fence_after_sync();
         if (warp < 4) {
             const int o = warp * 32 + lane;
             const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
@@ -725,7 +768,19 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restri
                 for (int i = 0; i < 4; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
         }
-        if (tid < 128) atomicAdd(gb + ob * 128 + tid, bsum);
+        // bias: lanes l and l ^ 16 hold the same outputs; then the 8 warps' sums
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bs[i] += __shfl_xor_sync(0xffffffffu, bs[i], 16);
+        if (lane < 16)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sbias[warp][o8 * 8 + i] = bs[i];
+        __syncthreads();
+        if (tid < 128) {
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += sbias[w][tid];
+            atomicAdd(gb + ob * 128 + tid, s);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();

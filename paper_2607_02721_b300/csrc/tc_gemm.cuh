@@ -1,5 +1,5 @@
 // 5th-generation tensor-core building blocks for sm_103a (inline PTX, no CUTLASS):
-// shared-memory matrix descriptors for the no-swizzle K-major canonical layout,
+// shared-memory matrix descriptors for the no-swizzle K-major and MN-major canonical layouts,
 // tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in tensor memory), commit to an
 // mbarrier, bounded mbarrier waits, TMEM allocation and 32x32b loads.
 //
@@ -22,6 +22,15 @@ __device__ __forceinline__ uint32_t kmajor_off(uint32_t r, uint32_t k, uint32_t 
     return (r >> 3) * (K >> 3) * 128u + (k >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
 }
 
+// MN-major, no swizzle: the core matrices hold 8 consecutive M (or N) elements (16
+// bytes) in each of their 8 rows, one row per k; core matrices adjacent along M/N are
+// SBO = 128 bytes apart and those adjacent along K are LBO = MN/8 * 128 bytes apart:
+// byte(mn, k) = (k / 8) * LBO + (mn / 8) * 128 + (k % 8) * 16 + (mn % 8) * 2, so a
+// 16-byte run of 8 consecutive mn at one k is stored as it is in a [K][MN] array.
+__device__ __forceinline__ uint32_t mnmajor_off(uint32_t mn, uint32_t k, uint32_t MN) {
+    return (k >> 3) * (MN >> 3) * 128u + (mn >> 3) * 128u + (k & 7u) * 16u + (mn & 7u) * 2u;
+}
+
 // SM100 shared-memory matrix descriptor: start >> 4 at [0,14), LBO >> 4 at [16,30),
 // SBO >> 4 at [32,46), version 1 at [46,48), base offset 0, layout 0 (no swizzle).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -37,6 +46,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at [17,23), M >> 4 at [24,29).
 __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+// The same with A and B MN-major (bits 15, 16 = 1).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(uint32_t M, uint32_t N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {

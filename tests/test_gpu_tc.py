@@ -35,6 +35,22 @@ def test_tc_gemm_matches_fp64(ctx, K, N):
     assert np.all(np.abs(C - ref) <= 1e-6 * scale + 1e-12)
 
 
+@pytest.mark.parametrize("K,N", [(16, 16), (64, 256), (128, 64), (128, 256), (32, 128)])
+def test_tc_gemm_mn_major_matches_fp64(ctx, K, N):
+    """The MN-major operand layout (A^T B with A [K][128], B [K][N] copied into shared
+    memory as they are) against the FP64 product."""
+    import torch
+
+    g = torch.Generator().manual_seed(K * 1000 + N + 7)
+    At = torch.randn(K, 128, generator=g).to(torch.bfloat16)
+    Bt = torch.randn(K, N, generator=g).to(torch.bfloat16)
+    C = ctx.debug_tc_gemm_mn(At.cuda(), Bt.cuda()).cpu().numpy().astype(np.float64)
+    a, b = At.double().numpy(), Bt.double().numpy()
+    ref = a.T @ b
+    scale = np.abs(a).T @ np.abs(b)
+    assert np.all(np.abs(C - ref) <= 1e-6 * scale + 1e-12), float(np.abs(C - ref).max())
+
+
 def _check_product(C, A, B):
     a, b = A.double().numpy(), B.double().numpy()
     scale = np.abs(a) @ np.abs(b).T
