@@ -605,6 +605,8 @@ def run_surrogate(args):
         scfg.batch = args.train_batch
     if args.train_lr:
         scfg.lr = args.train_lr
+    if args.cheap_stride:
+        scfg.cheap_stride = args.cheap_stride
     rec, s_exact, s_hat = surrogate_record(ctx, sid, cams, m, scfg, sopts, args.psnr_stride)
     res = {"mode": "surrogate", "config": cfg, "resolution": args.resolution}
     res.update(rec)
@@ -929,6 +931,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=100)
     ap.add_argument("--train-batch", type=int, default=0, help="surrogate training rows per step (0: default)")
     ap.add_argument("--train-lr", type=float, default=0.0, help="surrogate learning rate (0: default)")
+    ap.add_argument("--cheap-stride", type=int, default=0, help="surrogate: cheap score on every n-th view (0: default)")
     ap.add_argument("--psnr-stride", type=int, default=5)
     ap.add_argument("--fill-only", action="store_true")
     ap.add_argument("--surrogate-direct", action="store_true",

@@ -121,7 +121,7 @@ def test_fullsize_resolution_chain_and_scene_total(setup):
 
 def test_surrogate_meets_target_at_full_size(setup):
     """Surrogate-assisted scoring (exact scores on 20 of the 200 views, the network, a cheap
-    quarter-resolution score on every 4th view) against exact scoring of all 200 views:
+    quarter-resolution score on every 6th view) against exact scoring of all 200 views:
     the 90%-pruned render's PSNR (against the full render, every 10th view) loses at most
     0.1 dB, beats the 20 scored views' exact scores alone by at least 1 dB, and the whole
     surrogate path takes less time than exact scoring (CUDA events, after a warm-up)."""

@@ -55,7 +55,7 @@ def test_surrogate_gain_over_subset_scores(ctx, torch):
     ctx.set_queries(sid, cams)
     s_ex, _ = ctx.score(sid)
     s_ex = s_ex.clone()
-    cfg = surrogate.SurrogateConfig(train_views=4)
+    cfg = surrogate.SurrogateConfig(train_views=4, cheap_stride=4)
     s_hat, s_sub = surrogate.surrogate_scores(ctx, sid, cams, cfg)
     a = s_ex.double().cpu().numpy()
     h = s_hat.double().cpu().numpy()
