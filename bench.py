@@ -74,7 +74,7 @@ def workload(name: str):
 
 
 # --tile-shape: library codes (CSGS_TILE_*; 0 = the autotuner's choice)
-TILE_SHAPES = {"auto": 0, "16x16": 1, "32x8": 2, "16x8": 3}
+TILE_SHAPES = {"auto": 0, "16x16": 1, "32x8": 2, "16x8": 3, "8x8": 4}
 
 # --score-resolution: (library code, description) of the query resolutions of Sec. 3.5
 SCORE_RESOLUTIONS = {"pixel": (0, "per-pixel (max over pixel-rays)"), "scene": (1, "per-scene (one query)"),

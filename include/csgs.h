@@ -98,6 +98,7 @@ typedef struct {
 #define CSGS_TILE_16X16 1
 #define CSGS_TILE_32X8 2
 #define CSGS_TILE_16X8 3
+#define CSGS_TILE_8X8 4
 
 /* Scoring / rendering conventions.  The paper fixes only the definitions; the
  * thresholds are those of the standard 3DGS rasteriser it relies on. */
@@ -126,7 +127,7 @@ typedef struct {
 typedef struct {
     int32_t view_batch;    /* views projected per launch */
     int32_t sort_blocks;   /* radix-sort grid (CTAs) */
-    int32_t tile_shape;    /* CSGS_TILE_16X16, CSGS_TILE_32X8 or CSGS_TILE_16X8 */
+    int32_t tile_shape;    /* CSGS_TILE_16X16, CSGS_TILE_32X8, CSGS_TILE_16X8 or CSGS_TILE_8X8 */
     int32_t persist_ctas;  /* persistent compositing CTAs, 0 = one CTA per tile */
     float probe_ms;        /* the chosen configuration's time for the probe views */
 } csgs_tuning;
@@ -227,7 +228,7 @@ csgs_status csgs_score_batch(csgs_ctx* ctx, int32_t n_scenes, const int32_t* sce
  * on the first probe_views query views (0: min(16, views)), one dimension after the
  * other: view batches {1,2,4,8,16} x sort grids {74,148,296,592,1184,1776} blocks at the
  * requested shape (16x16 for CSGS_TILE_AUTO); then, for CSGS_TILE_AUTO (and not the
- * per-tile resolution), the shapes 32x8 and 16x8 at the best pair; then, for the
+ * per-tile resolution), the shapes 32x8, 16x8 and 8x8 at the best pair; then, for the
  * per-pixel score with opts->persist_ctas 0, persistent launches of r, r - 1 and r - 2
  * CTAs per SM (r: the kernel's resident limit) against one CTA per tile.  The choices
  * are kept with the scene and apply to later csgs_score / csgs_score_batch calls on it

@@ -69,8 +69,8 @@ class Tuning(ctypes.Structure):
 
 
 # Tile shapes (CSGS_TILE_*): 0 = the scene's autotuned shape (else 16x16).
-TILE_AUTO, TILE_16X16, TILE_32X8, TILE_16X8 = 0, 1, 2, 3
-TILE_SHAPE_NAMES = {TILE_16X16: "16x16", TILE_32X8: "32x8", TILE_16X8: "16x8"}
+TILE_AUTO, TILE_16X16, TILE_32X8, TILE_16X8, TILE_8X8 = 0, 1, 2, 3, 4
+TILE_SHAPE_NAMES = {TILE_16X16: "16x16", TILE_32X8: "32x8", TILE_16X8: "16x8", TILE_8X8: "8x8"}
 
 
 class Stats(ctypes.Structure):

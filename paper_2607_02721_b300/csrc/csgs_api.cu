@@ -205,6 +205,9 @@ void set_tile_shape(KOpts* k, int shape) {
     } else if (shape == CSGS_TILE_16X8) {
         k->tile_lw = 4;
         k->tile_lh = 3;
+    } else if (shape == CSGS_TILE_8X8) {
+        k->tile_lw = 3;
+        k->tile_lh = 3;
     }
 }
 
@@ -218,7 +221,7 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
         !(o->cut2 > 0.f) || !(o->dilation >= 0.f) || !(o->clamp_fov > 0.f) || !finite3(o->obj_w, 3) ||
         o->obj_w[0] < 0.f || o->obj_w[1] < 0.f || o->obj_w[2] < 0.f || o->view_batch < 0)
         return fail(ctx, CSGS_E_INVAL, "invalid scoring options");
-    if (o->tile_shape < CSGS_TILE_AUTO || o->tile_shape > CSGS_TILE_16X8)
+    if (o->tile_shape < CSGS_TILE_AUTO || o->tile_shape > CSGS_TILE_8X8)
         return fail(ctx, CSGS_E_INVAL, "tile_shape %d is not supported", o->tile_shape);
     if (o->persist_ctas < -1 || o->persist_ctas > (1 << 20))
         return fail(ctx, CSGS_E_INVAL, "persist_ctas %d is out of range", o->persist_ctas);
@@ -993,9 +996,9 @@ csgs_status prepare_scoring(csgs_ctx* ctx, SceneRec** sc, const int* vb, int ns,
         if ((r = upload_cams(ctx, sc[k], ko))) return r;
         if (sc[k]->n > nmax) nmax = sc[k]->n;
         if (vb[k] > vbmax) vbmax = vb[k];
-        // ranges for the shape with the most tiles (16x8), so that any scene's shape fits
+        // ranges for the shape with the most tiles (8x8), so that any scene's shape fits
         for (auto& c : sc[k]->cams)
-            if (tiles_of(c, 4, 3) > tiles) tiles = tiles_of(c, 4, 3);
+            if (tiles_of(c, 3, 3) > tiles) tiles = tiles_of(c, 3, 3);
     }
     if ((r = ensure_view_buffers(ctx, nmax, vbmax, tiles))) return r;
     if ((r = ensure(ctx, ctx->partial, sizeof(double) * 1024))) return r;
@@ -1292,7 +1295,7 @@ csgs_status csgs_autotune(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts
         if (r) break;
     }
     if (!r && opts->tile_shape == CSGS_TILE_AUTO && ko.resolution != CSGS_RES_TILE) {
-        for (int shape : {CSGS_TILE_32X8, CSGS_TILE_16X8}) {
+        for (int shape : {CSGS_TILE_32X8, CSGS_TILE_16X8, CSGS_TILE_8X8}) {
             KOpts kk = ko;
             set_tile_shape(&kk, shape);
             float t = 1e30f;

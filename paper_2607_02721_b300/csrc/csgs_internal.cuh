@@ -14,7 +14,7 @@ void count_launches(long long k);
 long long launches();
 
 // Screen tiles: one CTA composites one tile of 2^lw x 2^lh pixels.  Shapes (CSGS_TILE_*):
-// 16x16 (the default, and the query of the per-tile resolution), 32x8 and 16x8; the
+// 16x16 (the default, and the query of the per-tile resolution), 32x8, 16x8 and 8x8; the
 // footprint test is per pixel, so the shape changes only the work split, not which pairs
 // contribute.
 constexpr int kTileLw16 = 4, kTileLh16 = 4;

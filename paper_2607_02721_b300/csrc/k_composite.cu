@@ -48,6 +48,7 @@ struct TileCfg {
 using Tile16x16 = TileCfg<4, 4>;
 using Tile32x8 = TileCfg<5, 3>;
 using Tile16x8 = TileCfg<4, 3>;
+using Tile8x8 = TileCfg<3, 3>;
 
 // Modes: the render, and the query resolutions of Sec. 3.5.  Pixel and channel
 // resolutions run two passes (A(q) first); tile, image and scene are one pass that
@@ -757,6 +758,9 @@ int composite_resident_ctas(int lw, int lh) {
     else if (lw == 4 && lh == 3)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_composite<kScorePixel, kL1, false, Tile16x8, true>,
                                                       Tile16x8::kThreads, 0);
+    else if (lw == 3 && lh == 3)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_composite<kScorePixel, kL1, false, Tile8x8, true>,
+                                                      Tile8x8::kThreads, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_composite<kScorePixel, kL1, false, Tile16x16, true>,
                                                       Tile16x16::kThreads, 0);
@@ -786,6 +790,8 @@ static void launch_shape(const CompositeArgs& a, cudaStream_t st) {
         launch_one<MODE, VAR, STATS, Tile32x8>(a, st);
     else if (MODE != kScoreTile && a.o.tile_lw == 4 && a.o.tile_lh == 3)
         launch_one<MODE, VAR, STATS, Tile16x8>(a, st);
+    else if (MODE != kScoreTile && a.o.tile_lw == 3 && a.o.tile_lh == 3)
+        launch_one<MODE, VAR, STATS, Tile8x8>(a, st);
     else
         launch_one<MODE, VAR, STATS, Tile16x16>(a, st);
 }

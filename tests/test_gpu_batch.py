@@ -148,7 +148,7 @@ def test_autotune_keeps_scores(ctx, scenes):
     ref = ref.cpu().numpy()
     tu = ctx.autotune(scenes[1], csgs.default_opts(), probe_views=4)
     assert tu["view_batch"] in (1, 2, 4) and tu["sort_blocks"] in (74, 148, 296, 592, 1184, 1776)
-    assert tu["tile_shape"] in (csgs.TILE_16X16, csgs.TILE_32X8, csgs.TILE_16X8)
+    assert tu["tile_shape"] in (csgs.TILE_16X16, csgs.TILE_32X8, csgs.TILE_16X8, csgs.TILE_8X8)
     assert tu["persist_ctas"] == 0 or tu["persist_ctas"] % 148 == 0 and tu["probe_ms"] > 0
     s, S = ctx.score(scenes[1], fixed)
     np.testing.assert_array_equal(s.cpu().numpy(), ref)
@@ -159,7 +159,7 @@ def test_autotune_keeps_scores(ctx, scenes):
     assert Sa == Se
 
 
-@pytest.mark.parametrize("shape", [csgs.TILE_16X16, csgs.TILE_16X8], ids=["16x16", "16x8"])
+@pytest.mark.parametrize("shape", [csgs.TILE_16X16, csgs.TILE_16X8, csgs.TILE_8X8], ids=["16x16", "16x8", "8x8"])
 def test_persistent_compositing_matches_one_cta_per_tile(ctx, scenes, shape):
     """The persistent launch (few CTAs taking tiles from a queue, longest lists first) gives
     the per-tile launch's per-pixel scores bit for bit, for grids below, at and above the
@@ -180,7 +180,7 @@ def test_persistent_compositing_matches_one_cta_per_tile(ctx, scenes, shape):
         assert S[k] == ref_S[k]
 
 
-@pytest.mark.parametrize("shape", [csgs.TILE_32X8, csgs.TILE_16X8], ids=["32x8", "16x8"])
+@pytest.mark.parametrize("shape", [csgs.TILE_32X8, csgs.TILE_16X8, csgs.TILE_8X8], ids=["32x8", "16x8", "8x8"])
 def test_batch_tile_shapes_match_single_scene_and_oracle(ctx, scenes, shape):
     """A captured batch in another tile shape returns csgs_score's scores scene by scene,
     and the ragged 200x120 scene matches the oracle."""

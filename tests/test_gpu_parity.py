@@ -285,7 +285,8 @@ def test_unit_weights_render_bit_identical(ctx, small, small_sid, torch):
 
 # ---------------------------------------------------------------- edge cases
 
-TILE_SHAPES = [("16x16", csgs.TILE_16X16), ("32x8", csgs.TILE_32X8), ("16x8", csgs.TILE_16X8)]
+TILE_SHAPES = [("16x16", csgs.TILE_16X16), ("32x8", csgs.TILE_32X8), ("16x8", csgs.TILE_16X8),
+               ("8x8", csgs.TILE_8X8)]
 
 
 @pytest.mark.parametrize("shape", TILE_SHAPES, ids=[s[0] for s in TILE_SHAPES])
@@ -311,8 +312,9 @@ def test_ragged_image_and_tiny_scene(ctx, torch, shape):
 
 @pytest.mark.parametrize("shape", TILE_SHAPES[1:], ids=[s[0] for s in TILE_SHAPES[1:]])
 def test_tile_shapes_match_oracle(ctx, workload, shape):
-    """32x8 tiles (warps of 8x4 pixels in four columns and two bands) and 16x8 tiles (two
-    columns, two bands, 128-thread CTAs): the per-pixel and per-channel scores, the
+    """32x8 tiles (warps of 8x4 pixels in four columns and two bands), 16x8 tiles (two
+    columns, two bands, 128-thread CTAs) and 8x8 tiles (one column, two bands, 64-thread
+    CTAs): the per-pixel and per-channel scores, the
     per-scene sums and renders against the oracle.  The footprint test is per pixel, so
     the shape changes only the FP32 rounding of the tile-centred exponent."""
     sc, cams, _, sa, sid = workload
