@@ -121,6 +121,12 @@ typedef struct {
                               from a queue until none is left; 0 = the scene's choice by
                               csgs_autotune (else one CTA per tile), -1 = one CTA per tile.
                               Scores do not depend on it */
+    int32_t accumulate;    /* 1: s_dev already holds the scores of other query views of the same
+                              scene at the same resolution, and the call leaves in it the maximum
+                              over both query sets (s is a maximum over queries, Eq. sen, so this
+                              equals scoring the union; S is returned for the union).  Pixel,
+                              channel, tile and image resolutions; CSGS_E_INVAL for the per-scene
+                              one, whose s is a ratio of sums.  0: s_dev is overwritten */
 } csgs_score_opts;
 
 /* What csgs_autotune chose for a scene. */
@@ -204,8 +210,10 @@ csgs_status csgs_free_scene(csgs_ctx* ctx, int32_t scene_id);
 csgs_status csgs_set_queries(csgs_ctx* ctx, int32_t scene_id, const csgs_camera* cams, int32_t n_views);
 
 /* Sensitivity scores (Algorithm 1, steps 2-3; Eq. sen) over all query views.
- * s_dev: device float[N], written with s_i.  S_out: host double, total
- * sensitivity S (may be NULL).  Synchronises.  Returns CSGS_E_EMPTY when S = 0. */
+ * s_dev: device float[N], written with s_i (with opts->accumulate: the maximum of its
+ * previous contents and this query set's s_i).  S_out: host double, total
+ * sensitivity S of what s_dev holds on return (may be NULL).  Synchronises.  Returns
+ * CSGS_E_EMPTY when S = 0. */
 csgs_status csgs_score(csgs_ctx* ctx, int32_t scene_id, const csgs_score_opts* opts, float* s_dev, double* S_out);
 
 /* Sensitivity scores of several scenes in one submission (Algorithm 1, steps 2-3, per

@@ -60,7 +60,7 @@ class ScoreOpts(ctypes.Structure):
                 ("alpha_min", ctypes.c_float), ("rho_max", ctypes.c_float), ("t_min", ctypes.c_float),
                 ("cut2", ctypes.c_float), ("dilation", ctypes.c_float), ("clamp_fov", ctypes.c_float),
                 ("view_batch", ctypes.c_int32), ("collect_stats", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
-                ("persist_ctas", ctypes.c_int32)]
+                ("persist_ctas", ctypes.c_int32), ("accumulate", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):

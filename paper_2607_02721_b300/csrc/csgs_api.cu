@@ -225,6 +225,9 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
         return fail(ctx, CSGS_E_INVAL, "tile_shape %d is not supported", o->tile_shape);
     if (o->persist_ctas < -1 || o->persist_ctas > (1 << 20))
         return fail(ctx, CSGS_E_INVAL, "persist_ctas %d is out of range", o->persist_ctas);
+    if (o->accumulate != 0 && o->accumulate != 1) return fail(ctx, CSGS_E_INVAL, "accumulate must be 0 or 1");
+    if (o->accumulate && o->resolution == CSGS_RES_SCENE)
+        return fail(ctx, CSGS_E_INVAL, "the per-scene resolution cannot accumulate over query sets");
     k->alpha_min = o->alpha_min;
     k->rho_max = o->rho_max;
     k->t_min = o->t_min;
@@ -241,6 +244,7 @@ csgs_status make_kopts(csgs_ctx* ctx, const csgs_score_opts* o, KOpts* k) {
     k->narrow_keys = ctx->wide_keys ? 0 : 1;
     set_tile_shape(k, o->tile_shape);
     k->persist_ctas = o->persist_ctas > 0 ? o->persist_ctas : 0;
+    k->accumulate = o->accumulate;
     return CSGS_OK;
 }
 
@@ -491,6 +495,7 @@ void csgs_default_opts(csgs_score_opts* o) {
     o->collect_stats = 0;
     o->tile_shape = CSGS_TILE_AUTO;
     o->persist_ctas = 0;
+    o->accumulate = 0;
 }
 
 csgs_status csgs_create(csgs_ctx** out, int32_t device, void* cuda_stream) {
@@ -907,7 +912,8 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
     const SceneDev sd = scene_dev(*s);
     const int grid = s->tuned_sb > 0 ? s->tuned_sb : ctx->sort_blocks;
     set_u64(ctx->d_nconst, (unsigned long long)n, st);
-    CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
+    // the maxima of earlier query sets stay when accumulating
+    if (!ko.accumulate) CUDA_TRY(ctx, cudaMemsetAsync(s_dev, 0, sizeof(float) * (size_t)n, st));
     if (ko.resolution == CSGS_RES_SCENE) CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA, 0, sizeof(double), st));
     if (ko.resolution == CSGS_RES_IMAGE) CUDA_TRY(ctx, cudaMemsetAsync(ctx->vbuf.p, 0, sizeof(float) * (size_t)n, st));
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev_start, st));

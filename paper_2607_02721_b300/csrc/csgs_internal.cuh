@@ -58,6 +58,7 @@ struct KOpts {
     int narrow_keys;  // depth keys: 1 = narrow (27-bit, relative to the near plane), 0 = the float bits
     int tile_lw, tile_lh;  // tile shape: 2^tile_lw x 2^tile_lh pixels
     int persist_ctas;      // per-pixel score: CTAs of a persistent compositing launch (0: one per tile)
+    int accumulate;        // scoring: take the maximum with the scores already in the output
 };
 
 // One projected Gaussian in one view (48 bytes, 16-byte aligned).

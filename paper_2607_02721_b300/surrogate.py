@@ -7,7 +7,7 @@ exact scores of the scored subset (s = max(exp(prediction) - eps, s_subset)).
 
 Inputs per Gaussian: its attributes, view statistics over all views (views reached,
 mean and max projected footprint area) and, with ``lowres_factor`` > 0, the log of a
-cheap score: the same per-pixel sensitivity over every ``cheap_stride``-th view rendered
+cheap score: the same per-pixel sensitivity over the scored views and every ``cheap_stride``-th view rendered
 at 1/f of the resolution (1/f^2 of the pixel queries).  The cheap score reaches views
 the exact scorer skips and carries their occlusion; the network learns, on the scored
 views, how the full-resolution score follows from it, from the view statistics and
@@ -47,11 +47,12 @@ class SurrogateConfig:
     # > 0: cheap score at 1/f resolution as an input (0: attributes and view statistics
     # only, which on the 3M workload matched the scored subset alone, 17.00 dB)
     lowres_factor: int = 4
-    # cheap score over every cheap_stride-th view (its cost is per view: projection and
-    # binning of every Gaussian); 3M workload, 20 scored views, f = 4, pruned-render PSNR,
-    # Spearman with the exact scores and total time: every 4th view 19.05 dB, 0.935, 79 ms;
-    # every 6th 19.09 dB, 0.923, 71 ms; every 8th 19.01 dB, 0.852, 66 ms; every view 18.87 dB
-    # (150 training steps); exact scoring 18.88 dB in 160 ms
+    # cheap score over the scored views and every cheap_stride-th view (its cost is per view:
+    # projection and binning of every Gaussian; the scored views' cheap scores are computed
+    # for the training rows anyway); 3M workload, 20 scored views, f = 4, pruned-render
+    # PSNR, Spearman with the exact scores and total time: every 4th view 19.06 dB, 0.935,
+    # 75 ms; every 6th 19.13 dB, 0.923, 67 ms; every 8th 19.00 dB, 0.851, 64 ms; every 12th
+    # 19.09 dB, 0.883, 60 ms; exact scoring 18.88 dB in 160 ms
     cheap_stride: int = 6
     # tile shape of the cheap (reduced-resolution) scoring when the caller leaves the shape
     # to the library: 8x8 tiles (a code of the library's TILE_* constants); 34 views of
@@ -97,6 +98,18 @@ def _score_or_zero(ctx, sid, cams, opts):
             raise
         s = ctx.torch.zeros(ctx.scene_size(sid), dtype=ctx.torch.float32, device=ctx.device)
     return s.clone()
+
+
+def _score_into(ctx, sid, opts, out):
+    """csgs_score into `out` (with opts.accumulate: the maximum with its contents); a query
+    set whose every query has A = 0 leaves it as it is."""
+    from . import CSGS_E_EMPTY, CsgsError
+
+    try:
+        ctx.score(sid, opts, out=out)
+    except CsgsError as e:
+        if e.status != CSGS_E_EMPTY:
+            raise
 
 
 def surrogate_scores(ctx, sid: int, cams, cfg: SurrogateConfig | None = None, opts=None, timings: dict | None = None):
@@ -152,7 +165,19 @@ def surrogate_scores(ctx, sid: int, cams, cfg: SurrogateConfig | None = None, op
     ctx.mlp_init(cfg.seed)
     ctx.mlp_train(X, t, batch=cfg.batch, steps=cfg.steps, lr=cfg.lr, seed=cfg.seed + 1)
     mark("trained")
-    cheap = _score_or_zero(ctx, sid, low[::max(1, cfg.cheap_stride)], low_opts) if low is not None else None
+    cheap = None
+    if low is not None:
+        # the cheap score over the scored views' reduced-resolution copies (already computed
+        # for the training rows) and every cheap_stride-th view: s is a maximum over queries
+        # (Eq. sen), so the other views are scored into a copy of the first with accumulate
+        in_sub = set(int(v) for v in sub)
+        extra = [v for v in range(0, nv, max(1, cfg.cheap_stride)) if v not in in_sub]
+        cheap = low_sub.clone()
+        if extra:
+            acc = copy.copy(low_opts)
+            acc.accumulate = 1
+            ctx.set_queries(sid, low[extra])
+            _score_into(ctx, sid, acc, cheap)
     extra = ctx.log_target(cheap, cfg.eps) if cheap is not None else None
     mark("cheap_all")
     ctx.set_queries(sid, cams)

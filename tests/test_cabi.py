@@ -42,7 +42,7 @@ def test_default_opts_are_the_rasteriser_conventions(lib):
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.rho_max - 0.99) < 1e-7
     assert abs(o.t_min - 1e-4) < 1e-10 and o.cut2 == 9.0 and abs(o.dilation - 0.3) < 1e-7
     assert list(o.obj_w) == [1.0, 1.0, 1.0]
-    assert o.tile_shape == csgs.TILE_AUTO and o.view_batch == 0 and o.persist_ctas == 0
+    assert o.tile_shape == csgs.TILE_AUTO and o.view_batch == 0 and o.persist_ctas == 0 and o.accumulate == 0
 
 
 def test_struct_layouts_match_header(lib, tmp_path):
@@ -72,7 +72,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
-    assert ctypes.sizeof(csgs.ScoreOpts) == 60
+    assert ctypes.sizeof(csgs.ScoreOpts) == 64
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

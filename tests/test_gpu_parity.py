@@ -207,6 +207,34 @@ def test_score_is_deterministic(ctx, small_sid):
     assert bool((a == b).all())
 
 
+@pytest.mark.parametrize("res", [csgs.RES_PIXEL, csgs.RES_CHANNEL, csgs.RES_TILE, csgs.RES_IMAGE],
+                         ids=["pixel", "channel", "tile", "image"])
+def test_accumulated_query_sets_equal_their_union(ctx, small, res):
+    """s is a maximum over queries (Eq. sen): scoring views 0-2, then views 3-7 into the same
+    buffer with accumulate, gives the scores of views 0-7 and S of the union: bit for bit
+    where each query's terms are reduced in a fixed order (pixel, channel, tile), to FP32
+    summation order for the image resolution (its per-view sums are float atomics)."""
+    sc, cams, _, _ = small
+    sid = ctx.load_scene(sc)
+    try:
+        ctx.set_queries(sid, cams)
+        ref, Sref = ctx.score(sid, csgs.default_opts(resolution=res))
+        ctx.set_queries(sid, cams[:3])
+        s, _ = ctx.score(sid, csgs.default_opts(resolution=res))
+        ctx.set_queries(sid, cams[3:])
+        s, S = ctx.score(sid, csgs.default_opts(resolution=res, accumulate=1), out=s)
+        if res == csgs.RES_IMAGE:
+            np.testing.assert_allclose(s.cpu().numpy(), ref.cpu().numpy(), rtol=1e-5, atol=1e-12)
+            assert abs(S - Sref) <= 1e-5 * Sref
+        else:
+            np.testing.assert_array_equal(s.cpu().numpy(), ref.cpu().numpy())
+            assert S == Sref
+        with pytest.raises(csgs.CsgsError):
+            ctx.score(sid, csgs.default_opts(resolution=csgs.RES_SCENE, accumulate=1), out=s)
+    finally:
+        ctx.free_scene(sid)
+
+
 def test_view_batching_does_not_change_scores(ctx, small_sid):
     a, Sa = ctx.score(small_sid, csgs.default_opts(view_batch=1))
     b, Sb = ctx.score(small_sid, csgs.default_opts(view_batch=8))
