@@ -62,17 +62,10 @@ __device__ __forceinline__ void sh_colour(const float* shc, float x, float y, fl
     }
 }
 
-template <int DEG>
-__device__ __forceinline__ void project_one(const float mu[3], const float cov3[6], float op, const float* shc,
-                                            const CamDev& c, const KOpts& o, Proj& r) {
-    r.valid = false;
-    const ff::F2 X = ff::dot3_plus(c.R[0], c.R[1], c.R[2], c.t[0], mu[0], mu[1], mu[2]);
-    const ff::F2 Yc = ff::dot3_plus(c.R[3], c.R[4], c.R[5], c.t[1], mu[0], mu[1], mu[2]);
-    const ff::F2 Z = ff::dot3_plus(c.R[6], c.R[7], c.R[8], c.t[2], mu[0], mu[1], mu[2]);
-    const float z = Z.hi;
-    if (!(z > c.near_z)) return;
-    if (!(op >= o.alpha_min)) return;  // rho <= alpha < alpha_min everywhere
-
+// The EWA 2-D covariance (entries ca, cb, cc of Sigma' = J Sc J^T + dilation I) of a
+// Gaussian with camera-space mean (x, y, z) and world covariance cov3.
+__device__ __forceinline__ void ewa_cov2(const float cov3[6], const CamDev& c, const KOpts& o, float x, float y,
+                                         float z, float& ca, float& cb, float& cc) {
     // camera-space covariance  Sc = R Sigma R^T   (Sigma symmetric: 00 01 02 11 12 22)
     const float s00 = cov3[0], s01 = cov3[1], s02 = cov3[2], s11 = cov3[3], s12 = cov3[4], s22 = cov3[5];
     float T[9];
@@ -92,16 +85,31 @@ __device__ __forceinline__ void project_one(const float mu[3], const float cov3[
 
     // Jacobian of the perspective map linearised at the (clamped) mean
     const float invz = 1.f / z;
-    float txz = fminf(fmaxf(X.hi * invz, -c.limx), c.limx);
-    float tyz = fminf(fmaxf(Yc.hi * invz, -c.limy), c.limy);
+    float txz = fminf(fmaxf(x * invz, -c.limx), c.limx);
+    float tyz = fminf(fmaxf(y * invz, -c.limy), c.limy);
     const float j00 = c.fx * invz, j02 = -c.fx * txz * invz;
     const float j11 = c.fy * invz, j12 = -c.fy * tyz * invz;
     // cov2 = J Sc J^T
     const float u0 = j00 * Sc[0] + j02 * Sc[6], u1 = j00 * Sc[1] + j02 * Sc[7], u2 = j00 * Sc[2] + j02 * Sc[8];
     const float v1 = j11 * Sc[4] + j12 * Sc[7], v2 = j11 * Sc[5] + j12 * Sc[8];
-    float ca = u0 * j00 + u2 * j02 + o.dilation;
-    float cb = u1 * j11 + u2 * j12;
-    float cc = v1 * j11 + v2 * j12 + o.dilation;
+    ca = u0 * j00 + u2 * j02 + o.dilation;
+    cb = u1 * j11 + u2 * j12;
+    cc = v1 * j11 + v2 * j12 + o.dilation;
+}
+
+template <int DEG>
+__device__ __forceinline__ void project_one(const float mu[3], const float cov3[6], float op, const float* shc,
+                                            const CamDev& c, const KOpts& o, Proj& r) {
+    r.valid = false;
+    const ff::F2 X = ff::dot3_plus(c.R[0], c.R[1], c.R[2], c.t[0], mu[0], mu[1], mu[2]);
+    const ff::F2 Yc = ff::dot3_plus(c.R[3], c.R[4], c.R[5], c.t[1], mu[0], mu[1], mu[2]);
+    const ff::F2 Z = ff::dot3_plus(c.R[6], c.R[7], c.R[8], c.t[2], mu[0], mu[1], mu[2]);
+    const float z = Z.hi;
+    if (!(z > c.near_z)) return;
+    if (!(op >= o.alpha_min)) return;  // rho <= alpha < alpha_min everywhere
+
+    float ca, cb, cc;
+    ewa_cov2(cov3, c, o, X.hi, Yc.hi, z, ca, cb, cc);
     // determinant with Kahan's compensated 2x2 formula
     float w = __fmul_rn(cb, cb);
     float e = __fmaf_rn(-cb, cb, w);
@@ -281,28 +289,56 @@ __global__ void k_check_finite(const float* __restrict__ p, int64_t n, DevCounte
 // Per-Gaussian statistics over query views (features of the surrogate model): number
 // of views whose image the footprint touches, and the mean and maximum area (px^2) of
 // the projected 3-sigma ellipse, pi * cut2 * sqrt(det cov2D), over those views.
-template <int DEG>
+// What the view statistics take from the projection of one Gaussian in one view: whether
+// its footprint reaches the image (the projection's tests: in front of the near plane,
+// alpha >= alpha_min, the opacity-aware bounding box over the pixel centres) and the
+// ellipse's area pi cut2 sqrt(det Sigma').  The pixel mean is plain FP32 here (the
+// projection's two-float mean moves the box by ~1e-4 px), and no colour is evaluated.
+__device__ __forceinline__ bool stats_one(const float mu[3], const float cov3[6], float m_eff, const CamDev& c,
+                                          const KOpts& o, float& area) {
+    const float x = fmaf(c.R[0], mu[0], fmaf(c.R[1], mu[1], fmaf(c.R[2], mu[2], c.t[0])));
+    const float y = fmaf(c.R[3], mu[0], fmaf(c.R[4], mu[1], fmaf(c.R[5], mu[2], c.t[1])));
+    const float z = fmaf(c.R[6], mu[0], fmaf(c.R[7], mu[1], fmaf(c.R[8], mu[2], c.t[2])));
+    if (!(z > c.near_z)) return false;
+    float ca, cb, cc;
+    ewa_cov2(cov3, c, o, x, y, z, ca, cb, cc);
+    const float det = ca * cc - cb * cb;
+    if (!(det > 0.f)) return false;
+    const float invz = 1.f / z;
+    const float mx = fmaf(c.fx * x, invz, c.cx), my = fmaf(c.fy * y, invz, c.cy);
+    const float rx = sqrtf(m_eff * ca) * 1.001f + 0.01f;
+    const float ry = sqrtf(m_eff * cc) * 1.001f + 0.01f;
+    const float fx0 = fmaxf(ceilf(mx - rx), 0.f), fx1 = fminf(floorf(mx + rx), (float)(c.W - 1));
+    const float fy0 = fmaxf(ceilf(my - ry), 0.f), fy1 = fminf(floorf(my + ry), (float)(c.H - 1));
+    if (!(fx0 <= fx1) || !(fy0 <= fy1)) return false;
+    area = 3.14159265358979f * o.cut2 * sqrtf(det);
+    return true;
+}
+
+// Per-Gaussian view statistics over nv views: count of views reached, mean and maximum
+// footprint area (added to the previous values with accumulate).
 __global__ void __launch_bounds__(256) k_view_stats(SceneDev sc, const CamDev* __restrict__ cams, int nv, KOpts o,
                                                     float* __restrict__ stats, int accumulate) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc.n) return;
-    float mu[3], cov3[6], op;
-    float shc[3 * (DEG + 1) * (DEG + 1)];
-    load_gaussian<DEG>(sc, i, nullptr, mu, cov3, op, shc);
+    float mu[3], cov3[6], op, dc[3];  // dc: the DC colour coefficients, unused here
+    load_gaussian<0>(sc, i, nullptr, mu, cov3, op, dc);
     float cnt = 0.f, sum = 0.f, mx = 0.f;
     if (accumulate) {
         cnt = stats[3 * i];
         sum = stats[3 * i + 1] * cnt;
         mx = stats[3 * i + 2];
     }
-    for (int v = 0; v < nv; ++v) {
-        Proj r;
-        project_one<DEG>(mu, cov3, op, shc, cams[v], o, r);
-        if (!r.valid) continue;
-        const float area = 3.14159265358979f * o.cut2 * sqrtf(r.ca * r.cc - r.cb * r.cb);
-        cnt += 1.f;
-        sum += area;
-        mx = fmaxf(mx, area);
+    if (op >= o.alpha_min) {  // rho <= alpha < alpha_min everywhere otherwise
+        // the box's Mahalanobis radius: the footprint cut, or where alpha k falls below alpha_min
+        const float m_eff = fminf(o.cut2, fmaf(2.f / kLog2e, log2f(op) - o.l2amin, 1e-4f));
+        for (int v = 0; v < nv; ++v) {
+            float area;
+            if (!stats_one(mu, cov3, m_eff, cams[v], o, area)) continue;
+            cnt += 1.f;
+            sum += area;
+            mx = fmaxf(mx, area);
+        }
     }
     stats[3 * i] = cnt;
     stats[3 * i + 1] = cnt > 0.f ? sum / cnt : 0.f;
@@ -523,7 +559,7 @@ void launch_view_stats(const SceneDev& sc, const CamDev* d_cams, int nv, const K
     const int blocks = (sc.n + threads - 1) / threads;
     // validity and footprint do not depend on the colour: the degree-0 instantiation reads
     // only the DC coefficients and evaluates no higher harmonics, whatever the scene's degree
-    k_view_stats<0><<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate);
+    k_view_stats<<<blocks, threads, 0, st>>>(sc, d_cams, nv, o, stats, accumulate);
     count_launches(1);
 }
 
