@@ -497,7 +497,7 @@ def run_ours(args):
     roof["project"]["visible_fraction"] = vis_frac
     roof["project"]["note"] = "one launch projects one view batch"
     roof["sort"]["note"] = ("one launch = the binning chain of one view (depth sort, emit, tile sort, ranges); "
-                            "chains of three views overlap each other and the compositing")
+                            "chains of four views overlap each other and the compositing")
 
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True, "scaling": "strong",
