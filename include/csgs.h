@@ -409,15 +409,15 @@ csgs_status csgs_get_stats(csgs_ctx* ctx, csgs_stats* out);
  *   the process exits; n must not exceed CSGS_NOALLOC_MAX_N (else CSGS_E_INVAL).
  *   It runs on the calling thread's current CUDA device, on cuda_stream (a
  *   cudaStream_t, NULL = the legacy default stream).  The first call on a device
- *   looks the array's device address up (cudaGetSymbolAddress); make that first
- *   call before any stream capture.  Every call ends by synchronising cuda_stream
- *   (it reads the distinct count back to the host).  If a CUDA error from earlier
+ *   looks the array's device address up (cudaGetSymbolAddress).  Every call ends by
+ *   synchronising cuda_stream (it reads the distinct count back to the host), so no
+ *   call can be made while cuda_stream is being captured.  If a CUDA error from earlier
  *   work is already pending on the calling thread, the call returns CSGS_E_CUDA
  *   without launching anything and leaves that error pending; otherwise
- *   CSGS_E_CUDA reports this call's own launch or copy failure.  Every call shares the one array, which keeps
- *   the last call's contents (the counts are cleared by each call): calls that
- *   overlap on the GPU - other streams, other host threads - race and must be
- *   serialised by the caller.  No cudaMalloc, cudaFree or allocating library call
+ *   CSGS_E_CUDA reports this call's own launch or copy failure.  Every call shares
+ *   the one array, which keeps the last call's contents (the counts are cleared by
+ *   each call): calls that overlap on the GPU - other streams, other host threads -
+ *   race and must be serialised by the caller.  No cudaMalloc, cudaFree or allocating library call
  *   is made.  Arguments and outputs as csgs_sample_coreset_p (without the draw
  *   list); *n_distinct is written on the host after the stream is synchronised. */
 csgs_status csgs_sample_coreset_noalloc(const double* p_dev, int64_t n, int64_t m, uint64_t seed, int32_t* idx_dev,
