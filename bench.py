@@ -839,22 +839,32 @@ def run_mlp(args):
     fwd_ms = e0.elapsed_time(e1) / args.steps
     from paper_2607_02721_b300 import surrogate
 
-    batch, steps = surrogate.SurrogateConfig().batch, 50
-    ctx.mlp_train(X, t, batch=batch, steps=3, lr=1e-3, seed=1)
-    torch.cuda.synchronize()
-    e0.record(ctx.stream)
-    ctx.mlp_train(X, t, batch=batch, steps=steps, lr=1e-3, seed=2)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    step_ms = e0.elapsed_time(e1) / steps
+    def train_step_ms(batch, steps=50):
+        ctx.mlp_train(X, t, batch=batch, steps=3, lr=1e-3, seed=1)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        ctx.mlp_train(X, t, batch=batch, steps=steps, lr=1e-3, seed=2)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
     pk = peaks()
     bf16 = pk.get("bf16_tflops")
     fwd_tf = flops_row * n / fwd_ms / 1e9
+    # the surrogate's training batch, and four times it (the kernels' cost at a batch that
+    # fills every SM several times over)
+    batch = surrogate.SurrogateConfig().batch
+    step_ms = train_step_ms(batch)
     train_tf = 3.0 * flops_row * batch / step_ms / 1e9  # forward + two backward GEMM sets
+    big = 4 * batch
+    big_ms = train_step_ms(big) if n >= big else None
+    big_tf = 3.0 * flops_row * big / big_ms / 1e9 if big_ms else None
     print(json.dumps({"mode": "mlp", "rows": n, "forward_ms": fwd_ms, "forward_tflops": fwd_tf,
                       "train_batch": batch, "train_step_ms": step_ms, "train_tflops": train_tf,
                       "peak_tflops": bf16, "forward_frac": fwd_tf / bf16 if bf16 else None,
                       "train_frac": train_tf / bf16 if bf16 else None,
+                      "train_batch_x4": big, "train_step_ms_x4": big_ms, "train_tflops_x4": big_tf,
+                      "train_frac_x4": big_tf / bf16 if (big_tf and bf16) else None,
                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)"}), flush=True)
     ctx.close()
     return 0

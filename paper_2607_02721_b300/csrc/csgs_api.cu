@@ -1781,11 +1781,15 @@ csgs_status csgs_mlp_train(csgs_ctx* ctx, const void* X_dev, const float* t_dev,
     CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->err, 0, sizeof(uint32_t), ctx->st));
     const MlpBufs mb = mlp_bufs(ctx);
     const MlpTemp mt = mlp_temp(ctx);
+    // the gradient's accumulated entries start at zero; each step's last kernel clears them
+    // again, and its batch gather clears the loss
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->mG.p, 0, sizeof(float) * kMlpParams, ctx->st));
     for (int step = 1; step <= steps; ++step) {
-        gather_batch(X_dev, t_dev, n_rows, batch, seed, (uint32_t)step, ctx->mXb.p, P<float>(ctx->mTb), ctx->st);
-        mlp_gradient(mb, ctx->mXb.p, P<float>(ctx->mTb), batch, P<float>(ctx->mY), P<float>(ctx->mG),
-                     P<float>(ctx->mLoss), mt, reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
-        mlp_adam(mb, P<float>(ctx->mG), P<float>(ctx->mM), P<float>(ctx->mV), lr, step, ctx->st);
+        gather_batch(X_dev, t_dev, n_rows, batch, seed, (uint32_t)step, ctx->mXb.p, P<float>(ctx->mTb),
+                     P<float>(ctx->mLoss), ctx->st);
+        mlp_train_step(mb, ctx->mXb.p, P<float>(ctx->mTb), batch, P<float>(ctx->mY), P<float>(ctx->mG),
+                       P<float>(ctx->mLoss), mt, P<float>(ctx->mM), P<float>(ctx->mV), lr, step,
+                       reinterpret_cast<int*>(&ctx->d_ctr->err), ctx->st);
         if ((step & 63) == 0 && (r = launch_check(ctx, "mlp train"))) return r;
     }
     if ((r = check_err(ctx, "mlp train"))) return r;

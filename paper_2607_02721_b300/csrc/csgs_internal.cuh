@@ -245,8 +245,9 @@ void surrogate_combine_prior(const float* y, const float* p, const float* s_exac
                              int fill_only, float* out, cudaStream_t st);
 void surrogate_combine(const float* y, const float* s_exact, int64_t n, float eps, int fill_only, float* out,
                        cudaStream_t st);
+// zero (may be null): a float set to 0 by the same launch (the training loss of the step)
 void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,
-                  cudaStream_t st);
+                  float* zero, cudaStream_t st);
 void probabilities_from_scores(const float* s, int64_t n, const double* S, double* p, cudaStream_t st);
 void sample_draws(const double* p, int64_t n, int64_t m, uint64_t seed, const SampleTemp& t, int32_t* draws,
                   int32_t* idx, float* w, cudaStream_t st);
@@ -280,6 +281,10 @@ void mlp_refresh(const MlpBufs& m, cudaStream_t st);
 void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cudaStream_t st);
 void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
                   const MlpTemp& tmp, int* err, cudaStream_t st);
-void mlp_adam(const MlpBufs& m, const float* G, float* mo, float* vo, float lr, int step, cudaStream_t st);
+// One training step on a gathered batch: the gradient kernels, then the split-K sums and
+// Adam in one kernel.  G's bias and output-weight entries must be zero on entry (they are
+// zero again on return) and *loss zero (it holds the batch's loss on return).
+void mlp_train_step(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
+                    const MlpTemp& tmp, float* mo, float* vo, float lr, int step, int* err, cudaStream_t st);
 
 }  // namespace csgs

@@ -787,14 +787,11 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad(const __nv_bfloat16* __restri
     if (warp == 0) tc::tmem_dealloc(taddr, NIN < 32 ? 32 : NIN);
 }
 
-// Adam on the FP32 master block; refreshes the BF16 copies (W1b, W2b, W2Tb).
-__global__ void k_mlp_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
-                           float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2,
-                           __nv_bfloat16* __restrict__ W1b, __nv_bfloat16* __restrict__ W2b,
-                           __nv_bfloat16* __restrict__ W2Tb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float g = G[i];
+// Adam on parameter i of the FP32 master block with gradient g; refreshes its BF16 copies.
+__device__ __forceinline__ void adam_one(int i, float g, float* __restrict__ P, float* __restrict__ m,
+                                         float* __restrict__ v, float lr, float b1, float b2, float eps, float c1,
+                                         float c2, __nv_bfloat16* __restrict__ W1b, __nv_bfloat16* __restrict__ W2b,
+                                         __nv_bfloat16* __restrict__ W2Tb) {
     const float mi = b1 * m[i] + (1.f - b1) * g;
     const float vi = b2 * v[i] + (1.f - b2) * g * g;
     m[i] = mi;
@@ -808,6 +805,31 @@ __global__ void k_mlp_adam(float* __restrict__ P, const float* __restrict__ G, f
         W2b[j] = __float2bfloat16_rn(pi);
         W2Tb[k * kH + o] = __float2bfloat16_rn(pi);
     }
+}
+
+// One kernel for the end of a training step: the weight gradients summed over the split-K
+// partials in split order (as k_sum_partials does), the bias and output-weight gradients
+// read from their accumulators in G and cleared for the next step, and Adam.
+__global__ void k_mlp_sum_adam(const float* __restrict__ part2, const float* __restrict__ part1, int splits,
+                               float* __restrict__ G, float* __restrict__ P, float* __restrict__ m,
+                               float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2,
+                               __nv_bfloat16* __restrict__ W1b, __nv_bfloat16* __restrict__ W2b,
+                               __nv_bfloat16* __restrict__ W2Tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    const int nW1 = kH * kIn, oW2 = nW1 + kH, nW2 = kH * kH;
+    float g;
+    if (i < nW1) {
+        g = 0.f;
+        for (int s = 0; s < splits; ++s) g += part1[(size_t)s * nW1 + i];
+    } else if (i >= oW2 && i < oW2 + nW2) {
+        g = 0.f;
+        for (int s = 0; s < splits; ++s) g += part2[(size_t)s * nW2 + (i - oW2)];
+    } else {
+        g = G[i];
+        G[i] = 0.f;
+    }
+    adam_one(i, g, P, m, v, lr, b1, b2, eps, c1, c2, W1b, W2b, W2Tb);
 }
 
 __global__ void k_mlp_refresh(const float* __restrict__ P, int n, __nv_bfloat16* __restrict__ W1b,
@@ -914,8 +936,12 @@ void mlp_forward(const MlpBufs& m, const void* X, int B, float* y, int* err, cud
     count_launches(1);
 }
 
-void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
-                  const MlpTemp& tmp, int* err, cudaStream_t st) {
+// The gradient kernels of one batch: forward (y, loss, d/dw3, d/db3 into G), dh1, and the
+// two weight-gradient GEMMs (split-K partials in tmp.wpart, bias gradients into G).  G's
+// bias and output-weight entries and *loss accumulate: the caller zeroes them.  Returns
+// the number of split-K partials.
+static int mlp_backward_core(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G,
+                             float* loss, const MlpTemp& tmp, int* err, cudaStream_t st) {
     const __nv_bfloat16* Xb = reinterpret_cast<const __nv_bfloat16*>(X);
     const MlpDev d = dev_view(m);
     float* gW1 = G;
@@ -924,8 +950,6 @@ void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float*
     float* gb2 = gW2 + kH * kH;
     float* gw3 = gb2 + kH;
     float* gb3 = gw3 + kH;
-    cudaMemsetAsync(G, 0, sizeof(float) * kMlpParams, st);
-    cudaMemsetAsync(loss, 0, sizeof(float), st);
     const size_t smem_f = (size_t)kH * kIn * 2 + (size_t)kH * kH * 2 + (size_t)kRows * kIn * 2 +
                           (size_t)kRows * kHc * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_fwd2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
@@ -944,16 +968,32 @@ void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float*
     const size_t smem_w1 = (size_t)128 * 128 * 2 + (size_t)kIn * 128 * 2 + 1024;
     cudaFuncSetAttribute(k_mlp_wgrad<kIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w1);
     k_mlp_wgrad<kIn><<<dim3(splits, 2), 256, smem_w1, st>>>(tmp.dz1, Xb, B, rows_per_cta, part1, gb1, err);
-    k_sum_partials<<<(kH * kH + 255) / 256, 256, 0, st>>>(part2, splits, kH * kH, gW2);
-    k_sum_partials<<<(kH * kIn + 255) / 256, 256, 0, st>>>(part1, splits, kH * kIn, gW1);
-    count_launches(6);
+    count_launches(4);
+    return splits;
 }
 
-void mlp_adam(const MlpBufs& m, const float* G, float* mo, float* vo, float lr, int step, cudaStream_t st) {
+void mlp_gradient(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
+                  const MlpTemp& tmp, int* err, cudaStream_t st) {
+    cudaMemsetAsync(G, 0, sizeof(float) * kMlpParams, st);
+    cudaMemsetAsync(loss, 0, sizeof(float), st);
+    const int splits = mlp_backward_core(m, X, t, B, y, G, loss, tmp, err, st);
+    float* gW1 = G;
+    float* gW2 = G + kH * kIn + kH;
+    const float* part2 = tmp.wpart;
+    const float* part1 = tmp.wpart + (size_t)splits * kH * kH;
+    k_sum_partials<<<(kH * kH + 255) / 256, 256, 0, st>>>(part2, splits, kH * kH, gW2);
+    k_sum_partials<<<(kH * kIn + 255) / 256, 256, 0, st>>>(part1, splits, kH * kIn, gW1);
+    count_launches(2);
+}
+
+void mlp_train_step(const MlpBufs& m, const void* X, const float* t, int B, float* y, float* G, float* loss,
+                    const MlpTemp& tmp, float* mo, float* vo, float lr, int step, int* err, cudaStream_t st) {
+    const int splits = mlp_backward_core(m, X, t, B, y, G, loss, tmp, err, st);
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = (float)(1.0 - pow(0.9, (double)step)), c2 = (float)(1.0 - pow(0.999, (double)step));
-    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, st>>>(m.P, G, mo, vo, kMlpParams, lr, b1, b2, eps, c1, c2, m.W1b,
-                                                         m.W2b, m.W2Tb);
+    k_mlp_sum_adam<<<(kMlpParams + 255) / 256, 256, 0, st>>>(tmp.wpart, tmp.wpart + (size_t)splits * kH * kH, splits, G,
+                                                             m.P, mo, vo, lr, b1, b2, eps, c1, c2, m.W1b, m.W2b,
+                                                             m.W2Tb);
     count_launches(1);
 }
 

@@ -177,8 +177,10 @@ __global__ void k_combine(const float* __restrict__ y, const float* __restrict__
 // minibatch rows: row j of step `step` = floor(x * n / 2^32), x a Philox word (key = seed,
 // counter = (j, step)); gathers the features and targets into contiguous buffers
 __global__ void k_gather_batch(const uint4* __restrict__ X, const float* __restrict__ t, int64_t n, int B,
-                               uint64_t seed, uint32_t step, uint4* __restrict__ Xb, float* __restrict__ tb) {
+                               uint64_t seed, uint32_t step, uint4* __restrict__ Xb, float* __restrict__ tb,
+                               float* __restrict__ zero) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0 && zero) *zero = 0.f;
     if (j >= B) return;
     const uint4 r = philox4x32_10(make_uint4((uint32_t)j, step, 0x5EEDu, 0u),
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
@@ -405,9 +407,9 @@ void surrogate_combine(const float* y, const float* s_exact, int64_t n, float ep
 }
 
 void gather_batch(const void* X, const float* t, int64_t n, int B, uint64_t seed, uint32_t step, void* Xb, float* tb,
-                  cudaStream_t st) {
+                  float* zero, cudaStream_t st) {
     k_gather_batch<<<(B + 255) / 256, 256, 0, st>>>(reinterpret_cast<const uint4*>(X), t, n, B, seed, step,
-                                                     reinterpret_cast<uint4*>(Xb), tb);
+                                                     reinterpret_cast<uint4*>(Xb), tb, zero);
     count_launches(1);
 }
 
