@@ -618,6 +618,13 @@ __global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restr
         if (tid == 0) mma_tile(taddr, sA, sB, kH, kIdesc1, false, &bar);
         const int next = tile + gridDim.x;
         if (next < ntiles) load_tile(next * kRows);
+        const bool valid = r0 + row < B;
+        // this row's GELU'(z1) for the first two 16-column chunks, loaded under the MMA; each
+        // later chunk's is loaded two chunks ahead into the registers the chunk before freed
+        const float4* grow = reinterpret_cast<const float4*>(gd1 + (size_t)(r0 + row) * kH + qt * 64);
+        float4 gq[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) gq[i] = valid ? grow[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         const bool ok = tc::mbar_wait(&bar, phase, kWaitBudget);
         phase ^= 1u;
         if (!__syncthreads_and(ok)) {
@@ -625,22 +632,26 @@ __global__ void __launch_bounds__(512, 1) k_mlp_dh1(const __nv_bfloat16* __restr
             break;
         }
         tc::fence_after_sync();
-        const bool valid = r0 + row < B;
 #pragma unroll
-        for (int c0 = qt * 64; c0 < qt * 64 + 64; c0 += 16) {
+        for (int ch = 0; ch < 4; ++ch) {
+            const int c0 = qt * 64 + ch * 16;
             float v[16];
             tc::tmem_ld16(tl + (uint32_t)c0, v);
-            if (valid) {
-                const float4* gr = reinterpret_cast<const float4*>(gd1 + (size_t)(r0 + row) * kH + c0);
-                float gd[16];
+            float gd[16];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float4 f = gr[i];
-                    gd[4 * i] = f.x;
-                    gd[4 * i + 1] = f.y;
-                    gd[4 * i + 2] = f.z;
-                    gd[4 * i + 3] = f.w;
-                }
+            for (int i = 0; i < 4; ++i) {
+                const float4 f = gq[(ch & 1) * 4 + i];
+                gd[4 * i] = f.x;
+                gd[4 * i + 1] = f.y;
+                gd[4 * i + 2] = f.z;
+                gd[4 * i + 3] = f.w;
+            }
+            if (ch < 2) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    gq[(ch & 1) * 4 + i] = valid ? grow[(ch + 2) * 4 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (valid) {
                 uint32_t pk[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) pk[i] = pack_bf16(v[2 * i] * gd[2 * i], v[2 * i + 1] * gd[2 * i + 1]);
