@@ -362,8 +362,11 @@ __global__ void __launch_bounds__(1024) k_scan_top_u32(uint32_t* __restrict__ pa
 }
 
 // Emit, phase 3: every warp expands its 32 Gaussians' tile rectangles into a
-// contiguous run of instances, lane f of each round writing instance f of the run
-// (coalesced), in depth order and row-major tile order within a Gaussian.  The key is
+// contiguous run of instances, lane l of each round of 32 writing instance f0 + l
+// (coalesced), in depth order and row-major tile order within a Gaussian.  The owner of
+// an instance is the last non-empty Gaussian run starting at or before it: from the bits
+// of the run starts inside the round's window (one OR reduction) and the count of runs
+// started before it (one ballot).  The key is
 // (view << tbits) | tile id, the value the Gaussian id.
 __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __restrict__ order,
                                                             const uint2* __restrict__ rects, int n, int nv,
@@ -390,23 +393,27 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
         const uint32_t off = block_exclusive_scan(cnt, ws, &tot) + partial[c];
         const uint32_t wbase = __shfl_sync(0xffffffffu, off, 0);
         const uint32_t wtot = __shfl_sync(0xffffffffu, off + cnt, 31) - wbase;
-        s_e[warp][lane] = off - wbase;
-        s_g[warp][lane] = gid;
-        s_r[warp][lane] = rc;
+        const uint32_t e = off - wbase;  // this lane's run start within the warp's instances
+        // the non-empty runs, compacted in lane order (their starts strictly increase)
+        const uint32_t nz = __ballot_sync(0xffffffffu, cnt > 0u);
+        if (cnt > 0u) {
+            const int ci = __popc(nz & ((1u << lane) - 1u));
+            s_e[warp][ci] = e;
+            s_g[warp][ci] = gid;
+            s_r[warp][ci] = rc;
+        }
         __syncwarp();
         const bool fits = (unsigned long long)wbase + wtot <= cap;
         if (!fits && lane == 0 && wtot) atomicOr(&ctr->err, kErrCapacity);
-        for (uint32_t f = lane; fits && f < wtot; f += 32) {
-            // owner: the largest lane whose run starts at or before f
-            int lo = 0, hi = 31;
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_e[warp][mid] <= f)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
+        for (uint32_t f0 = 0; fits && f0 < wtot; f0 += 32) {
+            // run starts inside the window [f0, f0 + 32) as bits, and the runs started before
+            // it: position f0 + l belongs to the last run starting at or before it
+            const uint32_t bit = (cnt > 0u && e >= f0 && e < f0 + 32u) ? 1u << (e - f0) : 0u;
+            const uint32_t m = __reduce_or_sync(0xffffffffu, bit);
+            const int before = __popc(__ballot_sync(0xffffffffu, cnt > 0u && e < f0));
+            const uint32_t f = f0 + lane;
+            if (f >= wtot) continue;  // only in the last window: the loop ends for every lane
+            const int lo = before + __popc(m & ((2u << lane) - 1u)) - 1;
             const uint2 r = s_r[warp][lo];
             const uint32_t local = f - s_e[warp][lo];
             const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu;
