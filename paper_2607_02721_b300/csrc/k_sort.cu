@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __
     __shared__ uint32_t ws[32];
     const int nb = (n + kScanThreads - 1) / kScanThreads;
     for (int c = blockIdx.x; c < nb * nv; c += gridDim.x) {
-        const int v = c / nb, cb = c - v * nb;
+        const int v = nv == 1 ? 0 : c / nb, cb = c - v * nb;
         const size_t vo = (size_t)v * n;
         const int j = cb * kScanThreads + threadIdx.x;
         const uint32_t c_ = j < n ? tile_count(__ldg(rects + vo + __ldg(order + vo + j))) : 0u;
@@ -378,10 +378,11 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
     __shared__ uint32_t s_e[kScanThreads / 32][32];
     __shared__ uint32_t s_g[kScanThreads / 32][32];
     __shared__ uint2 s_r[kScanThreads / 32][32];
+    __shared__ float s_iw[kScanThreads / 32][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nb = (n + kScanThreads - 1) / kScanThreads;
     for (int c = blockIdx.x; c < nb * nv; c += gridDim.x) {
-        const int v = c / nb, cb = c - v * nb;
+        const int v = nv == 1 ? 0 : c / nb, cb = c - v * nb;
         const size_t vo = (size_t)v * n;
         const uint32_t tiles_x = (uint32_t)tiles_x_of(cams[v], lw);
         const uint32_t vkey = (uint32_t)v << tbits;
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
             s_e[warp][ci] = e;
             s_g[warp][ci] = gid;
             s_r[warp][ci] = rc;
+            s_iw[warp][ci] = __frcp_rn((float)((rc.y & 0xFFFFu) - (rc.x & 0xFFFFu)));
         }
         __syncwarp();
         const bool fits = (unsigned long long)wbase + wtot <= cap;
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_down(const uint32_t* __re
             // local / w in FP32: (local + 0.5) / w lies at least 0.5 / w from an integer and the
             // product with the rounded reciprocal is within (local + 0.5) 2^-23 / w of it, so
             // the floor is exact for local < 2^22 (integer division beyond)
-            const uint32_t dy = local < (1u << 22) ? (uint32_t)(((float)local + 0.5f) * __frcp_rn((float)w)) : local / w;
+            const uint32_t dy = local < (1u << 22) ? (uint32_t)(((float)local + 0.5f) * s_iw[warp][lo]) : local / w;
             const uint32_t tx = x0 + (local - dy * w), ty = y0 + dy;
             ikeys[wbase + f] = vkey | (ty * tiles_x + tx);
             ivals[wbase + f] = s_g[warp][lo];
