@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_rs_scatter(const uint32_t* 
         hist += blockIdx.y * hstride;
     }
     const uint32_t* __restrict__ row_total = hist + (size_t)D * gridDim.x;
-    __shared__ uint32_t wcnt[kSortWarps][D + 1];
+    __shared__ __align__(16) uint32_t wcnt[kSortWarps][D + 1];  // (D + 1) kSortWarps is a multiple of 4
     __shared__ uint32_t gbase[D];
     __shared__ uint32_t lstart[D];
     __shared__ uint32_t skey[kSubTile];
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_rs_scatter(const uint32_t* 
             pre += t[e];
         }
     }
-    for (int k = tid; k < kSortWarps * (int)(D + 1); k += kSortThreads) (&wcnt[0][0])[k] = 0;
+    for (int k = tid; k < kSortWarps * (int)(D + 1) / 4; k += kSortThreads)
+        reinterpret_cast<uint4*>(&wcnt[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     const uint32_t n = read_n(d_n, n_max);
     uint32_t begin, end;
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_rs_scatter(const uint32_t* 
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < DPT; ++e) gbase[tid * DPT + e] += cnt_d[e];
-        for (int k = tid; k < kSortWarps * (int)(D + 1); k += kSortThreads) (&wcnt[0][0])[k] = 0;
+        for (int k = tid; k < kSortWarps * (int)(D + 1) / 4; k += kSortThreads)
+            reinterpret_cast<uint4*>(&wcnt[0][0])[k] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
     }
 }
