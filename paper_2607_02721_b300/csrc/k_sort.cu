@@ -12,6 +12,8 @@
 // instead of a latency-bound one over a single view's.  No CUB: the sort is a
 // reduce-then-scan radix sort with 8- or 9-bit digits and warp-level stable ranking (one
 // ballot per digit bit).
+#include <type_traits>
+
 #include "csgs_internal.cuh"
 
 namespace csgs {
@@ -189,32 +191,45 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_rs_scatter(const uint32_t* 
     for (uint32_t sub = begin; sub < end; sub += kSubTile) {
         const uint32_t nvalid = min((uint32_t)kSubTile, end - sub);
         uint32_t key[kSortGroups], val[kSortGroups], dig[kSortGroups], rank[kSortGroups];
+        // loads and ranks of the sub-tile; FULL: every key of the sub-tile exists (all but a
+        // chunk's last sub-tile), so no lane needs the bounds test or the invalid class
+        auto load_rank = [&](auto full) {
+            constexpr bool FULL = decltype(full)::value;
 #pragma unroll
-        for (int g = 0; g < kSortGroups; ++g) {
-            const uint32_t i = sub + warp * (32 * kSortGroups) + g * 32 + lane;
-            const bool ok = i < end;
-            key[g] = ok ? __ldg(kin + i) : 0u;
-            val[g] = ok ? (vin ? __ldg(vin + i) : i) : 0u;
-            dig[g] = ok ? (key[g] >> shift) & (D - 1u) : D;
-        }
-        // lanes holding the same digit: one ballot per digit bit (NBITS, unrolled; match.any
-        // is slower when the digits are spread out); invalid lanes (digit D) form their own
-        // class.  The per-warp digit counters then give stable ranks in (group, lane) order.
-#pragma unroll
-        for (int g = 0; g < kSortGroups; ++g) {
-            const uint32_t d = dig[g];
-            uint32_t pm = __ballot_sync(0xffffffffu, d < D);
-            if (d >= D) pm = ~pm;
-#pragma unroll
-            for (int bb = 0; bb < NBITS; ++bb) {
-                const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bb) & 1u);
-                pm &= ((d >> bb) & 1u) ? bal : ~bal;
+            for (int g = 0; g < kSortGroups; ++g) {
+                const uint32_t i = sub + warp * (32 * kSortGroups) + g * 32 + lane;
+                const bool ok = FULL || i < end;
+                key[g] = ok ? __ldg(kin + i) : 0u;
+                val[g] = ok ? (vin ? __ldg(vin + i) : i) : 0u;
+                dig[g] = ok ? (key[g] >> shift) & (D - 1u) : D;
             }
-            rank[g] = wcnt[warp][d] + __popc(pm & lt);
-            __syncwarp();
-            if (lane == __ffs(pm) - 1) wcnt[warp][d] += __popc(pm);
-            __syncwarp();
-        }
+            // lanes holding the same digit: one ballot per digit bit (NBITS, unrolled;
+            // match.any is slower when the digits are spread out); invalid lanes (digit D)
+            // form their own class.  The per-warp digit counters then give stable ranks in
+            // (group, lane) order.
+#pragma unroll
+            for (int g = 0; g < kSortGroups; ++g) {
+                const uint32_t d = dig[g];
+                uint32_t pm = 0xffffffffu;
+                if (!FULL) {
+                    pm = __ballot_sync(0xffffffffu, d < D);
+                    if (d >= D) pm = ~pm;
+                }
+#pragma unroll
+                for (int bb = 0; bb < NBITS; ++bb) {
+                    const uint32_t bal = __ballot_sync(0xffffffffu, (d >> bb) & 1u);
+                    pm &= ((d >> bb) & 1u) ? bal : ~bal;
+                }
+                rank[g] = wcnt[warp][d] + __popc(pm & lt);
+                __syncwarp();
+                if (lane == __ffs(pm) - 1) wcnt[warp][d] += __popc(pm);
+                __syncwarp();
+            }
+        };
+        if (nvalid == (uint32_t)kSubTile)
+            load_rank(std::true_type{});
+        else
+            load_rank(std::false_type{});
         __syncthreads();
         // this thread's digits: per-warp exclusive offsets within the digit, and its count
         uint32_t cnt_d[DPT], csum = 0;
