@@ -66,14 +66,22 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const uint32_t* __rest
     // a chunk is a whole number of 2048-key sub-tiles: 8 coalesced loads in flight per thread
     for (uint32_t base = begin; base < end; base += kSubTile) {
         uint32_t d[kSortGroups];
+        if (base + kSubTile <= end) {  // a full sub-tile: no bounds tests
 #pragma unroll
-        for (int g = 0; g < kSortGroups; ++g) {
-            const uint32_t i = base + g * kSortThreads + threadIdx.x;
-            d[g] = i < end ? (__ldg(keys + i) >> shift) & (D - 1u) : D;
+            for (int g = 0; g < kSortGroups; ++g)
+                d[g] = (__ldg(keys + base + g * kSortThreads + threadIdx.x) >> shift) & (D - 1u);
+#pragma unroll
+            for (int g = 0; g < kSortGroups; ++g) atomicAdd(h + d[g], 1u);
+        } else {
+#pragma unroll
+            for (int g = 0; g < kSortGroups; ++g) {
+                const uint32_t i = base + g * kSortThreads + threadIdx.x;
+                d[g] = i < end ? (__ldg(keys + i) >> shift) & (D - 1u) : D;
+            }
+#pragma unroll
+            for (int g = 0; g < kSortGroups; ++g)
+                if (d[g] < D) atomicAdd(h + d[g], 1u);
         }
-#pragma unroll
-        for (int g = 0; g < kSortGroups; ++g)
-            if (d[g] < D) atomicAdd(h + d[g], 1u);
     }
     __syncthreads();
 #pragma unroll
