@@ -946,6 +946,10 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             size_t e1 = pt.begin(slot.st);
             const uint32_t* iv = bin_batch(ctx, sl, n, 1, keys_v, rects_v, &cam, s->d_cams + v0 + k, ko, grid, slot.st);
             pt.end(1, e1, slot.st);
+            // the view's tiles, longest lists first, at the end of its binning chain (the
+            // compositing stream then only composites)
+            tile_order(P<uint2>(slot.ranges), tiles_of(cam, ko.tile_lw, ko.tile_lh), P<uint32_t>(slot.torder) + 1,
+                       P<uint32_t>(slot.torder), slot.st);
             CUDA_TRY(ctx, cudaEventRecord(slot.ready, slot.st));
             const int ci = view % ncs;  // compositing stream of this view
             cudaStream_t cs = ci ? ctx->cst[ci - 1] : st;
@@ -967,10 +971,7 @@ csgs_status enqueue_scene_score(csgs_ctx* ctx, SceneRec* s, const KOpts& ko, int
             a.stats = stats & 1;
             if (ko.resolution == CSGS_RES_IMAGE)
                 CUDA_TRY(ctx, cudaMemsetAsync(&ctx->d_ctr->sumA_view, 0, sizeof(double), st));
-            // the view's tiles, longest lists first (compositing stream: the binning chain,
-            // which the slot's next view waits for, stays as short as it was)
-            tile_order(P<uint2>(slot.ranges), tiles_of(cam, ko.tile_lw, ko.tile_lh), P<uint32_t>(slot.torder) + 1,
-                       P<uint32_t>(slot.torder), cs);
+
             size_t e2 = pt.begin(cs);
             launch_composite_score(a, cs);
             if (ko.resolution == CSGS_RES_IMAGE) image_fold(s_dev, P<float>(ctx->vbuf), n, &ctx->d_ctr->sumA_view, st);
