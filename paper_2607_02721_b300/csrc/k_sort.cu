@@ -343,9 +343,17 @@ __global__ void __launch_bounds__(kScanThreads) k_emit_reduce(const uint32_t* __
         const size_t vo = (size_t)v * n;
         const int j = cb * kScanThreads + threadIdx.x;
         const uint32_t c_ = j < n ? tile_count(__ldg(rects + vo + __ldg(order + vo + j))) : 0u;
-        uint32_t tot;
-        block_exclusive_scan(c_, ws, &tot);
-        if (threadIdx.x == 0) partial[c] = tot;
+        // the chunk's total: warp sums, then the CTA's
+        const uint32_t wsum = __reduce_add_sync(0xffffffffu, c_);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = wsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0u;
+#pragma unroll
+            for (int w = 0; w < kScanThreads / 32; ++w) tot += ws[w];
+            partial[c] = tot;
+        }
+        __syncthreads();  // ws is rewritten by the next chunk
     }
 }
 
